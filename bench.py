@@ -1,0 +1,330 @@
+"""Benchmark: HDBSCAN* (default) / EMST throughput in Mpoints/s on one GB300, one JSON line.
+
+Default workload (one step = one full wm_hdbscan call: k-d tree, core distances, MemoGFK rounds
+of BCCP* + Kruskal, ordered dendrogram and reachability plot):
+  n = 1,000,000 points in d = 3 from a mixture of 50 isotropic Gaussians (centres uniform in
+  [0,100)^3, sigmas log-uniform in [0.1, 5], Dirichlet(1) weights) plus 5% uniform noise,
+  FP32 coordinates, seed 0, minPts = 10, start point 0.
+
+Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events on the call's
+stream; a 256 MiB buffer is written between steps (outside the events) to flush the 129 MB L2.
+value = points processed by all ranks / max-over-ranks time.  `e2e` repeats the step through the
+same C ABI with host buffers (pinned input, host outputs), copies inside the timed region.
+
+Multi-GPU: one independent replica per rank ("replicas only": the method has no exchange step),
+weak scaling, no collective on the data path.
+
+--impl reference times the FP64 CPU oracle (brute-force Prim etc.) on a bounded sample of the
+same workload on this host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synthdata  # noqa: E402
+
+METRIC = "EMST/HDBSCAN* Mpoints/s on 1 GB300 vs plain form; served p50/p99 latency"
+FP32_LANES_PER_SM = 128
+N_SM = 152
+
+WORKLOADS = {
+    "hdbscan-gmm-1m-3d": dict(problem="hdbscan", gen="gmm", n=1_000_000, d=3, min_pts=10, seed=0),
+    "emst-uniform-10k-2d-fp64": dict(problem="emst", gen="uniform64", n=10_000, d=2, seed=0),
+    "emst-uniform-10m-2d": dict(problem="emst", gen="uniform", n=10_000_000, d=2, seed=0),
+    "emst-uniform-10m-3d": dict(problem="emst", gen="uniform", n=10_000_000, d=3, seed=0),
+    "emst-varden-10m-3d": dict(problem="emst", gen="varden", n=10_000_000, d=3, seed=0),
+}
+
+
+def make_points(w):
+    if w["gen"] == "gmm":
+        return synthdata.gaussian_mixture(w["n"], w["d"], seed=w["seed"])
+    if w["gen"] == "uniform64":
+        return synthdata.uniform(w["n"], w["d"], seed=w["seed"], dtype=np.float64)
+    if w["gen"] == "uniform":
+        return synthdata.uniform(w["n"], w["d"], seed=w["seed"], dtype=np.float32)
+    if w["gen"] == "varden":
+        return synthdata.varden_blobs(w["n"], w["d"], seed=w["seed"])
+    raise ValueError(w["gen"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return self
+
+        def reader():
+            for line in self.proc.stdout:
+                self.rows.append([c.strip() for c in line.split(",")])
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, val in zip(names, r[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args, w, ws, rank):
+    """The FP64 CPU oracle timed on a bounded sample of the workload (rank 0 only)."""
+    if rank != 0:
+        return
+    import oracle
+    x = make_points(w)
+    ns = args.ref_sample
+    xs = np.ascontiguousarray(x[:ns])
+    oracle.build()
+
+    def step():
+        if w["problem"] == "hdbscan":
+            oracle.hdbscan(xs, w["min_pts"], s=0)
+        else:
+            oracle.emst(xs)
+    for _ in range(args.warmup if args.ref_warmup is None else args.ref_warmup):
+        step()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        step()
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    v = ns / t / 1e6
+    cores = os.cpu_count()
+    line = {"metric": METRIC, "impl": "reference", "value": v, "unit": "Mpoints/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, **{k: w[k] for k in w if k != "gen"}, "generator": w["gen"],
+                       "sample_points": ns},
+            "cpu_baseline": {"value": v, "unit": "Mpoints/s", "cores": cores, "kind": "oracle",
+                             "sample": f"first {ns} of the {w['n']} points (the generator shuffles rows), "
+                                       f"brute-force FP64 oracle, OpenMP on {cores} host threads"},
+            "e2e": {"value": v, "unit": "Mpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(w, sample):
+    import oracle
+    oracle.build()
+    x = make_points(w)
+    xs = np.ascontiguousarray(x[:sample])
+    t0 = time.perf_counter()
+    if w["problem"] == "hdbscan":
+        oracle.hdbscan(xs, w["min_pts"], s=0)
+    else:
+        oracle.emst(xs)
+    t = time.perf_counter() - t0
+    cores = os.cpu_count()
+    return {"value": sample / t / 1e6, "unit": "Mpoints/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {sample} of the {w['n']} points, one brute-force FP64 oracle run "
+                      f"({t:.1f} s, OpenMP on {cores} host threads)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="hdbscan-gmm-1m-3d", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--cpu-sample", type=int, default=60_000)
+    ap.add_argument("--ref-sample", type=int, default=40_000)
+    ap.add_argument("--ref-warmup", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    ws, rank, local = dist_setup()
+
+    if args.impl == "reference":
+        run_reference(args, w, ws, rank)
+        return
+
+    import torch
+    import paper_2104_01126_gb300 as wm
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    wm.load()
+
+    x = make_points(w)
+    n, d = x.shape
+    xd = torch.from_numpy(x).cuda()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(inp):
+        if w["problem"] == "hdbscan":
+            return wm.hdbscan(inp, min_pts=w["min_pts"], start=0, precision=args.precision, return_stats=True)
+        return wm.emst(inp, precision=args.precision, return_stats=True)
+
+    for _ in range(args.warmup):
+        step(xd)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = wm.kernel_launch_count()
+    times, stats = [], []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = step(xd)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            stats.append(r["stats"])
+    torch.cuda.synchronize()
+    launches = wm.kernel_launch_count() - l0
+    if dist:
+        dist.barrier()
+    ms = sum(times) / len(times)
+    ms_max = ms
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = n * ws / (ms_max * 1e-3) / 1e6
+
+    # ---- roofline of the dominant kernel with known algorithmic work (FP32 pipe)
+    s0 = stats[-1]
+    clocks = clk.summary()
+    peak = N_SM * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12   # TFLOP/s at the maximum SM clock
+    cands = []
+    if s0.ms_knn_kernel > 0:
+        fl = s0.knn_evals * (3 * d - 1)
+        cands.append(("knn_fast_kernel", s0.ms_knn_kernel, 1, fl, f"{3 * d - 1} flop per distance evaluation"))
+    if s0.ms_tile_kernel > 0:
+        per = 3 * d - 1 + (2 if w["problem"] == "hdbscan" else 0)
+        fl = s0.bccp_tile_evals * per
+        cands.append(("bccp_tile_kernel", s0.ms_tile_kernel, max(s0.tile_launches, 1), fl,
+                      f"{per} flop per distance evaluation"))
+    roof = None
+    if cands:
+        name, kms, launches_k, flops, note = max(cands, key=lambda c: c[1])
+        per_launch_ms = kms / launches_k
+        achieved = flops / launches_k / (per_launch_ms * 1e-3) / 1e12
+        roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "launch_ms": per_launch_ms, "work": note,
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(x).pin_memory()
+        for _ in range(1):
+            step(xh)
+        et = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            step(xh)
+            torch.cuda.synchronize()
+            et.append(time.perf_counter() - t0)
+        e_ms = sum(et) / len(et) * 1e3
+        if dist:
+            t = torch.tensor([e_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        h2d = n * d * x.dtype.itemsize
+        if w["problem"] == "hdbscan":
+            d2h = (n - 1) * 16 + n * 8 + (n - 1) * 24 + n * 4 + n * 8
+        else:
+            d2h = (n - 1) * 16 + 8
+        e2e = {"value": n * ws / (e_ms * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": e_ms,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args.cpu_sample)
+
+    if rank == 0:
+        cfg = {"workload": args.workload, "n": n, "d": d, "generator": w["gen"], "seed": w["seed"],
+               "precision": args.precision, "l2": "256 MiB buffer written between timed steps",
+               "parallelism": f"replicas{ws}"}
+        if w["problem"] == "hdbscan":
+            cfg["min_pts"] = w["min_pts"]
+        phases = {k: round(getattr(s0, k), 3) for k in ("ms_build_tree", "ms_core_dist", "ms_wspd", "ms_bccp",
+                                                       "ms_kruskal", "ms_dendrogram", "ms_knn_kernel",
+                                                       "ms_tile_kernel", "ms_getpairs")}
+        counters = {k: int(getattr(s0, k)) for k in ("rounds", "pairs_retrieved", "bccp_evals", "bccp_tile_evals",
+                                                    "knn_evals", "fp64_rechecks", "candidate_edges", "tree_depth",
+                                                    "tile_launches", "getpairs_launches")}
+        line = {"metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+                "config": cfg, "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+                "cpu_baseline": cpu, "phases_ms": phases, "counters": counters,
+                "step_ms": [round(t, 3) for t in times]}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

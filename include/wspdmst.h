@@ -1,0 +1,198 @@
+/*
+ * wspdmst.h -- C ABI of the GB300 EMST / HDBSCAN* library (libwspdmst.so).
+ *
+ * The library computes, on one CUDA GPU (sm_103a), the problems stated in Sec. 2.1 of
+ * Wang, Yu, Gu, Shun, "Fast Parallel Algorithms for Euclidean Minimum Spanning Tree and
+ * Hierarchical Spatial Clustering" (SIGMOD'21):
+ *   - EMST: a minimum spanning tree of the complete Euclidean graph of n points in d dimensions;
+ *   - HDBSCAN*: the MST of the mutual reachability graph G_MR (core distance = distance to the
+ *     minPts-th nearest neighbour counting the point itself, d_m(p,q) = max{cd(p), cd(q), d(p,q)}),
+ *     its ordered dendrogram for a start point s and the reachability plot from s (Sec. 4).
+ * Both follow the method of Sec. 3: a spatial-median k-d tree, the well-separated pair
+ * decomposition traversed lazily by MemoGFK rounds (Algorithm 3) with batched BCCP / BCCP*
+ * computations, and batched Kruskal over a union-find shared across rounds; the dendrogram and
+ * plot come from the top-down heavy/light construction of Sec. 4.2.
+ *
+ * Canonical result.  Every edge comparison uses the strict total key
+ *     K(u,v) = (w2, min(u,v), max(u,v))   (lexicographic),
+ * where w2 is the squared weight evaluated in IEEE FP64 as sum_{k=0}^{d-1} (x_k(u)-x_k(v))^2 in
+ * dimension order with one rounding per subtract, multiply and add (no fused multiply-add); for
+ * HDBSCAN* w2 = max(cd2(u), cd2(v), that value).  The returned tree is the unique MST under K,
+ * listed in increasing K order (Kruskal order), each edge with u < v and w = sqrt(w2).
+ * (HDBSCAN*: this holds for inputs in general position, i.e. all pairwise FP64 squared
+ * distances distinct; otherwise the tree returned is still an MST of G_MR.)
+ *
+ * Ids.  Point ids are input row indices 0..n-1.  Dendrogram node n+i is the i-th merge in K
+ * order; leaves are the ids 0..n-1 (scipy-linkage-like numbering).
+ *
+ * Pointers.  Every input and output pointer may be host memory or device memory of the
+ * current CUDA device; the library detects which with cudaPointerGetAttributes.  Outputs are
+ * caller-owned and must be sized as stated.  Device work is issued on opts->stream; every call
+ * returns only after its outputs are complete (it synchronises that stream).
+ *
+ * Errors.  Every call returns WM_OK (0) or a negative code; wm_strerror() gives the text and
+ * wm_last_error_detail() a message for the last failure on the calling thread.  On error the
+ * output buffers hold unspecified values.  No call aborts the process.
+ *
+ * Thread safety.  Calls on distinct wm_opts.workspace arenas (or distinct threads using the
+ * library-managed workspace of different devices) may run concurrently; calls sharing the
+ * library-managed workspace of one device are serialised by an internal mutex.
+ */
+#ifndef WSPDMST_H
+#define WSPDMST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ codes and enums */
+#define WM_OK 0
+#define WM_EINVAL (-1)    /* bad argument: n < 1, d not in [1,16], minPts < 1 or > n,
+                              non-finite coordinate or |coordinate| > 2^60, bad enum value */
+#define WM_ENOMEM (-2)    /* device memory (or the caller's workspace) exhausted */
+#define WM_ETIMEOUT (-3)  /* a bounded device-side wait gave up */
+#define WM_ECUDA (-4)     /* a CUDA runtime call failed */
+#define WM_EINTERNAL (-5) /* an internal consistency check failed (a bug) */
+
+#define WM_F32 0 /* coordinates stored as float  */
+#define WM_F64 1 /* coordinates stored as double */
+#define WM_AOS 0 /* pts[i*d + k]: row per point              */
+#define WM_SOA 1 /* pts[k*n + i]: one contiguous array per dim */
+
+#define WM_PREC_FP32_SCREEN 0 /* FP32 distance screen, FP64 recheck of every candidate inside a
+                                  rigorous error band (default) */
+#define WM_PREC_FP64 1        /* the plain form: every point distance evaluated in FP64 */
+
+/* ------------------------------------------------------------------------- records */
+
+/* One tree edge: endpoints (u < v) and weight w (Euclidean or mutual-reachability distance,
+ * not squared).  16 bytes. */
+typedef struct {
+    int32_t u, v;
+    double w;
+} wm_edge;
+
+/* One dendrogram merge (internal node n+i).  left/right are node ids (leaf = point id);
+ * height = weight of the merging edge; size = number of points below.  24 bytes. */
+typedef struct {
+    int32_t left, right;
+    double height;
+    int32_t size;
+    int32_t reserved;
+} wm_dnode;
+
+/* Per-call statistics (optional output). */
+typedef struct {
+    double ms_total;      /* wall time of the call, host clock                      */
+    double ms_ingest;     /* device phase times (CUDA events on the call's stream)  */
+    double ms_build_tree;
+    double ms_core_dist;
+    double ms_wspd;       /* GetRho + GetPairs traversals (including inline BCCP)   */
+    double ms_bccp;       /* BCCP / BCCP* tile kernel                               */
+    double ms_kruskal;    /* edge sort + batched Kruskal                             */
+    double ms_dendrogram;
+    int64_t rounds;       /* MemoGFK rounds                                         */
+    int64_t pairs_retrieved;   /* well-separated pairs whose BCCP was evaluated     */
+    int64_t bccp_evals;        /* point-pair distance evaluations in BCCP / BCCP*   */
+    int64_t bccp_tile_evals;   /* of which in the tile kernel                        */
+    int64_t knn_evals;         /* point-pair distance evaluations in the k-NN pass   */
+    int64_t fp64_rechecks;     /* FP64 re-evaluations of screened candidates         */
+    int64_t candidate_edges;   /* edges handed to Kruskal over all rounds            */
+    int64_t tree_nodes;
+    int64_t tree_depth;
+    size_t workspace_bytes_used;   /* peak workspace use of this call               */
+    double max_rel_screen_err;     /* max |fp32 - fp64| / fp64 over rechecked winners */
+    int32_t tie_overflow;          /* HDBSCAN*: some point had more equal-distance
+                                      neighbours at its core distance than kept      */
+    int32_t reserved;
+    double ms_knn_kernel;          /* CUDA-event time of the k-NN kernel (one launch)   */
+    double ms_tile_kernel;         /* CUDA-event time summed over BCCP tile launches    */
+    int64_t tile_launches;         /* number of BCCP tile kernel launches               */
+    double ms_getpairs;            /* CUDA-event time summed over GetPairs level launches */
+    int64_t getpairs_launches;     /* number of GetPairs level launches                 */
+} wm_stats;
+
+/* Options.  A zero-initialised struct (or NULL) gives the defaults. */
+typedef struct {
+    void *stream;           /* cudaStream_t to issue work on; NULL = legacy default stream */
+    int32_t precision;      /* WM_PREC_FP32_SCREEN (0, default) or WM_PREC_FP64            */
+    int32_t reserved0;
+    void *workspace;        /* optional caller-owned device scratch arena; NULL = the
+                               library manages a grow-only per-device cache               */
+    size_t workspace_bytes; /* size of `workspace` in bytes                                */
+    wm_stats *stats;        /* optional: filled on return                                  */
+} wm_opts;
+
+/* ---------------------------------------------------------------------- entry points */
+
+/*
+ * wm_emst -- Euclidean minimum spanning tree (Sec. 2.1 "EMST"; method: Sec. 3.1, Algorithm 3).
+ *   pts        n points, dtype WM_F32/WM_F64, layout WM_AOS/WM_SOA (host or device)
+ *   n >= 1, 1 <= d <= 16
+ *   out_edges  n-1 wm_edge, K order (host or device; may be NULL when n == 1)
+ *   out_total_weight  sum of the n-1 weights (host pointer; may be NULL)
+ *   opts       may be NULL
+ * Returns WM_OK or WM_EINVAL / WM_ENOMEM / WM_ETIMEOUT / WM_ECUDA / WM_EINTERNAL.
+ */
+int wm_emst(const void *pts, int64_t n, int32_t d, int32_t dtype, int32_t layout,
+            wm_edge *out_edges, double *out_total_weight, const wm_opts *opts);
+
+/*
+ * wm_hdbscan -- HDBSCAN* (Sec. 2.1 "HDBSCAN*"; method: Sec. 3.2.2 with the disjunctive
+ * well-separation, Algorithm 3 with BCCP*, and Sec. 4 for the ordered dendrogram).
+ *   min_pts          1 <= min_pts <= n
+ *   out_mst          n-1 wm_edge of the MST of G_MR, K order           (may be NULL)
+ *   out_core_dist    n doubles, cd(p) (not squared); a point is noise at a cut eps when
+ *                    cd(p) > eps (its self-edge, Sec. 2.1)               (may be NULL)
+ *   out_dendro       n-1 wm_dnode, the ordered dendrogram of `start`     (may be NULL)
+ *   out_order        n int32, the reachability-plot order (Prim order from `start`)
+ *   out_reach        n doubles, bar heights; out_reach[0] = +infinity    (may be NULL)
+ *   start            the start point s, 0 <= start < n
+ */
+int wm_hdbscan(const void *pts, int64_t n, int32_t d, int32_t dtype, int32_t layout,
+               int32_t min_pts, wm_edge *out_mst, double *out_core_dist, wm_dnode *out_dendro,
+               int32_t *out_order, double *out_reach, int32_t start, const wm_opts *opts);
+
+/*
+ * wm_single_linkage -- ordered dendrogram and reachability plot of any weighted spanning tree
+ * (Sec. 4: with the EMST as input this is single-linkage clustering).
+ *   tree       n-1 wm_edge forming a spanning tree of 0..n-1 (any order; the library orders
+ *              them by K using w2 = w*w as the primary key)
+ *   out_dendro n-1 wm_dnode; out_order n int32; out_reach n doubles (each may be NULL)
+ * Returns WM_EINVAL when the edges do not form a spanning tree.
+ */
+int wm_single_linkage(const wm_edge *tree, int64_t n, int32_t start, wm_dnode *out_dendro,
+                      int32_t *out_order, double *out_reach, const wm_opts *opts);
+
+/*
+ * wm_query_footprint -- an upper estimate of the device workspace, in bytes, that a call with
+ * these sizes needs (min_pts = 0 for EMST).  Data-dependent buffers (WSPD traversal frontiers,
+ * candidate edges) are estimated; a call whose data needs more returns WM_ENOMEM when a
+ * caller arena is used, and grows its cache otherwise.
+ */
+int wm_query_footprint(int64_t n, int32_t d, int32_t min_pts, size_t *bytes);
+
+/* Frees the library-managed workspace cache of the current device. */
+int wm_release_cache(void);
+
+/* Text for an error code. */
+const char *wm_strerror(int code);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *wm_last_error_detail(void);
+
+/* Number of CUDA kernels this library has launched in this process (all devices, all
+ * threads) -- a diagnostic counter for benchmarks.  Touches no device. */
+int64_t wm_kernel_launch_count(void);
+
+/* Library version string. */
+const char *wm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WSPDMST_H */

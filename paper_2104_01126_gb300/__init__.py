@@ -1,0 +1,337 @@
+"""Python binding of libwspdmst: EMST and HDBSCAN* on one GB300 GPU.
+
+Thin ctypes marshalling over the C ABI in ``include/wspdmst.h``; every step of the computation
+runs in the library's CUDA kernels.  Inputs may be numpy arrays (host) or torch tensors (host
+or CUDA); results come back on the same side as the input (numpy for host inputs, torch CUDA
+tensors for device inputs).  PyTorch supplies device memory (outputs and the optional
+workspace arena) and the current CUDA stream.
+
+The library must have been built (``python -m paper_2104_01126_gb300.build``); importing the
+binding does not fall back to anything else: a missing or unloadable library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["emst", "hdbscan", "single_linkage", "query_footprint", "library_path", "load",
+           "WMError", "Stats", "version"]
+
+WM_F32, WM_F64 = 0, 1
+WM_AOS, WM_SOA = 0, 1
+PREC = {"fp32": 0, "fp32_screen": 0, "fp64": 1}
+
+
+class WMError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str):
+        super().__init__(f"{where}: {detail or 'error'} (code {code})")
+        self.code = code
+
+
+class _Edge(ctypes.Structure):
+    _fields_ = [("u", ctypes.c_int32), ("v", ctypes.c_int32), ("w", ctypes.c_double)]
+
+
+class _DNode(ctypes.Structure):
+    _fields_ = [("left", ctypes.c_int32), ("right", ctypes.c_int32), ("height", ctypes.c_double),
+                ("size", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("ms_total", ctypes.c_double), ("ms_ingest", ctypes.c_double),
+                ("ms_build_tree", ctypes.c_double), ("ms_core_dist", ctypes.c_double),
+                ("ms_wspd", ctypes.c_double), ("ms_bccp", ctypes.c_double),
+                ("ms_kruskal", ctypes.c_double), ("ms_dendrogram", ctypes.c_double),
+                ("rounds", ctypes.c_int64), ("pairs_retrieved", ctypes.c_int64),
+                ("bccp_evals", ctypes.c_int64), ("bccp_tile_evals", ctypes.c_int64),
+                ("knn_evals", ctypes.c_int64), ("fp64_rechecks", ctypes.c_int64),
+                ("candidate_edges", ctypes.c_int64), ("tree_nodes", ctypes.c_int64),
+                ("tree_depth", ctypes.c_int64), ("workspace_bytes_used", ctypes.c_size_t),
+                ("max_rel_screen_err", ctypes.c_double), ("tie_overflow", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("ms_knn_kernel", ctypes.c_double),
+                ("ms_tile_kernel", ctypes.c_double), ("tile_launches", ctypes.c_int64),
+                ("ms_getpairs", ctypes.c_double), ("getpairs_launches", ctypes.c_int64)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_void_p), ("precision", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t), ("stats", ctypes.POINTER(_Stats))]
+
+
+EDGE_DTYPE = np.dtype([("u", np.int32), ("v", np.int32), ("w", np.float64)])
+DNODE_DTYPE = np.dtype([("left", np.int32), ("right", np.int32), ("height", np.float64),
+                        ("size", np.int32), ("reserved", np.int32)])
+assert EDGE_DTYPE.itemsize == ctypes.sizeof(_Edge) == 16
+assert DNODE_DTYPE.itemsize == ctypes.sizeof(_DNode) == 24
+
+
+@dataclass
+class Stats:
+    ms_total: float = 0.0
+    ms_ingest: float = 0.0
+    ms_build_tree: float = 0.0
+    ms_core_dist: float = 0.0
+    ms_wspd: float = 0.0
+    ms_bccp: float = 0.0
+    ms_kruskal: float = 0.0
+    ms_dendrogram: float = 0.0
+    rounds: int = 0
+    pairs_retrieved: int = 0
+    bccp_evals: int = 0
+    bccp_tile_evals: int = 0
+    knn_evals: int = 0
+    fp64_rechecks: int = 0
+    candidate_edges: int = 0
+    tree_nodes: int = 0
+    tree_depth: int = 0
+    workspace_bytes_used: int = 0
+    max_rel_screen_err: float = 0.0
+    tie_overflow: int = 0
+    ms_knn_kernel: float = 0.0
+    ms_tile_kernel: float = 0.0
+    tile_launches: int = 0
+    ms_getpairs: float = 0.0
+    getpairs_launches: int = 0
+
+    @classmethod
+    def _from(cls, s: _Stats) -> "Stats":
+        return cls(**{f: getattr(s, f) for f in cls.__dataclass_fields__})
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libwspdmst.so (building it first if it is missing and nvcc is available)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"libwspdmst not built: {path} is missing")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        lib.wm_emst.restype = ctypes.c_int
+        lib.wm_emst.argtypes = [P, i64, i32, i32, i32, P, P, ctypes.POINTER(_Opts)]
+        lib.wm_hdbscan.restype = ctypes.c_int
+        lib.wm_hdbscan.argtypes = [P, i64, i32, i32, i32, i32, P, P, P, P, P, i32, ctypes.POINTER(_Opts)]
+        lib.wm_single_linkage.restype = ctypes.c_int
+        lib.wm_single_linkage.argtypes = [P, i64, i32, P, P, P, ctypes.POINTER(_Opts)]
+        lib.wm_query_footprint.restype = ctypes.c_int
+        lib.wm_query_footprint.argtypes = [i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
+        lib.wm_release_cache.restype = ctypes.c_int
+        lib.wm_strerror.restype = ctypes.c_char_p
+        lib.wm_strerror.argtypes = [ctypes.c_int]
+        lib.wm_last_error_detail.restype = ctypes.c_char_p
+        lib.wm_version.restype = ctypes.c_char_p
+        lib.wm_kernel_launch_count.restype = ctypes.c_int64
+        _lib = lib
+        return lib
+
+
+def version() -> str:
+    return load().wm_version().decode()
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        lib = load()
+        raise WMError(rc, where, (lib.wm_last_error_detail() or b"").decode() or lib.wm_strerror(rc).decode())
+
+
+# ----------------------------------------------------------------------------- marshalling
+def _torch():
+    try:
+        import torch  # noqa: F401
+        return torch
+    except Exception:  # pragma: no cover - torch is present in this project
+        return None
+
+
+def _is_cuda_tensor(x) -> bool:
+    t = _torch()
+    return t is not None and isinstance(x, t.Tensor) and x.is_cuda
+
+
+def _points(x):
+    """Returns (keepalive, pointer, n, d, dtype code, on_device, torch device or None)."""
+    t = _torch()
+    if t is not None and isinstance(x, t.Tensor):
+        if x.dim() != 2:
+            raise ValueError("points must have shape (n, d)")
+        if x.dtype not in (t.float32, t.float64):
+            x = x.to(t.float64)
+        x = x.contiguous()
+        code = WM_F32 if x.dtype == t.float32 else WM_F64
+        return x, x.data_ptr(), x.shape[0], x.shape[1], code, x.is_cuda, (x.device if x.is_cuda else None)
+    a = np.asarray(x)
+    if a.ndim != 2:
+        raise ValueError("points must have shape (n, d)")
+    if a.dtype not in (np.float32, np.float64):
+        a = a.astype(np.float64)
+    a = np.ascontiguousarray(a)
+    code = WM_F32 if a.dtype == np.float32 else WM_F64
+    return a, a.ctypes.data, a.shape[0], a.shape[1], code, False, None
+
+
+def _opts(precision: str, stream, stats: _Stats, workspace=None):
+    o = _Opts()
+    o.precision = PREC[precision]
+    o.stream = stream or None
+    o.stats = ctypes.pointer(stats)
+    if workspace is not None:
+        o.workspace = workspace[0]
+        o.workspace_bytes = workspace[1]
+    return o
+
+
+def _current_stream(device):
+    t = _torch()
+    if device is None or t is None:
+        return None
+    return t.cuda.current_stream(device).cuda_stream
+
+
+def _out_buffer(nbytes: int, device):
+    """A caller-owned output buffer: a torch uint8 CUDA tensor, or a numpy byte array."""
+    t = _torch()
+    if device is not None:
+        buf = t.empty(max(nbytes, 16), dtype=t.uint8, device=device)
+        return buf, buf.data_ptr()
+    buf = np.empty(max(nbytes, 16), dtype=np.uint8)
+    return buf, buf.ctypes.data
+
+
+def _edges_result(buf, m: int, device):
+    t = _torch()
+    if device is not None:
+        raw = buf[: 16 * m].view(t.int32).view(m, 4) if m > 0 else t.empty((0, 4), dtype=t.int32, device=device)
+        u = raw[:, 0].clone()
+        v = raw[:, 1].clone()
+        w = buf[: 16 * m].view(t.float64).view(m, 2)[:, 1].clone() if m > 0 else t.empty(0, dtype=t.float64, device=device)
+        return u, v, w
+    e = np.frombuffer(buf, dtype=EDGE_DTYPE, count=m)
+    return e["u"].copy(), e["v"].copy(), e["w"].copy()
+
+
+def _dnode_result(buf, m: int, device):
+    t = _torch()
+    if device is not None:
+        if m == 0:
+            z = t.empty(0, dtype=t.int32, device=device)
+            return z, z.clone(), t.empty(0, dtype=t.float64, device=device), z.clone()
+        i32 = buf[: 24 * m].view(t.int32).view(m, 6)
+        f64 = buf[: 24 * m].view(t.float64).view(m, 3)
+        return i32[:, 0].clone(), i32[:, 1].clone(), f64[:, 1].clone(), i32[:, 4].clone()
+    e = np.frombuffer(buf, dtype=DNODE_DTYPE, count=m)
+    return e["left"].copy(), e["right"].copy(), e["height"].copy(), e["size"].copy()
+
+
+# ---------------------------------------------------------------------------------- API
+def emst(points, precision: str = "fp32", stream=None, return_stats: bool = False, workspace=None):
+    """Euclidean MST (wm_emst).  Returns dict(u, v, w, total[, stats]); edges in K order."""
+    lib = load()
+    keep, ptr, n, d, code, on_dev, dev = _points(points)
+    m = max(n - 1, 0)
+    buf, bptr = _out_buffer(16 * m, dev)
+    total = ctypes.c_double(0.0)
+    st = _Stats()
+    if stream is None and on_dev:
+        stream = _current_stream(dev)
+    o = _opts(precision, stream, st, workspace)
+    rc = lib.wm_emst(ptr, n, d, code, WM_AOS, bptr if m > 0 else None, ctypes.byref(total), ctypes.byref(o))
+    _check(rc, "wm_emst")
+    u, v, w = _edges_result(buf, m, dev)
+    out = {"u": u, "v": v, "w": w, "total": total.value}
+    if return_stats:
+        out["stats"] = Stats._from(st)
+    del keep
+    return out
+
+
+def hdbscan(points, min_pts: int = 10, start: int = 0, precision: str = "fp32", stream=None,
+            return_stats: bool = False, workspace=None):
+    """HDBSCAN* (wm_hdbscan): MST of G_MR, core distances, ordered dendrogram, reachability plot."""
+    lib = load()
+    keep, ptr, n, d, code, on_dev, dev = _points(points)
+    m = max(n - 1, 0)
+    ebuf, eptr = _out_buffer(16 * m, dev)
+    cbuf, cptr = _out_buffer(8 * n, dev)
+    dbuf, dptr = _out_buffer(24 * m, dev)
+    obuf, optr = _out_buffer(4 * n, dev)
+    rbuf, rptr = _out_buffer(8 * n, dev)
+    st = _Stats()
+    if stream is None and on_dev:
+        stream = _current_stream(dev)
+    o = _opts(precision, stream, st, workspace)
+    rc = lib.wm_hdbscan(ptr, n, d, code, WM_AOS, int(min_pts), eptr if m else None, cptr, dptr if m else None,
+                        optr, rptr, int(start), ctypes.byref(o))
+    _check(rc, "wm_hdbscan")
+    u, v, w = _edges_result(ebuf, m, dev)
+    left, right, height, size = _dnode_result(dbuf, m, dev)
+    t = _torch()
+    if dev is not None:
+        cd = cbuf[: 8 * n].view(t.float64).clone()
+        order = obuf[: 4 * n].view(t.int32).clone()
+        reach = rbuf[: 8 * n].view(t.float64).clone()
+    else:
+        cd = np.frombuffer(cbuf, dtype=np.float64, count=n).copy()
+        order = np.frombuffer(obuf, dtype=np.int32, count=n).copy()
+        reach = np.frombuffer(rbuf, dtype=np.float64, count=n).copy()
+    out = {"u": u, "v": v, "w": w, "cd": cd, "left": left, "right": right, "height": height,
+           "size": size, "order": order, "reach": reach}
+    if return_stats:
+        out["stats"] = Stats._from(st)
+    del keep
+    return out
+
+
+def single_linkage(n: int, u, v, w, start: int = 0, stream=None):
+    """Ordered dendrogram + reachability plot of a weighted spanning tree (wm_single_linkage)."""
+    lib = load()
+    m = max(n - 1, 0)
+    rec = np.zeros(max(m, 1), dtype=EDGE_DTYPE)
+    rec["u"][:m] = np.asarray(u)[:m]
+    rec["v"][:m] = np.asarray(v)[:m]
+    rec["w"][:m] = np.asarray(w)[:m]
+    dbuf = np.empty(max(24 * m, 24), np.uint8)
+    order = np.empty(n, np.int32)
+    reach = np.empty(n, np.float64)
+    st = _Stats()
+    o = _opts("fp32", stream, st)
+    rc = lib.wm_single_linkage(rec.ctypes.data if m else None, n, int(start), dbuf.ctypes.data if m else None,
+                               order.ctypes.data, reach.ctypes.data, ctypes.byref(o))
+    _check(rc, "wm_single_linkage")
+    left, right, height, size = _dnode_result(dbuf, m, None)
+    return {"left": left, "right": right, "height": height, "size": size, "order": order, "reach": reach}
+
+
+def query_footprint(n: int, d: int, min_pts: int = 0) -> int:
+    lib = load()
+    b = ctypes.c_size_t(0)
+    _check(lib.wm_query_footprint(n, d, min_pts, ctypes.byref(b)), "wm_query_footprint")
+    return b.value
+
+
+def kernel_launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().wm_kernel_launch_count())
+
+
+def release_cache():
+    _check(load().wm_release_cache(), "wm_release_cache")

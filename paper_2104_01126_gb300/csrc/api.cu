@@ -1,0 +1,686 @@
+// api.cu -- the C ABI (include/wspdmst.h) and the host orchestration of the MemoGFK rounds
+// (Algorithm 3).  Every step of the computation runs in the kernels of this library; the host
+// only sequences launches and reads back the few scalars that steer the rounds (rho_hi, counts).
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "wm_internal.cuh"
+#include "wspd.cuh"
+#include "hdb.cuh"
+
+namespace wm {
+
+std::atomic<long long> g_launch_count{0};
+
+int ingest_points(const void *dev_src, int n, int d, int dtype, int layout, Points &P, Arena &ar, cudaStream_t st,
+                  unsigned *pinned);
+int build_tree(Points &P, Tree &T, Arena &ar, cudaStream_t st, int *pinned);
+int filter_connected(const EdgeK *in, int m, const int *uf, EdgeK *out, int *count_dev, cudaStream_t st);
+int batch_kruskal(const EdgeK *e, int m, int *uf, int *R, EdgeK *out, int out_base, int *accepted, Arena &ar,
+                  cudaStream_t st, int *pinned);
+
+// ----------------------------------------------------------------------------- error state
+static thread_local std::string g_detail;
+static void set_detail(const char *fmt, const char *a = "", long long b = 0)
+{
+    char buf[512];
+    snprintf(buf, sizeof buf, fmt, a, b);
+    g_detail = buf;
+}
+
+// pinned host scratch for scalar readbacks (one per thread)
+static int *pinned_scratch()
+{
+    static thread_local int *p = nullptr;
+    if (!p) {
+        if (cudaMallocHost((void **)&p, 1 << 16) != cudaSuccess) p = nullptr;
+    }
+    return p;
+}
+
+// ------------------------------------------------------------------ library-managed cache
+struct DevCache {
+    std::mutex mu;
+    char *ptr = nullptr;
+    size_t cap = 0;
+};
+static DevCache g_cache[64];
+
+struct Caps {
+    long long frontier, big, edges;
+};
+
+static size_t estimate_bytes(long long n, int d, int min_pts, const Caps &c)
+{
+    long long N = 2 * n;
+    size_t b = 0;
+    b += (size_t)n * d * 8;                 // device copy of the input
+    b += (size_t)n * d * 12 * 2;            // points + build scratch
+    b += (size_t)n * 16;                    // pid, pos, uf, R
+    b += (size_t)N * (8 * d + 48);          // tree arrays (+ build scratch counters)
+    b += (size_t)n * 8;                     // small lists
+    b += (size_t)c.frontier * 8 * 2;
+    b += (size_t)c.big * 12;
+    b += (size_t)c.edges * 16 * 3 + (size_t)c.edges * 24;   // batch, filtered, sort tmp, kruskal
+    b += (size_t)n * 16 * 2;                // output tree + conversion
+    if (min_pts > 0) {
+        long long kk = min_pts + 16;
+        b += (size_t)n * 12 + (size_t)n * 8;            // cd64, cd32, node bounds
+        b += (size_t)n * kk * 16 * 2;                   // repair edges + sort tmp
+        b += (size_t)n * 160;                           // dendrogram / Euler tour scratch
+    }
+    return b + (64u << 20);
+}
+
+static Caps default_caps(long long n, int min_pts)
+{
+    Caps c;
+    c.frontier = 8 * n + (1 << 20);
+    c.big = 2 * n + (1 << 18);
+    c.edges = 4 * n + (1 << 20) + (min_pts > 0 ? (long long)n * (min_pts + 16) : 0);
+    return c;
+}
+
+// ------------------------------------------------------------------------------- kernels
+namespace {
+
+__global__ void init_uf_kernel(int *uf, int *R, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uf[i] = i;
+        R[i] = 0x7fffffff;
+    }
+}
+
+// wm_edge output: u, v, w = sqrt(w2)
+__global__ void to_wm_edge_kernel(const EdgeK *__restrict__ e, int m, wm_edge *__restrict__ out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        EdgeK x = e[i];
+        wm_edge o;
+        o.u = edge_u(x);
+        o.v = edge_v(x);
+        o.w = sqrt(edge_w2(x));
+        out[i] = o;
+    }
+}
+
+// pairwise FP64 sum of sqrt(w2) (block partials, then one block)
+__global__ void sum_sqrt_kernel(const EdgeK *__restrict__ e, int m, double *partial)
+{
+    __shared__ double sm[256];
+    double s = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) s += sqrt(edge_w2(e[i]));
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+        if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sm[0];
+}
+
+__global__ void sum_partials_kernel(const double *partial, int m, double *out)
+{
+    __shared__ double sm[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) s += partial[i];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+        if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sm[0];
+}
+
+// first index in the K-sorted edge array whose w2 >= bound (binary search, one thread)
+__global__ void lower_bound_w2_kernel(const EdgeK *__restrict__ e, int m, double bound, int *out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int lo = 0, hi = m;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (edge_w2(e[mid]) < bound) lo = mid + 1; else hi = mid;
+    }
+    *out = lo;
+}
+
+__global__ void copy_edges_kernel(const EdgeK *__restrict__ src, int m, EdgeK *__restrict__ dst)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) dst[i] = src[i];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ call state
+struct Call {
+    cudaStream_t st = nullptr;
+    Arena ar;
+    int *pin = nullptr;
+    wm_stats stats{};
+    int precision = WM_PREC_FP32_SCREEN;
+    std::vector<cudaEvent_t> evs;
+    double event_ms(cudaEvent_t a, cudaEvent_t b)
+    {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        return ms;
+    }
+};
+
+static bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+#define WM_TRY(x)                                   \
+    do {                                            \
+        int rc_ = (x);                              \
+        if (rc_) return rc_;                        \
+    } while (0)
+#define WM_CK(x)                                                                     \
+    do {                                                                             \
+        cudaError_t e_ = (x);                                                        \
+        if (e_ != cudaSuccess) {                                                     \
+            set_detail("CUDA error %s (line %lld)", cudaGetErrorString(e_), __LINE__); \
+            return WM_ECUDA;                                                         \
+        }                                                                            \
+    } while (0)
+
+struct Timer {
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    double ms() const { return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count(); }
+};
+
+// MemoGFK rounds (Algorithm 3).  On return E_out holds the n-1 tree edges in K order.
+// hdb: optional HDBSCAN* state (node cd bounds, per-position cd2, sorted repair edges).
+static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps &caps, EdgeK *E_out, int *uf,
+                   int *R, unsigned *overflow_bits)
+{
+    const int n = P.n;
+    cudaStream_t st = C.st;
+    Arena &ar = C.ar;
+    *overflow_bits = 0;
+    if (n <= 1) return 0;
+    size_t mark = ar.off;
+    int2 *fa = ar.get<int2>(caps.frontier), *fb = ar.get<int2>(caps.frontier);
+    int2 *big = ar.get<int2>(caps.big);
+    int *jobs = ar.get<int>(caps.big + 1);
+    EdgeK *batch = ar.get<EdgeK>(caps.edges), *filt = ar.get<EdgeK>(caps.edges), *tmp = ar.get<EdgeK>(caps.edges);
+    int *cnts = ar.get<int>(16);
+    double *rho = ar.get<double>(2);
+    unsigned *ovf = ar.get<unsigned>(2);
+    unsigned long long *stat = ar.get<unsigned long long>(8);
+    if (ar.failed) return WM_ENOMEM;
+    WM_CK(cudaMemsetAsync(stat, 0, 8 * sizeof(unsigned long long), st));
+    WM_CK(cudaMemsetAsync(ovf, 0, 2 * sizeof(unsigned), st));
+
+    TravArgs a;
+    a.N = T.N; a.n = n; a.d = P.d;
+    a.lo = T.lo; a.hi = T.hi; a.diam2 = T.diam2;
+    a.begin = T.begin; a.end = T.end; a.left = T.left; a.right = T.right; a.comp = T.comp;
+    a.x32 = P.x32; a.x64 = P.x64; a.pid = P.pid;
+    a.fp64 = C.precision == WM_PREC_FP64;
+    a.eta = a.fp64 ? 0.0 : 2.0 * (double)P.delta * std::sqrt((double)P.d) * (1.0 + 1e-6);
+    if (hdb) {
+        a.cdmin = hdb->cdmin; a.cdmax = hdb->cdmax; a.cd32 = hdb->cd32; a.cd64 = hdb->cd64;
+    }
+    a.frontier_cap = (int)caps.frontier;
+    a.big = big; a.big_count = cnts + 4; a.big_cap = (int)caps.big;
+    a.edges = batch; a.edge_count = cnts + 5; a.edge_cap = (int)caps.edges;
+    a.overflow = ovf;
+    a.stat = stat;
+    a.rho_out = rho;
+
+    int nE = 0;
+    double rho_lo = 0.0;
+    long long beta = 2;
+    int rpos = 0;   // HDBSCAN*: next unconsumed repair edge
+    const double inf = INFINITY;
+    int rounds = 0;
+    while (nE < n - 1) {
+        if (++rounds > 4096) { set_detail("MemoGFK made no progress%s (%lld rounds)", "", rounds); return WM_EINTERNAL; }
+        Timer tw;
+        launch_comp_labels(T, P, uf, st);
+        // ---- GetRho
+        WM_CK(cudaMemcpyAsync(rho, &inf, sizeof(double), cudaMemcpyHostToDevice, st));
+        a.beta = (int)std::min<long long>(beta, 0x7fffffff);
+        unsigned ob = 0;
+        WM_TRY(run_traversal(0, a, fa, fb, cnts, st, C.pin, &ob, nullptr));
+        if (ob) { *overflow_bits = ob; return 0; }
+        double rho_hi;
+        WM_CK(cudaMemcpy(&rho_hi, rho, sizeof(double), cudaMemcpyDeviceToHost));
+        if (rho_hi < rho_lo) rho_hi = rho_lo;
+        // ---- GetPairs (+ in-place BCCP of small pairs)
+        a.rho_lo = rho_lo;
+        a.rho_hi = rho_hi;
+        WM_CK(cudaMemsetAsync(cnts + 4, 0, 2 * sizeof(int), st));
+        cudaEvent_t g0, g1;
+        cudaEventCreate(&g0);
+        cudaEventCreate(&g1);
+        cudaEventRecord(g0, st);
+        int glev = 0;
+        WM_TRY(run_traversal(1, a, fa, fb, cnts, st, C.pin, &ob, &glev));
+        cudaEventRecord(g1, st);
+        cudaEventSynchronize(g1);
+        C.stats.ms_getpairs += C.event_ms(g0, g1);
+        C.stats.getpairs_launches += glev;
+        cudaEventDestroy(g0);
+        cudaEventDestroy(g1);
+        if (ob) { *overflow_bits = ob; return 0; }
+        WM_CK(cudaMemcpyAsync(C.pin, cnts + 4, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        WM_CK(cudaStreamSynchronize(st));
+        int mbig = C.pin[0];
+        C.stats.ms_wspd += tw.ms();
+        // ---- BCCP tiles over the queued larger pairs
+        Timer tb;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, st);
+        WM_TRY(run_bccp_tiles(a, mbig, jobs, cnts + 6, st, ar, hdb != nullptr, a.fp64 != 0));
+        cudaEventRecord(e1, st);
+        WM_CK(cudaMemcpyAsync(C.pin, cnts + 5, sizeof(int), cudaMemcpyDeviceToHost, st));
+        WM_CK(cudaMemcpyAsync(C.pin + 1, ovf, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        WM_CK(cudaStreamSynchronize(st));
+        if (mbig > 0) {
+            double ms = C.event_ms(e0, e1);
+            C.stats.ms_bccp += ms;
+            C.stats.ms_tile_kernel += ms;
+            C.stats.tile_launches += 1;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (C.pin[1]) { *overflow_bits = (unsigned)C.pin[1]; return 0; }
+        int m = C.pin[0];
+        // ---- HDBSCAN*: repair edges of this weight range join the batch
+        if (hdb && hdb->nrep > rpos) {
+            int hi_idx;
+            if (rho_hi == inf) {
+                hi_idx = hdb->nrep;
+            } else {
+                launch(lower_bound_w2_kernel, 1, 32, 0, st, hdb->rep, hdb->nrep, rho_hi, cnts + 7);
+                WM_CK(cudaMemcpyAsync(C.pin, cnts + 7, sizeof(int), cudaMemcpyDeviceToHost, st));
+                WM_CK(cudaStreamSynchronize(st));
+                hi_idx = C.pin[0];
+            }
+            int take = hi_idx - rpos;
+            if (take > 0) {
+                if ((long long)m + take > caps.edges) { *overflow_bits = 2; return 0; }
+                launch(copy_edges_kernel, grid_for(take, 256), 256, 0, st, hdb->rep + rpos, take, batch + m);
+                m += take;
+                rpos = hi_idx;
+            }
+        }
+        C.stats.ms_bccp += 0.0;
+        // ---- sort + Kruskal
+        Timer tk;
+        int accepted = 0;
+        if (m > 0) {
+            WM_TRY(filter_connected(batch, m, uf, filt, cnts + 8, st));
+            WM_CK(cudaMemcpyAsync(C.pin, cnts + 8, sizeof(int), cudaMemcpyDeviceToHost, st));
+            WM_CK(cudaStreamSynchronize(st));
+            int mf = C.pin[0];
+            C.stats.candidate_edges += mf;
+            EdgeK *sorted = filt;
+            WM_TRY(radix_sort_edges(filt, tmp, mf, st, ar, &sorted));
+            WM_TRY(batch_kruskal(sorted, mf, uf, R, E_out, nE, &accepted, ar, st, C.pin));
+        }
+        C.stats.ms_kruskal += tk.ms();
+        nE += accepted;
+        if (rho_hi == inf && nE < n - 1) {
+            set_detail("MemoGFK round with rho_hi = inf left the forest incomplete%s (%lld edges)", "", nE);
+            return WM_EINTERNAL;
+        }
+        rho_lo = rho_hi;
+        beta *= 2;
+    }
+    WM_CK(cudaMemcpyAsync(C.pin, stat, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    WM_CK(cudaStreamSynchronize(st));
+    unsigned long long hs[8];
+    memcpy(hs, C.pin, sizeof hs);
+    C.stats.rounds = rounds;
+    C.stats.pairs_retrieved = (int64_t)hs[0];
+    C.stats.bccp_evals = (int64_t)hs[1];
+    C.stats.fp64_rechecks += (int64_t)hs[2];
+    C.stats.bccp_tile_evals = (int64_t)hs[3];
+    ar.off = mark;
+    return 0;
+}
+
+// ---------------------------------------------------------------------- shared front half
+struct Prepared {
+    Points P;
+    Tree T;
+};
+
+static int prepare(Call &C, const void *pts, int64_t n, int32_t d, int32_t dtype, int32_t layout, Prepared &S)
+{
+    cudaStream_t st = C.st;
+    const void *dsrc = pts;
+    size_t bytes = (size_t)n * d * (dtype == WM_F32 ? 4 : 8);
+    if (!is_device_ptr(pts)) {
+        void *buf = C.ar.take(bytes);
+        if (!buf) return WM_ENOMEM;
+        WM_CK(cudaMemcpyAsync(buf, pts, bytes, cudaMemcpyHostToDevice, st));
+        dsrc = buf;
+    }
+    Timer ti;
+    int rc = ingest_points(dsrc, (int)n, d, dtype, layout, S.P, C.ar, st, (unsigned *)C.pin);
+    if (rc == WM_EINVAL) { set_detail("non-finite coordinate or |coordinate| > 2^60%s", ""); return rc; }
+    if (rc) return rc;
+    C.stats.ms_ingest = ti.ms();
+    Timer tt;
+    WM_TRY(build_tree(S.P, S.T, C.ar, st, C.pin));
+    C.stats.ms_build_tree = tt.ms();
+    C.stats.tree_nodes = S.T.N;
+    C.stats.tree_depth = S.T.depth;
+    return 0;
+}
+
+static int write_edges(Call &C, const EdgeK *E, int m, wm_edge *out, double *total)
+{
+    cudaStream_t st = C.st;
+    if (m > 0 && out) {
+        bool dev = is_device_ptr(out);
+        wm_edge *dst = out;
+        if (!dev) {
+            dst = C.ar.get<wm_edge>(m);
+            if (!dst) return WM_ENOMEM;
+        }
+        launch(to_wm_edge_kernel, grid_for(m, 256), 256, 0, st, E, m, dst);
+        if (!dev) WM_CK(cudaMemcpyAsync(out, dst, sizeof(wm_edge) * m, cudaMemcpyDeviceToHost, st));
+    }
+    if (total) {
+        double *part = C.ar.get<double>(256 + 1);
+        if (!part) return WM_ENOMEM;
+        if (m > 0) {
+            int g = grid_for(m, 256, 256);
+            launch(sum_sqrt_kernel, g, 256, 0, st, E, m, part);
+            launch(sum_partials_kernel, 1, 256, 0, st, part, g, part + 256);
+            WM_CK(cudaMemcpyAsync(C.pin, part + 256, sizeof(double), cudaMemcpyDeviceToHost, st));
+        } else {
+            double z = 0.0;
+            memcpy(C.pin, &z, sizeof z);
+        }
+    }
+    WM_CK(cudaStreamSynchronize(st));
+    if (total) memcpy(total, C.pin, sizeof(double));
+    return 0;
+}
+
+// ------------------------------------------------------------------------ the call driver
+typedef int (*Body)(Call &C, void *ctx, const Caps &caps, unsigned *overflow);
+
+static int run_call(const wm_opts *opts, long long n, int d, int min_pts, Body body, void *ctx)
+{
+    g_detail.clear();
+    Timer total;
+    int dev = 0;
+    WM_CK(cudaGetDevice(&dev));
+    Call C;
+    C.st = opts ? (cudaStream_t)opts->stream : nullptr;
+    C.precision = opts ? opts->precision : WM_PREC_FP32_SCREEN;
+    if (C.precision != WM_PREC_FP32_SCREEN && C.precision != WM_PREC_FP64) {
+        set_detail("bad precision%s %lld", "", C.precision);
+        return WM_EINVAL;
+    }
+    C.pin = pinned_scratch();
+    if (!C.pin) { set_detail("cudaMallocHost failed%s", ""); return WM_ENOMEM; }
+    Caps caps = default_caps(n, min_pts);
+    const bool user_ws = opts && opts->workspace;
+    int rc = 0;
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        size_t need = estimate_bytes(n, d, min_pts, caps);
+        std::unique_lock<std::mutex> lk;
+        if (user_ws) {
+            C.ar.base = (char *)opts->workspace;
+            C.ar.cap = opts->workspace_bytes;
+        } else {
+            DevCache &dc = g_cache[dev & 63];
+            lk = std::unique_lock<std::mutex>(dc.mu);
+            if (dc.cap < need) {
+                if (dc.ptr) { cudaStreamSynchronize(C.st); cudaFree(dc.ptr); dc.ptr = nullptr; dc.cap = 0; }
+                if (cudaMalloc((void **)&dc.ptr, need) != cudaSuccess) {
+                    cudaGetLastError();
+                    set_detail("cudaMalloc of %s%lld bytes failed", "", (long long)need);
+                    return WM_ENOMEM;
+                }
+                dc.cap = need;
+            }
+            C.ar.base = dc.ptr;
+            C.ar.cap = dc.cap;
+        }
+        C.ar.off = 0;
+        C.ar.peak = 0;
+        C.ar.failed = false;
+        C.stats = wm_stats{};
+        unsigned ovf = 0;
+        rc = body(C, ctx, caps, &ovf);
+        if (rc == 0 && C.ar.failed) rc = WM_ENOMEM;
+        if (rc == WM_ENOMEM && !user_ws && !C.ar.failed) break;
+        if (rc == 0 && ovf == 0) break;
+        if (rc == WM_ENOMEM && user_ws) {
+            set_detail("caller workspace too small%s (%lld bytes given)", "", (long long)C.ar.cap);
+            break;
+        }
+        if (rc && rc != WM_ENOMEM) break;
+        // grow whichever capacity overflowed and start over
+        if (ovf & 1u) caps.frontier *= 2;
+        if (ovf & 2u) caps.edges *= 2;
+        if (ovf & 4u) caps.big *= 2;
+        if (rc == WM_ENOMEM) { caps.frontier += caps.frontier / 2; }
+        if (user_ws && ovf) { rc = WM_ENOMEM; set_detail("caller workspace too small for the WSPD frontier%s", ""); break; }
+        rc = WM_ENOMEM;
+    }
+    cudaError_t le = cudaGetLastError();
+    if (rc == 0 && le != cudaSuccess) {
+        set_detail("CUDA error %s%lld", cudaGetErrorString(le), 0);
+        rc = WM_ECUDA;
+    }
+    C.stats.workspace_bytes_used = C.ar.peak;
+    C.stats.ms_total = total.ms();
+    if (opts && opts->stats) *opts->stats = C.stats;
+    return rc;
+}
+
+// ------------------------------------------------------------------------------ bodies
+struct EmstCtx {
+    const void *pts;
+    long long n;
+    int d, dtype, layout;
+    wm_edge *out;
+    double *total;
+};
+
+static int emst_body(Call &C, void *vctx, const Caps &caps, unsigned *ovf)
+{
+    EmstCtx &x = *(EmstCtx *)vctx;
+    Prepared S;
+    WM_TRY(prepare(C, x.pts, x.n, x.d, x.dtype, x.layout, S));
+    const int n = (int)x.n;
+    int *uf = C.ar.get<int>(n), *R = C.ar.get<int>(n);
+    EdgeK *E = C.ar.get<EdgeK>(n);
+    if (C.ar.failed) return WM_ENOMEM;
+    launch(init_uf_kernel, grid_for(n, 256), 256, 0, C.st, uf, R, n);
+    WM_TRY(memogfk(C, S.P, S.T, nullptr, caps, E, uf, R, ovf));
+    if (*ovf) return 0;
+    return write_edges(C, E, n - 1, x.out, x.total);
+}
+
+struct HdbCtx {
+    const void *pts;
+    long long n;
+    int d, dtype, layout, min_pts, start;
+    wm_edge *mst;
+    double *cd;
+    wm_dnode *dendro;
+    int *order;
+    double *reach;
+};
+
+static int hdbscan_body(Call &C, void *vctx, const Caps &caps, unsigned *ovf)
+{
+    HdbCtx &x = *(HdbCtx *)vctx;
+    Prepared S;
+    WM_TRY(prepare(C, x.pts, x.n, x.d, x.dtype, x.layout, S));
+    const int n = (int)x.n;
+    HdbState H;
+    Timer tc;
+    WM_TRY(core_distances(S.P, S.T, x.min_pts, C.precision == WM_PREC_FP64, H, C.ar, C.st, C.pin, &C.stats));
+    C.stats.ms_core_dist = tc.ms();
+    int *uf = C.ar.get<int>(n), *R = C.ar.get<int>(n);
+    EdgeK *E = C.ar.get<EdgeK>(n);
+    if (C.ar.failed) return WM_ENOMEM;
+    launch(init_uf_kernel, grid_for(n, 256), 256, 0, C.st, uf, R, n);
+    WM_TRY(memogfk(C, S.P, S.T, &H, caps, E, uf, R, ovf));
+    if (*ovf) return 0;
+    WM_TRY(write_core_distances(S.P, H, x.cd, C.ar, C.st));
+    WM_TRY(write_edges(C, E, n - 1, x.mst, nullptr));
+    Timer td;
+    WM_TRY(dendrogram(E, n, x.start, x.dendro, x.order, x.reach, C.ar, C.st, C.pin));
+    C.stats.ms_dendrogram = td.ms();
+    return 0;
+}
+
+struct SlCtx {
+    const wm_edge *tree;
+    long long n;
+    int start;
+    wm_dnode *dendro;
+    int *order;
+    double *reach;
+};
+
+static int sl_body(Call &C, void *vctx, const Caps &, unsigned *ovf)
+{
+    SlCtx &x = *(SlCtx *)vctx;
+    *ovf = 0;
+    const int n = (int)x.n;
+    EdgeK *E = C.ar.get<EdgeK>(n), *tmp = C.ar.get<EdgeK>(n);
+    if (C.ar.failed) return WM_ENOMEM;
+    if (n > 1) {
+        const wm_edge *src = x.tree;
+        if (!is_device_ptr(src)) {
+            wm_edge *b = C.ar.get<wm_edge>(n - 1);
+            if (!b) return WM_ENOMEM;
+            WM_CK(cudaMemcpyAsync(b, src, sizeof(wm_edge) * (n - 1), cudaMemcpyHostToDevice, C.st));
+            src = b;
+        }
+        int *bad = C.ar.get<int>(1);
+        if (!bad) return WM_ENOMEM;
+        WM_TRY(edges_from_wm(src, n, E, bad, C.st));
+        EdgeK *sorted = E;
+        WM_TRY(radix_sort_edges(E, tmp, n - 1, C.st, C.ar, &sorted));
+        WM_CK(cudaMemcpyAsync(C.pin, bad, sizeof(int), cudaMemcpyDeviceToHost, C.st));
+        WM_CK(cudaStreamSynchronize(C.st));
+        if (C.pin[0]) { set_detail("tree edge with an endpoint outside [0, n) or a bad weight%s", ""); return WM_EINVAL; }
+        Timer td;
+        WM_TRY(dendrogram_impl(sorted, n, x.start, 0, x.dendro, x.order, x.reach, C.ar, C.st, C.pin));
+        C.stats.ms_dendrogram = td.ms();
+    } else {
+        WM_TRY(dendrogram_impl(E, n, x.start, 0, x.dendro, x.order, x.reach, C.ar, C.st, C.pin));
+    }
+    return 0;
+}
+
+}  // namespace wm
+
+// =========================================================================== C ABI
+using namespace wm;
+
+extern "C" {
+
+int wm_emst(const void *pts, int64_t n, int32_t d, int32_t dtype, int32_t layout, wm_edge *out_edges,
+            double *out_total_weight, const wm_opts *opts)
+{
+    g_detail.clear();
+    if (!pts || n < 1 || n > 0x3fffffff || d < 1 || d > kMaxDim || (dtype != WM_F32 && dtype != WM_F64) ||
+        (layout != WM_AOS && layout != WM_SOA) || (n > 1 && !out_edges && !out_total_weight)) {
+        set_detail("invalid argument to wm_emst%s (n=%lld)", "", (long long)n);
+        return WM_EINVAL;
+    }
+    EmstCtx c{pts, n, d, dtype, layout, out_edges, out_total_weight};
+    return run_call(opts, n, d, 0, emst_body, &c);
+}
+
+int wm_hdbscan(const void *pts, int64_t n, int32_t d, int32_t dtype, int32_t layout, int32_t min_pts, wm_edge *out_mst,
+               double *out_core_dist, wm_dnode *out_dendro, int32_t *out_order, double *out_reach, int32_t start,
+               const wm_opts *opts)
+{
+    g_detail.clear();
+    if (!pts || n < 1 || n > 0x3fffffff || d < 1 || d > kMaxDim || (dtype != WM_F32 && dtype != WM_F64) ||
+        (layout != WM_AOS && layout != WM_SOA) || min_pts < 1 || min_pts > n || start < 0 || start >= n) {
+        set_detail("invalid argument to wm_hdbscan%s (n=%lld)", "", (long long)n);
+        return WM_EINVAL;
+    }
+    HdbCtx c{pts, n, d, dtype, layout, min_pts, start, out_mst, out_core_dist, out_dendro, out_order, out_reach};
+    return run_call(opts, n, d, min_pts, hdbscan_body, &c);
+}
+
+int wm_single_linkage(const wm_edge *tree, int64_t n, int32_t start, wm_dnode *out_dendro, int32_t *out_order,
+                      double *out_reach, const wm_opts *opts)
+{
+    g_detail.clear();
+    if (n < 1 || n > 0x3fffffff || start < 0 || start >= n || (n > 1 && !tree)) {
+        set_detail("invalid argument to wm_single_linkage%s (n=%lld)", "", (long long)n);
+        return WM_EINVAL;
+    }
+    SlCtx c{tree, n, start, out_dendro, out_order, out_reach};
+    return run_call(opts, n, 1, 1, sl_body, &c);
+}
+
+int wm_query_footprint(int64_t n, int32_t d, int32_t min_pts, size_t *bytes)
+{
+    if (!bytes || n < 1 || d < 1 || d > kMaxDim || min_pts < 0) return WM_EINVAL;
+    *bytes = estimate_bytes(n, d, min_pts, default_caps(n, min_pts));
+    return WM_OK;
+}
+
+int wm_release_cache(void)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return WM_ECUDA;
+    DevCache &dc = g_cache[dev & 63];
+    std::lock_guard<std::mutex> lk(dc.mu);
+    if (dc.ptr) {
+        cudaDeviceSynchronize();
+        cudaFree(dc.ptr);
+    }
+    dc.ptr = nullptr;
+    dc.cap = 0;
+    return WM_OK;
+}
+
+const char *wm_strerror(int code)
+{
+    switch (code) {
+    case WM_OK: return "success";
+    case WM_EINVAL: return "invalid argument";
+    case WM_ENOMEM: return "out of device memory or workspace";
+    case WM_ETIMEOUT: return "a bounded device wait gave up";
+    case WM_ECUDA: return "CUDA runtime error";
+    case WM_EINTERNAL: return "internal consistency check failed";
+    default: return "unknown error code";
+    }
+}
+
+const char *wm_last_error_detail(void) { return g_detail.c_str(); }
+
+int64_t wm_kernel_launch_count(void) { return (int64_t)g_launch_count.load(); }
+
+const char *wm_version(void) { return "wspdmst 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,553 @@
+// kdtree.cu -- ingest of the input points and the spatial-median k-d tree (Sec. 2.3 "k-d tree";
+// Sec. 3.1.1: spatial-median splits down to one point per leaf).
+//
+// A node splits its tight bounding box at the midpoint of the widest dimension.  If every point
+// falls on one side (all points equal, or an extent of one float ulp) the node splits its points
+// by count instead, so every leaf holds exactly one point and the tree has 2n-1 nodes.
+//
+// Build: nodes with more than 32 points are split level by level over the whole GPU; each level
+// computes boxes with warp work-units of 256 points, counts the left side, and partitions the
+// points in place through a scratch copy.  A node of 2..32 points is finished by one warp, which
+// holds its points in registers and splits recursively with ballots and shuffles.
+#include <cstring>
+
+#include "wm_internal.cuh"
+
+namespace wm {
+
+namespace {
+
+// ---------------------------------------------------------------------------------- ingest
+__global__ void ingest_kernel(const void *__restrict__ src, int n, int d, int dtype, int layout,
+                              float *__restrict__ x32, double *__restrict__ x64, int *__restrict__ pid,
+                              unsigned *__restrict__ bad, unsigned *__restrict__ delta_bits)
+{
+    float dmax = 0.f;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)n * d;
+         t += (long long)gridDim.x * blockDim.x) {
+        // t indexes the SoA output: k = t / n, i = t % n
+        int k = (int)(t / n), i = (int)(t % n);
+        size_t sidx = layout == WM_SOA ? (size_t)t : (size_t)i * d + k;
+        double v;
+        float f;
+        if (dtype == WM_F32) {
+            f = ((const float *)src)[sidx];
+            v = (double)f;
+        } else {
+            v = ((const double *)src)[sidx];
+            f = __double2float_rn(v);
+            float e = (float)fabs(v - (double)f);
+            // round the error bound up
+            e = __fmul_ru(e, 1.0f + 1.0f / 8388608.0f);
+            dmax = fmaxf(dmax, e);
+        }
+        if (!isfinite(v) || fabs(v) > 1152921504606846976.0) atomicOr(bad, 1u);
+        x32[t] = f;
+        x64[t] = v;
+        if (k == 0) pid[i] = i;
+    }
+    for (int o = 16; o; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    if ((threadIdx.x & 31) == 0 && dmax > 0.f) atomicMax(delta_bits, __float_as_uint(dmax));
+}
+
+// ------------------------------------------------------------------------ top-level build
+constexpr int kUnit = 256;   // points per warp work-unit
+
+struct Level {
+    const int *act;      // active node ids (size > 32)
+    int A;
+    const int *unit_off; // [A+1] prefix of units per node
+};
+
+__device__ inline int find_unit_node(const int *__restrict__ unit_off, int A, int u)
+{
+    int lo = 0, hi = A - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (unit_off[mid] <= u) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void units_count_kernel(const int *__restrict__ act, int A, const int *__restrict__ nbegin,
+                                   const int *__restrict__ nend, int *__restrict__ units)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < A) {
+        int nd = act[j];
+        int sz = nend[nd] - nbegin[nd];
+        units[j] = (sz + kUnit - 1) / kUnit;
+    }
+}
+
+__global__ void box_init_kernel(const int *__restrict__ act, int A, int N, int d, float *lo, float *hi, int *cnt)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < A) {
+        int nd = act[j];
+        for (int k = 0; k < d; ++k) { lo[(size_t)k * N + nd] = INFINITY; hi[(size_t)k * N + nd] = -INFINITY; }
+        cnt[nd] = 0;
+    }
+}
+
+__global__ void box_units_kernel(Level L, const int *__restrict__ total_units, const int *__restrict__ nbegin,
+                                 const int *__restrict__ nend, const float *__restrict__ x32, int n, int N, int d,
+                                 float *lo, float *hi)
+{
+    const int lane = threadIdx.x & 31;
+    const int TU = *total_units;
+    for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < TU; u += (gridDim.x * blockDim.x) >> 5) {
+        int j = find_unit_node(L.unit_off, L.A, u);
+        int nd = L.act[j];
+        int b = nbegin[nd] + (u - L.unit_off[j]) * kUnit;
+        int e = min(b + kUnit, nend[nd]);
+        for (int k = 0; k < d; ++k) {
+            float mn = INFINITY, mx = -INFINITY;
+            for (int i = b + lane; i < e; i += 32) {
+                float v = x32[(size_t)k * n + i];
+                mn = fminf(mn, v);
+                mx = fmaxf(mx, v);
+            }
+            for (int o = 16; o; o >>= 1) {
+                mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            }
+            if (lane == 0) {
+                atomicMinF(&lo[(size_t)k * N + nd], mn);
+                atomicMaxF(&hi[(size_t)k * N + nd], mx);
+            }
+        }
+    }
+}
+
+__global__ void split_kernel(const int *__restrict__ act, int A, int N, int d, const float *__restrict__ lo,
+                             const float *__restrict__ hi, int *__restrict__ sdim, float *__restrict__ sval)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < A) {
+        int nd = act[j];
+        int best = 0;
+        float ext = -1.f;
+        for (int k = 0; k < d; ++k) {
+            float e = hi[(size_t)k * N + nd] - lo[(size_t)k * N + nd];
+            if (e > ext) { ext = e; best = k; }
+        }
+        float l = lo[(size_t)best * N + nd], h = hi[(size_t)best * N + nd];
+        sdim[j] = best;
+        sval[j] = l + (h - l) * 0.5f;
+    }
+}
+
+__global__ void count_units_kernel(Level L, const int *__restrict__ total_units, const int *__restrict__ nbegin,
+                                   const int *__restrict__ nend, const float *__restrict__ x32, int n,
+                                   const int *__restrict__ sdim, const float *__restrict__ sval, int *cnt)
+{
+    const int lane = threadIdx.x & 31;
+    const int TU = *total_units;
+    for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < TU; u += (gridDim.x * blockDim.x) >> 5) {
+        int j = find_unit_node(L.unit_off, L.A, u);
+        int nd = L.act[j];
+        int b = nbegin[nd] + (u - L.unit_off[j]) * kUnit;
+        int e = min(b + kUnit, nend[nd]);
+        int k = sdim[j];
+        float s = sval[j];
+        int c = 0;
+        for (int i = b + lane; i < e; i += 32) c += x32[(size_t)k * n + i] < s ? 1 : 0;
+        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0 && c) atomicAdd(&cnt[nd], c);
+    }
+}
+
+// Children of each active node; classification flags for the next level lists.
+__global__ void children_kernel(const int *__restrict__ act, int A, int next_id, int *nbegin, int *nend,
+                                int *nleft, int *nright, int *nparent, int *__restrict__ cnt, int *__restrict__ ndepth,
+                                int *__restrict__ count_split, int *__restrict__ is_big, int *__restrict__ is_small)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < A) {
+        int nd = act[j];
+        int b = nbegin[nd], e = nend[nd], sz = e - b;
+        int Lc = cnt[nd];
+        int cs = 0;
+        if (Lc == 0 || Lc == sz) { Lc = sz / 2; cs = 1; }
+        count_split[j] = cs;
+        cnt[nd] = Lc;
+        int l = next_id + 2 * j, r = l + 1;
+        nleft[nd] = l; nright[nd] = r;
+        nbegin[l] = b; nend[l] = b + Lc; nbegin[r] = b + Lc; nend[r] = e;
+        nparent[l] = nd; nparent[r] = nd;
+        nleft[l] = nright[l] = nleft[r] = nright[r] = -1;
+        ndepth[l] = ndepth[r] = ndepth[nd] + 1;
+        int sl = Lc, sr = sz - Lc;
+        is_big[2 * j] = sl > 32; is_big[2 * j + 1] = sr > 32;
+        is_small[2 * j] = sl > 1 && sl <= 32; is_small[2 * j + 1] = sr > 1 && sr <= 32;
+    }
+}
+
+__global__ void scatter_units_kernel(Level L, const int *__restrict__ total_units, const int *__restrict__ nbegin,
+                                     const int *__restrict__ nend, const float *__restrict__ x32,
+                                     const double *__restrict__ x64, const int *__restrict__ pid, int n, int d,
+                                     const int *__restrict__ sdim, const float *__restrict__ sval,
+                                     const int *__restrict__ count_split, const int *__restrict__ cnt,
+                                     int *__restrict__ curl, int *__restrict__ curr, float *__restrict__ t32,
+                                     double *__restrict__ t64, int *__restrict__ tpid)
+{
+    const int lane = threadIdx.x & 31;
+    const int TU = *total_units;
+    for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < TU; u += (gridDim.x * blockDim.x) >> 5) {
+        int j = find_unit_node(L.unit_off, L.A, u);
+        int nd = L.act[j];
+        int nb = nbegin[nd];
+        int b = nb + (u - L.unit_off[j]) * kUnit;
+        int e = min(b + kUnit, nend[nd]);
+        int k = sdim[j];
+        float s = sval[j];
+        int cs = count_split[j];
+        int Lc = cnt[nd];
+        for (int i0 = b; i0 < e; i0 += 32) {
+            int i = i0 + lane;
+            bool valid = i < e;
+            int dst = i;
+            if (!cs) {
+                bool fl = valid && x32[(size_t)k * n + i] < s;
+                unsigned bl = __ballot_sync(0xffffffffu, fl);
+                unsigned br = __ballot_sync(0xffffffffu, valid && !fl);
+                int bsl = 0, bsr = 0;
+                if (lane == 0) {
+                    if (bl) bsl = atomicAdd(&curl[nd], __popc(bl));
+                    if (br) bsr = atomicAdd(&curr[nd], __popc(br));
+                }
+                bsl = __shfl_sync(0xffffffffu, bsl, 0);
+                bsr = __shfl_sync(0xffffffffu, bsr, 0);
+                if (fl) dst = nb + bsl + __popc(bl & lanemask_lt());
+                else dst = nb + Lc + bsr + __popc(br & lanemask_lt());
+            }
+            if (valid) {
+                for (int kk = 0; kk < d; ++kk) {
+                    t32[(size_t)kk * n + dst] = x32[(size_t)kk * n + i];
+                    t64[(size_t)kk * n + dst] = x64[(size_t)kk * n + i];
+                }
+                tpid[dst] = pid[i];
+            }
+        }
+    }
+}
+
+__global__ void copyback_units_kernel(Level L, const int *__restrict__ total_units, const int *__restrict__ nbegin,
+                                      const int *__restrict__ nend, float *__restrict__ x32, double *__restrict__ x64,
+                                      int *__restrict__ pid, int n, int d, const float *__restrict__ t32,
+                                      const double *__restrict__ t64, const int *__restrict__ tpid)
+{
+    const int lane = threadIdx.x & 31;
+    const int TU = *total_units;
+    for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < TU; u += (gridDim.x * blockDim.x) >> 5) {
+        int j = find_unit_node(L.unit_off, L.A, u);
+        int nd = L.act[j];
+        int b = nbegin[nd] + (u - L.unit_off[j]) * kUnit;
+        int e = min(b + kUnit, nend[nd]);
+        for (int i = b + lane; i < e; i += 32) {
+            for (int kk = 0; kk < d; ++kk) {
+                x32[(size_t)kk * n + i] = t32[(size_t)kk * n + i];
+                x64[(size_t)kk * n + i] = t64[(size_t)kk * n + i];
+            }
+            pid[i] = tpid[i];
+        }
+    }
+}
+
+// compaction of the next level's lists: out[prefix[i]] = value(i) where flag[i]
+__global__ void compact_children_kernel(const int *__restrict__ flag, const int *__restrict__ pre, int m,
+                                        int next_id, int *__restrict__ out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m && flag[i]) out[pre[i]] = next_id + i;
+}
+
+// ------------------------------------------------------------------ warp-local small subtrees
+// One warp per node of 2..32 points.  Node ids of the subtree: base + 0 .. base + 2m - 3.
+template <int DM>
+__global__ void small_subtree_kernel(const int *__restrict__ small, const int *__restrict__ small_base, int S,
+                                     int *nbegin, int *nend, int *nleft, int *nright, int *nparent, int *ndepth,
+                                     float *lo, float *hi, float *x32, double *x64, int *pid, int n, int N, int d,
+                                     int *max_depth)
+{
+    const int lane = threadIdx.x & 31;
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (wid >= S) return;
+    const int root = small[wid];
+    int next = small_base[wid];
+    const int b0 = nbegin[root];
+    const int m = nend[root] - b0;
+    float c32[DM];
+    double c64[DM];
+    int myid = -1;
+    if (lane < m) {
+        for (int k = 0; k < DM; ++k) {
+            if (k < d) { c32[k] = x32[(size_t)k * n + b0 + lane]; c64[k] = x64[(size_t)k * n + b0 + lane]; }
+        }
+        myid = pid[b0 + lane];
+    }
+    // explicit stack of (lo_lane, hi_lane, node)
+    int st_lo[32], st_hi[32], st_nd[32];
+    int sp = 0;
+    st_lo[0] = 0; st_hi[0] = m; st_nd[0] = root; sp = 1;
+    int mdepth = 0;
+    while (sp > 0) {
+        --sp;
+        int rl = st_lo[sp], rh = st_hi[sp], nd = st_nd[sp];
+        int sz = rh - rl;
+        bool in = lane >= rl && lane < rh;
+        int dep = ndepth[nd];
+        mdepth = max(mdepth, dep);
+        // box over the lanes in range
+        int best = 0;
+        float ext = -1.f, bl = 0.f, bh = 0.f;
+        for (int k = 0; k < DM; ++k) {
+            if (k >= d) break;
+            float mn = in ? c32[k] : INFINITY, mx = in ? c32[k] : -INFINITY;
+            for (int o = 16; o; o >>= 1) {
+                mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            }
+            if (lane == 0) { lo[(size_t)k * N + nd] = mn; hi[(size_t)k * N + nd] = mx; }
+            if (mx - mn > ext) { ext = mx - mn; best = k; bl = mn; bh = mx; }
+        }
+        if (sz == 1) continue;   // leaf: box = the point
+        float sv = bl + (bh - bl) * 0.5f;
+        float cv = 0.f;
+        for (int k = 0; k < DM; ++k) if (k == best) cv = c32[k];
+        bool fl = in && cv < sv;
+        unsigned bal = __ballot_sync(0xffffffffu, fl);
+        int Lc = __popc(bal);
+        bool cs = (Lc == 0 || Lc == sz);
+        if (cs) { Lc = sz / 2; fl = in && (lane - rl) < Lc; bal = __ballot_sync(0xffffffffu, fl); }
+        unsigned bar = __ballot_sync(0xffffffffu, in && !fl);
+        int dst = lane;
+        if (in) dst = fl ? rl + __popc(bal & lanemask_lt()) : rl + Lc + __popc(bar & lanemask_lt());
+        // permute: lane dst receives from this lane; build the inverse with a shuffle search
+        int src = lane;
+        for (int q = 0; q < 32; ++q) {
+            int dq = __shfl_sync(0xffffffffu, dst, q);
+            if (dq == lane) src = q;
+        }
+        for (int k = 0; k < DM; ++k) {
+            if (k >= d) break;
+            c32[k] = __shfl_sync(0xffffffffu, c32[k], src);
+            c64[k] = __shfl_sync(0xffffffffu, c64[k], src);
+        }
+        myid = __shfl_sync(0xffffffffu, myid, src);
+        int l = next, r = next + 1;
+        next += 2;
+        if (lane == 0) {
+            nleft[nd] = l; nright[nd] = r;
+            nbegin[l] = b0 + rl; nend[l] = b0 + rl + Lc;
+            nbegin[r] = b0 + rl + Lc; nend[r] = b0 + rh;
+            nparent[l] = nd; nparent[r] = nd;
+            nleft[l] = nright[l] = nleft[r] = nright[r] = -1;
+            ndepth[l] = ndepth[r] = dep + 1;
+        }
+        __syncwarp();
+        // push right then left (left processed first)
+        st_lo[sp] = rl + Lc; st_hi[sp] = rh; st_nd[sp] = r; ++sp;
+        st_lo[sp] = rl; st_hi[sp] = rl + Lc; st_nd[sp] = l; ++sp;
+    }
+    if (lane < m) {
+        for (int k = 0; k < DM; ++k) {
+            if (k < d) { x32[(size_t)k * n + b0 + lane] = c32[k]; x64[(size_t)k * n + b0 + lane] = c64[k]; }
+        }
+        pid[b0 + lane] = myid;
+    }
+    if (lane == 0) atomicMax(max_depth, mdepth);
+}
+
+// Leaves created by the top levels (single points): box = the point.  Then widen every box by
+// delta (rounding outward) and store the rigorous diameter bound.
+__global__ void finish_boxes_kernel(int N, int n, int d, const int *__restrict__ nbegin, const int *__restrict__ nleft,
+                                    const float *__restrict__ x32, float *lo, float *hi, float delta,
+                                    float *__restrict__ diam2, const int *__restrict__ ndepth, int *max_depth)
+{
+    int dmax = 0;
+    for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < N; nd += gridDim.x * blockDim.x) {
+        bool leaf = nleft[nd] < 0;
+        float s = 0.f;
+        for (int k = 0; k < d; ++k) {
+            float l, h;
+            if (leaf) { l = h = x32[(size_t)k * n + nbegin[nd]]; }
+            else { l = lo[(size_t)k * N + nd]; h = hi[(size_t)k * N + nd]; }
+            if (delta > 0.f) { l = __fsub_rd(l, delta); h = __fadd_ru(h, delta); }
+            lo[(size_t)k * N + nd] = l;
+            hi[(size_t)k * N + nd] = h;
+            float e = __fsub_ru(h, l);
+            s = __fmaf_ru(e, e, s);
+        }
+        diam2[nd] = upper_w2(s);
+        dmax = max(dmax, ndepth[nd]);
+    }
+    for (int o = 16; o; o >>= 1) dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(max_depth, dmax);
+}
+
+__global__ void inverse_perm_kernel(const int *__restrict__ pid, int *__restrict__ pos, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) pos[pid[i]] = i;
+}
+
+__global__ void small_sizes_kernel(const int *small, int S, const int *nbegin, const int *nend, int *out)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < S) out[j] = 2 * (nend[small[j]] - nbegin[small[j]]) - 2;
+}
+
+__global__ void add_const_kernel(int *p, int m, int c)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < m) p[j] += c;
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------------- host drivers
+
+int ingest_points(const void *dev_src, int n, int d, int dtype, int layout, Points &P, Arena &ar,
+                  cudaStream_t st, unsigned *pinned)
+{
+    P.n = n; P.d = d;
+    P.x32 = ar.get<float>((size_t)n * d);
+    P.x64 = ar.get<double>((size_t)n * d);
+    P.pid = ar.get<int>(n);
+    P.pos = ar.get<int>(n);
+    unsigned *flags = ar.get<unsigned>(2);
+    if (ar.failed) return WM_ENOMEM;
+    cudaMemsetAsync(flags, 0, 2 * sizeof(unsigned), st);
+    launch(ingest_kernel, grid_for((long long)n * d, 256), 256, 0, st, dev_src, n, d, dtype, layout, P.x32, P.x64, P.pid,
+                                                                     flags, flags + 1);
+    cudaMemcpyAsync(pinned, flags, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;
+    if (pinned[0]) return WM_EINVAL;
+    unsigned db = pinned[1];
+    float dl;
+    memcpy(&dl, &db, sizeof(float));
+    P.delta = dl;
+    return 0;
+}
+
+int build_tree(Points &P, Tree &T, Arena &ar, cudaStream_t st, int *pinned)
+{
+    const int n = P.n, d = P.d;
+    const int N = 2 * n - 1;
+    T.N = N;
+    T.lo = ar.get<float>((size_t)N * d);
+    T.hi = ar.get<float>((size_t)N * d);
+    T.begin = ar.get<int>(N);
+    T.end = ar.get<int>(N);
+    T.left = ar.get<int>(N);
+    T.right = ar.get<int>(N);
+    T.parent = ar.get<int>(N);
+    T.diam2 = ar.get<float>(N);
+    T.comp = ar.get<int>(N);
+    T.arrive = ar.get<int>(N);
+    int *depth = ar.get<int>(N);
+    int *maxdep = ar.get<int>(1);
+    if (ar.failed) return WM_ENOMEM;
+    // root
+    int h0[6] = {0, n, -1, -1, -1, 0};
+    cudaMemcpyAsync(T.begin, &h0[0], sizeof(int), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(T.end, &h0[1], sizeof(int), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(T.left, &h0[2], sizeof(int), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(T.right, &h0[3], sizeof(int), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(T.parent, &h0[4], sizeof(int), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(depth, &h0[5], sizeof(int), cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(maxdep, 0, sizeof(int), st);
+
+    size_t mark = ar.off;
+    // scratch
+    int *act = ar.get<int>(n / 16 + 2), *act2 = ar.get<int>(n / 16 + 2);
+    int *units = ar.get<int>(n / 16 + 3);
+    int *tot = ar.get<int>(4);
+    int *sdim = ar.get<int>(n / 16 + 2);
+    float *sval = ar.get<float>(n / 16 + 2);
+    int *csplit = ar.get<int>(n / 16 + 2);
+    int *isbig = ar.get<int>(n / 8 + 4), *issmall = ar.get<int>(n / 8 + 4);
+    int *prebig = ar.get<int>(n / 8 + 4), *presmall = ar.get<int>(n / 8 + 4);
+    int *cnt = ar.get<int>(N), *curl = ar.get<int>(N), *curr = ar.get<int>(N);
+    int *small = ar.get<int>(n / 2 + 2), *small_sz = ar.get<int>(n / 2 + 2), *small_base = ar.get<int>(n / 2 + 2);
+    float *t32 = ar.get<float>((size_t)n * d);
+    double *t64 = ar.get<double>((size_t)n * d);
+    int *tpid = ar.get<int>(n);
+    if (ar.failed) return WM_ENOMEM;
+
+    int A = 0, S = 0, next_id = 1;
+    if (n > 32) {
+        cudaMemsetAsync(act, 0, sizeof(int), st);   // act[0] = root (0)
+        A = 1;
+    } else if (n > 1) {
+        cudaMemsetAsync(small, 0, sizeof(int), st);
+        S = 1;
+    }
+    cudaMemsetAsync(curl, 0, sizeof(int) * N, st);
+    cudaMemsetAsync(curr, 0, sizeof(int) * N, st);
+    int levels = 0;
+    while (A > 0) {
+        ++levels;
+        Level L{act, A, units};
+        launch(units_count_kernel, grid_for(A, 256, 1 << 20), 256, 0, st, act, A, T.begin, T.end, units);
+        int rc = scan_exclusive_i32(units, units, A, tot, st, ar);
+        if (rc) return rc;
+        const int gw = 152 * 8;   // blocks of 256 threads, 8 warps each
+        launch(box_init_kernel, grid_for(A, 256, 1 << 20), 256, 0, st, act, A, N, d, T.lo, T.hi, cnt);
+        launch(box_units_kernel, gw, 256, 0, st, L, tot, T.begin, T.end, P.x32, n, N, d, T.lo, T.hi);
+        launch(split_kernel, grid_for(A, 256, 1 << 20), 256, 0, st, act, A, N, d, T.lo, T.hi, sdim, sval);
+        launch(count_units_kernel, gw, 256, 0, st, L, tot, T.begin, T.end, P.x32, n, sdim, sval, cnt);
+        launch(children_kernel, grid_for(A, 256, 1 << 20), 256, 0, st, act, A, next_id, T.begin, T.end, T.left, T.right,
+                                                                   T.parent, cnt, depth, csplit, isbig, issmall);
+        launch(scatter_units_kernel, gw, 256, 0, st, L, tot, T.begin, T.end, P.x32, P.x64, P.pid, n, d, sdim, sval, csplit,
+                                                 cnt, curl, curr, t32, t64, tpid);
+        launch(copyback_units_kernel, gw, 256, 0, st, L, tot, T.begin, T.end, P.x32, P.x64, P.pid, n, d, t32, t64, tpid);
+        // next lists
+        rc = scan_exclusive_i32(isbig, prebig, 2 * A, tot + 1, st, ar);
+        if (rc) return rc;
+        rc = scan_exclusive_i32(issmall, presmall, 2 * A, tot + 2, st, ar);
+        if (rc) return rc;
+        launch(compact_children_kernel, grid_for(2 * A, 256, 1 << 20), 256, 0, st, isbig, prebig, 2 * A, next_id, act2);
+        launch(compact_children_kernel, grid_for(2 * A, 256, 1 << 20), 256, 0, st, issmall, presmall, 2 * A, next_id,
+                                                                               small + S);
+        cudaMemcpyAsync(pinned, tot + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;
+        next_id += 2 * A;
+        A = pinned[0];
+        S += pinned[1];
+        int *t = act; act = act2; act2 = t;
+    }
+    // sizes of the small roots and their node-id bases
+    if (S > 0) {
+        launch(small_sizes_kernel, grid_for(S, 256, 1 << 20), 256, 0, st, small, S, T.begin, T.end, small_sz);
+        int rc = scan_exclusive_i32(small_sz, small_base, S, tot + 3, st, ar);
+        if (rc) return rc;
+        launch(add_const_kernel, grid_for(S, 256, 1 << 20), 256, 0, st, small_base, S, next_id);
+        int blocks = (S + 7) / 8;
+#define WM_SMALL(DM) launch(small_subtree_kernel<DM>, blocks, 256, 0, st, small, small_base, S, T.begin, T.end, T.left, \
+        T.right, T.parent, depth, T.lo, T.hi, P.x32, P.x64, P.pid, n, N, d, maxdep)
+        if (d <= 2) WM_SMALL(2);
+        else if (d <= 3) WM_SMALL(3);
+        else if (d <= 4) WM_SMALL(4);
+        else if (d <= 5) WM_SMALL(5);
+        else if (d <= 8) WM_SMALL(8);
+        else WM_SMALL(16);
+#undef WM_SMALL
+    }
+    if (n == 1) {
+        int m1 = -1;
+        cudaMemcpyAsync(T.left, &m1, sizeof(int), cudaMemcpyHostToDevice, st);
+    }
+    launch(finish_boxes_kernel, grid_for(N, 256), 256, 0, st, N, n, d, T.begin, T.left, P.x32, T.lo, T.hi, P.delta, T.diam2,
+                                                         depth, maxdep);
+    launch(inverse_perm_kernel, grid_for(n, 256, 1 << 20), 256, 0, st, P.pid, P.pos, n);
+    cudaMemcpyAsync(pinned, maxdep, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;
+    T.depth = pinned[0] + 1;
+    ar.off = mark;   // release build scratch
+    return 0;
+}
+
+}  // namespace wm

@@ -1,0 +1,245 @@
+// util.cu -- device-wide primitives: exclusive prefix sum and a stable LSD radix sort of
+// 128-bit edge keys (the "prefix sum" and sorting primitives of Sec. 2.2, written for the GPU).
+#include "wm_internal.cuh"
+
+namespace wm {
+
+namespace {
+
+constexpr int kScanBlock = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanBlock * kScanItems;
+
+__device__ inline int block_exclusive_scan(int v, int *smem_warp, int &total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) smem_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < nw ? smem_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) smem_warp[lane] = w;
+    }
+    __syncthreads();
+    total = smem_warp[nw - 1];
+    int r = x - v + (warp > 0 ? smem_warp[warp - 1] : 0);
+    __syncthreads();
+    return r;
+}
+
+__global__ void scan_reduce_kernel(const int *__restrict__ in, int n, int *__restrict__ block_sums)
+{
+    __shared__ int sw[32];
+    long long base = (long long)blockIdx.x * kScanTile;
+    int s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        long long idx = base + (long long)threadIdx.x * kScanItems + i;
+        if (idx < n) s += in[idx];
+    }
+    int total;
+    block_exclusive_scan(s, sw, total);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+__global__ void scan_down_kernel(const int *__restrict__ in, int *__restrict__ out, int n,
+                                 const int *__restrict__ block_offs, int *total_dev, int nblocks)
+{
+    __shared__ int sw[32];
+    long long base = (long long)blockIdx.x * kScanTile;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        long long idx = base + (long long)threadIdx.x * kScanItems + i;
+        v[i] = idx < n ? in[idx] : 0;
+        s += v[i];
+    }
+    int total;
+    int ex = block_exclusive_scan(s, sw, total) + (block_offs ? block_offs[blockIdx.x] : 0);
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        long long idx = base + (long long)threadIdx.x * kScanItems + i;
+        if (idx < n) out[idx] = ex;
+        ex += v[i];
+    }
+    if (total_dev && blockIdx.x == nblocks - 1 && threadIdx.x == blockDim.x - 1) *total_dev = ex;
+}
+
+__global__ void fill_i32_kernel(int *p, int v, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+}  // namespace
+
+void fill_i32(int *p, int v, size_t n, cudaStream_t st)
+{
+    if (n == 0) return;
+    launch(fill_i32_kernel, grid_for((long long)n, 256), 256, 0, st, p, v, n);
+}
+
+// out[i] = sum_{j<i} in[j]; *total_dev (optional, device) = sum of all.  in may equal out.
+int scan_exclusive_i32(const int *in, int *out, int n, int *total_dev, cudaStream_t st, Arena &ar)
+{
+    if (n <= 0) {
+        if (total_dev) cudaMemsetAsync(total_dev, 0, sizeof(int), st);
+        return 0;
+    }
+    int nb = (n + kScanTile - 1) / kScanTile;
+    if (nb == 1) {
+        launch(scan_down_kernel, 1, kScanBlock, 0, st, in, out, n, nullptr, total_dev, 1);
+        return 0;
+    }
+    size_t mark = ar.off;
+    int *sums = ar.get<int>(nb);
+    if (!sums) return WM_ENOMEM;
+    launch(scan_reduce_kernel, nb, kScanBlock, 0, st, in, n, sums);
+    int rc = scan_exclusive_i32(sums, sums, nb, nullptr, st, ar);
+    if (rc) return rc;
+    launch(scan_down_kernel, nb, kScanBlock, 0, st, in, out, n, sums, total_dev, nb);
+    ar.off = mark;
+    return 0;
+}
+
+// ------------------------------------------------------------------------------ radix sort
+namespace {
+
+constexpr int kRsBlock = 256;
+
+__device__ inline unsigned digit_of(const EdgeK &e, int byte)
+{
+    unsigned long long w = byte < 8 ? e.lo : e.hi;
+    return (unsigned)(w >> ((byte & 7) * 8)) & 0xffu;
+}
+
+// Histogram of every byte position over all keys: ghist[byte*256 + digit].
+__global__ void rs_hist_all(const EdgeK *__restrict__ a, int m, unsigned *__restrict__ ghist)
+{
+    __shared__ unsigned h[16 * 256];
+    for (int i = threadIdx.x; i < 16 * 256; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
+        EdgeK e = a[i];
+#pragma unroll
+        for (int b = 0; b < 16; ++b) atomicAdd(&h[b * 256 + digit_of(e, b)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 16 * 256; i += blockDim.x)
+        if (h[i]) atomicAdd(&ghist[i], h[i]);
+}
+
+// Per-block histogram of one byte over the block's contiguous chunk: bh[digit*G + block].
+__global__ void rs_pass_hist(const EdgeK *__restrict__ a, int m, int byte, int chunk, int *__restrict__ bh)
+{
+    __shared__ int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    long long beg = (long long)blockIdx.x * chunk, end = beg + chunk < m ? beg + chunk : m;
+    for (long long i = beg + threadIdx.x; i < end; i += blockDim.x) atomicAdd(&h[digit_of(a[i], byte)], 1);
+    __syncthreads();
+    bh[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter: block processes its chunk in order, 256 keys per step.
+__global__ void __launch_bounds__(kRsBlock) rs_pass_scatter(const EdgeK *__restrict__ a, EdgeK *__restrict__ out, int m,
+                                                            int byte, int chunk, const int *__restrict__ offs)
+{
+    __shared__ int base[256];
+    __shared__ int wcnt[8][256];   // (step << 6) | count, entries of other steps read as 0
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    base[threadIdx.x] = offs[threadIdx.x * gridDim.x + blockIdx.x];
+    for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) (&wcnt[0][0])[i] = -1;
+    __syncthreads();
+    long long beg = (long long)blockIdx.x * chunk, end = beg + chunk < m ? beg + chunk : m;
+    int step = 0;
+    for (long long t0 = beg; t0 < end; t0 += kRsBlock, ++step) {
+        long long idx = t0 + threadIdx.x;
+        bool valid = idx < end;
+        EdgeK e;
+        unsigned dg = 256;
+        if (valid) { e = a[idx]; dg = digit_of(e, byte); }
+        unsigned peers = __match_any_sync(0xffffffffu, dg);
+        int rank = __popc(peers & lanemask_lt());
+        int leader = __ffs(peers) - 1;
+        if (valid && lane == leader) wcnt[warp][dg] = (step << 6) | __popc(peers);
+        __syncthreads();
+        if (valid) {
+            int off = base[dg] + rank;
+            for (int w = 0; w < warp; ++w) {
+                int c = wcnt[w][dg];
+                if (c >= 0 && (c >> 6) == step) off += c & 63;
+            }
+            out[off] = e;
+        }
+        __syncthreads();
+        {
+            int dgt = threadIdx.x, add = 0;
+            for (int w = 0; w < 8; ++w) {
+                int c = wcnt[w][dgt];
+                if (c >= 0 && (c >> 6) == step) add += c & 63;
+            }
+            base[dgt] += add;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+// Sorts m keys ascending as 128-bit unsigned integers (stable LSD, 8-bit digits, byte
+// positions on which all keys agree are skipped).  The result is in *result (keys or tmp).
+int radix_sort_edges(EdgeK *keys, EdgeK *tmp, int m, cudaStream_t st, Arena &ar, EdgeK **result)
+{
+    *result = keys;
+    if (m <= 1) return 0;
+    size_t mark = ar.off;
+    unsigned *ghist = ar.get<unsigned>(16 * 256);
+    unsigned *hhist = nullptr;
+    if (!ghist) return WM_ENOMEM;
+    cudaMemsetAsync(ghist, 0, sizeof(unsigned) * 16 * 256, st);
+    launch(rs_hist_all, grid_for(m, 256, 152 * 4), 256, 0, st, keys, m, ghist);
+    cudaMallocHost((void **)&hhist, sizeof(unsigned) * 16 * 256);
+    if (!hhist) { ar.off = mark; return WM_ENOMEM; }
+    cudaMemcpyAsync(hhist, ghist, sizeof(unsigned) * 16 * 256, cudaMemcpyDeviceToHost, st);
+    cudaError_t ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) { cudaFreeHost(hhist); ar.off = mark; return WM_ECUDA; }
+    bool need[16];
+    for (int b = 0; b < 16; ++b) {
+        need[b] = true;
+        for (int g = 0; g < 256; ++g)
+            if (hhist[b * 256 + g] == (unsigned)m) { need[b] = false; break; }
+    }
+    cudaFreeHost(hhist);
+    int G = (m + 2047) / 2048;
+    if (G > 1024) G = 1024;
+    int chunk = (m + G - 1) / G;
+    chunk = (chunk + kRsBlock - 1) / kRsBlock * kRsBlock;
+    G = (m + chunk - 1) / chunk;
+    int *bh = ar.get<int>((size_t)256 * G);
+    if (!bh) { ar.off = mark; return WM_ENOMEM; }
+    EdgeK *src = keys, *dst = tmp;
+    for (int b = 0; b < 16; ++b) {
+        if (!need[b]) continue;
+        launch(rs_pass_hist, G, 256, 0, st, src, m, b, chunk, bh);
+        int rc = scan_exclusive_i32(bh, bh, 256 * G, nullptr, st, ar);
+        if (rc) { ar.off = mark; return rc; }
+        launch(rs_pass_scatter, G, kRsBlock, 0, st, src, dst, m, b, chunk, bh);
+        EdgeK *t = src; src = dst; dst = t;
+    }
+    *result = src;
+    ar.off = mark;
+    return 0;
+}
+
+}  // namespace wm

@@ -1,0 +1,183 @@
+// wm_internal.cuh -- internal declarations shared by the CUDA translation units of libwspdmst.
+//
+// Data layout in HBM (all arrays are device-resident for the whole call):
+//   points  : SoA, permuted into k-d tree order.  x32[k*n + i] (float, the FP32 screen copy),
+//             x64[k*n + i] (double, the exact copy), pid[i] = input row of tree position i.
+//   tree    : one record per node, stored as parallel arrays indexed by node id (BFS order):
+//             box lo/hi [k*N + node] (float, rounded outward so they contain the FP64 points),
+//             begin/end (point range in tree order), left/right children (-1 at a leaf),
+//             parent, plus per-round comp label and, for HDBSCAN*, cd bounds.
+//   edges   : 16-byte records EdgeK {hi = bits of the FP64 w2, lo = (min id << 32) | max id},
+//             which compare as 128-bit unsigned integers exactly like the key K (w2 >= 0).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include <atomic>
+#include <utility>
+
+#include "../../include/wspdmst.h"
+
+namespace wm {
+
+constexpr int kMaxDim = 16;
+
+// ------------------------------------------------------------------ error bounds of the screen
+// Relative error bound of an FP32 sum of d <= 16 squared differences of exactly representable
+// inputs: each subtract, square and add contributes at most one half-ulp, (d+2)*2^-24 <= 2^-19.
+constexpr double kEps32 = 1.0 / 524288.0;                  // 2^-19
+// Relative error bound of the FP64 evaluation of w2 (same operation count): (d+2)*2^-53 < 2^-48.
+constexpr double kGam64 = 1.0 / 281474976710656.0;         // 2^-48
+// Margin used to turn FP32 box bounds into bounds on any FP64 w2 of the points inside.
+constexpr float kBoxRel = 1.0f / 262144.0f;                // 2^-18 > kEps32 + kGam64 + products
+// Absolute slack covering FP32 subnormal rounding (each op errs by at most 2^-150).
+constexpr float kAbsTiny = 7.17464814e-43f;                // 2^-140
+
+// ---------------------------------------------------------------------------- edge record
+struct __align__(16) EdgeK {
+    unsigned long long lo;   // (min id << 32) | max id
+    unsigned long long hi;   // bits of w2 (double, >= 0)
+};
+
+__host__ __device__ inline EdgeK make_edge(double w2, int a, int b)
+{
+    unsigned ua = (unsigned)(a < b ? a : b), ub = (unsigned)(a < b ? b : a);
+    EdgeK e;
+    e.lo = ((unsigned long long)ua << 32) | ub;
+#ifdef __CUDA_ARCH__
+    e.hi = (unsigned long long)__double_as_longlong(w2);
+#else
+    union { double d; unsigned long long u; } c; c.d = w2; e.hi = c.u;
+#endif
+    return e;
+}
+__host__ __device__ inline int edge_u(const EdgeK &e) { return (int)(e.lo >> 32); }
+__host__ __device__ inline int edge_v(const EdgeK &e) { return (int)(e.lo & 0xffffffffu); }
+__device__ inline double edge_w2(const EdgeK &e) { return __longlong_as_double((long long)e.hi); }
+__host__ __device__ inline bool edge_less(const EdgeK &a, const EdgeK &b)
+{
+    return a.hi != b.hi ? a.hi < b.hi : a.lo < b.lo;
+}
+
+// ------------------------------------------------------------------------- arena allocator
+struct Arena {
+    char *base = nullptr;
+    size_t cap = 0;
+    size_t off = 0;
+    size_t peak = 0;
+    bool failed = false;
+    void *take(size_t bytes)
+    {
+        size_t a = (off + 255) & ~size_t(255);
+        if (a + bytes > cap) { failed = true; return nullptr; }
+        off = a + bytes;
+        if (off > peak) peak = off;
+        return base + a;
+    }
+    template <class T> T *get(size_t count) { return (T *)take(sizeof(T) * (count ? count : 1)); }
+};
+
+// ---------------------------------------------------------------------------- point / tree
+struct Points {
+    int n = 0, d = 0;
+    float *x32 = nullptr;    // [d][n]
+    double *x64 = nullptr;   // [d][n]
+    int *pid = nullptr;      // tree position -> input id
+    int *pos = nullptr;      // input id -> tree position
+    float delta = 0.f;       // max |x64 - x32| over all coordinates (0 for FP32 input)
+};
+
+struct Tree {
+    int N = 0;                 // nodes
+    int depth = 0;             // levels
+    float *lo = nullptr, *hi = nullptr;   // [d][N]
+    int *begin = nullptr, *end = nullptr, *left = nullptr, *right = nullptr, *parent = nullptr;
+    float *diam2 = nullptr;    // rigorous upper bound of any FP64 w2 inside the node
+    int *comp = nullptr;       // per round: component id if all points in one, else -1
+    float *cdmin = nullptr, *cdmax = nullptr;   // HDBSCAN*: cd2 bounds (rounded outward)
+    int *arrive = nullptr;     // scratch counters for bottom-up passes
+};
+
+// -------------------------------------------------------------------- small device helpers
+__device__ inline float atomicMinF(float *addr, float v)
+{
+    return v >= 0.f ? __int_as_float(atomicMin((int *)addr, __float_as_int(v)))
+                    : __uint_as_float(atomicMax((unsigned *)addr, __float_as_uint(v)));
+}
+__device__ inline float atomicMaxF(float *addr, float v)
+{
+    return v >= 0.f ? __int_as_float(atomicMax((int *)addr, __float_as_int(v)))
+                    : __uint_as_float(atomicMin((unsigned *)addr, __float_as_uint(v)));
+}
+// WriteMin of a non-negative double (its bit pattern orders like the value).
+__device__ inline void atomicMinPosD(double *addr, double v)
+{
+    atomicMin((unsigned long long *)addr, (unsigned long long)__double_as_longlong(v));
+}
+
+// Exact FP64 squared distance in dimension order, one rounding per operation, no FMA.
+template <int D>
+__device__ inline double sqdist64(const double *__restrict__ x64, int n, int d, int i, int j)
+{
+    double s = 0.0;
+    const int dd = D > 0 ? D : d;
+#pragma unroll
+    for (int k = 0; k < (D > 0 ? D : kMaxDim); ++k) {
+        if (D <= 0 && k >= dd) break;
+        double t = __dsub_rn(x64[(size_t)k * n + i], x64[(size_t)k * n + j]);
+        s = __dadd_rn(s, __dmul_rn(t, t));
+    }
+    return s;
+}
+
+// Rigorous bounds on the FP64 w2 of any point pair inside boxes from FP32 box arithmetic.
+__device__ inline float lower_w2(float q) { float r = __fsub_rd(__fmul_rd(q, 1.0f - kBoxRel), kAbsTiny); return r > 0.f ? r : 0.f; }
+__device__ inline float upper_w2(float q) { return __fadd_ru(__fmul_ru(q, 1.0f + kBoxRel), kAbsTiny); }
+
+// Squared distance between two boxes (lower bound, FP32) and squared max distance (upper).
+__device__ inline void box_bounds(const float *__restrict__ lo, const float *__restrict__ hi, int N, int d,
+                                  int a, int b, float &lb, float &ub)
+{
+    float s = 0.f, t = 0.f;
+    for (int k = 0; k < d; ++k) {
+        float alo = lo[(size_t)k * N + a], ahi = hi[(size_t)k * N + a];
+        float blo = lo[(size_t)k * N + b], bhi = hi[(size_t)k * N + b];
+        float g = fmaxf(fmaxf(blo - ahi, alo - bhi), 0.f);
+        float m = fmaxf(bhi - alo, ahi - blo);
+        s = fmaf(g, g, s);
+        t = fmaf(m, m, t);
+    }
+    lb = lower_w2(s);
+    ub = upper_w2(t);
+}
+
+__device__ inline unsigned lanemask_lt() { unsigned m; asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m)); return m; }
+
+// ------------------------------------------------------------------------- host-side API
+// util.cu
+int scan_exclusive_i32(const int *in, int *out, int n, int *total_dev, cudaStream_t st, Arena &ar);
+int radix_sort_edges(EdgeK *keys, EdgeK *tmp, int m, cudaStream_t st, Arena &ar, EdgeK **result);
+void fill_i32(int *p, int v, size_t n, cudaStream_t st);
+
+// Every kernel launch of the library goes through launch(), which counts it.
+extern std::atomic<long long> g_launch_count;
+
+template <typename... KArgs, typename... Args>
+inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args &&...args)
+{
+    g_launch_count.fetch_add(1, std::memory_order_relaxed);
+    kernel<<<grid, block, smem, st>>>(std::forward<Args>(args)...);
+}
+
+// kernel launch helpers
+inline int grid_for(long long work, int block, int max_blocks = 152 * 16)
+{
+    long long g = (work + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > max_blocks) g = max_blocks;
+    return (int)g;
+}
+
+}  // namespace wm

@@ -1,0 +1,571 @@
+// wspd.cu -- the lazily traversed well-separated pair decomposition of MemoGFK (Sec. 3.1.1,
+// Algorithm 1; Sec. 3.1.3, Algorithm 3) and the BCCP / BCCP* computations (Sec. 2.3, 3.1.2, 3.2.2).
+//
+// Per round the host runs, with the union-find state of the previous rounds:
+//   comp labels  : every node gets the component id shared by all its points, or -1 (mixed);
+//   GetRho       : a pruned breadth-first FindPair traversal that WriteMins, over well-separated
+//                  unconnected pairs with |A|+|B| > beta, a lower bound of their BCCP;
+//   GetPairs     : a second traversal retrieving the well-separated unconnected pairs whose BCCP
+//                  can lie in [rho_lo, rho_hi); small pairs get their BCCP evaluated in place,
+//                  larger ones are queued for the tile kernel;
+//   BCCP tiles   : FP32 distance screen over A x B in warp tiles, then FP64 re-evaluation of every
+//                  candidate inside the rigorous error band of the screened minimum, and the
+//                  K-minimum edge is emitted when its FP64 w2 lies in [rho_lo, rho_hi).
+//
+// Recursion-free form: each traversal keeps a frontier of node pairs; one kernel launch expands
+// one level of the FindPair recursion (children appended with warp-aggregated atomics).
+//
+// Well-separation tests use boxes (the nodes' bounding volumes).  Geometric separation is
+// d(A,B) > max(diam A, diam B) with d and diam the box distance and box diagonal, made strict and
+// rigorous so that every cross pair is strictly heavier than every pair inside A or inside B; for
+// HDBSCAN* the disjunction with mutual unreachability (Sec. 3.2.2) is used.  Two single points
+// always form a pair.
+#include "wspd.cuh"
+
+namespace wm {
+
+namespace {
+
+__device__ inline bool is_leaf(const TravArgs &a, int x) { return a.left[x] < 0; }
+__device__ inline int nsize(const TravArgs &a, int x) { return a.end[x] - a.begin[x]; }
+
+// lower / upper bound of BCCP (or BCCP*) of (P,Q) on the w2 scale, and the well-separation test
+__device__ inline void pair_bounds(const TravArgs &a, int P, int Q, float &lbB, float &ubB, bool &ws)
+{
+    float lb, ub;
+    box_bounds(a.lo, a.hi, a.N, a.d, P, Q, lb, ub);
+    float dP = a.diam2[P], dQ = a.diam2[Q];
+    float dm = fmaxf(dP, dQ);
+    ws = lb > dm;
+    lbB = lb;
+    ubB = ub;
+    if (a.cdmin) {
+        float cminP = a.cdmin[P], cminQ = a.cdmin[Q], cmaxP = a.cdmax[P], cmaxQ = a.cdmax[Q];
+        float lhs = fmaxf(lb, fmaxf(cminP, cminQ));
+        float rhs = fmaxf(dm, fmaxf(cmaxP, cmaxQ));
+        ws = ws || lhs >= rhs;
+        lbB = lhs;
+        ubB = fmaxf(ub, fmaxf(cmaxP, cmaxQ));
+    }
+    if (is_leaf(a, P) && is_leaf(a, Q)) ws = true;
+}
+
+// threshold of the FP32 screen: any candidate whose screened value exceeds T cannot beat the
+// screened minimum s once both are evaluated exactly in FP64.
+__device__ inline float screen_threshold(float s, double eta)
+{
+    double t;
+    if (eta == 0.0) {
+        t = (double)s * (1.0 + 4.0 * kEps32) + 1.5e-42;
+    } else {
+        double r = sqrt((double)s * (1.0 + 2.0 * kEps32)) + eta;
+        double U = r * r * (1.0 + 2.0 * kGam64);
+        double q = sqrt(U * (1.0 + 2.0 * kGam64)) + eta;
+        t = q * q * (1.0 + 2.0 * kEps32) + 1.5e-42;
+    }
+    return __double2float_ru(t);
+}
+
+__device__ inline float dist32(const float *__restrict__ x32, int n, int d, int i, int j)
+{
+    float s = 0.f;
+    for (int k = 0; k < d; ++k) {
+        float t = x32[(size_t)k * n + i] - x32[(size_t)k * n + j];
+        s = fmaf(t, t, s);
+    }
+    return s;
+}
+
+__device__ inline double dist64(const double *__restrict__ x64, int n, int d, int i, int j)
+{
+    double s = 0.0;
+    for (int k = 0; k < d; ++k) {
+        double t = __dsub_rn(x64[(size_t)k * n + i], x64[(size_t)k * n + j]);
+        s = __dadd_rn(s, __dmul_rn(t, t));
+    }
+    return s;
+}
+
+// exact FP64 weight of positions (i,j), skipping the distance when core distances dominate
+__device__ inline double exact_w2(const TravArgs &a, int i, int j, float s32)
+{
+    if (a.cd64) {
+        double c = fmax(a.cd64[i], a.cd64[j]);
+        if (a.eta == 0.0 && s32 * (1.0f + 1.0f / 131072.0f) < fmaxf(a.cd32[i], a.cd32[j]) * (1.0f - 1.0f / 4194304.0f))
+            return c;
+        return fmax(c, dist64(a.x64, a.n, a.d, i, j));
+    }
+    return dist64(a.x64, a.n, a.d, i, j);
+}
+
+struct KMin {
+    unsigned long long hi, lo;   // w2 bits, (min id << 32) | max id
+};
+__device__ inline void kmin_update(KMin &m, double w2, int pu, int pv)
+{
+    unsigned long long h = (unsigned long long)__double_as_longlong(w2);
+    unsigned a = (unsigned)min(pu, pv), b = (unsigned)max(pu, pv);
+    unsigned long long l = ((unsigned long long)a << 32) | b;
+    if (h < m.hi || (h == m.hi && l < m.lo)) { m.hi = h; m.lo = l; }
+}
+
+// warp-aggregated append of `cnt` items (0..2) per lane; returns this lane's first slot
+__device__ inline int warp_append(int *counter, int cnt)
+{
+    const int lane = threadIdx.x & 31;
+    int x = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    int total = __shfl_sync(0xffffffffu, x, 31);
+    int base = 0;
+    if (lane == 31 && total) base = atomicAdd(counter, total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    return base + x - cnt;
+}
+
+// BCCP / BCCP* of a small pair, evaluated by one thread (Sec. 3.1.2: all |A||B| distances and a
+// WriteMin; here a thread-local minimum).  Adds its evaluation and recheck counts to ev / re.
+__device__ KMin bccp_inline(const TravArgs &a, int P, int Q, unsigned long long &ev, unsigned long long &re)
+{
+    const int pb = a.begin[P], pe = a.end[P], qb = a.begin[Q], qe = a.end[Q];
+    KMin best{~0ull, ~0ull};
+    if (a.fp64) {
+        for (int i = pb; i < pe; ++i)
+            for (int j = qb; j < qe; ++j) {
+                double w = dist64(a.x64, a.n, a.d, i, j);
+                if (a.cd64) w = fmax(w, fmax(a.cd64[i], a.cd64[j]));
+                kmin_update(best, w, a.pid[i], a.pid[j]);
+            }
+    } else {
+        float smin = INFINITY;
+        for (int i = pb; i < pe; ++i)
+            for (int j = qb; j < qe; ++j) {
+                float s = dist32(a.x32, a.n, a.d, i, j);
+                if (a.cd32) s = fmaxf(s, fmaxf(a.cd32[i], a.cd32[j]));
+                smin = fminf(smin, s);
+            }
+        float T = screen_threshold(smin, a.eta);
+        for (int i = pb; i < pe; ++i)
+            for (int j = qb; j < qe; ++j) {
+                float s = dist32(a.x32, a.n, a.d, i, j);
+                if (a.cd32) s = fmaxf(s, fmaxf(a.cd32[i], a.cd32[j]));
+                if (s <= T) {
+                    kmin_update(best, exact_w2(a, i, j, s), a.pid[i], a.pid[j]);
+                    ++re;
+                }
+            }
+    }
+    ev += (unsigned long long)((pe - pb) * (qe - qb));
+    return best;
+}
+
+__device__ inline bool in_range(const TravArgs &a, const KMin &m)
+{
+    double w2 = __longlong_as_double((long long)m.hi);
+    return m.hi != ~0ull && w2 >= a.rho_lo && w2 < a.rho_hi;
+}
+
+__device__ inline unsigned long long warp_sum_u64(unsigned long long v)
+{
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ----------------------------------------------------------------------- traversal kernels
+// warp-aggregated append of one edge per lane that has one
+__device__ inline void warp_emit(const TravArgs &a, bool has, const KMin &m)
+{
+    int slot = warp_append(a.edge_count, has ? 1 : 0);
+    if (has) {
+        if (slot < a.edge_cap) {
+            EdgeK e;
+            e.hi = m.hi;
+            e.lo = m.lo;
+            a.edges[slot] = e;
+        } else {
+            atomicOr(a.overflow, 2u);
+        }
+    }
+}
+
+// One level of FindPair.  MODE 0 = GetRho, MODE 1 = GetPairs.
+template <int MODE>
+__global__ void __launch_bounds__(256) findpair_level_kernel(TravArgs a, const int2 *__restrict__ in,
+                                                             const int *__restrict__ in_count, int2 *__restrict__ out,
+                                                             int *out_count, int *zero_count)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) *zero_count = 0;
+    const int m = *in_count;
+    const int stride = gridDim.x * blockDim.x;
+    const int limit = (m + 31) & ~31;   // whole warps iterate together
+    const int lane = threadIdx.x & 31;
+    unsigned long long n_pairs = 0, n_ev = 0, n_re = 0;
+    const bool stop = __shfl_sync(0xffffffffu, (int)(*(volatile unsigned *)a.overflow != 0), 0) != 0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t - lane < limit && !stop; t += stride) {
+        int push = 0;
+        int2 c0 = make_int2(0, 0), c1 = make_int2(0, 0);
+        bool big = false, has_edge = false;
+        KMin best{~0ull, ~0ull};
+        double rho_cand = INFINITY;
+        int2 me = make_int2(0, 0);
+        if (t < m) {
+            me = in[t];
+            int P = me.x, Q = me.y;
+            bool live = true;
+            if (MODE == 0 && nsize(a, P) + nsize(a, Q) <= a.beta) live = false;
+            if (live) {
+                int cp = a.comp[P];
+                if (cp >= 0 && cp == a.comp[Q]) live = false;
+            }
+            if (live) {
+                float lbB, ubB;
+                bool ws;
+                pair_bounds(a, P, Q, lbB, ubB, ws);
+                if (MODE == 0) {
+                    double rho = *(volatile double *)a.rho_out;
+                    if ((double)lbB >= rho) live = false;
+                    else if (ws) { rho_cand = (double)lbB; live = false; }
+                } else {
+                    if ((double)lbB >= a.rho_hi || (double)ubB < a.rho_lo) live = false;
+                    else if (ws) {
+                        long long prod = (long long)nsize(a, P) * nsize(a, Q);
+                        if (prod <= a.inline_max) {
+                            best = bccp_inline(a, P, Q, n_ev, n_re);
+                            has_edge = in_range(a, best);
+                        } else {
+                            big = true;
+                        }
+                        ++n_pairs;
+                        live = false;
+                    }
+                }
+                if (live) {
+                    // split the node with the larger diameter (a leaf cannot be split)
+                    bool splitP = !is_leaf(a, P) && (is_leaf(a, Q) || a.diam2[P] >= a.diam2[Q]);
+                    int S = splitP ? P : Q, O = splitP ? Q : P;
+                    c0 = make_int2(a.left[S], O);
+                    c1 = make_int2(a.right[S], O);
+                    push = 2;
+                }
+            }
+        }
+        int slot = warp_append(out_count, push);
+        if (push) {
+            if (slot + 2 <= a.frontier_cap) { out[slot] = c0; out[slot + 1] = c1; }
+            else atomicOr(a.overflow, 1u);
+        }
+        if (MODE == 0) {
+            for (int o = 16; o; o >>= 1) rho_cand = fmin(rho_cand, __shfl_xor_sync(0xffffffffu, rho_cand, o));
+            if (lane == 0 && rho_cand < INFINITY) atomicMinPosD(a.rho_out, rho_cand);
+        } else {
+            int bs = warp_append(a.big_count, big ? 1 : 0);
+            if (big) {
+                if (bs < a.big_cap) a.big[bs] = me;
+                else atomicOr(a.overflow, 4u);
+            }
+            warp_emit(a, has_edge, best);
+        }
+    }
+    if (MODE == 1) {
+        n_pairs = warp_sum_u64(n_pairs);
+        n_ev = warp_sum_u64(n_ev);
+        n_re = warp_sum_u64(n_re);
+        if (lane == 0 && n_pairs) {
+            atomicAdd(a.stat + 0, n_pairs);
+            atomicAdd(a.stat + 1, n_ev);
+            atomicAdd(a.stat + 2, n_re);
+        }
+    }
+}
+
+// Initial frontier: (left(A), right(A)) for every internal node A whose points are not all
+// connected (and, for GetRho, |A| > beta).
+__global__ void frontier_init_kernel(TravArgs a, int mode, int2 *__restrict__ out, int *out_count)
+{
+    const int limit = (a.N + 31) & ~31;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x - (threadIdx.x & 31) < limit; x += gridDim.x * blockDim.x) {
+        int push = 0;
+        if (x < a.N && a.left[x] >= 0 && a.comp[x] < 0 && (mode == 1 || nsize(a, x) > a.beta)) push = 1;
+        int slot = warp_append(out_count, push);
+        if (push) {
+            if (slot < a.frontier_cap) out[slot] = make_int2(a.left[x], a.right[x]);
+            else atomicOr(a.overflow, 1u);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------ component labels
+__global__ void uf_flatten_kernel(int *uf, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int r = i;
+        for (int it = 0; it < n && uf[r] != r; ++it) r = uf[r];
+        uf[i] = r;
+    }
+}
+
+// bottom-up: comp(leaf) = root of its point; comp(node) = common comp of the children or -1.
+__global__ void comp_labels_kernel(int N, const int *__restrict__ left, const int *__restrict__ right,
+                                   const int *__restrict__ parent, const int *__restrict__ begin,
+                                   const int *__restrict__ pid, const int *__restrict__ uf, int *comp, int *arrive)
+{
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x) {
+        if (left[x] >= 0) continue;
+        comp[x] = uf[pid[begin[x]]];
+        int cur = x;
+        for (int it = 0; it < N; ++it) {
+            int p = parent[cur];
+            if (p < 0) break;
+            __threadfence();
+            if (atomicAdd(&arrive[p], 1) == 0) break;
+            __threadfence();
+            int cl = ((volatile int *)comp)[left[p]], cr = ((volatile int *)comp)[right[p]];
+            comp[p] = (cl >= 0 && cl == cr) ? cl : -1;
+            cur = p;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------- BCCP tile kernel
+constexpr int kItems = 2;              // points of the larger side per lane
+constexpr int kTileA = 32 * kItems;
+// points of the smaller side staged per warp (8 warps per block, static shared memory < 48 KB)
+__host__ __device__ constexpr int tile_q(int dd) { return dd <= 8 ? 128 : 64; }
+
+__global__ void tile_jobs_kernel(const TravArgs a, int m, int tq, int *__restrict__ jobs)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < m) {
+        int P = a.big[j].x, Q = a.big[j].y;
+        int sp = nsize(a, P), sq = nsize(a, Q);
+        int big = max(sp, sq), small = min(sp, sq);
+        jobs[j] = ((big + kTileA - 1) / kTileA) * ((small + tq - 1) / tq);
+    }
+}
+
+__device__ inline int find_job_pair(const int *__restrict__ off, int m, int u)
+{
+    int lo = 0, hi = m - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= u) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int D, bool HDB, bool FP64>
+__global__ void __launch_bounds__(256) bccp_tile_kernel(TravArgs a, int m, const int *__restrict__ job_off,
+                                                        const int *__restrict__ total_jobs)
+{
+    constexpr int DD = D > 0 ? D : kMaxDim;
+    constexpr int kTileQ = tile_q(DD);
+    __shared__ float qs[8][kTileQ * (DD + 1)];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float *q = qs[wib];
+    const int d = D > 0 ? D : a.d;
+    const int TJ = *total_jobs;
+    const int n = a.n;
+    unsigned long long n_ev = 0, n_re = 0;
+    for (int job = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; job < TJ; job += (gridDim.x * blockDim.x) >> 5) {
+        int j = find_job_pair(job_off, m, job);
+        int P = a.big[j].x, Q = a.big[j].y;
+        int sp = nsize(a, P), sq = nsize(a, Q);
+        int A = sp >= sq ? P : Q, B = sp >= sq ? Q : P;   // A: larger side on the lanes
+        int sa = max(sp, sq), sb = min(sp, sq);
+        int nbq = (sb + kTileQ - 1) / kTileQ;
+        int r = job - job_off[j];
+        int ta = r / nbq, tb = r % nbq;
+        int a0 = a.begin[A] + ta * kTileA, a1 = min(a0 + kTileA, a.begin[A] + sa);
+        int b0 = a.begin[B] + tb * kTileQ, b1 = min(b0 + kTileQ, a.begin[B] + sb);
+        int nb = b1 - b0;
+        __syncwarp();
+        // stage the B chunk: q[jj*(DD+1) + k], last slot = cd (HDB)
+        for (int jj = lane; jj < nb; jj += 32) {
+#pragma unroll
+            for (int k = 0; k < DD; ++k)
+                if (D > 0 || k < d) q[jj * (DD + 1) + k] = a.x32[(size_t)k * n + b0 + jj];
+            q[jj * (DD + 1) + DD] = HDB ? a.cd32[b0 + jj] : 0.f;
+        }
+        __syncwarp();
+        float ax[kItems][DD];
+        float acd[kItems];
+        bool av[kItems];
+#pragma unroll
+        for (int it = 0; it < kItems; ++it) {
+            int i = a0 + lane + 32 * it;
+            av[it] = i < a1;
+            int ii = av[it] ? i : a0;
+#pragma unroll
+            for (int k = 0; k < DD; ++k)
+                if (D > 0 || k < d) ax[it][k] = a.x32[(size_t)k * n + ii];
+            acd[it] = HDB ? a.cd32[ii] : 0.f;
+        }
+        KMin best{~0ull, ~0ull};
+        if (!FP64) {
+            float mn[kItems];
+#pragma unroll
+            for (int it = 0; it < kItems; ++it) mn[it] = INFINITY;
+            for (int jj = 0; jj < nb; ++jj) {
+                const float *qq = q + jj * (DD + 1);
+                float qv[DD];
+#pragma unroll
+                for (int k = 0; k < DD; ++k)
+                    if (D > 0 || k < d) qv[k] = qq[k];
+#pragma unroll
+                for (int it = 0; it < kItems; ++it) {
+                    float s = 0.f;
+#pragma unroll
+                    for (int k = 0; k < DD; ++k) {
+                        if (D > 0 || k < d) {
+                            float t = ax[it][k] - qv[k];
+                            s = fmaf(t, t, s);
+                        }
+                    }
+                    if (HDB) s = fmaxf(s, fmaxf(acd[it], qq[DD]));
+                    mn[it] = fminf(mn[it], s);
+                }
+            }
+            float wmn = INFINITY;
+#pragma unroll
+            for (int it = 0; it < kItems; ++it) if (av[it]) wmn = fminf(wmn, mn[it]);
+            for (int o = 16; o; o >>= 1) wmn = fminf(wmn, __shfl_xor_sync(0xffffffffu, wmn, o));
+            float T = screen_threshold(wmn, a.eta);
+            int nre = 0;
+#pragma unroll
+            for (int it = 0; it < kItems; ++it) {
+                if (!av[it] || mn[it] > T) continue;
+                int i = a0 + lane + 32 * it;
+                for (int jj = 0; jj < nb; ++jj) {
+                    const float *qq = q + jj * (DD + 1);
+                    float s = 0.f;
+#pragma unroll
+                    for (int k = 0; k < DD; ++k) {
+                        if (D > 0 || k < d) {
+                            float t = ax[it][k] - qq[k];
+                            s = fmaf(t, t, s);
+                        }
+                    }
+                    if (HDB) s = fmaxf(s, fmaxf(acd[it], qq[DD]));
+                    if (s <= T) {
+                        kmin_update(best, exact_w2(a, i, b0 + jj, s), a.pid[i], a.pid[b0 + jj]);
+                        ++nre;
+                    }
+                }
+            }
+            for (int o = 16; o; o >>= 1) nre += __shfl_xor_sync(0xffffffffu, nre, o);
+            n_re += (unsigned long long)nre;
+        } else {
+#pragma unroll
+            for (int it = 0; it < kItems; ++it) {
+                if (!av[it]) continue;
+                int i = a0 + lane + 32 * it;
+                for (int jj = 0; jj < nb; ++jj) {
+                    double w = dist64(a.x64, n, d, i, b0 + jj);
+                    if (HDB) w = fmax(w, fmax(a.cd64[i], a.cd64[b0 + jj]));
+                    kmin_update(best, w, a.pid[i], a.pid[b0 + jj]);
+                }
+            }
+        }
+        // warp K-minimum
+        for (int o = 16; o; o >>= 1) {
+            unsigned long long oh = __shfl_xor_sync(0xffffffffu, best.hi, o);
+            unsigned long long ol = __shfl_xor_sync(0xffffffffu, best.lo, o);
+            if (oh < best.hi || (oh == best.hi && ol < best.lo)) { best.hi = oh; best.lo = ol; }
+        }
+        n_ev += (unsigned long long)((a1 - a0) * nb);
+        bool has = lane == 0 && in_range(a, best);
+        int slot = 0;
+        if (has) slot = atomicAdd(a.edge_count, 1);
+        if (has) {
+            if (slot < a.edge_cap) {
+                EdgeK e;
+                e.hi = best.hi;
+                e.lo = best.lo;
+                a.edges[slot] = e;
+            } else {
+                atomicOr(a.overflow, 2u);
+            }
+        }
+    }
+    if (lane == 0 && n_ev) {
+        atomicAdd(a.stat + 1, n_ev);
+        atomicAdd(a.stat + 3, n_ev);
+        atomicAdd(a.stat + 2, n_re);
+    }
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------- host side
+
+void launch_comp_labels(const Tree &T, const Points &P, int *uf, cudaStream_t st)
+{
+    launch(uf_flatten_kernel, grid_for(P.n, 256), 256, 0, st, uf, P.n);
+    cudaMemsetAsync(T.arrive, 0, sizeof(int) * T.N, st);
+    launch(comp_labels_kernel, grid_for(T.N, 256), 256, 0, st, T.N, T.left, T.right, T.parent, T.begin, P.pid, uf,
+                                                         T.comp, T.arrive);
+}
+
+// Runs one FindPair traversal to exhaustion.  Returns 0, or WM_ENOMEM-like codes; *overflow_out
+// receives the overflow bits (frontier 1, edges 2, big pairs 4).
+int run_traversal(int mode, TravArgs &a, int2 *fa, int2 *fb, int *counters, cudaStream_t st, int *pinned,
+                  unsigned *overflow_out, int *levels_out)
+{
+    cudaMemsetAsync(counters, 0, 3 * sizeof(int), st);
+    launch(frontier_init_kernel, grid_for(a.N, 256), 256, 0, st, a, mode, fa, counters + 0);
+    int level = 0;
+    const int grid = 152 * 8;
+    while (true) {
+        for (int b = 0; b < 6; ++b, ++level) {
+            int2 *in = (level & 1) ? fb : fa, *out = (level & 1) ? fa : fb;
+            int *cin = counters + (level % 3), *cout = counters + ((level + 1) % 3), *cz = counters + ((level + 2) % 3);
+            if (mode == 0)
+                launch(findpair_level_kernel<0>, grid, 256, 0, st, a, in, cin, out, cout, cz);
+            else
+                launch(findpair_level_kernel<1>, grid, 256, 0, st, a, in, cin, out, cout, cz);
+        }
+        cudaMemcpyAsync(pinned, counters + (level % 3), sizeof(int), cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(pinned + 1, a.overflow, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;
+        if (pinned[1]) { *overflow_out = (unsigned)pinned[1]; return 0; }
+        if (pinned[0] == 0) break;
+        if (level > 100000) return WM_EINTERNAL;
+    }
+    *overflow_out = 0;
+    if (levels_out) *levels_out = level;
+    return 0;
+}
+
+// BCCP tile kernel over the queued big pairs (m of them, count known on host).
+int run_bccp_tiles(TravArgs &a, int m, int *jobs, int *total, cudaStream_t st, Arena &ar, bool hdb, bool fp64)
+{
+    if (m <= 0) return 0;
+    int dd = (a.d == 2 || a.d == 3 || a.d == 5 || a.d == 7) ? a.d : kMaxDim;
+    launch(tile_jobs_kernel, grid_for(m, 256, 1 << 20), 256, 0, st, a, m, tile_q(dd), jobs);
+    int rc = scan_exclusive_i32(jobs, jobs, m, total, st, ar);
+    if (rc) return rc;
+    const int grid = 152 * 4;
+#define WM_TILE(DV)                                                                                     \
+    do {                                                                                                \
+        if (fp64) {                                                                                     \
+            if (hdb) launch(bccp_tile_kernel<DV, true, true>, grid, 256, 0, st, a, m, jobs, total);          \
+            else launch(bccp_tile_kernel<DV, false, true>, grid, 256, 0, st, a, m, jobs, total);             \
+        } else {                                                                                        \
+            if (hdb) launch(bccp_tile_kernel<DV, true, false>, grid, 256, 0, st, a, m, jobs, total);         \
+            else launch(bccp_tile_kernel<DV, false, false>, grid, 256, 0, st, a, m, jobs, total);            \
+        }                                                                                               \
+    } while (0)
+    switch (a.d) {
+    case 2: WM_TILE(2); break;
+    case 3: WM_TILE(3); break;
+    case 5: WM_TILE(5); break;
+    case 7: WM_TILE(7); break;
+    default: WM_TILE(0); break;
+    }
+#undef WM_TILE
+    return 0;
+}
+
+}  // namespace wm

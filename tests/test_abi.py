@@ -1,0 +1,51 @@
+"""The C-ABI library builds, loads and exports every symbol that include/wspdmst.h declares.
+
+No compute call is made here (the container has no GPU); wm_strerror / wm_version /
+wm_query_footprint touch no device.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2104_01126_gb300 as wm
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "wspdmst.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(wm_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_entry_points():
+    names = _declared()
+    for required in ["wm_emst", "wm_hdbscan", "wm_single_linkage", "wm_query_footprint", "wm_strerror",
+                     "wm_last_error_detail", "wm_release_cache", "wm_version"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(wm.build.build())
+    missing = [s for s in _declared() if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_record_layouts_match_header():
+    assert ctypes.sizeof(wm._Edge) == 16
+    assert ctypes.sizeof(wm._DNode) == 24
+    assert wm._Opts.workspace.offset == 16
+
+
+def test_error_strings_and_footprint_without_gpu():
+    lib = wm.load()
+    assert lib.wm_strerror(0) == b"success"
+    assert lib.wm_strerror(-1) == b"invalid argument"
+    assert b"sm_103a" in lib.wm_version()
+    assert wm.query_footprint(10_000, 2) > 0
+    assert wm.query_footprint(1_000_000, 3, 10) > wm.query_footprint(1_000_000, 3, 0)
+    b = ctypes.c_size_t(0)
+    assert lib.wm_query_footprint(0, 2, 0, ctypes.byref(b)) == -1
+    assert lib.wm_query_footprint(10, 17, 0, ctypes.byref(b)) == -1
