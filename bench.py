@@ -186,7 +186,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="hdbscan-gmm-1m-3d", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--cpu-sample", type=int, default=60_000)
+    ap.add_argument("--cpu-sample", type=int, default=120_000)
     ap.add_argument("--ref-sample", type=int, default=40_000)
     ap.add_argument("--ref-warmup", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
