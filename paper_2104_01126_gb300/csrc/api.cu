@@ -165,7 +165,7 @@ struct Call {
     int *pin = nullptr;
     wm_stats stats{};
     int precision = WM_PREC_FP32_SCREEN;
-    std::vector<cudaEvent_t> evs;
+    bool timing = true;   // per-kernel CUDA-event timing into stats
     double event_ms(cudaEvent_t a, cudaEvent_t b)
     {
         float ms = 0.f;
@@ -267,18 +267,22 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         a.rho_lo = rho_lo;
         a.rho_hi = rho_hi;
         WM_CK(cudaMemsetAsync(cnts + 4, 0, 2 * sizeof(int), st));
-        cudaEvent_t g0, g1;
-        cudaEventCreate(&g0);
-        cudaEventCreate(&g1);
-        cudaEventRecord(g0, st);
+        cudaEvent_t g0 = nullptr, g1 = nullptr;
+        if (C.timing) {
+            cudaEventCreate(&g0);
+            cudaEventCreate(&g1);
+            cudaEventRecord(g0, st);
+        }
         int glev = 0;
         WM_TRY(run_traversal(1, a, fa, fb, cnts, st, C.pin, &ob, &glev));
-        cudaEventRecord(g1, st);
-        cudaEventSynchronize(g1);
-        C.stats.ms_getpairs += C.event_ms(g0, g1);
+        if (C.timing) {
+            cudaEventRecord(g1, st);
+            cudaEventSynchronize(g1);
+            C.stats.ms_getpairs += C.event_ms(g0, g1);
+            cudaEventDestroy(g0);
+            cudaEventDestroy(g1);
+        }
         C.stats.getpairs_launches += glev;
-        cudaEventDestroy(g0);
-        cudaEventDestroy(g1);
         if (ob) { *overflow_bits = ob; return 0; }
         WM_CK(cudaMemcpyAsync(C.pin, cnts + 4, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         WM_CK(cudaStreamSynchronize(st));
@@ -286,23 +290,27 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         C.stats.ms_wspd += tw.ms();
         // ---- BCCP tiles over the queued larger pairs
         Timer tb;
-        cudaEvent_t e0, e1;
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
-        cudaEventRecord(e0, st);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (C.timing) {
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            cudaEventRecord(e0, st);
+        }
         WM_TRY(run_bccp_tiles(a, mbig, jobs, cnts + 6, st, ar, hdb != nullptr, a.fp64 != 0));
-        cudaEventRecord(e1, st);
+        if (C.timing) cudaEventRecord(e1, st);
         WM_CK(cudaMemcpyAsync(C.pin, cnts + 5, sizeof(int), cudaMemcpyDeviceToHost, st));
         WM_CK(cudaMemcpyAsync(C.pin + 1, ovf, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
         WM_CK(cudaStreamSynchronize(st));
         if (mbig > 0) {
-            double ms = C.event_ms(e0, e1);
+            double ms = C.timing ? C.event_ms(e0, e1) : tb.ms();
             C.stats.ms_bccp += ms;
             C.stats.ms_tile_kernel += ms;
             C.stats.tile_launches += 1;
         }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
+        if (C.timing) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+        }
         if (C.pin[1]) { *overflow_bits = (unsigned)C.pin[1]; return 0; }
         int m = C.pin[0];
         // ---- HDBSCAN*: repair edges of this weight range join the batch
@@ -335,7 +343,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
             int mf = C.pin[0];
             C.stats.candidate_edges += mf;
             EdgeK *sorted = filt;
-            WM_TRY(radix_sort_edges(filt, tmp, mf, st, ar, &sorted));
+            WM_TRY(radix_sort_edges(filt, tmp, mf, st, ar, &sorted, C.pin + 4096));
             WM_TRY(batch_kruskal(sorted, mf, uf, R, E_out, nE, &accepted, ar, st, C.pin));
         }
         C.stats.ms_kruskal += tk.ms();
@@ -583,7 +591,7 @@ static int sl_body(Call &C, void *vctx, const Caps &, unsigned *ovf)
         if (!bad) return WM_ENOMEM;
         WM_TRY(edges_from_wm(src, n, E, bad, C.st));
         EdgeK *sorted = E;
-        WM_TRY(radix_sort_edges(E, tmp, n - 1, C.st, C.ar, &sorted));
+        WM_TRY(radix_sort_edges(E, tmp, n - 1, C.st, C.ar, &sorted, C.pin + 4096));
         WM_CK(cudaMemcpyAsync(C.pin, bad, sizeof(int), cudaMemcpyDeviceToHost, C.st));
         WM_CK(cudaStreamSynchronize(C.st));
         if (C.pin[0]) { set_detail("tree edge with an endpoint outside [0, n) or a bad weight%s", ""); return WM_EINVAL; }

@@ -497,7 +497,7 @@ int core_distances(Points &P, Tree &T, int min_pts, bool fp64, HdbState &H, Aren
     EdgeK *tmp = ar.get<EdgeK>((size_t)nrep + 1);
     if (!tmp) return WM_ENOMEM;
     EdgeK *sorted = rep;
-    rc = radix_sort_edges(rep, tmp, nrep, st, ar, &sorted);
+    rc = radix_sort_edges(rep, tmp, nrep, st, ar, &sorted, pin + 4096);
     if (rc) return rc;
     if (sorted != rep) cudaMemcpyAsync(rep, sorted, sizeof(EdgeK) * nrep, cudaMemcpyDeviceToDevice, st);
     H.rep = rep;

@@ -199,28 +199,25 @@ __global__ void __launch_bounds__(kRsBlock) rs_pass_scatter(const EdgeK *__restr
 
 // Sorts m keys ascending as 128-bit unsigned integers (stable LSD, 8-bit digits, byte
 // positions on which all keys agree are skipped).  The result is in *result (keys or tmp).
-int radix_sort_edges(EdgeK *keys, EdgeK *tmp, int m, cudaStream_t st, Arena &ar, EdgeK **result)
+int radix_sort_edges(EdgeK *keys, EdgeK *tmp, int m, cudaStream_t st, Arena &ar, EdgeK **result, void *host_scratch)
 {
     *result = keys;
     if (m <= 1) return 0;
     size_t mark = ar.off;
     unsigned *ghist = ar.get<unsigned>(16 * 256);
-    unsigned *hhist = nullptr;
+    unsigned *hhist = (unsigned *)host_scratch;
     if (!ghist) return WM_ENOMEM;
     cudaMemsetAsync(ghist, 0, sizeof(unsigned) * 16 * 256, st);
     launch(rs_hist_all, grid_for(m, 256, 152 * 4), 256, 0, st, keys, m, ghist);
-    cudaMallocHost((void **)&hhist, sizeof(unsigned) * 16 * 256);
-    if (!hhist) { ar.off = mark; return WM_ENOMEM; }
     cudaMemcpyAsync(hhist, ghist, sizeof(unsigned) * 16 * 256, cudaMemcpyDeviceToHost, st);
     cudaError_t ce = cudaStreamSynchronize(st);
-    if (ce != cudaSuccess) { cudaFreeHost(hhist); ar.off = mark; return WM_ECUDA; }
+    if (ce != cudaSuccess) { ar.off = mark; return WM_ECUDA; }
     bool need[16];
     for (int b = 0; b < 16; ++b) {
         need[b] = true;
         for (int g = 0; g < 256; ++g)
             if (hhist[b * 256 + g] == (unsigned)m) { need[b] = false; break; }
     }
-    cudaFreeHost(hhist);
     int G = (m + 2047) / 2048;
     if (G > 1024) G = 1024;
     int chunk = (m + G - 1) / G;
