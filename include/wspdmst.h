@@ -168,6 +168,37 @@ int wm_single_linkage(const wm_edge *tree, int64_t n, int32_t start, wm_dnode *o
                       int32_t *out_order, double *out_reach, const wm_opts *opts);
 
 /*
+ * wm_emst_noalloc -- wm_emst for callers that cannot allocate.  The paper has no counterpart:
+ * this entry point exists for integrating the library, not for the method.
+ *
+ * Some callers must not allocate device memory at the moment they need an EMST: a host
+ * program (a database or inference server, say) that reserved nearly all device memory up
+ * front for its own pool, where a library cudaMalloc would fail or fragment that pool; a
+ * latency-critical loop that cannot afford cudaMalloc's implicit device synchronisation and
+ * unbounded latency; a plugin whose host hands it buffers and forbids it to allocate.  This
+ * variant computes exactly what wm_emst computes (same K-minimum tree, same order, same
+ * rounding) with all of its device scratch taken from one array of WM_NOALLOC_SCRATCH_BYTES
+ * bytes that the library declares statically in device memory.  It calls no cudaMalloc,
+ * cudaFree, cudaMallocHost or other allocating routine and creates no CUDA events.  The caller
+ * still owns the input and the outputs, which may be host or device memory as for wm_emst.
+ *
+ *   Limits   1 <= n <= WM_NOALLOC_MAX_POINTS, 1 <= d <= 16; a larger n returns WM_EINVAL.  An
+ *            input whose pair traversal needs more scratch than the array holds returns
+ *            WM_ENOMEM with a message (wm_emst, which allocates, still handles it).
+ *   Memory   every GPU on which the library is loaded holds the array until the process exits.
+ *   Set-up   the first call on a device, with that device current, looks up the array's device
+ *            address once (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   Sharing  all calls on a device use the same array, which keeps the last call's contents (the
+ *            call initialises everything it reads).  Calls whose GPU work overlapped would race
+ *            on it; within one process this entry point prevents that by holding a per-device
+ *            lock for the whole call and returning only after its GPU work has completed.
+ */
+#define WM_NOALLOC_MAX_POINTS 32768
+#define WM_NOALLOC_SCRATCH_BYTES (64u << 20)
+int wm_emst_noalloc(const void *pts, int64_t n, int32_t d, int32_t dtype, int32_t layout,
+                    wm_edge *out_edges, double *out_total_weight, const wm_opts *opts);
+
+/*
  * wm_query_footprint -- an upper estimate of the device workspace, in bytes, that a call with
  * these sizes needs (min_pts = 0 for EMST).  Data-dependent buffers (WSPD traversal frontiers,
  * candidate edges) are estimated; a call whose data needs more returns WM_ENOMEM when a

@@ -140,6 +140,8 @@ def load(build_if_missing: bool = True):
         lib.wm_last_error_detail.restype = ctypes.c_char_p
         lib.wm_version.restype = ctypes.c_char_p
         lib.wm_kernel_launch_count.restype = ctypes.c_int64
+        lib.wm_emst_noalloc.restype = ctypes.c_int
+        lib.wm_emst_noalloc.argtypes = [P, i64, i32, i32, i32, P, P, ctypes.POINTER(_Opts)]
         _lib = lib
         return lib
 
@@ -262,6 +264,26 @@ def emst(points, precision: str = "fp32", stream=None, return_stats: bool = Fals
         out["stats"] = Stats._from(st)
     del keep
     return out
+
+
+def emst_noalloc(points, precision: str = "fp32", stream=None):
+    """wm_emst_noalloc: the EMST with all device scratch taken from the library's static array
+    (n <= 32768), for callers that must not allocate device memory.  Outputs are allocated here
+    by the caller side of the binding, as the C entry point expects caller-owned outputs."""
+    lib = load()
+    keep, ptr, n, d, code, on_dev, dev = _points(points)
+    m = max(n - 1, 0)
+    buf, bptr = _out_buffer(16 * m, dev)
+    total = ctypes.c_double(0.0)
+    st = _Stats()
+    if stream is None and on_dev:
+        stream = _current_stream(dev)
+    o = _opts(precision, stream, st)
+    rc = lib.wm_emst_noalloc(ptr, n, d, code, WM_AOS, bptr if m > 0 else None, ctypes.byref(total), ctypes.byref(o))
+    _check(rc, "wm_emst_noalloc")
+    u, v, w = _edges_result(buf, m, dev)
+    del keep
+    return {"u": u, "v": v, "w": w, "total": total.value}
 
 
 def hdbscan(points, min_pts: int = 10, start: int = 0, precision: str = "fp32", stream=None,

@@ -692,3 +692,86 @@ int64_t wm_kernel_launch_count(void) { return (int64_t)g_launch_count.load(); }
 const char *wm_version(void) { return "wspdmst 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+// =========================================================== no-allocation EMST entry point
+// Device scratch for wm_emst_noalloc: one file-scope array per device, sized for
+// WM_NOALLOC_MAX_POINTS points of up to 16 dimensions.  Host code must not use the symbol
+// itself as a device address: its device address is looked up once per device below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[WM_NOALLOC_SCRATCH_BYTES];
+
+namespace wm {
+
+struct NoAllocDevice {
+    std::mutex mu;
+    void *scratch = nullptr;   // device address of g_noalloc_scratch on this device
+};
+static NoAllocDevice g_noalloc_dev[64];
+
+// host-side readback buffer of the no-allocation path (ordinary host memory, one per thread)
+static thread_local int g_noalloc_host[16384];
+
+}  // namespace wm
+
+extern "C" int wm_emst_noalloc(const void *pts, int64_t n, int32_t d, int32_t dtype, int32_t layout,
+                               wm_edge *out_edges, double *out_total_weight, const wm_opts *opts)
+{
+    using namespace wm;
+    g_detail.clear();
+    if (!pts || n < 1 || d < 1 || d > kMaxDim || (dtype != WM_F32 && dtype != WM_F64) ||
+        (layout != WM_AOS && layout != WM_SOA) || (n > 1 && !out_edges && !out_total_weight)) {
+        set_detail("invalid argument to wm_emst_noalloc%s (n=%lld)", "", (long long)n);
+        return WM_EINVAL;
+    }
+    if (n > WM_NOALLOC_MAX_POINTS) {
+        set_detail("wm_emst_noalloc: n = %s%lld exceeds WM_NOALLOC_MAX_POINTS (32768); use wm_emst", "",
+                   (long long)n);
+        return WM_EINVAL;
+    }
+    const int precision = opts ? opts->precision : WM_PREC_FP32_SCREEN;
+    if (precision != WM_PREC_FP32_SCREEN && precision != WM_PREC_FP64) {
+        set_detail("bad precision%s %lld", "", precision);
+        return WM_EINVAL;
+    }
+    Timer total;
+    int dev = 0;
+    WM_CK(cudaGetDevice(&dev));
+    NoAllocDevice &nd = g_noalloc_dev[dev & 63];
+    std::lock_guard<std::mutex> lk(nd.mu);
+    if (!nd.scratch) {
+        // once per device, with that device current
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            set_detail("wm_emst_noalloc: cudaGetSymbolAddress failed: %s%lld", cudaGetErrorString(e), 0);
+            return WM_ECUDA;
+        }
+        nd.scratch = p;
+    }
+    Call C;
+    C.st = opts ? (cudaStream_t)opts->stream : nullptr;
+    C.precision = precision;
+    C.timing = false;
+    C.pin = g_noalloc_host;
+    C.ar.base = (char *)nd.scratch;
+    C.ar.cap = WM_NOALLOC_SCRATCH_BYTES;
+    Caps caps;
+    caps.frontier = 16 * n + 4096;
+    caps.big = 2 * n + 1024;
+    caps.edges = 8 * n + 4096;
+    EmstCtx c{pts, n, d, dtype, layout, out_edges, out_total_weight};
+    unsigned ovf = 0;
+    int rc = emst_body(C, &c, caps, &ovf);
+    if (rc == 0 && (ovf || C.ar.failed)) rc = WM_ENOMEM;
+    if (rc == WM_ENOMEM)
+        set_detail("wm_emst_noalloc: this input needs more than the %s%lld-byte static scratch; use wm_emst", "",
+                   (long long)WM_NOALLOC_SCRATCH_BYTES);
+    cudaError_t le = cudaGetLastError();
+    if (rc == 0 && le != cudaSuccess) {
+        set_detail("CUDA error %s%lld", cudaGetErrorString(le), 0);
+        rc = WM_ECUDA;
+    }
+    C.stats.workspace_bytes_used = C.ar.peak;
+    C.stats.ms_total = total.ms();
+    if (opts && opts->stats) *opts->stats = C.stats;
+    return rc;
+}
