@@ -117,6 +117,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(ms_local: float, dist, device=None) -> float:
+    """The step time the job is charged: the maximum over ranks (replicas run independently)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms_local
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(points_per_rank: int, world_size: int, ms_max: float) -> float:
+    """Mpoints/s of the whole job: points processed by all ranks over the max-over-ranks time."""
+    return points_per_rank * world_size / (ms_max * 1e-3) / 1e6
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -243,12 +258,8 @@ def main():
     if dist:
         dist.barrier()
     ms = sum(times) / len(times)
-    ms_max = ms
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = n * ws / (ms_max * 1e-3) / 1e6
+    ms_max = max_over_ranks(ms, dist, device="cuda")
+    value = whole_job_value(n, ws, ms_max)
 
     # ---- roofline of the dominant kernel with known algorithmic work (FP32 pipe)
     s0 = stats[-1]
@@ -286,17 +297,13 @@ def main():
             step(xh)
             torch.cuda.synchronize()
             et.append(time.perf_counter() - t0)
-        e_ms = sum(et) / len(et) * 1e3
-        if dist:
-            t = torch.tensor([e_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
+        e_ms = max_over_ranks(sum(et) / len(et) * 1e3, dist, device="cuda")
         h2d = n * d * x.dtype.itemsize
         if w["problem"] == "hdbscan":
             d2h = (n - 1) * 16 + n * 8 + (n - 1) * 24 + n * 4 + n * 8
         else:
             d2h = (n - 1) * 16 + 8
-        e2e = {"value": n * ws / (e_ms * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": e_ms,
+        e2e = {"value": whole_job_value(n, ws, e_ms), "unit": "Mpoints/s", "ms_per_step": e_ms,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     cpu = None

@@ -113,6 +113,8 @@ typedef struct {
     int64_t tile_launches;         /* number of BCCP tile kernel launches               */
     double ms_getpairs;            /* CUDA-event time summed over GetPairs level launches */
     int64_t getpairs_launches;     /* number of GetPairs level launches                 */
+    int64_t getpairs_visits;       /* node pairs examined by the GetPairs traversals     */
+    int64_t getrho_visits;         /* node pairs examined by the GetRho traversals       */
 } wm_stats;
 
 /* Options.  A zero-initialised struct (or NULL) gives the defaults. */

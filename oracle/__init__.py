@@ -51,6 +51,10 @@ def _load():
             lib.wmo_sqdist.argtypes = [P, i32, i64, i64]
             lib.wmo_core_dist2.restype = ctypes.c_int
             lib.wmo_core_dist2.argtypes = [P, i64, i32, i32, P]
+            lib.wmo_core_dist2_subset.restype = ctypes.c_int
+            lib.wmo_core_dist2_subset.argtypes = [P, i64, i32, i32, P, i64, P]
+            lib.wmo_nearest_edge.restype = ctypes.c_int
+            lib.wmo_nearest_edge.argtypes = [P, i64, i32, i64, P, P]
             lib.wmo_prim.restype = ctypes.c_int
             lib.wmo_prim.argtypes = [P, i64, i32, P, P, P, P, P]
             lib.wmo_sort_edges.restype = ctypes.c_int
@@ -99,6 +103,26 @@ def core_dist2(x, min_pts: int) -> np.ndarray:
     out = np.empty(n, dtype=np.float64)
     _check(_load().wmo_core_dist2(_p(x), n, d, int(min_pts), _p(out)), "core_dist2")
     return out
+
+
+def core_dist2_subset(x, min_pts: int, idx) -> np.ndarray:
+    """Squared core distances of the points idx only (brute force over all points)."""
+    x = _pts(x)
+    n, d = x.shape
+    q = np.ascontiguousarray(idx, dtype=np.int64)
+    out = np.empty(len(q), dtype=np.float64)
+    _check(_load().wmo_core_dist2_subset(_p(x), n, d, int(min_pts), _p(q), len(q), _p(out)), "core_dist2_subset")
+    return out
+
+
+def nearest_edge(x, p: int):
+    """The K-minimum EMST edge incident to point p: (other endpoint, w2)."""
+    x = _pts(x)
+    n, d = x.shape
+    other = np.zeros(1, dtype=np.int32)
+    w2 = np.zeros(1, dtype=np.float64)
+    _check(_load().wmo_nearest_edge(_p(x), n, d, int(p), _p(other), _p(w2)), "nearest_edge")
+    return int(other[0]), float(w2[0])
 
 
 def prim_complete(x, cd2=None):

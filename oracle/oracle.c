@@ -101,6 +101,56 @@ int wmo_core_dist2(const double *x, int64_t n, int32_t d, int32_t minpts, double
     return err;
 }
 
+/* The same definition for m selected query points q[0..m) only (brute force over all n). */
+int wmo_core_dist2_subset(const double *x, int64_t n, int32_t d, int32_t minpts, const int64_t *q, int64_t m,
+                          double *cd2)
+{
+    if (minpts < 1 || (int64_t)minpts > n) return -1;
+    int err = 0;
+#pragma omp parallel
+    {
+        double *best = (double *)malloc(sizeof(double) * (size_t)minpts);
+        if (!best) {
+#pragma omp atomic write
+            err = -2;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t t = 0; t < m; ++t) {
+            if (!best) continue;
+            int64_t p = q[t];
+            int32_t cnt = 0;
+            for (int64_t r = 0; r < n; ++r) {
+                double v = (r == p) ? 0.0 : wmo_sqdist(x, d, p, r);
+                if (cnt < minpts || v < best[minpts - 1]) {
+                    int32_t j = cnt < minpts ? cnt++ : minpts - 1;
+                    while (j > 0 && best[j - 1] > v) { best[j] = best[j - 1]; --j; }
+                    best[j] = v;
+                }
+            }
+            cd2[t] = best[minpts - 1];
+        }
+        free(best);
+    }
+    return err;
+}
+
+/* The K-minimum edge from point p to any other point (EMST weights), brute force. */
+int wmo_nearest_edge(const double *x, int64_t n, int32_t d, int64_t p, int32_t *other, double *w2)
+{
+    double bw = INFINITY;
+    int64_t bq = -1;
+    for (int64_t r = 0; r < n; ++r) {
+        if (r == p) continue;
+        double v = wmo_sqdist(x, d, p, r);
+        int32_t a = (int32_t)(p < r ? p : r), b = (int32_t)(p < r ? r : p);
+        int32_t ca = (int32_t)(p < bq ? p : bq), cb = (int32_t)(p < bq ? bq : p);
+        if (bq < 0 || key_less(v, a, b, bw, ca, cb)) { bw = v; bq = r; }
+    }
+    *other = (int32_t)bq;
+    *w2 = bw;
+    return bq < 0 ? -1 : 0;
+}
+
 /* --------------------------------------------------- MST of the complete graph (Sec. 2.1) */
 
 /*

@@ -56,7 +56,8 @@ class _Stats(ctypes.Structure):
                 ("max_rel_screen_err", ctypes.c_double), ("tie_overflow", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("ms_knn_kernel", ctypes.c_double),
                 ("ms_tile_kernel", ctypes.c_double), ("tile_launches", ctypes.c_int64),
-                ("ms_getpairs", ctypes.c_double), ("getpairs_launches", ctypes.c_int64)]
+                ("ms_getpairs", ctypes.c_double), ("getpairs_launches", ctypes.c_int64),
+                ("getpairs_visits", ctypes.c_int64), ("getrho_visits", ctypes.c_int64)]
 
 
 class _Opts(ctypes.Structure):
@@ -99,6 +100,8 @@ class Stats:
     tile_launches: int = 0
     ms_getpairs: float = 0.0
     getpairs_launches: int = 0
+    getpairs_visits: int = 0
+    getrho_visits: int = 0
 
     @classmethod
     def _from(cls, s: _Stats) -> "Stats":

@@ -52,7 +52,7 @@ struct DevCache {
 static DevCache g_cache[64];
 
 struct Caps {
-    long long frontier, big, edges;
+    long long frontier, big, edges, pairs;
 };
 
 static size_t estimate_bytes(long long n, int d, int min_pts, const Caps &c)
@@ -65,7 +65,8 @@ static size_t estimate_bytes(long long n, int d, int min_pts, const Caps &c)
     b += (size_t)N * (8 * d + 48);          // tree arrays (+ build scratch counters)
     b += (size_t)n * 8;                     // small lists
     b += (size_t)c.frontier * 8 * 2;
-    b += (size_t)c.big * 12;
+    b += (size_t)c.big * 12 + (size_t)c.pairs * 8 * 3;
+    b += (size_t)N * (32 + 8 * (d <= 4 ? 4 : d <= 8 ? 8 : 16));   // packed node records
     b += (size_t)c.edges * 16 * 3 + (size_t)c.edges * 24;   // batch, filtered, sort tmp, kruskal
     b += (size_t)n * 16 * 2;                // output tree + conversion
     if (min_pts > 0) {
@@ -83,6 +84,7 @@ static Caps default_caps(long long n, int min_pts)
     c.frontier = 8 * n + (1 << 20);
     c.big = 2 * n + (1 << 18);
     c.edges = 4 * n + (1 << 20) + (min_pts > 0 ? (long long)n * (min_pts + 16) : 0);
+    c.pairs = 4 * n + (1 << 20);
     return c;
 }
 
@@ -217,13 +219,23 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     size_t mark = ar.off;
     int2 *fa = ar.get<int2>(caps.frontier), *fb = ar.get<int2>(caps.frontier);
     int2 *big = ar.get<int2>(caps.big);
+    int2 *plist0 = ar.get<int2>(caps.pairs), *plist1 = ar.get<int2>(caps.pairs), *plist2 = ar.get<int2>(caps.pairs);
     int *jobs = ar.get<int>(caps.big + 1);
+    const int dp = P.d <= 4 ? 4 : P.d <= 8 ? 8 : 16;
+    int4 *links = ar.get<int4>(T.N);
+    float4 *meta = ar.get<float4>(T.N);
+    float *box = ar.get<float>((size_t)T.N * 2 * dp);
     EdgeK *batch = ar.get<EdgeK>(caps.edges), *filt = ar.get<EdgeK>(caps.edges), *tmp = ar.get<EdgeK>(caps.edges);
     int *cnts = ar.get<int>(16);
     double *rho = ar.get<double>(2);
     unsigned *ovf = ar.get<unsigned>(2);
     unsigned long long *stat = ar.get<unsigned long long>(8);
     if (ar.failed) return WM_ENOMEM;
+    {
+        Tree T2 = T;
+        if (hdb) { T2.cdmin = hdb->cdmin; T2.cdmax = hdb->cdmax; }
+        pack_nodes(T2, P.d, dp, links, meta, box, st);
+    }
     WM_CK(cudaMemsetAsync(stat, 0, 8 * sizeof(unsigned long long), st));
     WM_CK(cudaMemsetAsync(ovf, 0, 2 * sizeof(unsigned), st));
 
@@ -238,7 +250,11 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         a.cdmin = hdb->cdmin; a.cdmax = hdb->cdmax; a.cd32 = hdb->cd32; a.cd64 = hdb->cd64;
     }
     a.frontier_cap = (int)caps.frontier;
-    a.big = big; a.big_count = cnts + 4; a.big_cap = (int)caps.big;
+    a.links = links; a.meta = meta; a.box = box; a.dp = dp;
+    a.list[0] = plist0; a.list[1] = plist1; a.list[2] = plist2; a.list[3] = big;
+    a.list_cap[0] = a.list_cap[1] = a.list_cap[2] = (int)caps.pairs; a.list_cap[3] = (int)caps.big;
+    a.list_count = cnts + 10;
+    a.big = big; a.big_count = cnts + 13;
     a.edges = batch; a.edge_count = cnts + 5; a.edge_cap = (int)caps.edges;
     a.overflow = ovf;
     a.stat = stat;
@@ -267,6 +283,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         a.rho_lo = rho_lo;
         a.rho_hi = rho_hi;
         WM_CK(cudaMemsetAsync(cnts + 4, 0, 2 * sizeof(int), st));
+        WM_CK(cudaMemsetAsync(cnts + 10, 0, 4 * sizeof(int), st));
         cudaEvent_t g0 = nullptr, g1 = nullptr;
         if (C.timing) {
             cudaEventCreate(&g0);
@@ -284,9 +301,12 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         }
         C.stats.getpairs_launches += glev;
         if (ob) { *overflow_bits = ob; return 0; }
-        WM_CK(cudaMemcpyAsync(C.pin, cnts + 4, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        WM_CK(cudaMemcpyAsync(C.pin, cnts + 10, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
         WM_CK(cudaStreamSynchronize(st));
-        int mbig = C.pin[0];
+        int lcounts[4] = {C.pin[0], C.pin[1], C.pin[2], C.pin[3]};
+        int mbig = lcounts[3];
+        // BCCP of the tiny / small / medium retrieved pairs
+        run_bccp_groups(a, lcounts, st);
         C.stats.ms_wspd += tw.ms();
         // ---- BCCP tiles over the queued larger pairs
         Timer tb;
@@ -359,6 +379,8 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     WM_CK(cudaStreamSynchronize(st));
     unsigned long long hs[8];
     memcpy(hs, C.pin, sizeof hs);
+    C.stats.getpairs_visits = (int64_t)hs[4];
+    C.stats.getrho_visits = (int64_t)hs[5];
     C.stats.rounds = rounds;
     C.stats.pairs_retrieved = (int64_t)hs[0];
     C.stats.bccp_evals = (int64_t)hs[1];
@@ -488,7 +510,7 @@ static int run_call(const wm_opts *opts, long long n, int d, int min_pts, Body b
         // grow whichever capacity overflowed and start over
         if (ovf & 1u) caps.frontier *= 2;
         if (ovf & 2u) caps.edges *= 2;
-        if (ovf & 4u) caps.big *= 2;
+        if (ovf & 4u) { caps.big *= 2; caps.pairs *= 2; }
         if (rc == WM_ENOMEM) { caps.frontier += caps.frontier / 2; }
         if (user_ws && ovf) { rc = WM_ENOMEM; set_detail("caller workspace too small for the WSPD frontier%s", ""); break; }
         rc = WM_ENOMEM;
@@ -754,10 +776,18 @@ extern "C" int wm_emst_noalloc(const void *pts, int64_t n, int32_t d, int32_t dt
     C.pin = g_noalloc_host;
     C.ar.base = (char *)nd.scratch;
     C.ar.cap = WM_NOALLOC_SCRATCH_BYTES;
+    // Capacities: what the fixed structures leave of the array, split between the traversal
+    // frontier (30%), the three small-pair lists (10% each), big pairs (5%) and edge batches (35%).
+    const long long N2 = 2 * n;
+    const int dp = d <= 4 ? 4 : d <= 8 ? 8 : 16;
+    long long fixed = n * d * 8 + n * d * 12 + 8 * n + N2 * (8LL * d + 40) + N2 * (32 + 8LL * dp) + 24 * n + (2 << 20);
+    long long rest = (long long)WM_NOALLOC_SCRATCH_BYTES - fixed;
+    if (rest < (4 << 20)) rest = 4 << 20;
     Caps caps;
-    caps.frontier = 16 * n + 4096;
-    caps.big = 2 * n + 1024;
-    caps.edges = 8 * n + 4096;
+    caps.frontier = rest * 30 / 100 / 16;
+    caps.pairs = rest * 10 / 100 / 8;
+    caps.big = rest * 5 / 100 / 12;
+    caps.edges = rest * 35 / 100 / 72;
     EmstCtx c{pts, n, d, dtype, layout, out_edges, out_total_weight};
     unsigned ovf = 0;
     int rc = emst_body(C, &c, caps, &ovf);

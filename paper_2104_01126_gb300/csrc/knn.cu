@@ -101,7 +101,13 @@ __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
             }
         }
         int cnt = 0;
-        V thr = (V)INFINITY;
+        V thr = (V)INFINITY;   // KL-th kept value (list full) or +inf
+        // cut: the band threshold of the current k-th value; a point screened above it can never
+        // be a candidate, and a node is skipped when its box bound exceeds cut (1 + 2^-17)
+        // (the bound is a rigorous lower bound of the true distance and a screened value is
+        // within 2^-19 of the true one, so every skipped point screens above cut as well).
+        // cut only decreases, so the final threshold T(s_k) is below every cut used.
+        V cut = (V)INFINITY;
         int sp = 0;
         if (lane == 0) stk[0] = 0;
         sp = 1;
@@ -121,7 +127,8 @@ __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
                     lb = fmaf(g, g, lb);
                 }
             }
-            bool need = valid && (cnt < KL || (V)lower_w2(lb) <= thr);
+            bool need = valid && (V)lower_w2(lb) <= cut * (V)(1.0f + 1.0f / 131072.0f) &&
+                        (cnt < KL || (V)lower_w2(lb) <= thr);
             if (!__any_sync(0xffffffffu, need)) continue;
             if (e - b <= 32) {
                 // scan the subtree's points
@@ -158,7 +165,7 @@ __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
                         }
                         s = (V)acc;
                     }
-                    if (valid && (cnt < KL || s < thr)) {
+                    if (valid && s <= cut && (cnt < KL || s < thr)) {
                         int pos = cnt < KL ? cnt : KL - 1;
                         while (pos > 0 && sv[(pos - 1) * 32 + lane] > s) {
                             sv[pos * 32 + lane] = sv[(pos - 1) * 32 + lane];
@@ -169,6 +176,10 @@ __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
                         sj[pos * 32 + lane] = b + p;
                         if (cnt < KL) ++cnt;
                         if (cnt == KL) thr = sv[(KL - 1) * 32 + lane];
+                        if (cnt >= a.k && pos < a.k) {
+                            V sk = sv[(a.k - 1) * 32 + lane];
+                            cut = FP64 ? sk : (V)knn_threshold((float)sk, a.eta);
+                        }
                     }
                 }
                 n_ev += (unsigned long long)m;

@@ -125,42 +125,6 @@ __device__ inline int warp_append(int *counter, int cnt)
     return base + x - cnt;
 }
 
-// BCCP / BCCP* of a small pair, evaluated by one thread (Sec. 3.1.2: all |A||B| distances and a
-// WriteMin; here a thread-local minimum).  Adds its evaluation and recheck counts to ev / re.
-__device__ KMin bccp_inline(const TravArgs &a, int P, int Q, unsigned long long &ev, unsigned long long &re)
-{
-    const int pb = a.begin[P], pe = a.end[P], qb = a.begin[Q], qe = a.end[Q];
-    KMin best{~0ull, ~0ull};
-    if (a.fp64) {
-        for (int i = pb; i < pe; ++i)
-            for (int j = qb; j < qe; ++j) {
-                double w = dist64(a.x64, a.n, a.d, i, j);
-                if (a.cd64) w = fmax(w, fmax(a.cd64[i], a.cd64[j]));
-                kmin_update(best, w, a.pid[i], a.pid[j]);
-            }
-    } else {
-        float smin = INFINITY;
-        for (int i = pb; i < pe; ++i)
-            for (int j = qb; j < qe; ++j) {
-                float s = dist32(a.x32, a.n, a.d, i, j);
-                if (a.cd32) s = fmaxf(s, fmaxf(a.cd32[i], a.cd32[j]));
-                smin = fminf(smin, s);
-            }
-        float T = screen_threshold(smin, a.eta);
-        for (int i = pb; i < pe; ++i)
-            for (int j = qb; j < qe; ++j) {
-                float s = dist32(a.x32, a.n, a.d, i, j);
-                if (a.cd32) s = fmaxf(s, fmaxf(a.cd32[i], a.cd32[j]));
-                if (s <= T) {
-                    kmin_update(best, exact_w2(a, i, j, s), a.pid[i], a.pid[j]);
-                    ++re;
-                }
-            }
-    }
-    ev += (unsigned long long)((pe - pb) * (qe - qb));
-    return best;
-}
-
 __device__ inline bool in_range(const TravArgs &a, const KMin &m)
 {
     double w2 = __longlong_as_double((long long)m.hi);
@@ -173,7 +137,6 @@ __device__ inline unsigned long long warp_sum_u64(unsigned long long v)
     return v;
 }
 
-// ----------------------------------------------------------------------- traversal kernels
 // warp-aggregated append of one edge per lane that has one
 __device__ inline void warp_emit(const TravArgs &a, bool has, const KMin &m)
 {
@@ -190,8 +153,54 @@ __device__ inline void warp_emit(const TravArgs &a, bool has, const KMin &m)
     }
 }
 
-// One level of FindPair.  MODE 0 = GetRho, MODE 1 = GetPairs.
-template <int MODE>
+// ------------------------------------------------------------------ packed node records
+// links = {begin, end, left, right}; meta = {diam2 bound, cdmin, cdmax, 0};
+// box[node][2*DP] = lo[0..DP), hi[0..DP) with padded dimensions set to 0.
+template <int DP>
+__device__ inline void pair_bounds_packed(const TravArgs &a, int P, int Q, const int4 &lp, const int4 &lq, float &lbB,
+                                          float &ubB, bool &ws, float &dP, float &dQ)
+{
+    const float4 *bp = (const float4 *)(a.box + (size_t)P * 2 * DP);
+    const float4 *bq = (const float4 *)(a.box + (size_t)Q * 2 * DP);
+    float s = 0.f, t = 0.f;
+#pragma unroll
+    for (int c = 0; c < DP / 4; ++c) {
+        float4 plo = bp[c], phi = bp[DP / 4 + c], qlo = bq[c], qhi = bq[DP / 4 + c];
+        float al[4] = {plo.x, plo.y, plo.z, plo.w}, ah[4] = {phi.x, phi.y, phi.z, phi.w};
+        float bl[4] = {qlo.x, qlo.y, qlo.z, qlo.w}, bh[4] = {qhi.x, qhi.y, qhi.z, qhi.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float g = fmaxf(fmaxf(bl[k] - ah[k], al[k] - bh[k]), 0.f);
+            float m = fmaxf(bh[k] - al[k], ah[k] - bl[k]);
+            s = fmaf(g, g, s);
+            t = fmaf(m, m, t);
+        }
+    }
+    float lb = lower_w2(s), ub = upper_w2(t);
+    float4 mp = a.meta[P], mq = a.meta[Q];
+    dP = mp.x;
+    dQ = mq.x;
+    float dm = fmaxf(dP, dQ);
+    ws = lb > dm;
+    lbB = lb;
+    ubB = ub;
+    if (a.cdmin) {
+        float lhs = fmaxf(lb, fmaxf(mp.y, mq.y));
+        float rhs = fmaxf(dm, fmaxf(mp.z, mq.z));
+        ws = ws || lhs >= rhs;
+        lbB = lhs;
+        ubB = fmaxf(ub, fmaxf(mp.z, mq.z));
+    }
+    if (lp.z < 0 && lq.z < 0) ws = true;   // two single points
+}
+
+// pair-size classes of a retrieved well-separated pair (by |A||B|)
+constexpr int kTinyMax = 8;      // one thread per pair
+constexpr int kSmallMax = 64;    // 8 lanes per pair
+constexpr int kMediumMax = 1024; // one warp per pair; larger pairs go to the tile kernel
+
+// One level of FindPair.  MODE 0 = GetRho, MODE 1 = GetPairs (classifies retrieved pairs).
+template <int MODE, int DP>
 __global__ void __launch_bounds__(256) findpair_level_kernel(TravArgs a, const int2 *__restrict__ in,
                                                              const int *__restrict__ in_count, int2 *__restrict__ out,
                                                              int *out_count, int *zero_count)
@@ -201,28 +210,29 @@ __global__ void __launch_bounds__(256) findpair_level_kernel(TravArgs a, const i
     const int stride = gridDim.x * blockDim.x;
     const int limit = (m + 31) & ~31;   // whole warps iterate together
     const int lane = threadIdx.x & 31;
-    unsigned long long n_pairs = 0, n_ev = 0, n_re = 0;
+    unsigned long long n_vis = 0, n_ret = 0;
     const bool stop = __shfl_sync(0xffffffffu, (int)(*(volatile unsigned *)a.overflow != 0), 0) != 0;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t - lane < limit && !stop; t += stride) {
         int push = 0;
         int2 c0 = make_int2(0, 0), c1 = make_int2(0, 0);
-        bool big = false, has_edge = false;
-        KMin best{~0ull, ~0ull};
+        int cls = -1;   // retrieved pair class: 0 tiny, 1 small, 2 medium, 3 big
         double rho_cand = INFINITY;
         int2 me = make_int2(0, 0);
         if (t < m) {
+            ++n_vis;
             me = in[t];
-            int P = me.x, Q = me.y;
-            bool live = true;
-            if (MODE == 0 && nsize(a, P) + nsize(a, Q) <= a.beta) live = false;
+            const int P = me.x, Q = me.y;
+            const int4 lp = a.links[P], lq = a.links[Q];
+            const int sp = lp.y - lp.x, sq = lq.y - lq.x;
+            bool live = !(MODE == 0 && sp + sq <= a.beta);
             if (live) {
                 int cp = a.comp[P];
                 if (cp >= 0 && cp == a.comp[Q]) live = false;
             }
             if (live) {
-                float lbB, ubB;
+                float lbB, ubB, dP, dQ;
                 bool ws;
-                pair_bounds(a, P, Q, lbB, ubB, ws);
+                pair_bounds_packed<DP>(a, P, Q, lp, lq, lbB, ubB, ws, dP, dQ);
                 if (MODE == 0) {
                     double rho = *(volatile double *)a.rho_out;
                     if ((double)lbB >= rho) live = false;
@@ -230,23 +240,18 @@ __global__ void __launch_bounds__(256) findpair_level_kernel(TravArgs a, const i
                 } else {
                     if ((double)lbB >= a.rho_hi || (double)ubB < a.rho_lo) live = false;
                     else if (ws) {
-                        long long prod = (long long)nsize(a, P) * nsize(a, Q);
-                        if (prod <= a.inline_max) {
-                            best = bccp_inline(a, P, Q, n_ev, n_re);
-                            has_edge = in_range(a, best);
-                        } else {
-                            big = true;
-                        }
-                        ++n_pairs;
+                        long long prod = (long long)sp * sq;
+                        cls = prod <= kTinyMax ? 0 : prod <= kSmallMax ? 1 : prod <= kMediumMax ? 2 : 3;
+                        ++n_ret;
                         live = false;
                     }
                 }
                 if (live) {
                     // split the node with the larger diameter (a leaf cannot be split)
-                    bool splitP = !is_leaf(a, P) && (is_leaf(a, Q) || a.diam2[P] >= a.diam2[Q]);
-                    int S = splitP ? P : Q, O = splitP ? Q : P;
-                    c0 = make_int2(a.left[S], O);
-                    c1 = make_int2(a.right[S], O);
+                    bool splitP = lp.z >= 0 && (lq.z < 0 || dP >= dQ);
+                    int O = splitP ? Q : P;
+                    c0 = make_int2(splitP ? lp.z : lq.z, O);
+                    c1 = make_int2(splitP ? lp.w : lq.w, O);
                     push = 2;
                 }
             }
@@ -260,22 +265,108 @@ __global__ void __launch_bounds__(256) findpair_level_kernel(TravArgs a, const i
             for (int o = 16; o; o >>= 1) rho_cand = fmin(rho_cand, __shfl_xor_sync(0xffffffffu, rho_cand, o));
             if (lane == 0 && rho_cand < INFINITY) atomicMinPosD(a.rho_out, rho_cand);
         } else {
-            int bs = warp_append(a.big_count, big ? 1 : 0);
-            if (big) {
-                if (bs < a.big_cap) a.big[bs] = me;
-                else atomicOr(a.overflow, 4u);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                int bs = warp_append(a.list_count + c, cls == c ? 1 : 0);
+                if (cls == c) {
+                    if (bs < a.list_cap[c]) a.list[c][bs] = me;
+                    else atomicOr(a.overflow, 4u);
+                }
             }
-            warp_emit(a, has_edge, best);
         }
     }
-    if (MODE == 1) {
-        n_pairs = warp_sum_u64(n_pairs);
-        n_ev = warp_sum_u64(n_ev);
-        n_re = warp_sum_u64(n_re);
-        if (lane == 0 && n_pairs) {
-            atomicAdd(a.stat + 0, n_pairs);
-            atomicAdd(a.stat + 1, n_ev);
-            atomicAdd(a.stat + 2, n_re);
+    n_vis = warp_sum_u64(n_vis);
+    n_ret = warp_sum_u64(n_ret);
+    if (lane == 0 && n_vis) {
+        atomicAdd(a.stat + (MODE == 0 ? 5 : 4), n_vis);
+        if (n_ret) atomicAdd(a.stat + 0, n_ret);
+    }
+}
+
+// ------------------------------------------------------------- BCCP of tiny/small/medium pairs
+// A group of G lanes evaluates one pair: lane g takes the evaluations e = g, g+G, ... of the
+// |A| x |B| product (a = e / |B|, b = e % |B|).  FP32 screen, group minimum, band threshold,
+// FP64 recheck of every candidate inside the band, group K-minimum; the group leader emits the
+// edge when its FP64 w2 lies in [rho_lo, rho_hi).
+template <int G>
+__global__ void __launch_bounds__(256) bccp_group_kernel(TravArgs a, const int2 *__restrict__ pairs,
+                                                         const int *__restrict__ count)
+{
+    const int m = *count;
+    const int lane = threadIdx.x & 31, g = lane & (G - 1);
+    constexpr int PPW = 32 / G;   // pairs per warp
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int n = a.n, d = a.d;
+    unsigned long long n_ev = 0, n_re = 0;
+    for (int base = warp * PPW; base < m; base += nwarps * PPW) {
+        const int pi = base + lane / G;
+        const bool valid = pi < m;
+        int pb = 0, qb = 0, na = 0, nb = 0;
+        if (valid) {
+            int2 pr = pairs[pi];
+            int4 lp = a.links[pr.x], lq = a.links[pr.y];
+            pb = lp.x; na = lp.y - lp.x; qb = lq.x; nb = lq.y - lq.x;
+        }
+        const int tot = na * nb;
+        KMin best{~0ull, ~0ull};
+        if (a.fp64) {
+            for (int e = g; e < tot; e += G) {
+                int i = pb + e / nb, j = qb + e % nb;
+                double w = dist64(a.x64, n, d, i, j);
+                if (a.cd64) w = fmax(w, fmax(a.cd64[i], a.cd64[j]));
+                kmin_update(best, w, a.pid[i], a.pid[j]);
+            }
+        } else {
+            float smin = INFINITY;
+            for (int e = g; e < tot; e += G) {
+                int i = pb + e / nb, j = qb + e % nb;
+                float s = dist32(a.x32, n, d, i, j);
+                if (a.cd32) s = fmaxf(s, fmaxf(a.cd32[i], a.cd32[j]));
+                smin = fminf(smin, s);
+            }
+#pragma unroll
+            for (int o = G / 2; o; o >>= 1) smin = fminf(smin, __shfl_xor_sync(0xffffffffu, smin, o));
+            const float T = screen_threshold(smin, a.eta);
+            for (int e = g; e < tot; e += G) {
+                int i = pb + e / nb, j = qb + e % nb;
+                float s = dist32(a.x32, n, d, i, j);
+                if (a.cd32) s = fmaxf(s, fmaxf(a.cd32[i], a.cd32[j]));
+                if (s <= T) {
+                    kmin_update(best, exact_w2(a, i, j, s), a.pid[i], a.pid[j]);
+                    ++n_re;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = G / 2; o; o >>= 1) {
+            unsigned long long oh = __shfl_xor_sync(0xffffffffu, best.hi, o);
+            unsigned long long ol = __shfl_xor_sync(0xffffffffu, best.lo, o);
+            if (oh < best.hi || (oh == best.hi && ol < best.lo)) { best.hi = oh; best.lo = ol; }
+        }
+        if (g == 0) n_ev += (unsigned long long)tot;
+        warp_emit(a, valid && g == 0 && in_range(a, best), best);
+    }
+    n_ev = warp_sum_u64(n_ev);
+    n_re = warp_sum_u64(n_re);
+    if (lane == 0 && n_ev) {
+        atomicAdd(a.stat + 1, n_ev);
+        atomicAdd(a.stat + 2, n_re);
+    }
+}
+
+__global__ void pack_nodes_kernel(int N, int d, int DP, const float *__restrict__ lo, const float *__restrict__ hi,
+                                  const int *__restrict__ begin, const int *__restrict__ end,
+                                  const int *__restrict__ left, const int *__restrict__ right,
+                                  const float *__restrict__ diam2, const float *__restrict__ cdmin,
+                                  const float *__restrict__ cdmax, int4 *__restrict__ links, float4 *__restrict__ meta,
+                                  float *__restrict__ box)
+{
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x) {
+        links[x] = make_int4(begin[x], end[x], left[x], right[x]);
+        meta[x] = make_float4(diam2[x], cdmin ? cdmin[x] : 0.f, cdmax ? cdmax[x] : 0.f, 0.f);
+        for (int k = 0; k < DP; ++k) {
+            box[(size_t)x * 2 * DP + k] = k < d ? lo[(size_t)k * N + x] : 0.f;
+            box[(size_t)x * 2 * DP + DP + k] = k < d ? hi[(size_t)k * N + x] : 0.f;
         }
     }
 }
@@ -521,10 +612,15 @@ int run_traversal(int mode, TravArgs &a, int2 *fa, int2 *fb, int *counters, cuda
         for (int b = 0; b < 6; ++b, ++level) {
             int2 *in = (level & 1) ? fb : fa, *out = (level & 1) ? fa : fb;
             int *cin = counters + (level % 3), *cout = counters + ((level + 1) % 3), *cz = counters + ((level + 2) % 3);
-            if (mode == 0)
-                launch(findpair_level_kernel<0>, grid, 256, 0, st, a, in, cin, out, cout, cz);
-            else
-                launch(findpair_level_kernel<1>, grid, 256, 0, st, a, in, cin, out, cout, cz);
+#define WM_FP(DPV)                                                                          \
+    do {                                                                                    \
+        if (mode == 0) launch(findpair_level_kernel<0, DPV>, grid, 256, 0, st, a, in, cin, out, cout, cz); \
+        else launch(findpair_level_kernel<1, DPV>, grid, 256, 0, st, a, in, cin, out, cout, cz);           \
+    } while (0)
+            if (a.dp == 4) WM_FP(4);
+            else if (a.dp == 8) WM_FP(8);
+            else WM_FP(16);
+#undef WM_FP
         }
         cudaMemcpyAsync(pinned, counters + (level % 3), sizeof(int), cudaMemcpyDeviceToHost, st);
         cudaMemcpyAsync(pinned + 1, a.overflow, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
@@ -536,6 +632,23 @@ int run_traversal(int mode, TravArgs &a, int2 *fa, int2 *fb, int *counters, cuda
     *overflow_out = 0;
     if (levels_out) *levels_out = level;
     return 0;
+}
+
+// BCCP of the tiny, small and medium pair lists (counts read back by the host).
+void run_bccp_groups(TravArgs &a, const int *counts_host, cudaStream_t st)
+{
+    if (counts_host[0] > 0)
+        launch(bccp_group_kernel<1>, grid_for((long long)counts_host[0], 256), 256, 0, st, a, a.list[0], a.list_count + 0);
+    if (counts_host[1] > 0)
+        launch(bccp_group_kernel<8>, grid_for((long long)counts_host[1] * 8, 256), 256, 0, st, a, a.list[1], a.list_count + 1);
+    if (counts_host[2] > 0)
+        launch(bccp_group_kernel<32>, grid_for((long long)counts_host[2] * 32, 256), 256, 0, st, a, a.list[2], a.list_count + 2);
+}
+
+void pack_nodes(const Tree &T, int d, int dp, int4 *links, float4 *meta, float *box, cudaStream_t st)
+{
+    launch(pack_nodes_kernel, grid_for(T.N, 256), 256, 0, st, T.N, d, dp, T.lo, T.hi, T.begin, T.end, T.left, T.right,
+           T.diam2, T.cdmin, T.cdmax, links, meta, box);
 }
 
 // BCCP tile kernel over the queued big pairs (m of them, count known on host).

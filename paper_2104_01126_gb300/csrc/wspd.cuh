@@ -21,21 +21,31 @@ struct TravArgs {
     int beta = 2;
     double rho_lo = 0.0, rho_hi = 0.0;
     double *rho_out = nullptr; // GetRho result (WriteMin target)
-    long long inline_max = 64; // pairs with |A||B| <= this are evaluated inside the traversal
     int frontier_cap = 0;
-    int2 *big = nullptr;
-    int *big_count = nullptr;
-    int big_cap = 0;
+    // packed node records used by the traversals (see wspd.cu)
+    const int4 *links = nullptr;
+    const float4 *meta = nullptr;
+    const float *box = nullptr;
+    int dp = 4;                         // box stride: d rounded up to 4, 8 or 16
+    // retrieved well-separated pairs by size class: 0 tiny, 1 small, 2 medium, 3 big (tiles)
+    int2 *list[4] = {nullptr, nullptr, nullptr, nullptr};
+    int *list_count = nullptr;          // [4]
+    int list_cap[4] = {0, 0, 0, 0};
+    int2 *big = nullptr;                // = list[3]
+    int *big_count = nullptr;           // = list_count + 3
     EdgeK *edges = nullptr;
     int *edge_count = nullptr;
     int edge_cap = 0;
     unsigned *overflow = nullptr;      // bit 0 frontier, bit 1 edges, bit 2 big pairs
-    unsigned long long *stat = nullptr; // [0] pairs, [1] evals, [2] fp64 rechecks, [3] tile evals
+    unsigned long long *stat = nullptr; // [0] pairs retrieved, [1] evals, [2] fp64 rechecks,
+                                        // [3] tile evals, [4] GetPairs visits, [5] GetRho visits
 };
 
 void launch_comp_labels(const Tree &T, const Points &P, int *uf, cudaStream_t st);
 int run_traversal(int mode, TravArgs &a, int2 *fa, int2 *fb, int *counters, cudaStream_t st, int *pinned,
                   unsigned *overflow_out, int *levels_out);
 int run_bccp_tiles(TravArgs &a, int m, int *jobs, int *total, cudaStream_t st, Arena &ar, bool hdb, bool fp64);
+void run_bccp_groups(TravArgs &a, const int *counts_host, cudaStream_t st);
+void pack_nodes(const Tree &T, int d, int dp, int4 *links, float4 *meta, float *box, cudaStream_t st);
 
 }  // namespace wm

@@ -417,3 +417,17 @@ def test_figure1_caption_facts():
     for valley in facts["plot_valleys_in_order"]:
         assert set(order[k:k + len(valley)]) == set(valley)
         k += len(valley)
+
+
+def test_core_dist_subset_and_nearest_edge_agree_with_full_oracle():
+    x = synthdata.gaussian_mixture(500, 3, seed=3).astype(np.float64)
+    idx = np.array([0, 7, 123, 499])
+    assert np.array_equal(oracle.core_dist2_subset(x, 7, idx), oracle.core_dist2(x, 7)[idx])
+    e = oracle.emst(x)
+    es = _edge_set(e["u"], e["v"])
+    iu, iv, w2 = _all_edges_sorted(x)
+    for p in (0, 11, 250):
+        q, w = oracle.nearest_edge(x, p)
+        assert (min(p, q), max(p, q)) in es            # cut property of the singleton {p}
+        first = np.flatnonzero((iu == p) | (iv == p))[0]
+        assert (iu[first], iv[first]) == (min(p, q), max(p, q)) and w2[first] == w
