@@ -115,6 +115,7 @@ typedef struct {
     int64_t getpairs_launches;     /* number of GetPairs level launches                 */
     int64_t getpairs_visits;       /* node pairs examined by the GetPairs traversals     */
     int64_t getrho_visits;         /* node pairs examined by the GetRho traversals       */
+    int64_t bccp_dual_evals;       /* distance evaluations in the pruned BCCP of huge pairs */
 } wm_stats;
 
 /* Options.  A zero-initialised struct (or NULL) gives the defaults. */

@@ -57,7 +57,8 @@ class _Stats(ctypes.Structure):
                 ("reserved", ctypes.c_int32), ("ms_knn_kernel", ctypes.c_double),
                 ("ms_tile_kernel", ctypes.c_double), ("tile_launches", ctypes.c_int64),
                 ("ms_getpairs", ctypes.c_double), ("getpairs_launches", ctypes.c_int64),
-                ("getpairs_visits", ctypes.c_int64), ("getrho_visits", ctypes.c_int64)]
+                ("getpairs_visits", ctypes.c_int64), ("getrho_visits", ctypes.c_int64),
+                ("bccp_dual_evals", ctypes.c_int64)]
 
 
 class _Opts(ctypes.Structure):
@@ -102,6 +103,7 @@ class Stats:
     getpairs_launches: int = 0
     getpairs_visits: int = 0
     getrho_visits: int = 0
+    bccp_dual_evals: int = 0
 
     @classmethod
     def _from(cls, s: _Stats) -> "Stats":

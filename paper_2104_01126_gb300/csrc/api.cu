@@ -21,7 +21,7 @@ int ingest_points(const void *dev_src, int n, int d, int dtype, int layout, Poin
                   unsigned *pinned);
 int build_tree(Points &P, Tree &T, Arena &ar, cudaStream_t st, int *pinned);
 int filter_connected(const EdgeK *in, int m, const int *uf, EdgeK *out, int *count_dev, cudaStream_t st);
-int batch_kruskal(const EdgeK *e, int m, int *uf, int *R, EdgeK *out, int out_base, int *accepted, Arena &ar,
+int batch_kruskal(const EdgeK *e, int m, int n, int *uf, int *R, EdgeK *out, int out_base, int *accepted, Arena &ar,
                   cudaStream_t st, int *pinned);
 
 // ----------------------------------------------------------------------------- error state
@@ -32,6 +32,14 @@ static void set_detail(const char *fmt, const char *a = "", long long b = 0)
     snprintf(buf, sizeof buf, fmt, a, b);
     g_detail = buf;
 }
+static void set_detail(const char *fmt, long long b, const char *a)
+{
+    char buf[512];
+    snprintf(buf, sizeof buf, fmt, b, a);
+    g_detail = buf;
+}
+
+void set_error_detail(const char *msg) { g_detail = msg; }
 
 // pinned host scratch for scalar readbacks (one per thread)
 static int *pinned_scratch()
@@ -65,7 +73,7 @@ static size_t estimate_bytes(long long n, int d, int min_pts, const Caps &c)
     b += (size_t)N * (8 * d + 48);          // tree arrays (+ build scratch counters)
     b += (size_t)n * 8;                     // small lists
     b += (size_t)c.frontier * 8 * 2;
-    b += (size_t)c.big * 12 + (size_t)c.pairs * 8 * 3;
+    b += (size_t)c.big * 64 + (size_t)c.pairs * 8 * 3 + (size_t)152 * 64 * 4 * 96;
     b += (size_t)N * (32 + 8 * (d <= 4 ? 4 : d <= 8 ? 8 : 16));   // packed node records
     b += (size_t)c.edges * 16 * 3 + (size_t)c.edges * 24;   // batch, filtered, sort tmp, kruskal
     b += (size_t)n * 16 * 2;                // output tree + conversion
@@ -220,13 +228,20 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     int2 *fa = ar.get<int2>(caps.frontier), *fb = ar.get<int2>(caps.frontier);
     int2 *big = ar.get<int2>(caps.big);
     int2 *plist0 = ar.get<int2>(caps.pairs), *plist1 = ar.get<int2>(caps.pairs), *plist2 = ar.get<int2>(caps.pairs);
-    int *jobs = ar.get<int>(caps.big + 1);
+    long long *jobs = ar.get<long long>(caps.big + 1);
+    EdgeK *pair_best = ar.get<EdgeK>(caps.big + 1);
+    int2 *huge = ar.get<int2>(caps.big);
+    EdgeK *huge_best = ar.get<EdgeK>(caps.big + 1);
+    unsigned *huge_sbest = ar.get<unsigned>(caps.big + 1);
+    long long *huge_items = ar.get<long long>(caps.big + 1);
+    const int stack_warps = 152 * 8 * 8;   // warps of the dual-tree kernel (grid-stride)
+    int *dual_stack = ar.get<int>((size_t)stack_warps * (T.depth + 4));
     const int dp = P.d <= 4 ? 4 : P.d <= 8 ? 8 : 16;
     int4 *links = ar.get<int4>(T.N);
     float4 *meta = ar.get<float4>(T.N);
     float *box = ar.get<float>((size_t)T.N * 2 * dp);
     EdgeK *batch = ar.get<EdgeK>(caps.edges), *filt = ar.get<EdgeK>(caps.edges), *tmp = ar.get<EdgeK>(caps.edges);
-    int *cnts = ar.get<int>(16);
+    int *cnts = ar.get<int>(32);   // [10..14] pair-list counts, [16..17] and [18..19] 64-bit job totals
     double *rho = ar.get<double>(2);
     unsigned *ovf = ar.get<unsigned>(2);
     unsigned long long *stat = ar.get<unsigned long long>(8);
@@ -251,10 +266,13 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     }
     a.frontier_cap = (int)caps.frontier;
     a.links = links; a.meta = meta; a.box = box; a.dp = dp;
-    a.list[0] = plist0; a.list[1] = plist1; a.list[2] = plist2; a.list[3] = big;
-    a.list_cap[0] = a.list_cap[1] = a.list_cap[2] = (int)caps.pairs; a.list_cap[3] = (int)caps.big;
+    a.list[0] = plist0; a.list[1] = plist1; a.list[2] = plist2; a.list[3] = big; a.list[4] = huge;
+    a.list_cap[0] = a.list_cap[1] = a.list_cap[2] = (int)caps.pairs; a.list_cap[3] = a.list_cap[4] = (int)caps.big;
+    a.huge_best = huge_best; a.huge_sbest = huge_sbest;
+    a.stack = dual_stack; a.stack_cap = T.depth + 4;
     a.list_count = cnts + 10;
     a.big = big; a.big_count = cnts + 13;
+    a.pair_best = pair_best;
     a.edges = batch; a.edge_count = cnts + 5; a.edge_cap = (int)caps.edges;
     a.overflow = ovf;
     a.stat = stat;
@@ -283,7 +301,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         a.rho_lo = rho_lo;
         a.rho_hi = rho_hi;
         WM_CK(cudaMemsetAsync(cnts + 4, 0, 2 * sizeof(int), st));
-        WM_CK(cudaMemsetAsync(cnts + 10, 0, 4 * sizeof(int), st));
+        WM_CK(cudaMemsetAsync(cnts + 10, 0, 5 * sizeof(int), st));
         cudaEvent_t g0 = nullptr, g1 = nullptr;
         if (C.timing) {
             cudaEventCreate(&g0);
@@ -301,9 +319,9 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         }
         C.stats.getpairs_launches += glev;
         if (ob) { *overflow_bits = ob; return 0; }
-        WM_CK(cudaMemcpyAsync(C.pin, cnts + 10, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        WM_CK(cudaMemcpyAsync(C.pin, cnts + 10, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
         WM_CK(cudaStreamSynchronize(st));
-        int lcounts[4] = {C.pin[0], C.pin[1], C.pin[2], C.pin[3]};
+        int lcounts[5] = {C.pin[0], C.pin[1], C.pin[2], C.pin[3], C.pin[4]};
         int mbig = lcounts[3];
         // BCCP of the tiny / small / medium retrieved pairs
         run_bccp_groups(a, lcounts, st);
@@ -316,12 +334,14 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
             cudaEventCreate(&e1);
             cudaEventRecord(e0, st);
         }
-        WM_TRY(run_bccp_tiles(a, mbig, jobs, cnts + 6, st, ar, hdb != nullptr, a.fp64 != 0));
+        WM_TRY(run_bccp_tiles(a, mbig, jobs, (long long *)(cnts + 16), st, ar, hdb != nullptr, a.fp64 != 0));
+        WM_TRY(run_bccp_huge(a, lcounts[4], huge_items, (long long *)(cnts + 18), st, ar, hdb != nullptr, a.fp64 != 0,
+                             stack_warps));
         if (C.timing) cudaEventRecord(e1, st);
         WM_CK(cudaMemcpyAsync(C.pin, cnts + 5, sizeof(int), cudaMemcpyDeviceToHost, st));
         WM_CK(cudaMemcpyAsync(C.pin + 1, ovf, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
         WM_CK(cudaStreamSynchronize(st));
-        if (mbig > 0) {
+        if (mbig > 0 || lcounts[4] > 0) {
             double ms = C.timing ? C.event_ms(e0, e1) : tb.ms();
             C.stats.ms_bccp += ms;
             C.stats.ms_tile_kernel += ms;
@@ -364,7 +384,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
             C.stats.candidate_edges += mf;
             EdgeK *sorted = filt;
             WM_TRY(radix_sort_edges(filt, tmp, mf, st, ar, &sorted, C.pin + 4096));
-            WM_TRY(batch_kruskal(sorted, mf, uf, R, E_out, nE, &accepted, ar, st, C.pin));
+            WM_TRY(batch_kruskal(sorted, mf, n, uf, R, E_out, nE, &accepted, ar, st, C.pin));
         }
         C.stats.ms_kruskal += tk.ms();
         nE += accepted;
@@ -380,6 +400,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     unsigned long long hs[8];
     memcpy(hs, C.pin, sizeof hs);
     C.stats.getpairs_visits = (int64_t)hs[4];
+    C.stats.bccp_dual_evals = (int64_t)hs[6];
     C.stats.getrho_visits = (int64_t)hs[5];
     C.stats.rounds = rounds;
     C.stats.pairs_retrieved = (int64_t)hs[0];
@@ -472,6 +493,7 @@ static int run_call(const wm_opts *opts, long long n, int d, int min_pts, Body b
     Caps caps = default_caps(n, min_pts);
     const bool user_ws = opts && opts->workspace;
     int rc = 0;
+    unsigned ovf_seen = 0;   // capacities that overflowed in earlier attempts
     for (int attempt = 0; attempt < 8; ++attempt) {
         size_t need = estimate_bytes(n, d, min_pts, caps);
         std::unique_lock<std::mutex> lk;
@@ -485,7 +507,11 @@ static int run_call(const wm_opts *opts, long long n, int d, int min_pts, Body b
                 if (dc.ptr) { cudaStreamSynchronize(C.st); cudaFree(dc.ptr); dc.ptr = nullptr; dc.cap = 0; }
                 if (cudaMalloc((void **)&dc.ptr, need) != cudaSuccess) {
                     cudaGetLastError();
-                    set_detail("cudaMalloc of %s%lld bytes failed", "", (long long)need);
+                    char what[96];
+                    snprintf(what, sizeof what, "%s%s%s", (ovf_seen & 1u) ? " frontier" : "",
+                             (ovf_seen & 2u) ? " edge-batch" : "", (ovf_seen & 4u) ? " pair-list" : "");
+                    set_detail("cudaMalloc of %lld bytes failed (capacities grown after overflow of:%s)",
+                               (long long)need, ovf_seen ? what : " none");
                     return WM_ENOMEM;
                 }
                 dc.cap = need;
@@ -507,6 +533,7 @@ static int run_call(const wm_opts *opts, long long n, int d, int min_pts, Body b
             break;
         }
         if (rc && rc != WM_ENOMEM) break;
+        ovf_seen |= ovf;
         // grow whichever capacity overflowed and start over
         if (ovf & 1u) caps.frontier *= 2;
         if (ovf & 2u) caps.edges *= 2;
@@ -786,7 +813,7 @@ extern "C" int wm_emst_noalloc(const void *pts, int64_t n, int32_t d, int32_t dt
     Caps caps;
     caps.frontier = rest * 30 / 100 / 16;
     caps.pairs = rest * 10 / 100 / 8;
-    caps.big = rest * 5 / 100 / 12;
+    caps.big = rest * 5 / 100 / 64;
     caps.edges = rest * 35 / 100 / 72;
     EmstCtx c{pts, n, d, dtype, layout, out_edges, out_total_weight};
     unsigned ovf = 0;

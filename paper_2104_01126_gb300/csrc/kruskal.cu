@@ -8,6 +8,8 @@
 // that hold neither retry in the next step.  The lowest-priority edge touching a root always
 // wins it, so every step accepts or rejects at least one edge, and an edge is accepted only when
 // no earlier pending edge touches the component it links, which is the sequential condition.
+#include <cstdio>
+
 #include "wm_internal.cuh"
 
 namespace wm {
@@ -61,6 +63,15 @@ __global__ void filter_connected_kernel(const EdgeK *__restrict__ in, int m, con
         if (lane == 0 && b) base = atomicAdd(count, __popc(b));
         base = __shfl_sync(0xffffffffu, base, 0);
         if (keep) out[base + __popc(b & lanemask_lt())] = e;
+    }
+}
+
+// Every edge handed to Kruskal must have 0 <= u < v < n.
+__global__ void validate_edges_kernel(const EdgeK *__restrict__ e, int m, int n, int *bad)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        int u = edge_u(e[i]), v = edge_v(e[i]);
+        if (u < 0 || u >= v || v >= n) atomicOr(bad, 1);
     }
 }
 
@@ -136,10 +147,15 @@ __global__ void flag_accept_kernel(const int *__restrict__ status, int m, int *_
 }
 
 __global__ void append_accept_kernel(const EdgeK *__restrict__ e, const int *__restrict__ status,
-                                     const int *__restrict__ pre, int m, EdgeK *__restrict__ out, int out_base)
+                                     const int *__restrict__ pre, int m, EdgeK *__restrict__ out, int out_base,
+                                     int out_cap, int *bad)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
-        if (status[i] == kAccept) out[out_base + pre[i]] = e[i];
+        if (status[i] == kAccept) {
+            int k = out_base + pre[i];
+            if (k < out_cap) out[k] = e[i];
+            else atomicOr(bad, 2);
+        }
 }
 
 }  // namespace
@@ -153,7 +169,7 @@ int filter_connected(const EdgeK *in, int m, const int *uf, EdgeK *out, int *cou
 
 // Kruskal over a K-sorted batch e[0..m).  R[n] must hold INT_MAX everywhere on entry (kept so).
 // Accepted edges are appended to out at out_base; *accepted receives their number.
-int batch_kruskal(const EdgeK *e, int m, int *uf, int *R, EdgeK *out, int out_base, int *accepted, Arena &ar,
+int batch_kruskal(const EdgeK *e, int m, int n, int *uf, int *R, EdgeK *out, int out_base, int *accepted, Arena &ar,
                   cudaStream_t st, int *pinned)
 {
     *accepted = 0;
@@ -162,7 +178,16 @@ int batch_kruskal(const EdgeK *e, int m, int *uf, int *R, EdgeK *out, int out_ba
     int *listA = ar.get<int>(m), *listB = ar.get<int>(m), *status = ar.get<int>(m + 1), *pre = ar.get<int>(m + 1);
     int2 *roots = ar.get<int2>(m);
     int *cnt = ar.get<int>(4);
+    int *bad = ar.get<int>(1);
     if (ar.failed) return WM_ENOMEM;
+    cudaMemsetAsync(bad, 0, sizeof(int), st);
+    launch(validate_edges_kernel, grid_for(m, 256), 256, 0, st, e, m, n, bad);
+    cudaMemcpyAsync(pinned, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;
+    if (pinned[0]) {
+        set_error_detail("a candidate edge handed to Kruskal has an endpoint outside [0, n) or u >= v");
+        return WM_EINTERNAL;
+    }
     launch(init_list_kernel, grid_for(m, 256), 256, 0, st, listA, m, status);
     int hm = m;
     cudaMemcpyAsync(cnt, &hm, sizeof(int), cudaMemcpyHostToDevice, st);
@@ -183,15 +208,26 @@ int batch_kruskal(const EdgeK *e, int m, int *uf, int *R, EdgeK *out, int out_ba
         cudaMemcpyAsync(pinned, cnt + (step & 1), sizeof(int), cudaMemcpyDeviceToHost, st);
         if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;
         if (pinned[0] == 0) break;
-        if (step > 4 * (m + 8)) return WM_EINTERNAL;
+        if (step > 4 * (m + 8)) {
+            char msg[160];
+            snprintf(msg, sizeof msg, "batched Kruskal made no progress (reservations): %d of %d edges pending",
+                     pinned[0], m);
+            set_error_detail(msg);
+            return WM_EINTERNAL;
+        }
     }
     launch(flag_accept_kernel, grid, 256, 0, st, status, m, pre);
     int rc = scan_exclusive_i32(pre, pre, m, cnt + 2, st, ar);
     if (rc) return rc;
-    launch(append_accept_kernel, grid, 256, 0, st, e, status, pre, m, out, out_base);
+    launch(append_accept_kernel, grid, 256, 0, st, e, status, pre, m, out, out_base, n - 1, bad);
     cudaMemcpyAsync(pinned, cnt + 2, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(pinned + 1, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;
     *accepted = pinned[0];
+    if (pinned[1]) {
+        set_error_detail("Kruskal accepted more than n-1 edges in total");
+        return WM_EINTERNAL;
+    }
     ar.off = mark;
     return 0;
 }

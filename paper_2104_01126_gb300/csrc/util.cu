@@ -10,63 +10,66 @@ constexpr int kScanBlock = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanBlock * kScanItems;
 
-__device__ inline int block_exclusive_scan(int v, int *smem_warp, int &total)
+template <typename T>
+__device__ inline T block_exclusive_scan(T v, T *smem_warp, T &total)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int x = v;
+    T x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, x, o);
+        T y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
     if (lane == 31) smem_warp[warp] = x;
     __syncthreads();
     if (warp == 0) {
-        int w = lane < nw ? smem_warp[lane] : 0;
+        T w = lane < nw ? smem_warp[lane] : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, w, o);
+            T y = __shfl_up_sync(0xffffffffu, w, o);
             if (lane >= o) w += y;
         }
         if (lane < nw) smem_warp[lane] = w;
     }
     __syncthreads();
     total = smem_warp[nw - 1];
-    int r = x - v + (warp > 0 ? smem_warp[warp - 1] : 0);
+    T r = x - v + (warp > 0 ? smem_warp[warp - 1] : 0);
     __syncthreads();
     return r;
 }
 
-__global__ void scan_reduce_kernel(const int *__restrict__ in, int n, int *__restrict__ block_sums)
+template <typename T>
+__global__ void scan_reduce_kernel(const T *__restrict__ in, int n, T *__restrict__ block_sums)
 {
-    __shared__ int sw[32];
+    __shared__ T sw[32];
     long long base = (long long)blockIdx.x * kScanTile;
-    int s = 0;
+    T s = 0;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         long long idx = base + (long long)threadIdx.x * kScanItems + i;
         if (idx < n) s += in[idx];
     }
-    int total;
+    T total;
     block_exclusive_scan(s, sw, total);
     if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
 }
 
-__global__ void scan_down_kernel(const int *__restrict__ in, int *__restrict__ out, int n,
-                                 const int *__restrict__ block_offs, int *total_dev, int nblocks)
+template <typename T>
+__global__ void scan_down_kernel(const T *__restrict__ in, T *__restrict__ out, int n,
+                                 const T *__restrict__ block_offs, T *total_dev, int nblocks)
 {
-    __shared__ int sw[32];
+    __shared__ T sw[32];
     long long base = (long long)blockIdx.x * kScanTile;
-    int v[kScanItems];
-    int s = 0;
+    T v[kScanItems];
+    T s = 0;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         long long idx = base + (long long)threadIdx.x * kScanItems + i;
         v[i] = idx < n ? in[idx] : 0;
         s += v[i];
     }
-    int total;
-    int ex = block_exclusive_scan(s, sw, total) + (block_offs ? block_offs[blockIdx.x] : 0);
+    T total;
+    T ex = block_exclusive_scan(s, sw, total) + (block_offs ? block_offs[blockIdx.x] : 0);
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         long long idx = base + (long long)threadIdx.x * kScanItems + i;
@@ -90,26 +93,37 @@ void fill_i32(int *p, int v, size_t n, cudaStream_t st)
 }
 
 // out[i] = sum_{j<i} in[j]; *total_dev (optional, device) = sum of all.  in may equal out.
-int scan_exclusive_i32(const int *in, int *out, int n, int *total_dev, cudaStream_t st, Arena &ar)
+template <typename T>
+static int scan_exclusive_t(const T *in, T *out, int n, T *total_dev, cudaStream_t st, Arena &ar)
 {
     if (n <= 0) {
-        if (total_dev) cudaMemsetAsync(total_dev, 0, sizeof(int), st);
+        if (total_dev) cudaMemsetAsync(total_dev, 0, sizeof(T), st);
         return 0;
     }
     int nb = (n + kScanTile - 1) / kScanTile;
     if (nb == 1) {
-        launch(scan_down_kernel, 1, kScanBlock, 0, st, in, out, n, nullptr, total_dev, 1);
+        launch(scan_down_kernel<T>, 1, kScanBlock, 0, st, in, out, n, (const T *)nullptr, total_dev, 1);
         return 0;
     }
     size_t mark = ar.off;
-    int *sums = ar.get<int>(nb);
+    T *sums = ar.get<T>(nb);
     if (!sums) return WM_ENOMEM;
-    launch(scan_reduce_kernel, nb, kScanBlock, 0, st, in, n, sums);
-    int rc = scan_exclusive_i32(sums, sums, nb, nullptr, st, ar);
+    launch(scan_reduce_kernel<T>, nb, kScanBlock, 0, st, in, n, sums);
+    int rc = scan_exclusive_t<T>(sums, sums, nb, (T *)nullptr, st, ar);
     if (rc) return rc;
-    launch(scan_down_kernel, nb, kScanBlock, 0, st, in, out, n, sums, total_dev, nb);
+    launch(scan_down_kernel<T>, nb, kScanBlock, 0, st, in, out, n, (const T *)sums, total_dev, nb);
     ar.off = mark;
     return 0;
+}
+
+int scan_exclusive_i32(const int *in, int *out, int n, int *total_dev, cudaStream_t st, Arena &ar)
+{
+    return scan_exclusive_t<int>(in, out, n, total_dev, st, ar);
+}
+
+int scan_exclusive_i64(const long long *in, long long *out, int n, long long *total_dev, cudaStream_t st, Arena &ar)
+{
+    return scan_exclusive_t<long long>(in, out, n, total_dev, st, ar);
 }
 
 // ------------------------------------------------------------------------------ radix sort

@@ -158,6 +158,9 @@ __device__ inline unsigned lanemask_lt() { unsigned m; asm("mov.u32 %0, %%lanema
 // ------------------------------------------------------------------------- host-side API
 // util.cu
 int scan_exclusive_i32(const int *in, int *out, int n, int *total_dev, cudaStream_t st, Arena &ar);
+int scan_exclusive_i64(const long long *in, long long *out, int n, long long *total_dev, cudaStream_t st, Arena &ar);
+// message for the last failure on this thread (read by wm_last_error_detail)
+void set_error_detail(const char *msg);
 // host_scratch: at least 16 KiB of host memory (pinned preferred) for the digit histogram readback
 int radix_sort_edges(EdgeK *keys, EdgeK *tmp, int m, cudaStream_t st, Arena &ar, EdgeK **result, void *host_scratch);
 void fill_i32(int *p, int v, size_t n, cudaStream_t st);

@@ -197,7 +197,8 @@ __device__ inline void pair_bounds_packed(const TravArgs &a, int P, int Q, const
 // pair-size classes of a retrieved well-separated pair (by |A||B|)
 constexpr int kTinyMax = 8;      // one thread per pair
 constexpr int kSmallMax = 64;    // 8 lanes per pair
-constexpr int kMediumMax = 1024; // one warp per pair; larger pairs go to the tile kernel
+constexpr int kMediumMax = 1024; // one warp per pair
+constexpr long long kBigMax = 65536; // warp tiles (brute force); larger pairs: pruned dual-tree BCCP
 
 // One level of FindPair.  MODE 0 = GetRho, MODE 1 = GetPairs (classifies retrieved pairs).
 template <int MODE, int DP>
@@ -241,7 +242,7 @@ __global__ void __launch_bounds__(256) findpair_level_kernel(TravArgs a, const i
                     if ((double)lbB >= a.rho_hi || (double)ubB < a.rho_lo) live = false;
                     else if (ws) {
                         long long prod = (long long)sp * sq;
-                        cls = prod <= kTinyMax ? 0 : prod <= kSmallMax ? 1 : prod <= kMediumMax ? 2 : 3;
+                        cls = prod <= kTinyMax ? 0 : prod <= kSmallMax ? 1 : prod <= kMediumMax ? 2 : prod <= kBigMax ? 3 : 4;
                         ++n_ret;
                         live = false;
                     }
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(256) findpair_level_kernel(TravArgs a, const i
             if (lane == 0 && rho_cand < INFINITY) atomicMinPosD(a.rho_out, rho_cand);
         } else {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
+            for (int c = 0; c < 5; ++c) {
                 int bs = warp_append(a.list_count + c, cls == c ? 1 : 0);
                 if (cls == c) {
                     if (bs < a.list_cap[c]) a.list[c][bs] = me;
@@ -425,18 +426,287 @@ constexpr int kTileA = 32 * kItems;
 // points of the smaller side staged per warp (8 warps per block, static shared memory < 48 KB)
 __host__ __device__ constexpr int tile_q(int dd) { return dd <= 8 ? 128 : 64; }
 
-__global__ void tile_jobs_kernel(const TravArgs a, int m, int tq, int *__restrict__ jobs)
+__global__ void tile_jobs_kernel(const TravArgs a, int m, int tq, long long *__restrict__ jobs)
 {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j < m) {
+        EdgeK none;
+        none.hi = ~0ull;
+        none.lo = ~0ull;
+        a.pair_best[j] = none;
         int P = a.big[j].x, Q = a.big[j].y;
         int sp = nsize(a, P), sq = nsize(a, Q);
         int big = max(sp, sq), small = min(sp, sq);
-        jobs[j] = ((big + kTileA - 1) / kTileA) * ((small + tq - 1) / tq);
+        jobs[j] = (long long)((big + kTileA - 1) / kTileA) * ((small + tq - 1) / tq);
     }
 }
 
-__device__ inline int find_job_pair(const int *__restrict__ off, int m, int u)
+// ---------------------------------------------------------- pruned BCCP of huge pairs
+// A huge well-separated pair (A,B) is split into work items of 32 consecutive points of its larger
+// side A; a warp holds one item (a point per lane) and walks B's subtree depth first, nearer child
+// first.  A node is skipped when, for every lane, its box bound (BCCP*: also the cd bounds)
+// exceeds the pair's current threshold: the band threshold of the pair's screened minimum so far
+// (shared by all items of the pair through a WriteMin on its FP32 bits) and rho_hi (an edge at or
+// above rho_hi would not be emitted).  A subtree of <= 32 points is screened in FP32, its warp
+// minimum lowers the shared bound, and every pair screened at or below the threshold is
+// re-evaluated in FP64 and folded into the pair's 16-byte K-minimum slot.  The K-minimum itself
+// is never skipped: its FP64 weight is below the band threshold of any screened value seen.
+__global__ void huge_items_kernel(const TravArgs a, int m, long long *__restrict__ items)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < m) {
+        int P = a.list[4][j].x, Q = a.list[4][j].y;
+        int4 lp = a.links[P], lq = a.links[Q];
+        int big = max(lp.y - lp.x, lq.y - lq.x);
+        items[j] = (big + 31) / 32;
+        EdgeK none;
+        none.hi = ~0ull;
+        none.lo = ~0ull;
+        a.huge_best[j] = none;
+        a.huge_sbest[j] = 0x7f800000u;   // +inf
+    }
+}
+
+template <int DP, int DM, bool HDB, bool FP64>
+__global__ void __launch_bounds__(256) bccp_dual_kernel(TravArgs a, int m, const long long *__restrict__ item_off,
+                                                        const long long *__restrict__ total_items)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    int *stk = a.stack + (size_t)gw * a.stack_cap;
+    const long long TI = *total_items;
+    const int n = a.n, d = a.d;
+    const float rho_hi_f = __double2float_ru(a.rho_hi);
+    unsigned long long n_ev = 0, n_re = 0;
+    for (long long item = gw; item < TI; item += nw) {
+        int lo = 0, hi = m - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (item_off[mid] <= item) lo = mid; else hi = mid - 1;
+        }
+        const int j = lo;
+        const int P = a.list[4][j].x, Q = a.list[4][j].y;
+        const int4 lp = a.links[P], lq = a.links[Q];
+        const bool pbig = lp.y - lp.x >= lq.y - lq.x;
+        const int Aend = pbig ? lp.y : lq.y;
+        const int Broot = pbig ? Q : P;
+        const int i = (pbig ? lp.x : lq.x) + (int)(item - item_off[j]) * 32 + lane;
+        const bool valid = i < Aend;
+        const int ii = valid ? i : (pbig ? lp.x : lq.x);
+        float qx[DM];
+        double qx64[DM];
+#pragma unroll
+        for (int k = 0; k < DM; ++k) {
+            if (k < d) {
+                qx[k] = a.x32[(size_t)k * n + ii];
+                if (FP64) qx64[k] = a.x64[(size_t)k * n + ii];
+            }
+        }
+        const float qcd = HDB ? a.cd32[ii] : 0.f;
+        const int qpid = a.pid[ii];
+        KMin best{~0ull, ~0ull};
+        // threshold (screened scale) and its reload from the shared WriteMin
+        auto cur_thr = [&]() -> float {
+            float t;
+            if (FP64) {
+                unsigned long long hb = ((volatile unsigned long long *)&a.huge_best[j].hi)[0];
+                t = hb == ~0ull ? INFINITY : __double2float_ru(__longlong_as_double((long long)hb));
+            } else {
+                float sb = __uint_as_float(((volatile unsigned *)a.huge_sbest)[j]);
+                t = sb == INFINITY ? INFINITY : screen_threshold(sb, a.eta);
+            }
+            return fminf(t, rho_hi_f);
+        };
+        float thr = cur_thr();
+        int sp = 0;
+        if (lane == 0) stk[0] = Broot;
+        sp = 1;
+        __syncwarp();
+        for (int guard = 0; sp > 0 && guard < 2 * a.N + 2; ++guard) {
+            const int node = stk[sp - 1];
+            __syncwarp();
+            --sp;
+            const int4 ln = a.links[node];
+            const float *bx = a.box + (size_t)node * 2 * DP;
+            float lb = 0.f;
+#pragma unroll
+            for (int k = 0; k < DM; ++k) {
+                if (k < d) {
+                    float g = fmaxf(fmaxf(bx[k] - qx[k], qx[k] - bx[DP + k]), 0.f);
+                    lb = fmaf(g, g, lb);
+                }
+            }
+            float lbw = lower_w2(lb);
+            if (HDB) lbw = fmaxf(lbw, fmaxf(qcd * (1.0f - 1.0f / 4194304.0f), a.meta[node].y));
+            const bool need = valid && lbw <= thr * (1.0f + 1.0f / 131072.0f);
+            if (!__any_sync(0xffffffffu, need)) continue;
+            const int bsz = ln.y - ln.x;
+            if (bsz <= 32) {
+                const int b0 = ln.x;
+                float px[DM];
+                double px64[DM];
+#pragma unroll
+                for (int k = 0; k < DM; ++k) {
+                    if (k < d) {
+                        px[k] = lane < bsz ? a.x32[(size_t)k * n + b0 + lane] : 0.f;
+                        if (FP64) px64[k] = lane < bsz ? a.x64[(size_t)k * n + b0 + lane] : 0.0;
+                    }
+                }
+                const float pcd = (HDB && lane < bsz) ? a.cd32[b0 + lane] : 0.f;
+                const int ppid = lane < bsz ? a.pid[b0 + lane] : 0;
+                if (FP64) {
+                    for (int p = 0; p < bsz; ++p) {
+                        double acc = 0.0;
+#pragma unroll
+                        for (int k = 0; k < DM; ++k) {
+                            if (k < d) {
+                                double t = __dsub_rn(qx64[k], __shfl_sync(0xffffffffu, px64[k], p));
+                                acc = __dadd_rn(acc, __dmul_rn(t, t));
+                            }
+                        }
+                        int bp = __shfl_sync(0xffffffffu, ppid, p);
+                        if (HDB) acc = fmax(acc, fmax(a.cd64[ii], a.cd64[b0 + p]));
+                        if (valid) kmin_update(best, acc, qpid, bp);
+                    }
+                    n_ev += (unsigned long long)bsz;
+                    // publish this warp's best so other items prune against it
+                    KMin wb = best;
+                    for (int o = 16; o; o >>= 1) {
+                        unsigned long long oh = __shfl_xor_sync(0xffffffffu, wb.hi, o);
+                        unsigned long long ol = __shfl_xor_sync(0xffffffffu, wb.lo, o);
+                        if (oh < wb.hi || (oh == wb.hi && ol < wb.lo)) { wb.hi = oh; wb.lo = ol; }
+                    }
+                    if (lane == 0 && wb.hi != ~0ull) {
+                        EdgeK *slot = a.huge_best + j;
+                        EdgeK mine;
+                        mine.hi = wb.hi;
+                        mine.lo = wb.lo;
+                        EdgeK cur = *slot;
+                        for (int it = 0; it < (1 << 20) && edge_less(mine, cur); ++it) {
+                            EdgeK old = atomicCAS(slot, cur, mine);
+                            if (old.hi == cur.hi && old.lo == cur.lo) break;
+                            cur = old;
+                        }
+                    }
+                    __syncwarp();
+                } else {
+                    float smin = INFINITY;
+                    for (int p = 0; p < bsz; ++p) {
+                        float acc = 0.f;
+#pragma unroll
+                        for (int k = 0; k < DM; ++k) {
+                            if (k < d) {
+                                float t = qx[k] - __shfl_sync(0xffffffffu, px[k], p);
+                                acc = fmaf(t, t, acc);
+                            }
+                        }
+                        if (HDB) acc = fmaxf(acc, fmaxf(qcd, __shfl_sync(0xffffffffu, pcd, p)));
+                        if (valid) smin = fminf(smin, acc);
+                    }
+                    for (int o = 16; o; o >>= 1) smin = fminf(smin, __shfl_xor_sync(0xffffffffu, smin, o));
+                    if (lane == 0 && smin < INFINITY) atomicMin(a.huge_sbest + j, __float_as_uint(smin));
+                    thr = fminf(thr, fminf(screen_threshold(smin, a.eta), rho_hi_f));
+                    thr = fminf(thr, cur_thr());
+                    for (int p = 0; p < bsz; ++p) {
+                        float acc = 0.f;
+#pragma unroll
+                        for (int k = 0; k < DM; ++k) {
+                            if (k < d) {
+                                float t = qx[k] - __shfl_sync(0xffffffffu, px[k], p);
+                                acc = fmaf(t, t, acc);
+                            }
+                        }
+                        if (HDB) acc = fmaxf(acc, fmaxf(qcd, __shfl_sync(0xffffffffu, pcd, p)));
+                        int bp = __shfl_sync(0xffffffffu, ppid, p);
+                        if (valid && acc <= thr) {
+                            kmin_update(best, exact_w2(a, ii, b0 + p, acc), qpid, bp);
+                            ++n_re;
+                        }
+                    }
+                    n_ev += (unsigned long long)bsz;
+                }
+                if (FP64) thr = cur_thr();
+            } else {
+                // push the farther child first so the nearer one is visited next
+                const int c0 = ln.z, c1 = ln.w;
+                const float *b0x = a.box + (size_t)c0 * 2 * DP, *b1x = a.box + (size_t)c1 * 2 * DP;
+                float l0 = 0.f, l1 = 0.f;
+#pragma unroll
+                for (int k = 0; k < DM; ++k) {
+                    if (k < d) {
+                        float g0 = fmaxf(fmaxf(b0x[k] - qx[k], qx[k] - b0x[DP + k]), 0.f);
+                        float g1 = fmaxf(fmaxf(b1x[k] - qx[k], qx[k] - b1x[DP + k]), 0.f);
+                        l0 = fmaf(g0, g0, l0);
+                        l1 = fmaf(g1, g1, l1);
+                    }
+                }
+                if (!valid) { l0 = 0.f; l1 = 0.f; }
+                for (int o = 16; o; o >>= 1) {
+                    l0 += __shfl_xor_sync(0xffffffffu, l0, o);
+                    l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+                }
+                if (sp + 2 > a.stack_cap) break;   // cannot happen: cap = tree depth + 4
+                if (lane == 0) {
+                    stk[sp] = l0 <= l1 ? c1 : c0;
+                    stk[sp + 1] = l0 <= l1 ? c0 : c1;
+                }
+                __syncwarp();
+                sp += 2;
+            }
+        }
+        // fold this item's K-minimum into the pair's slot
+        for (int o = 16; o; o >>= 1) {
+            unsigned long long oh = __shfl_xor_sync(0xffffffffu, best.hi, o);
+            unsigned long long ol = __shfl_xor_sync(0xffffffffu, best.lo, o);
+            if (oh < best.hi || (oh == best.hi && ol < best.lo)) { best.hi = oh; best.lo = ol; }
+        }
+        if (lane == 0 && best.hi != ~0ull) {
+            EdgeK *slot = a.huge_best + j;
+            EdgeK mine;
+            mine.hi = best.hi;
+            mine.lo = best.lo;
+            EdgeK cur = *slot;
+            for (int it = 0; it < (1 << 20) && edge_less(mine, cur); ++it) {
+                EdgeK old = atomicCAS(slot, cur, mine);
+                if (old.hi == cur.hi && old.lo == cur.lo) break;
+                cur = old;
+            }
+        }
+        __syncwarp();
+    }
+    n_ev = warp_sum_u64(n_ev);
+    n_re = warp_sum_u64(n_re);
+    if (lane == 0 && n_ev) {
+        atomicAdd(a.stat + 1, n_ev);
+        atomicAdd(a.stat + 2, n_re);
+        atomicAdd(a.stat + 6, n_ev);
+    }
+}
+
+__global__ void huge_emit_kernel(TravArgs a, int m)
+{
+    const int lane = threadIdx.x & 31;
+    const int limit = (m + 31) & ~31;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j - lane < limit; j += gridDim.x * blockDim.x) {
+        KMin b{~0ull, ~0ull};
+        if (j < m) { b.hi = a.huge_best[j].hi; b.lo = a.huge_best[j].lo; }
+        warp_emit(a, j < m && in_range(a, b), b);
+    }
+}
+
+// one edge per big pair: its K-minimum, when in [rho_lo, rho_hi)
+__global__ void big_emit_kernel(TravArgs a, int m)
+{
+    const int lane = threadIdx.x & 31;
+    const int limit = (m + 31) & ~31;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j - lane < limit; j += gridDim.x * blockDim.x) {
+        KMin b{~0ull, ~0ull};
+        if (j < m) { b.hi = a.pair_best[j].hi; b.lo = a.pair_best[j].lo; }
+        warp_emit(a, j < m && in_range(a, b), b);
+    }
+}
+
+__device__ inline int find_job_pair(const long long *__restrict__ off, int m, long long u)
 {
     int lo = 0, hi = m - 1;
     while (lo < hi) {
@@ -447,8 +717,8 @@ __device__ inline int find_job_pair(const int *__restrict__ off, int m, int u)
 }
 
 template <int D, bool HDB, bool FP64>
-__global__ void __launch_bounds__(256) bccp_tile_kernel(TravArgs a, int m, const int *__restrict__ job_off,
-                                                        const int *__restrict__ total_jobs)
+__global__ void __launch_bounds__(256) bccp_tile_kernel(TravArgs a, int m, const long long *__restrict__ job_off,
+                                                        const long long *__restrict__ total_jobs)
 {
     constexpr int DD = D > 0 ? D : kMaxDim;
     constexpr int kTileQ = tile_q(DD);
@@ -456,18 +726,18 @@ __global__ void __launch_bounds__(256) bccp_tile_kernel(TravArgs a, int m, const
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     float *q = qs[wib];
     const int d = D > 0 ? D : a.d;
-    const int TJ = *total_jobs;
+    const long long TJ = *total_jobs;
     const int n = a.n;
     unsigned long long n_ev = 0, n_re = 0;
-    for (int job = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; job < TJ; job += (gridDim.x * blockDim.x) >> 5) {
+    for (long long job = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; job < TJ; job += (gridDim.x * blockDim.x) >> 5) {
         int j = find_job_pair(job_off, m, job);
         int P = a.big[j].x, Q = a.big[j].y;
         int sp = nsize(a, P), sq = nsize(a, Q);
         int A = sp >= sq ? P : Q, B = sp >= sq ? Q : P;   // A: larger side on the lanes
         int sa = max(sp, sq), sb = min(sp, sq);
         int nbq = (sb + kTileQ - 1) / kTileQ;
-        int r = job - job_off[j];
-        int ta = r / nbq, tb = r % nbq;
+        long long r = job - job_off[j];
+        int ta = (int)(r / nbq), tb = (int)(r % nbq);
         int a0 = a.begin[A] + ta * kTileA, a1 = min(a0 + kTileA, a.begin[A] + sa);
         int b0 = a.begin[B] + tb * kTileQ, b1 = min(b0 + kTileQ, a.begin[B] + sb);
         int nb = b1 - b0;
@@ -566,17 +836,17 @@ __global__ void __launch_bounds__(256) bccp_tile_kernel(TravArgs a, int m, const
             if (oh < best.hi || (oh == best.hi && ol < best.lo)) { best.hi = oh; best.lo = ol; }
         }
         n_ev += (unsigned long long)((a1 - a0) * nb);
-        bool has = lane == 0 && in_range(a, best);
-        int slot = 0;
-        if (has) slot = atomicAdd(a.edge_count, 1);
-        if (has) {
-            if (slot < a.edge_cap) {
-                EdgeK e;
-                e.hi = best.hi;
-                e.lo = best.lo;
-                a.edges[slot] = e;
-            } else {
-                atomicOr(a.overflow, 2u);
+        if (lane == 0 && best.hi != ~0ull) {
+            // WriteMin of the tile's K-minimum into the pair's 16-byte slot
+            EdgeK *slot = a.pair_best + j;
+            EdgeK mine;
+            mine.hi = best.hi;
+            mine.lo = best.lo;
+            EdgeK cur = *slot;
+            for (int it = 0; it < (1 << 20) && edge_less(mine, cur); ++it) {
+                EdgeK old = atomicCAS(slot, cur, mine);
+                if (old.hi == cur.hi && old.lo == cur.lo) break;
+                cur = old;
             }
         }
     }
@@ -627,7 +897,10 @@ int run_traversal(int mode, TravArgs &a, int2 *fa, int2 *fb, int *counters, cuda
         if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;
         if (pinned[1]) { *overflow_out = (unsigned)pinned[1]; return 0; }
         if (pinned[0] == 0) break;
-        if (level > 100000) return WM_EINTERNAL;
+        if (level > 100000) {
+            set_error_detail("WSPD traversal did not terminate within 100000 levels");
+            return WM_EINTERNAL;
+        }
     }
     *overflow_out = 0;
     if (levels_out) *levels_out = level;
@@ -651,13 +924,43 @@ void pack_nodes(const Tree &T, int d, int dp, int4 *links, float4 *meta, float *
            T.diam2, T.cdmin, T.cdmax, links, meta, box);
 }
 
+// Pruned BCCP of the huge pairs (m of them): one warp per 32 points of a pair's larger side.
+int run_bccp_huge(TravArgs &a, int m, long long *items, long long *total, cudaStream_t st, Arena &ar, bool hdb,
+                  bool fp64, int stack_warps)
+{
+    if (m <= 0) return 0;
+    launch(huge_items_kernel, grid_for(m, 256, 1 << 20), 256, 0, st, a, m, items);
+    int rc = scan_exclusive_i64(items, items, m, total, st, ar);
+    if (rc) return rc;
+    const int blocks = stack_warps / 8;
+#define WM_DUAL(DPV, DMV)                                                                                     \
+    do {                                                                                                      \
+        if (fp64) {                                                                                           \
+            if (hdb) launch(bccp_dual_kernel<DPV, DMV, true, true>, blocks, 256, 0, st, a, m, items, total);   \
+            else launch(bccp_dual_kernel<DPV, DMV, false, true>, blocks, 256, 0, st, a, m, items, total);      \
+        } else {                                                                                              \
+            if (hdb) launch(bccp_dual_kernel<DPV, DMV, true, false>, blocks, 256, 0, st, a, m, items, total);  \
+            else launch(bccp_dual_kernel<DPV, DMV, false, false>, blocks, 256, 0, st, a, m, items, total);     \
+        }                                                                                                     \
+    } while (0)
+    if (a.d <= 2) WM_DUAL(4, 2);
+    else if (a.d <= 3) WM_DUAL(4, 3);
+    else if (a.d <= 4) WM_DUAL(4, 4);
+    else if (a.d <= 8) WM_DUAL(8, 8);
+    else WM_DUAL(16, 16);
+#undef WM_DUAL
+    launch(huge_emit_kernel, grid_for(m, 256), 256, 0, st, a, m);
+    return 0;
+}
+
 // BCCP tile kernel over the queued big pairs (m of them, count known on host).
-int run_bccp_tiles(TravArgs &a, int m, int *jobs, int *total, cudaStream_t st, Arena &ar, bool hdb, bool fp64)
+int run_bccp_tiles(TravArgs &a, int m, long long *jobs, long long *total, cudaStream_t st, Arena &ar, bool hdb,
+                   bool fp64)
 {
     if (m <= 0) return 0;
     int dd = (a.d == 2 || a.d == 3 || a.d == 5 || a.d == 7) ? a.d : kMaxDim;
     launch(tile_jobs_kernel, grid_for(m, 256, 1 << 20), 256, 0, st, a, m, tile_q(dd), jobs);
-    int rc = scan_exclusive_i32(jobs, jobs, m, total, st, ar);
+    int rc = scan_exclusive_i64(jobs, jobs, m, total, st, ar);
     if (rc) return rc;
     const int grid = 152 * 4;
 #define WM_TILE(DV)                                                                                     \
@@ -678,6 +981,7 @@ int run_bccp_tiles(TravArgs &a, int m, int *jobs, int *total, cudaStream_t st, A
     default: WM_TILE(0); break;
     }
 #undef WM_TILE
+    launch(big_emit_kernel, grid_for(m, 256), 256, 0, st, a, m);
     return 0;
 }
 

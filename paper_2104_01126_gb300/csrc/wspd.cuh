@@ -27,11 +27,17 @@ struct TravArgs {
     const float4 *meta = nullptr;
     const float *box = nullptr;
     int dp = 4;                         // box stride: d rounded up to 4, 8 or 16
-    // retrieved well-separated pairs by size class: 0 tiny, 1 small, 2 medium, 3 big (tiles)
-    int2 *list[4] = {nullptr, nullptr, nullptr, nullptr};
-    int *list_count = nullptr;          // [4]
-    int list_cap[4] = {0, 0, 0, 0};
+    // retrieved well-separated pairs by size class: 0 tiny, 1 small, 2 medium, 3 big (tiles),
+    // 4 huge (pruned dual-tree BCCP)
+    int2 *list[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int *list_count = nullptr;          // [5]
+    int list_cap[5] = {0, 0, 0, 0, 0};
     int2 *big = nullptr;                // = list[3]
+    EdgeK *pair_best = nullptr;         // per big pair: K-minimum over its tiles
+    EdgeK *huge_best = nullptr;         // per huge pair: K-minimum
+    unsigned *huge_sbest = nullptr;     // per huge pair: screened minimum (FP32 bits), WriteMin
+    int *stack = nullptr;               // per-warp traversal stacks of the dual-tree kernel
+    int stack_cap = 0;
     int *big_count = nullptr;           // = list_count + 3
     EdgeK *edges = nullptr;
     int *edge_count = nullptr;
@@ -44,8 +50,11 @@ struct TravArgs {
 void launch_comp_labels(const Tree &T, const Points &P, int *uf, cudaStream_t st);
 int run_traversal(int mode, TravArgs &a, int2 *fa, int2 *fb, int *counters, cudaStream_t st, int *pinned,
                   unsigned *overflow_out, int *levels_out);
-int run_bccp_tiles(TravArgs &a, int m, int *jobs, int *total, cudaStream_t st, Arena &ar, bool hdb, bool fp64);
+int run_bccp_tiles(TravArgs &a, int m, long long *jobs, long long *total, cudaStream_t st, Arena &ar, bool hdb,
+                   bool fp64);
 void run_bccp_groups(TravArgs &a, const int *counts_host, cudaStream_t st);
+int run_bccp_huge(TravArgs &a, int m, long long *items, long long *total, cudaStream_t st, Arena &ar, bool hdb,
+                  bool fp64, int stack_warps);
 void pack_nodes(const Tree &T, int d, int dp, int4 *links, float4 *meta, float *box, cudaStream_t st);
 
 }  // namespace wm
