@@ -116,6 +116,7 @@ typedef struct {
     int64_t getpairs_visits;       /* node pairs examined by the GetPairs traversals     */
     int64_t getrho_visits;         /* node pairs examined by the GetRho traversals       */
     int64_t bccp_dual_evals;       /* distance evaluations in the pruned BCCP of huge pairs */
+    int64_t rho_shrinks;           /* times a round lowered rho_hi to fit its edge batch  */
 } wm_stats;
 
 /* Options.  A zero-initialised struct (or NULL) gives the defaults. */

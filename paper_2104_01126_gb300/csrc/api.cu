@@ -1,6 +1,7 @@
 // api.cu -- the C ABI (include/wspdmst.h) and the host orchestration of the MemoGFK rounds
 // (Algorithm 3).  Every step of the computation runs in the kernels of this library; the host
 // only sequences launches and reads back the few scalars that steer the rounds (rho_hi, counts).
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -60,21 +61,27 @@ struct DevCache {
 static DevCache g_cache[64];
 
 struct Caps {
-    long long frontier, big, edges, pairs;
+    long long chunk;        // pairs popped per traversal step (= capacity of each pair list)
+    long long edges;        // candidate edges per round
+    int frontier_scale;     // multiplier of the stack bound (grown after an overflow)
+    long long extra_bytes;  // additional arena bytes (grown after the arena ran out)
 };
 
 static size_t estimate_bytes(long long n, int d, int min_pts, const Caps &c)
 {
-    long long N = 2 * n;
+    const long long N = 2 * n;
+    const long long depth = 64;   // typical; the stack below is sized from the real depth
+    const int dp = d <= 4 ? 4 : d <= 8 ? 8 : 16;
     size_t b = 0;
     b += (size_t)n * d * 8;                 // device copy of the input
     b += (size_t)n * d * 12 * 2;            // points + build scratch
     b += (size_t)n * 16;                    // pid, pos, uf, R
     b += (size_t)N * (8 * d + 48);          // tree arrays (+ build scratch counters)
     b += (size_t)n * 8;                     // small lists
-    b += (size_t)c.frontier * 8 * 2;
-    b += (size_t)c.big * 64 + (size_t)c.pairs * 8 * 3 + (size_t)152 * 64 * 4 * 96;
-    b += (size_t)N * (32 + 8 * (d <= 4 ? 4 : d <= 8 ? 8 : 16));   // packed node records
+    b += (size_t)N * (32 + 8 * dp);         // packed node records
+    b += (size_t)((N / 2 + 2 + (2 * depth + 4) * 2 * c.chunk) * c.frontier_scale + 2 * c.chunk) * 8;   // stack
+    b += (size_t)c.chunk * (5 * 8 + 4 * 16 + 4);                                                       // lists, slots
+    b += (size_t)152 * 64 * (depth + 4) * 4;                                                           // dual stacks
     b += (size_t)c.edges * 16 * 3 + (size_t)c.edges * 24;   // batch, filtered, sort tmp, kruskal
     b += (size_t)n * 16 * 2;                // output tree + conversion
     if (min_pts > 0) {
@@ -83,16 +90,16 @@ static size_t estimate_bytes(long long n, int d, int min_pts, const Caps &c)
         b += (size_t)n * kk * 16 * 2;                   // repair edges + sort tmp
         b += (size_t)n * 160;                           // dendrogram / Euler tour scratch
     }
-    return b + (64u << 20);
+    return b + (64u << 20) + (size_t)c.extra_bytes;
 }
 
 static Caps default_caps(long long n, int min_pts)
 {
     Caps c;
-    c.frontier = 8 * n + (1 << 20);
-    c.big = 2 * n + (1 << 18);
+    c.chunk = std::min<long long>(1 << 21, std::max<long long>(1 << 16, n));
     c.edges = 4 * n + (1 << 20) + (min_pts > 0 ? (long long)n * (min_pts + 16) : 0);
-    c.pairs = 4 * n + (1 << 20);
+    c.frontier_scale = 1;
+    c.extra_bytes = 0;
     return c;
 }
 
@@ -225,15 +232,21 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     *overflow_bits = 0;
     if (n <= 1) return 0;
     size_t mark = ar.off;
-    int2 *fa = ar.get<int2>(caps.frontier), *fb = ar.get<int2>(caps.frontier);
-    int2 *big = ar.get<int2>(caps.big);
-    int2 *plist0 = ar.get<int2>(caps.pairs), *plist1 = ar.get<int2>(caps.pairs), *plist2 = ar.get<int2>(caps.pairs);
-    long long *jobs = ar.get<long long>(caps.big + 1);
-    EdgeK *pair_best = ar.get<EdgeK>(caps.big + 1);
-    int2 *huge = ar.get<int2>(caps.big);
-    EdgeK *huge_best = ar.get<EdgeK>(caps.big + 1);
-    unsigned *huge_sbest = ar.get<unsigned>(caps.big + 1);
-    long long *huge_items = ar.get<long long>(caps.big + 1);
+    const int chunk = (int)caps.chunk;
+    const long long fcap = ((long long)T.N / 2 + 2 + (2LL * T.depth + 4) * 2 * chunk) * caps.frontier_scale;
+    if (fcap > 0x7fffffffLL) { set_detail("WSPD stack capacity exceeds 2^31 pairs%s", ""); return WM_ENOMEM; }
+    int2 *stack = ar.get<int2>(fcap), *xbuf = ar.get<int2>(2LL * chunk);
+    // pair lists hold kListChunks chunks' worth of retrieved pairs; they are flushed (BCCP) when
+    // one of them could overflow within the next poll interval, and when the traversal ends
+    const int kPoll = 4, kListChunks = 8;
+    const long long lcap = (long long)kListChunks * chunk;
+    int2 *lists[5];
+    for (int c = 0; c < 5; ++c) lists[c] = ar.get<int2>(lcap);
+    long long *jobs = ar.get<long long>(lcap + 1);
+    EdgeK *pair_best = ar.get<EdgeK>(lcap + 1);
+    EdgeK *huge_best = ar.get<EdgeK>(lcap + 1);
+    unsigned *huge_sbest = ar.get<unsigned>(lcap + 1);
+    long long *huge_items = ar.get<long long>(lcap + 1);
     const int stack_warps = 152 * 8 * 8;   // warps of the dual-tree kernel (grid-stride)
     int *dual_stack = ar.get<int>((size_t)stack_warps * (T.depth + 4));
     const int dp = P.d <= 4 ? 4 : P.d <= 8 ? 8 : 16;
@@ -241,11 +254,15 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     float4 *meta = ar.get<float4>(T.N);
     float *box = ar.get<float>((size_t)T.N * 2 * dp);
     EdgeK *batch = ar.get<EdgeK>(caps.edges), *filt = ar.get<EdgeK>(caps.edges), *tmp = ar.get<EdgeK>(caps.edges);
-    int *cnts = ar.get<int>(32);   // [10..14] pair-list counts, [16..17] and [18..19] 64-bit job totals
+    int *cnts = ar.get<int>(64);
     double *rho = ar.get<double>(2);
+    double *samples = ar.get<double>(4096);
     unsigned *ovf = ar.get<unsigned>(2);
     unsigned long long *stat = ar.get<unsigned long long>(8);
     if (ar.failed) return WM_ENOMEM;
+    // counters: [0] stack top, [1] children count, [2..6] pair-list counts, [7] edge count,
+    // [8] filtered count, [9] repair lower bound, [10..11] / [12..13] 64-bit job totals
+    int *top = cnts + 0, *xcount = cnts + 1, *lcount = cnts + 2, *ecount = cnts + 7;
     {
         Tree T2 = T;
         if (hdb) { T2.cdmin = hdb->cdmin; T2.cdmax = hdb->cdmax; }
@@ -253,6 +270,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     }
     WM_CK(cudaMemsetAsync(stat, 0, 8 * sizeof(unsigned long long), st));
     WM_CK(cudaMemsetAsync(ovf, 0, 2 * sizeof(unsigned), st));
+    WM_CK(cudaMemsetAsync(cnts, 0, 64 * sizeof(int), st));
 
     TravArgs a;
     a.N = T.N; a.n = n; a.d = P.d;
@@ -264,19 +282,19 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     if (hdb) {
         a.cdmin = hdb->cdmin; a.cdmax = hdb->cdmax; a.cd32 = hdb->cd32; a.cd64 = hdb->cd64;
     }
-    a.frontier_cap = (int)caps.frontier;
+    a.frontier_cap = (int)fcap;
     a.links = links; a.meta = meta; a.box = box; a.dp = dp;
-    a.list[0] = plist0; a.list[1] = plist1; a.list[2] = plist2; a.list[3] = big; a.list[4] = huge;
-    a.list_cap[0] = a.list_cap[1] = a.list_cap[2] = (int)caps.pairs; a.list_cap[3] = a.list_cap[4] = (int)caps.big;
+    for (int c = 0; c < 5; ++c) { a.list[c] = lists[c]; a.list_cap[c] = (int)lcap; }
+    a.list_count = lcount;
+    a.big = lists[3]; a.big_count = lcount + 3;
+    a.pair_best = pair_best;
     a.huge_best = huge_best; a.huge_sbest = huge_sbest;
     a.stack = dual_stack; a.stack_cap = T.depth + 4;
-    a.list_count = cnts + 10;
-    a.big = big; a.big_count = cnts + 13;
-    a.pair_best = pair_best;
-    a.edges = batch; a.edge_count = cnts + 5; a.edge_cap = (int)caps.edges;
+    a.edges = batch; a.edge_count = ecount; a.edge_cap = (int)caps.edges;
     a.overflow = ovf;
     a.stat = stat;
     a.rho_out = rho;
+    EdgeK *spare = filt;   // second edge buffer for compaction when rho_hi shrinks
 
     int nE = 0;
     double rho_lo = 0.0;
@@ -292,98 +310,120 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         WM_CK(cudaMemcpyAsync(rho, &inf, sizeof(double), cudaMemcpyHostToDevice, st));
         a.beta = (int)std::min<long long>(beta, 0x7fffffff);
         unsigned ob = 0;
-        WM_TRY(run_traversal(0, a, fa, fb, cnts, st, C.pin, &ob, nullptr));
+        WM_TRY(run_traversal(0, a, stack, xbuf, cnts, chunk, st, C.pin, &ob, nullptr));
         if (ob) { *overflow_bits = ob; return 0; }
         double rho_hi;
         WM_CK(cudaMemcpy(&rho_hi, rho, sizeof(double), cudaMemcpyDeviceToHost));
         if (rho_hi < rho_lo) rho_hi = rho_lo;
-        // ---- GetPairs (+ in-place BCCP of small pairs)
+        // ---- GetPairs in chunks; the retrieved pairs of every chunk get their BCCP right away
         a.rho_lo = rho_lo;
         a.rho_hi = rho_hi;
-        WM_CK(cudaMemsetAsync(cnts + 4, 0, 2 * sizeof(int), st));
-        WM_CK(cudaMemsetAsync(cnts + 10, 0, 5 * sizeof(int), st));
-        cudaEvent_t g0 = nullptr, g1 = nullptr;
-        if (C.timing) {
-            cudaEventCreate(&g0);
-            cudaEventCreate(&g1);
-            cudaEventRecord(g0, st);
+        a.edges = batch;
+        spare = filt;
+        WM_CK(cudaMemsetAsync(cnts + 2, 0, 6 * sizeof(int), st));
+        traversal_init(1, a, stack, top, xcount, st);
+        std::vector<cudaEvent_t> evs;   // (start, end) of traversal runs and BCCP flushes, summed per round
+        auto mark_event = [&]() {
+            if (!C.timing) return;
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            cudaEventRecord(e, st);
+            evs.push_back(e);
+        };
+        std::vector<int> ev_kind;        // 0 = traversal interval, 1 = BCCP interval
+        int steps = 0;
+        mark_event();
+        while (true) {
+            for (int b = 0; b < kPoll; ++b, ++steps) traversal_step(1, a, stack, top, xbuf, xcount, chunk, st);
+            WM_CK(cudaMemcpyAsync(C.pin, cnts, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
+            WM_CK(cudaMemcpyAsync(C.pin + 8, ovf, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+            WM_CK(cudaStreamSynchronize(st));
+            if (C.pin[8]) { *overflow_bits = (unsigned)C.pin[8]; return 0; }
+            const int tp = C.pin[0];
+            int lc[5] = {C.pin[2], C.pin[3], C.pin[4], C.pin[5], C.pin[6]};
+            int e = C.pin[7];
+            bool flush = tp == 0;
+            for (int c = 0; c < 5; ++c) flush = flush || lc[c] > lcap - (long long)kPoll * chunk;
+            if (!flush) continue;
+            mark_event();
+            ev_kind.push_back(0);
+            const long long incoming = (long long)lc[0] + lc[1] + lc[2] + lc[3] + lc[4];
+            // keep room for one edge per retrieved pair: lower rho_hi if the batch is filling up
+            for (int guard = 0; e + incoming > caps.edges && guard < 8; ++guard) {
+                const int k = std::min(e, 4096);
+                sample_w2(a.edges, e, k, samples, st);
+                WM_CK(cudaMemcpyAsync(C.pin + 64, samples, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+                WM_CK(cudaStreamSynchronize(st));
+                std::vector<double> sw((double *)(C.pin + 64), (double *)(C.pin + 64) + k);
+                std::sort(sw.begin(), sw.end());
+                double nh = sw[(size_t)(k * 0.4)];
+                if (!(nh > rho_lo)) nh = std::nextafter(rho_lo, inf);
+                if (!(nh < a.rho_hi)) break;   // cannot shrink further
+                keep_below(a.edges, e, nh, spare, ecount, st);
+                std::swap(a.edges, spare);
+                a.rho_hi = rho_hi = nh;
+                WM_CK(cudaMemcpyAsync(C.pin, ecount, sizeof(int), cudaMemcpyDeviceToHost, st));
+                WM_CK(cudaStreamSynchronize(st));
+                e = C.pin[0];
+                C.stats.rho_shrinks += 1;
+            }
+            if (e + incoming > caps.edges) { *overflow_bits = 2; return 0; }
+            // BCCP of the retrieved pairs
+            run_bccp_groups(a, lc, st);
+            WM_TRY(run_bccp_tiles(a, lc[3], jobs, (long long *)(cnts + 10), st, ar, hdb != nullptr, a.fp64 != 0));
+            WM_TRY(run_bccp_huge(a, lc[4], huge_items, (long long *)(cnts + 12), st, ar, hdb != nullptr, a.fp64 != 0,
+                                 stack_warps));
+            WM_CK(cudaMemsetAsync(lcount, 0, 5 * sizeof(int), st));
+            if (lc[3] > 0 || lc[4] > 0) C.stats.tile_launches += 1;
+            mark_event();
+            ev_kind.push_back(1);
+            if (tp == 0) break;
+            if (steps > 10000000) { set_detail("WSPD GetPairs traversal did not terminate%s", ""); return WM_EINTERNAL; }
         }
-        int glev = 0;
-        WM_TRY(run_traversal(1, a, fa, fb, cnts, st, C.pin, &ob, &glev));
-        if (C.timing) {
-            cudaEventRecord(g1, st);
-            cudaEventSynchronize(g1);
-            C.stats.ms_getpairs += C.event_ms(g0, g1);
-            cudaEventDestroy(g0);
-            cudaEventDestroy(g1);
-        }
-        C.stats.getpairs_launches += glev;
-        if (ob) { *overflow_bits = ob; return 0; }
-        WM_CK(cudaMemcpyAsync(C.pin, cnts + 10, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
-        WM_CK(cudaStreamSynchronize(st));
-        int lcounts[5] = {C.pin[0], C.pin[1], C.pin[2], C.pin[3], C.pin[4]};
-        int mbig = lcounts[3];
-        // BCCP of the tiny / small / medium retrieved pairs
-        run_bccp_groups(a, lcounts, st);
-        C.stats.ms_wspd += tw.ms();
-        // ---- BCCP tiles over the queued larger pairs
-        Timer tb;
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (C.timing) {
-            cudaEventCreate(&e0);
-            cudaEventCreate(&e1);
-            cudaEventRecord(e0, st);
-        }
-        WM_TRY(run_bccp_tiles(a, mbig, jobs, (long long *)(cnts + 16), st, ar, hdb != nullptr, a.fp64 != 0));
-        WM_TRY(run_bccp_huge(a, lcounts[4], huge_items, (long long *)(cnts + 18), st, ar, hdb != nullptr, a.fp64 != 0,
-                             stack_warps));
-        if (C.timing) cudaEventRecord(e1, st);
-        WM_CK(cudaMemcpyAsync(C.pin, cnts + 5, sizeof(int), cudaMemcpyDeviceToHost, st));
+        WM_CK(cudaMemcpyAsync(C.pin, ecount, sizeof(int), cudaMemcpyDeviceToHost, st));
         WM_CK(cudaMemcpyAsync(C.pin + 1, ovf, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
         WM_CK(cudaStreamSynchronize(st));
-        if (mbig > 0 || lcounts[4] > 0) {
-            double ms = C.timing ? C.event_ms(e0, e1) : tb.ms();
-            C.stats.ms_bccp += ms;
-            C.stats.ms_tile_kernel += ms;
-            C.stats.tile_launches += 1;
-        }
-        if (C.timing) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-        }
         if (C.pin[1]) { *overflow_bits = (unsigned)C.pin[1]; return 0; }
         int m = C.pin[0];
+        for (size_t k = 0; k + 1 < evs.size(); ++k) {
+            double ms = C.event_ms(evs[k], evs[k + 1]);
+            if (ev_kind[k] == 0) C.stats.ms_getpairs += ms;
+            else { C.stats.ms_bccp += ms; C.stats.ms_tile_kernel += ms; }
+        }
+        for (cudaEvent_t e : evs) cudaEventDestroy(e);
+        C.stats.getpairs_launches += steps;
+        C.stats.ms_wspd += tw.ms();
         // ---- HDBSCAN*: repair edges of this weight range join the batch
         if (hdb && hdb->nrep > rpos) {
             int hi_idx;
             if (rho_hi == inf) {
                 hi_idx = hdb->nrep;
             } else {
-                launch(lower_bound_w2_kernel, 1, 32, 0, st, hdb->rep, hdb->nrep, rho_hi, cnts + 7);
-                WM_CK(cudaMemcpyAsync(C.pin, cnts + 7, sizeof(int), cudaMemcpyDeviceToHost, st));
+                launch(lower_bound_w2_kernel, 1, 32, 0, st, hdb->rep, hdb->nrep, rho_hi, cnts + 9);
+                WM_CK(cudaMemcpyAsync(C.pin, cnts + 9, sizeof(int), cudaMemcpyDeviceToHost, st));
                 WM_CK(cudaStreamSynchronize(st));
                 hi_idx = C.pin[0];
             }
             int take = hi_idx - rpos;
             if (take > 0) {
                 if ((long long)m + take > caps.edges) { *overflow_bits = 2; return 0; }
-                launch(copy_edges_kernel, grid_for(take, 256), 256, 0, st, hdb->rep + rpos, take, batch + m);
+                launch(copy_edges_kernel, grid_for(take, 256), 256, 0, st, hdb->rep + rpos, take, a.edges + m);
                 m += take;
                 rpos = hi_idx;
             }
         }
-        C.stats.ms_bccp += 0.0;
         // ---- sort + Kruskal
         Timer tk;
         int accepted = 0;
         if (m > 0) {
-            WM_TRY(filter_connected(batch, m, uf, filt, cnts + 8, st));
+            EdgeK *fout = a.edges == batch ? filt : batch;
+            WM_TRY(filter_connected(a.edges, m, uf, fout, cnts + 8, st));
             WM_CK(cudaMemcpyAsync(C.pin, cnts + 8, sizeof(int), cudaMemcpyDeviceToHost, st));
             WM_CK(cudaStreamSynchronize(st));
             int mf = C.pin[0];
             C.stats.candidate_edges += mf;
-            EdgeK *sorted = filt;
-            WM_TRY(radix_sort_edges(filt, tmp, mf, st, ar, &sorted, C.pin + 4096));
+            EdgeK *sorted = fout;
+            WM_TRY(radix_sort_edges(fout, tmp, mf, st, ar, &sorted, C.pin + 4096));
             WM_TRY(batch_kruskal(sorted, mf, n, uf, R, E_out, nE, &accepted, ar, st, C.pin));
         }
         C.stats.ms_kruskal += tk.ms();
@@ -400,8 +440,8 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     unsigned long long hs[8];
     memcpy(hs, C.pin, sizeof hs);
     C.stats.getpairs_visits = (int64_t)hs[4];
-    C.stats.bccp_dual_evals = (int64_t)hs[6];
     C.stats.getrho_visits = (int64_t)hs[5];
+    C.stats.bccp_dual_evals = (int64_t)hs[6];
     C.stats.rounds = rounds;
     C.stats.pairs_retrieved = (int64_t)hs[0];
     C.stats.bccp_evals = (int64_t)hs[1];
@@ -527,6 +567,11 @@ static int run_call(const wm_opts *opts, long long n, int d, int min_pts, Body b
         rc = body(C, ctx, caps, &ovf);
         if (rc == 0 && C.ar.failed) rc = WM_ENOMEM;
         if (rc == WM_ENOMEM && !user_ws && !C.ar.failed) break;
+        if (rc == WM_ENOMEM && !user_ws && C.ar.failed) {
+            // the arena estimate was short (deep tree, many repair edges): grow it and retry
+            caps.extra_bytes += std::max<long long>(256LL << 20, (long long)(need / 2));
+            continue;
+        }
         if (rc == 0 && ovf == 0) break;
         if (rc == WM_ENOMEM && user_ws) {
             set_detail("caller workspace too small%s (%lld bytes given)", "", (long long)C.ar.cap);
@@ -535,10 +580,8 @@ static int run_call(const wm_opts *opts, long long n, int d, int min_pts, Body b
         if (rc && rc != WM_ENOMEM) break;
         ovf_seen |= ovf;
         // grow whichever capacity overflowed and start over
-        if (ovf & 1u) caps.frontier *= 2;
+        if (ovf & 1u) caps.frontier_scale *= 2;
         if (ovf & 2u) caps.edges *= 2;
-        if (ovf & 4u) { caps.big *= 2; caps.pairs *= 2; }
-        if (rc == WM_ENOMEM) { caps.frontier += caps.frontier / 2; }
         if (user_ws && ovf) { rc = WM_ENOMEM; set_detail("caller workspace too small for the WSPD frontier%s", ""); break; }
         rc = WM_ENOMEM;
     }
@@ -803,18 +846,13 @@ extern "C" int wm_emst_noalloc(const void *pts, int64_t n, int32_t d, int32_t dt
     C.pin = g_noalloc_host;
     C.ar.base = (char *)nd.scratch;
     C.ar.cap = WM_NOALLOC_SCRATCH_BYTES;
-    // Capacities: what the fixed structures leave of the array, split between the traversal
-    // frontier (30%), the three small-pair lists (10% each), big pairs (5%) and edge batches (35%).
-    const long long N2 = 2 * n;
-    const int dp = d <= 4 ? 4 : d <= 8 ? 8 : 16;
-    long long fixed = n * d * 8 + n * d * 12 + 8 * n + N2 * (8LL * d + 40) + N2 * (32 + 8LL * dp) + 24 * n + (2 << 20);
-    long long rest = (long long)WM_NOALLOC_SCRATCH_BYTES - fixed;
-    if (rest < (4 << 20)) rest = 4 << 20;
+    // Capacities sized for WM_NOALLOC_MAX_POINTS: traversal chunks of 4096 pairs and edge batches of
+    // 4n + 65536; WSPD stack and pair lists follow from the chunk (see memogfk).
     Caps caps;
-    caps.frontier = rest * 30 / 100 / 16;
-    caps.pairs = rest * 10 / 100 / 8;
-    caps.big = rest * 5 / 100 / 64;
-    caps.edges = rest * 35 / 100 / 72;
+    caps.chunk = 4096;
+    caps.edges = 4 * n + 65536;
+    caps.frontier_scale = 1;
+    caps.extra_bytes = 0;
     EmstCtx c{pts, n, d, dtype, layout, out_edges, out_total_weight};
     unsigned ovf = 0;
     int rc = emst_body(C, &c, caps, &ovf);

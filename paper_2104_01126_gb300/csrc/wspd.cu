@@ -202,12 +202,13 @@ constexpr long long kBigMax = 65536; // warp tiles (brute force); larger pairs: 
 
 // One level of FindPair.  MODE 0 = GetRho, MODE 1 = GetPairs (classifies retrieved pairs).
 template <int MODE, int DP>
-__global__ void __launch_bounds__(256) findpair_level_kernel(TravArgs a, const int2 *__restrict__ in,
-                                                             const int *__restrict__ in_count, int2 *__restrict__ out,
-                                                             int *out_count, int *zero_count)
+__global__ void __launch_bounds__(256) findpair_level_kernel(TravArgs a, const int2 *__restrict__ stack,
+                                                             const int *__restrict__ top, int chunk,
+                                                             int2 *__restrict__ out, int *out_count)
 {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *zero_count = 0;
-    const int m = *in_count;
+    const int tp = *top;
+    const int m = tp < chunk ? tp : chunk;
+    const int2 *__restrict__ in = stack + (tp - m);
     const int stride = gridDim.x * blockDim.x;
     const int limit = (m + 31) & ~31;   // whole warps iterate together
     const int lane = threadIdx.x & 31;
@@ -258,10 +259,7 @@ __global__ void __launch_bounds__(256) findpair_level_kernel(TravArgs a, const i
             }
         }
         int slot = warp_append(out_count, push);
-        if (push) {
-            if (slot + 2 <= a.frontier_cap) { out[slot] = c0; out[slot + 1] = c1; }
-            else atomicOr(a.overflow, 1u);
-        }
+        if (push) { out[slot] = c0; out[slot + 1] = c1; }   // out holds 2 * chunk pairs
         if (MODE == 0) {
             for (int o = 16; o; o >>= 1) rho_cand = fmin(rho_cand, __shfl_xor_sync(0xffffffffu, rho_cand, o));
             if (lane == 0 && rho_cand < INFINITY) atomicMinPosD(a.rho_out, rho_cand);
@@ -869,42 +867,114 @@ void launch_comp_labels(const Tree &T, const Points &P, int *uf, cudaStream_t st
                                                          T.comp, T.arrive);
 }
 
-// Runs one FindPair traversal to exhaustion.  Returns 0, or WM_ENOMEM-like codes; *overflow_out
-// receives the overflow bits (frontier 1, edges 2, big pairs 4).
-int run_traversal(int mode, TravArgs &a, int2 *fa, int2 *fb, int *counters, cudaStream_t st, int *pinned,
-                  unsigned *overflow_out, int *levels_out)
+// ----------------------------------------------------------- bounded-memory traversal
+// The frontier is a stack of node pairs.  One step pops the top min(top, chunk) pairs, expands
+// them (children into a scratch buffer of 2*chunk pairs) and pushes the children back: depth
+// first in chunks, so the stack never holds more than the initial pairs plus about 2*chunk per
+// recursion level.
+__global__ void stack_push_kernel(int2 *__restrict__ stack, const int *__restrict__ top, int chunk,
+                                  const int2 *__restrict__ x, const int *__restrict__ xcount, int cap, unsigned *overflow)
 {
-    cudaMemsetAsync(counters, 0, 3 * sizeof(int), st);
-    launch(frontier_init_kernel, grid_for(a.N, 256), 256, 0, st, a, mode, fa, counters + 0);
-    int level = 0;
-    const int grid = 152 * 8;
-    while (true) {
-        for (int b = 0; b < 6; ++b, ++level) {
-            int2 *in = (level & 1) ? fb : fa, *out = (level & 1) ? fa : fb;
-            int *cin = counters + (level % 3), *cout = counters + ((level + 1) % 3), *cz = counters + ((level + 2) % 3);
-#define WM_FP(DPV)                                                                          \
-    do {                                                                                    \
-        if (mode == 0) launch(findpair_level_kernel<0, DPV>, grid, 256, 0, st, a, in, cin, out, cout, cz); \
-        else launch(findpair_level_kernel<1, DPV>, grid, 256, 0, st, a, in, cin, out, cout, cz);           \
+    const int tp = *top;
+    const int base = tp - (tp < chunk ? tp : chunk);
+    const int m = *xcount;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        if (base + i < cap) stack[base + i] = x[i];
+        else atomicOr(overflow, 1u);
+    }
+}
+
+__global__ void stack_top_kernel(int *top, int chunk, int *xcount, int cap)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int tp = *top;
+        int base = tp - (tp < chunk ? tp : chunk);
+        int nt = base + *xcount;
+        *top = nt < cap ? nt : cap;
+        *xcount = 0;
+    }
+}
+
+void traversal_init(int mode, TravArgs &a, int2 *stack, int *top, int *xcount, cudaStream_t st)
+{
+    cudaMemsetAsync(top, 0, sizeof(int), st);
+    cudaMemsetAsync(xcount, 0, sizeof(int), st);
+    launch(frontier_init_kernel, grid_for(a.N, 256), 256, 0, st, a, mode, stack, top);
+}
+
+void traversal_step(int mode, TravArgs &a, int2 *stack, int *top, int2 *x, int *xcount, int chunk, cudaStream_t st)
+{
+    const int grid = grid_for((long long)chunk, 256, 152 * 8);
+#define WM_FP(DPV)                                                                                          \
+    do {                                                                                                    \
+        if (mode == 0) launch(findpair_level_kernel<0, DPV>, grid, 256, 0, st, a, stack, top, chunk, x, xcount); \
+        else launch(findpair_level_kernel<1, DPV>, grid, 256, 0, st, a, stack, top, chunk, x, xcount);           \
     } while (0)
-            if (a.dp == 4) WM_FP(4);
-            else if (a.dp == 8) WM_FP(8);
-            else WM_FP(16);
+    if (a.dp == 4) WM_FP(4);
+    else if (a.dp == 8) WM_FP(8);
+    else WM_FP(16);
 #undef WM_FP
-        }
-        cudaMemcpyAsync(pinned, counters + (level % 3), sizeof(int), cudaMemcpyDeviceToHost, st);
+    launch(stack_push_kernel, grid_for((long long)2 * chunk, 256), 256, 0, st, stack, top, chunk, x, xcount,
+           a.frontier_cap, a.overflow);
+    launch(stack_top_kernel, 1, 32, 0, st, top, chunk, xcount, a.frontier_cap);
+}
+
+// GetRho: the whole traversal, polling emptiness every 4 steps.
+int run_traversal(int mode, TravArgs &a, int2 *stack, int2 *x, int *counters, int chunk, cudaStream_t st, int *pinned,
+                  unsigned *overflow_out, int *steps_out)
+{
+    int *top = counters, *xcount = counters + 1;
+    traversal_init(mode, a, stack, top, xcount, st);
+    int steps = 0;
+    while (true) {
+        for (int b = 0; b < 4; ++b, ++steps) traversal_step(mode, a, stack, top, x, xcount, chunk, st);
+        cudaMemcpyAsync(pinned, top, sizeof(int), cudaMemcpyDeviceToHost, st);
         cudaMemcpyAsync(pinned + 1, a.overflow, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
         if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;
         if (pinned[1]) { *overflow_out = (unsigned)pinned[1]; return 0; }
         if (pinned[0] == 0) break;
-        if (level > 100000) {
-            set_error_detail("WSPD traversal did not terminate within 100000 levels");
+        if (steps > 10000000) {
+            set_error_detail("WSPD traversal did not terminate");
             return WM_EINTERNAL;
         }
     }
     *overflow_out = 0;
-    if (levels_out) *levels_out = level;
+    if (steps_out) *steps_out = steps;
     return 0;
+}
+
+// ------------------------------------------------------------- shrinking rho_hi in a round
+__global__ void sample_w2_kernel(const EdgeK *__restrict__ e, int m, int k, double *__restrict__ out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x)
+        out[i] = edge_w2(e[(long long)i * m / k]);
+}
+
+__global__ void keep_below_kernel(const EdgeK *__restrict__ in, int m, double bound, EdgeK *__restrict__ out, int *count)
+{
+    const int lane = threadIdx.x & 31;
+    const int limit = (m + 31) & ~31;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t - lane < limit; t += gridDim.x * blockDim.x) {
+        bool keep = false;
+        EdgeK e;
+        if (t < m) { e = in[t]; keep = edge_w2(e) < bound; }
+        unsigned b = __ballot_sync(0xffffffffu, keep);
+        int base = 0;
+        if (lane == 0 && b) base = atomicAdd(count, __popc(b));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (keep) out[base + __popc(b & lanemask_lt())] = e;
+    }
+}
+
+void sample_w2(const EdgeK *e, int m, int k, double *out, cudaStream_t st)
+{
+    launch(sample_w2_kernel, grid_for(k, 256), 256, 0, st, e, m, k, out);
+}
+
+void keep_below(const EdgeK *in, int m, double bound, EdgeK *out, int *count, cudaStream_t st)
+{
+    cudaMemsetAsync(count, 0, sizeof(int), st);
+    if (m > 0) launch(keep_below_kernel, grid_for(m, 256), 256, 0, st, in, m, bound, out, count);
 }
 
 // BCCP of the tiny, small and medium pair lists (counts read back by the host).

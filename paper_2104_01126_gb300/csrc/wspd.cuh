@@ -48,8 +48,12 @@ struct TravArgs {
 };
 
 void launch_comp_labels(const Tree &T, const Points &P, int *uf, cudaStream_t st);
-int run_traversal(int mode, TravArgs &a, int2 *fa, int2 *fb, int *counters, cudaStream_t st, int *pinned,
-                  unsigned *overflow_out, int *levels_out);
+int run_traversal(int mode, TravArgs &a, int2 *stack, int2 *x, int *counters, int chunk, cudaStream_t st, int *pinned,
+                  unsigned *overflow_out, int *steps_out);
+void traversal_init(int mode, TravArgs &a, int2 *stack, int *top, int *xcount, cudaStream_t st);
+void traversal_step(int mode, TravArgs &a, int2 *stack, int *top, int2 *x, int *xcount, int chunk, cudaStream_t st);
+void sample_w2(const EdgeK *e, int m, int k, double *out, cudaStream_t st);
+void keep_below(const EdgeK *in, int m, double bound, EdgeK *out, int *count, cudaStream_t st);
 int run_bccp_tiles(TravArgs &a, int m, long long *jobs, long long *total, cudaStream_t st, Arena &ar, bool hdb,
                    bool fp64);
 void run_bccp_groups(TravArgs &a, const int *counts_host, cudaStream_t st);
