@@ -117,6 +117,54 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def serving_mix(count, seed=0, n_lo=1_000, n_hi=200_000):
+    """Requests shaped like the serving configuration: n log-uniform in [n_lo, n_hi], d in
+    {2,3,5,7}, minPts in {10,50}, Gaussian-mixture or uniform points, EMST or HDBSCAN*."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    jobs = []
+    for i in range(count):
+        n = int(np.exp(g.uniform(np.log(n_lo), np.log(n_hi))))
+        d = int(g.choice([2, 3, 5, 7]))
+        kind = "emst" if g.random() < 0.5 else "hdbscan"
+        mp = int(g.choice([10, 50]))
+        if g.random() < 0.5:
+            x = synthdata.gaussian_mixture(n, d, seed=seed * 100003 + i)
+        else:
+            x = synthdata.uniform(n, d, seed=seed * 100003 + i, dtype=np.float32)
+        jobs.append((kind, x, mp))
+    return jobs
+
+
+def run_serving(wm, jobs, workers, budget, rate_hz=None, seed=1):
+    """Submits the jobs (all at once, or as a Poisson stream at rate_hz); returns latencies (ms)
+    and the wall time (s)."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    lat = []
+    with wm.Server(hbm_budget_bytes=budget, workers=workers) as srv:
+        t0 = time.perf_counter()
+        tickets = []
+        next_t = t0
+        for kind, x, mp in jobs:
+            if rate_hz:
+                next_t += g.exponential(1.0 / rate_hz)
+                delay = next_t - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+            tickets.append(srv.submit(x, kind=kind, min_pts=mp))
+        failed = 0
+        for t in tickets:
+            try:
+                _, l = srv.wait(t)
+                lat.append(l)
+            except wm.WMError as e:
+                failed += 1
+                print(f"served job failed: {e}", file=sys.stderr)
+        wall = time.perf_counter() - t0
+        peak = srv.counters()
+        peak["failed"] = failed
+    return np.array(lat), wall, peak
+
+
 def load_peaks():
     """Measured peaks (MEASURED_PEAKS.json, written by the pool's driver), else the fallback."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -217,6 +265,10 @@ def main():
     ap.add_argument("--ref-warmup", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-workers", type=int, default=4)
+    ap.add_argument("--serve-budget-gb", type=float, default=64.0)
+    ap.add_argument("--no-plain", action="store_true")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     ws, rank, local = dist_setup()
@@ -331,6 +383,51 @@ def main():
         e2e = {"value": whole_job_value(n, ws, e_ms), "unit": "Mpoints/s", "ms_per_step": e_ms,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    # ---- the plain form: the same workload in FP64, one job at a time
+    plain = None
+    if not args.no_plain and args.precision == "fp32":
+        saved = args.precision
+        args.precision = "fp64"
+        step(xd)
+        torch.cuda.synchronize()
+        pt = []
+        for _ in range(max(1, min(args.steps, 2))):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(xd)
+            e1.record(stream)
+            e1.synchronize()
+            pt.append(e0.elapsed_time(e1))
+        args.precision = saved
+        p_ms = max_over_ranks(sum(pt) / len(pt), dist, device="cuda")
+        plain = {"value": whole_job_value(n, ws, p_ms), "unit": "Mpoints/s", "ms_per_step": p_ms,
+                 "precision": "fp64", "note": "same workload, every distance in FP64, one job at a time"}
+
+    # ---- served: continuous batching of a mixed request stream
+    served = None
+    if args.serve_requests > 0:
+        jobs = serving_mix(args.serve_requests, seed=rank)
+        pts = sum(len(x) for _, x, _ in jobs)
+        budget = int(args.serve_budget_gb * (1 << 30))
+        run_serving(wm, jobs[: min(8, len(jobs))], args.serve_workers, budget)     # warm-up
+        lat_sat, wall_sat, peak_sat = run_serving(wm, jobs, args.serve_workers, budget)
+        cap = len(jobs) / wall_sat
+        rate = 0.5 * cap
+        lat, wall, peak = run_serving(wm, jobs, args.serve_workers, budget, rate_hz=rate, seed=7 + rank)
+        served = {"requests": len(jobs), "points": pts, "workers": args.serve_workers,
+                  "hbm_budget_gb": args.serve_budget_gb,
+                  "saturation": {"jobs_per_s": cap, "mpoints_per_s": pts / wall_sat / 1e6,
+                                 "p50_ms": float(np.percentile(lat_sat, 50)),
+                                 "p99_ms": float(np.percentile(lat_sat, 99)),
+                                 "peak_running": peak_sat["peak_running"]},
+                  "rate_hz": rate, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                  "mpoints_per_s": pts / wall / 1e6, "peak_running": peak["peak_running"],
+                  "failed": peak["failed"] + peak_sat["failed"],
+                  "mix": "n log-uniform [1e3, 2e5], d in {2,3,5,7}, minPts in {10,50}, gmm or uniform, "
+                         "EMST or HDBSCAN*; Poisson arrivals at half the measured saturation rate"}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, args.cpu_sample)
@@ -353,7 +450,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
                 "config": cfg, "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
-                "cpu_baseline": cpu, "phases_ms": phases, "counters": counters,
+                "cpu_baseline": cpu, "plain_form": plain, "served": served, "phases_ms": phases,
+                "counters": counters,
                 "step_ms": [round(t, 3) for t in times]}
         print(json.dumps(line), flush=True)
     if dist:

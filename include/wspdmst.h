@@ -202,6 +202,58 @@ int wm_single_linkage(const wm_edge *tree, int64_t n, int32_t start, wm_dnode *o
 int wm_emst_noalloc(const void *pts, int64_t n, int32_t d, int32_t dtype, int32_t layout,
                     wm_edge *out_edges, double *out_total_weight, const wm_opts *opts);
 
+/* ------------------------------------------------------------------------- serving */
+/*
+ * A server runs EMST / HDBSCAN* jobs as they arrive, several at a time on one device
+ * (continuous batching; the paper's method is one job at a time).  Each of `workers` host
+ * threads owns a CUDA stream; a job is admitted when its workspace estimate
+ * (wm_query_footprint) fits in what is left of `hbm_budget_bytes`, its workspace comes from a
+ * stream-ordered pool and returns to it when the job ends, so jobs that arrive while others run
+ * start as soon as a worker and memory are free, and their kernels overlap on the device.
+ * A job whose estimate exceeds the whole budget is rejected at submission (WM_ENOMEM).
+ * Results are identical to running the same job alone with wm_emst / wm_hdbscan.
+ */
+typedef struct wm_server wm_server;
+
+#define WM_JOB_EMST 0
+#define WM_JOB_HDBSCAN 1
+
+typedef struct {
+    int32_t kind;            /* WM_JOB_EMST or WM_JOB_HDBSCAN */
+    int32_t dtype, layout;   /* as wm_emst */
+    int32_t d;
+    int64_t n;
+    const void *pts;         /* caller-owned until the job completes (host or device) */
+    int32_t min_pts, start;  /* HDBSCAN* only */
+    int32_t precision;       /* WM_PREC_* */
+    int32_t reserved;
+    /* caller-owned outputs, sized as for wm_emst / wm_hdbscan; NULL to skip */
+    wm_edge *out_edges;
+    double *out_total_weight;   /* EMST */
+    double *out_core_dist;
+    wm_dnode *out_dendro;
+    int32_t *out_order;
+    double *out_reach;
+} wm_job;
+
+/* status codes of a ticket */
+#define WM_JOB_QUEUED 1
+#define WM_JOB_RUNNING 2
+#define WM_JOB_DONE 0        /* success */
+
+int wm_server_create(int32_t device, size_t hbm_budget_bytes, int32_t workers, wm_server **out);
+/* Waits for every submitted job, then stops the workers and frees the server. */
+int wm_server_destroy(wm_server *s);
+/* Queues a job; *ticket identifies it.  Never blocks on the device. */
+int wm_submit(wm_server *s, const wm_job *job, int64_t *ticket);
+/* Non-blocking: *status = WM_JOB_QUEUED / WM_JOB_RUNNING / WM_JOB_DONE or the job's negative
+ * error code; *latency_ms (may be NULL) = submit-to-completion time once finished. */
+int wm_poll(wm_server *s, int64_t ticket, int32_t *status, double *latency_ms);
+/* Blocks until the job has finished; returns its result code. */
+int wm_wait(wm_server *s, int64_t ticket, double *latency_ms);
+/* Counters: jobs finished, peak admitted bytes, peak number of jobs running together. */
+int wm_server_counters(wm_server *s, int64_t *finished, size_t *peak_bytes, int32_t *peak_running);
+
 /*
  * wm_query_footprint -- an upper estimate of the device workspace, in bytes, that a call with
  * these sizes needs (min_pts = 0 for EMST).  Data-dependent buffers (WSPD traversal frontiers,

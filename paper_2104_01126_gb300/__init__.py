@@ -67,6 +67,15 @@ class _Opts(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_size_t), ("stats", ctypes.POINTER(_Stats))]
 
 
+class _Job(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("dtype", ctypes.c_int32), ("layout", ctypes.c_int32),
+                ("d", ctypes.c_int32), ("n", ctypes.c_int64), ("pts", ctypes.c_void_p),
+                ("min_pts", ctypes.c_int32), ("start", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("out_edges", ctypes.c_void_p),
+                ("out_total_weight", ctypes.c_void_p), ("out_core_dist", ctypes.c_void_p),
+                ("out_dendro", ctypes.c_void_p), ("out_order", ctypes.c_void_p), ("out_reach", ctypes.c_void_p)]
+
+
 EDGE_DTYPE = np.dtype([("u", np.int32), ("v", np.int32), ("w", np.float64)])
 DNODE_DTYPE = np.dtype([("left", np.int32), ("right", np.int32), ("height", np.float64),
                         ("size", np.int32), ("reserved", np.int32)])
@@ -146,6 +155,19 @@ def load(build_if_missing: bool = True):
         lib.wm_last_error_detail.restype = ctypes.c_char_p
         lib.wm_version.restype = ctypes.c_char_p
         lib.wm_kernel_launch_count.restype = ctypes.c_int64
+        lib.wm_server_create.restype = ctypes.c_int
+        lib.wm_server_create.argtypes = [i32, ctypes.c_size_t, i32, ctypes.POINTER(ctypes.c_void_p)]
+        lib.wm_server_destroy.restype = ctypes.c_int
+        lib.wm_server_destroy.argtypes = [P]
+        lib.wm_submit.restype = ctypes.c_int
+        lib.wm_submit.argtypes = [P, ctypes.POINTER(_Job), ctypes.POINTER(ctypes.c_int64)]
+        lib.wm_poll.restype = ctypes.c_int
+        lib.wm_poll.argtypes = [P, i64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
+        lib.wm_wait.restype = ctypes.c_int
+        lib.wm_wait.argtypes = [P, i64, ctypes.POINTER(ctypes.c_double)]
+        lib.wm_server_counters.restype = ctypes.c_int
+        lib.wm_server_counters.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_size_t),
+                                           ctypes.POINTER(ctypes.c_int32)]
         lib.wm_emst_noalloc.restype = ctypes.c_int
         lib.wm_emst_noalloc.argtypes = [P, i64, i32, i32, i32, P, P, ctypes.POINTER(_Opts)]
         _lib = lib
@@ -363,3 +385,94 @@ def kernel_launch_count() -> int:
 
 def release_cache():
     _check(load().wm_release_cache(), "wm_release_cache")
+
+
+# ------------------------------------------------------------------------------- serving
+class Server:
+    """Continuous-batching server (wm_server_*): jobs run concurrently on one device, admitted
+    against an HBM budget.  Host inputs and outputs only (numpy); each submitted job keeps its
+    buffers alive until it is waited for."""
+
+    def __init__(self, hbm_budget_bytes: int, workers: int = 4, device: int = 0):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.wm_server_create(device, int(hbm_budget_bytes), int(workers), ctypes.byref(h)),
+               "wm_server_create")
+        self._h = h
+        self._lib = lib
+        self._keep = {}
+
+    def submit(self, points, kind: str = "emst", min_pts: int = 10, start: int = 0, precision: str = "fp32") -> int:
+        x = np.ascontiguousarray(points)
+        if x.dtype not in (np.float32, np.float64):
+            x = x.astype(np.float64)
+        n, d = x.shape
+        m = max(n - 1, 0)
+        job = _Job()
+        job.kind = 0 if kind == "emst" else 1
+        job.dtype = WM_F32 if x.dtype == np.float32 else WM_F64
+        job.layout = WM_AOS
+        job.d = d
+        job.n = n
+        job.pts = x.ctypes.data
+        job.min_pts = int(min_pts)
+        job.start = int(start)
+        job.precision = PREC[precision]
+        bufs = {"x": x, "edges": np.zeros(max(m, 1), dtype=EDGE_DTYPE), "total": np.zeros(1)}
+        job.out_edges = bufs["edges"].ctypes.data if m else None
+        if job.kind == 0:
+            job.out_total_weight = bufs["total"].ctypes.data
+        else:
+            bufs.update(cd=np.zeros(n), dendro=np.zeros(max(m, 1), dtype=DNODE_DTYPE),
+                        order=np.zeros(n, np.int32), reach=np.zeros(n))
+            job.out_core_dist = bufs["cd"].ctypes.data
+            job.out_dendro = bufs["dendro"].ctypes.data if m else None
+            job.out_order = bufs["order"].ctypes.data
+            job.out_reach = bufs["reach"].ctypes.data
+        t = ctypes.c_int64(0)
+        _check(self._lib.wm_submit(self._h, ctypes.byref(job), ctypes.byref(t)), "wm_submit")
+        self._keep[t.value] = (job, bufs, kind, n)
+        return t.value
+
+    def poll(self, ticket: int):
+        st = ctypes.c_int32(0)
+        lat = ctypes.c_double(0.0)
+        _check(self._lib.wm_poll(self._h, ticket, ctypes.byref(st), ctypes.byref(lat)), "wm_poll")
+        return st.value, lat.value
+
+    def wait(self, ticket: int):
+        """Blocks until the job is done; returns (result dict, latency in ms)."""
+        lat = ctypes.c_double(0.0)
+        rc = self._lib.wm_wait(self._h, ticket, ctypes.byref(lat))
+        job, bufs, kind, n = self._keep.pop(ticket)
+        _check(rc, "wm_wait")
+        m = max(n - 1, 0)
+        e = bufs["edges"][:m]
+        out = {"u": e["u"].copy(), "v": e["v"].copy(), "w": e["w"].copy()}
+        if kind == "emst":
+            out["total"] = float(bufs["total"][0])
+        else:
+            dn = bufs["dendro"][:m]
+            out.update(cd=bufs["cd"], left=dn["left"].copy(), right=dn["right"].copy(),
+                       height=dn["height"].copy(), size=dn["size"].copy(), order=bufs["order"],
+                       reach=bufs["reach"])
+        return out, lat.value
+
+    def counters(self):
+        f = ctypes.c_int64(0)
+        b = ctypes.c_size_t(0)
+        r = ctypes.c_int32(0)
+        _check(self._lib.wm_server_counters(self._h, ctypes.byref(f), ctypes.byref(b), ctypes.byref(r)),
+               "wm_server_counters")
+        return {"finished": f.value, "peak_bytes": b.value, "peak_running": r.value}
+
+    def close(self):
+        if self._h:
+            _check(self._lib.wm_server_destroy(self._h), "wm_server_destroy")
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

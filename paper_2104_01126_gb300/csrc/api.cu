@@ -6,7 +6,11 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <condition_variable>
+#include <deque>
 #include <mutex>
+#include <thread>
+#include <unordered_map>
 #include <string>
 #include <vector>
 
@@ -70,7 +74,9 @@ struct Caps {
 static size_t estimate_bytes(long long n, int d, int min_pts, const Caps &c)
 {
     const long long N = 2 * n;
-    const long long depth = 64;   // typical; the stack below is sized from the real depth
+    long long lg = 1;
+    while ((1LL << lg) < n) ++lg;
+    const long long depth = 2 * lg + 16;   // typical; memogfk sizes the stack from the real depth
     const int dp = d <= 4 ? 4 : d <= 8 ? 8 : 16;
     size_t b = 0;
     b += (size_t)n * d * 8;                 // device copy of the input
@@ -90,13 +96,13 @@ static size_t estimate_bytes(long long n, int d, int min_pts, const Caps &c)
         b += (size_t)n * kk * 16 * 2;                   // repair edges + sort tmp
         b += (size_t)n * 160;                           // dendrogram / Euler tour scratch
     }
-    return b + (64u << 20) + (size_t)c.extra_bytes;
+    return b + (8u << 20) + (size_t)n * 64 + (size_t)c.extra_bytes;
 }
 
 static Caps default_caps(long long n, int min_pts)
 {
     Caps c;
-    c.chunk = std::min<long long>(1 << 21, std::max<long long>(1 << 16, n));
+    c.chunk = std::min<long long>(1 << 21, std::max<long long>(1 << 12, 4 * n));
     c.edges = 4 * n + (1 << 20) + (min_pts > 0 ? (long long)n * (min_pts + 16) : 0);
     c.frontier_scale = 1;
     c.extra_bytes = 0;
@@ -347,32 +353,38 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
             if (!flush) continue;
             mark_event();
             ev_kind.push_back(0);
-            const long long incoming = (long long)lc[0] + lc[1] + lc[2] + lc[3] + lc[4];
-            // keep room for one edge per retrieved pair: lower rho_hi if the batch is filling up
-            for (int guard = 0; e + incoming > caps.edges && guard < 8; ++guard) {
-                const int k = std::min(e, 4096);
-                sample_w2(a.edges, e, k, samples, st);
+            // BCCP of the retrieved pairs.  Emission is capacity-checked; if this flush overflows the
+            // edge batch, its partial output is dropped, rho_hi is lowered to a quantile of the valid
+            // edges (pairs seen so far were retrieved under the larger bound, so they stay complete
+            // for the smaller range) and the flush is redone from the intact lists.
+            const int e_before = e;
+            for (int attempt = 0;; ++attempt) {
+                run_bccp_groups(a, lc, st);
+                WM_TRY(run_bccp_tiles(a, lc[3], jobs, (long long *)(cnts + 10), st, ar, hdb != nullptr, a.fp64 != 0));
+                WM_TRY(run_bccp_huge(a, lc[4], huge_items, (long long *)(cnts + 12), st, ar, hdb != nullptr,
+                                     a.fp64 != 0, stack_warps));
+                WM_CK(cudaMemcpyAsync(C.pin, ecount, sizeof(int), cudaMemcpyDeviceToHost, st));
+                WM_CK(cudaMemcpyAsync(C.pin + 1, ovf, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+                WM_CK(cudaStreamSynchronize(st));
+                if (!(C.pin[1] & 2u)) break;
+                if (attempt >= 8) { *overflow_bits = 2; return 0; }
+                const int valid = std::min<long long>(C.pin[0], caps.edges) > 0 ? (int)std::min<long long>(C.pin[0], caps.edges) : 0;
+                const int k = std::min(valid, 4096);
+                if (k < 1) { *overflow_bits = 2; return 0; }
+                sample_w2(a.edges, valid, k, samples, st);
                 WM_CK(cudaMemcpyAsync(C.pin + 64, samples, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
                 WM_CK(cudaStreamSynchronize(st));
                 std::vector<double> sw((double *)(C.pin + 64), (double *)(C.pin + 64) + k);
                 std::sort(sw.begin(), sw.end());
                 double nh = sw[(size_t)(k * 0.4)];
                 if (!(nh > rho_lo)) nh = std::nextafter(rho_lo, inf);
-                if (!(nh < a.rho_hi)) break;   // cannot shrink further
-                keep_below(a.edges, e, nh, spare, ecount, st);
+                if (!(nh < a.rho_hi)) { *overflow_bits = 2; return 0; }   // cannot shrink: grow and restart
+                keep_below(a.edges, e_before, nh, spare, ecount, st);
                 std::swap(a.edges, spare);
                 a.rho_hi = rho_hi = nh;
-                WM_CK(cudaMemcpyAsync(C.pin, ecount, sizeof(int), cudaMemcpyDeviceToHost, st));
-                WM_CK(cudaStreamSynchronize(st));
-                e = C.pin[0];
+                WM_CK(cudaMemsetAsync(ovf, 0, sizeof(unsigned), st));
                 C.stats.rho_shrinks += 1;
             }
-            if (e + incoming > caps.edges) { *overflow_bits = 2; return 0; }
-            // BCCP of the retrieved pairs
-            run_bccp_groups(a, lc, st);
-            WM_TRY(run_bccp_tiles(a, lc[3], jobs, (long long *)(cnts + 10), st, ar, hdb != nullptr, a.fp64 != 0));
-            WM_TRY(run_bccp_huge(a, lc[4], huge_items, (long long *)(cnts + 12), st, ar, hdb != nullptr, a.fp64 != 0,
-                                 stack_warps));
             WM_CK(cudaMemsetAsync(lcount, 0, 5 * sizeof(int), st));
             if (lc[3] > 0 || lc[4] > 0) C.stats.tile_launches += 1;
             mark_event();
@@ -582,7 +594,12 @@ static int run_call(const wm_opts *opts, long long n, int d, int min_pts, Body b
         // grow whichever capacity overflowed and start over
         if (ovf & 1u) caps.frontier_scale *= 2;
         if (ovf & 2u) caps.edges *= 2;
-        if (user_ws && ovf) { rc = WM_ENOMEM; set_detail("caller workspace too small for the WSPD frontier%s", ""); break; }
+        if (user_ws && ovf && estimate_bytes(n, d, min_pts, caps) > opts->workspace_bytes) {
+            rc = WM_ENOMEM;
+            set_detail("caller workspace too small: this input needs about %lld bytes%s",
+                       (long long)estimate_bytes(n, d, min_pts, caps), "");
+            break;
+        }
         rc = WM_ENOMEM;
     }
     cudaError_t le = cudaGetLastError();
@@ -870,3 +887,231 @@ extern "C" int wm_emst_noalloc(const void *pts, int64_t n, int32_t d, int32_t dt
     if (opts && opts->stats) *opts->stats = C.stats;
     return rc;
 }
+
+// ======================================================================== serving loop
+namespace wm {
+
+struct ServerJob {
+    wm_job spec;
+    int64_t ticket = 0;
+    int status = WM_JOB_QUEUED;
+    size_t footprint = 0;
+    std::chrono::steady_clock::time_point t_submit, t_done;
+};
+
+}  // namespace wm
+
+struct wm_server {
+    int device = 0;
+    size_t budget = 0;
+    size_t in_use = 0, peak = 0;
+    int running = 0, peak_running = 0;
+    int64_t finished = 0;
+    int64_t next_ticket = 1;
+    bool stop = false;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_mem, cv_done;
+    std::deque<wm::ServerJob *> queue;
+    std::unordered_map<int64_t, wm::ServerJob *> jobs;
+    std::vector<std::thread> threads;
+    cudaMemPool_t pool = nullptr;
+};
+
+namespace wm {
+
+static size_t job_footprint(const wm_job &j)
+{
+    size_t b = 0;
+    wm_query_footprint(j.n, j.d, j.kind == WM_JOB_HDBSCAN ? j.min_pts : 0, &b);
+    return b;
+}
+
+static int run_job(const wm_job &j, void *ws, size_t ws_bytes, cudaStream_t st)
+{
+    wm_opts o{};
+    o.stream = st;
+    o.precision = j.precision;
+    o.workspace = ws;
+    o.workspace_bytes = ws_bytes;
+    if (j.kind == WM_JOB_EMST)
+        return wm_emst(j.pts, j.n, j.d, j.dtype, j.layout, j.out_edges, j.out_total_weight, &o);
+    return wm_hdbscan(j.pts, j.n, j.d, j.dtype, j.layout, j.min_pts, j.out_edges, j.out_core_dist, j.out_dendro,
+                      j.out_order, j.out_reach, j.start, &o);
+}
+
+static void server_worker(wm_server *s)
+{
+    cudaSetDevice(s->device);
+    cudaStream_t st = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    while (true) {
+        ServerJob *job = nullptr;
+        size_t fp = 0;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty(); });
+            if (s->queue.empty()) break;   // stop requested and nothing left
+            job = s->queue.front();
+            s->queue.pop_front();
+            fp = job->footprint;
+            // admission: wait until the job's workspace fits in the budget
+            s->cv_mem.wait(lk, [&] { return s->in_use + fp <= s->budget; });
+            s->in_use += fp;
+            s->peak = std::max(s->peak, s->in_use);
+            s->running += 1;
+            s->peak_running = std::max(s->peak_running, s->running);
+            job->status = WM_JOB_RUNNING;
+        }
+        int rc = WM_ENOMEM;
+        for (int attempt = 0; attempt < 4; ++attempt) {
+            void *ws = nullptr;
+            if (cudaMallocFromPoolAsync(&ws, fp, s->pool, st) != cudaSuccess) {
+                cudaGetLastError();
+                rc = WM_ENOMEM;
+                break;
+            }
+            rc = run_job(job->spec, ws, fp, st);
+            cudaFreeAsync(ws, st);
+            cudaStreamSynchronize(st);
+            if (rc != WM_ENOMEM) break;
+            // the data needed more workspace than estimated: grow within the budget and rerun
+            std::unique_lock<std::mutex> lk(s->mu);
+            size_t more = fp;
+            if (fp + more > s->budget) break;
+            s->cv_mem.wait(lk, [&] { return s->in_use + more <= s->budget; });
+            s->in_use += more;
+            s->peak = std::max(s->peak, s->in_use);
+            fp += more;
+        }
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->in_use -= fp;
+            s->running -= 1;
+            s->finished += 1;
+            job->t_done = std::chrono::steady_clock::now();
+            job->status = rc;
+        }
+        s->cv_mem.notify_all();
+        s->cv_done.notify_all();
+    }
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+}
+
+}  // namespace wm
+
+extern "C" {
+
+int wm_server_create(int32_t device, size_t hbm_budget_bytes, int32_t workers, wm_server **out)
+{
+    using namespace wm;
+    if (!out || workers < 1 || workers > 64 || hbm_budget_bytes == 0) return WM_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return WM_EINVAL;
+    wm_server *s = new wm_server();
+    s->device = device;
+    s->budget = hbm_budget_bytes;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(device);
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        cudaSetDevice(prev);
+        delete s;
+        return WM_ECUDA;
+    }
+    uint64_t keep = hbm_budget_bytes;   // keep up to the budget cached in the pool between jobs
+    cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    cudaSetDevice(prev);
+    for (int i = 0; i < workers; ++i) s->threads.emplace_back(server_worker, s);
+    *out = s;
+    return WM_OK;
+}
+
+int wm_server_destroy(wm_server *s)
+{
+    if (!s) return WM_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    for (auto &t : s->threads) t.join();
+    for (auto &kv : s->jobs) delete kv.second;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(s->device);
+    cudaMemPoolDestroy(s->pool);
+    cudaSetDevice(prev);
+    delete s;
+    return WM_OK;
+}
+
+int wm_submit(wm_server *s, const wm_job *job, int64_t *ticket)
+{
+    using namespace wm;
+    if (!s || !job || !ticket || !job->pts || job->n < 1 || job->d < 1 || job->d > kMaxDim ||
+        (job->kind != WM_JOB_EMST && job->kind != WM_JOB_HDBSCAN) ||
+        (job->kind == WM_JOB_HDBSCAN && (job->min_pts < 1 || job->min_pts > job->n)))
+        return WM_EINVAL;
+    ServerJob *j = new ServerJob();
+    j->spec = *job;
+    j->footprint = job_footprint(*job);
+    if (j->footprint > s->budget) {
+        delete j;
+        return WM_ENOMEM;   // admission rejection: can never fit the budget
+    }
+    j->t_submit = std::chrono::steady_clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        j->ticket = s->next_ticket++;
+        s->jobs[j->ticket] = j;
+        s->queue.push_back(j);
+        *ticket = j->ticket;
+    }
+    s->cv_work.notify_one();
+    return WM_OK;
+}
+
+int wm_poll(wm_server *s, int64_t ticket, int32_t *status, double *latency_ms)
+{
+    if (!s || !status) return WM_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(ticket);
+    if (it == s->jobs.end()) return WM_EINVAL;
+    *status = it->second->status;
+    if (latency_ms) {
+        *latency_ms = (it->second->status <= 0)
+                          ? std::chrono::duration<double, std::milli>(it->second->t_done - it->second->t_submit).count()
+                          : -1.0;
+    }
+    return WM_OK;
+}
+
+int wm_wait(wm_server *s, int64_t ticket, double *latency_ms)
+{
+    if (!s) return WM_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(ticket);
+    if (it == s->jobs.end()) return WM_EINVAL;
+    wm::ServerJob *j = it->second;
+    s->cv_done.wait(lk, [&] { return j->status <= 0; });
+    if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(j->t_done - j->t_submit).count();
+    return j->status;
+}
+
+int wm_server_counters(wm_server *s, int64_t *finished, size_t *peak_bytes, int32_t *peak_running)
+{
+    if (!s) return WM_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (finished) *finished = s->finished;
+    if (peak_bytes) *peak_bytes = s->peak;
+    if (peak_running) *peak_running = s->peak_running;
+    return WM_OK;
+}
+
+}  // extern "C"
