@@ -311,7 +311,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     while (nE < n - 1) {
         if (++rounds > 4096) { set_detail("MemoGFK made no progress%s (%lld rounds)", "", rounds); return WM_EINTERNAL; }
         Timer tw;
-        launch_comp_labels(T, P, uf, st);
+        launch_comp_labels(T, P, uf, meta, st);
         // ---- GetRho
         WM_CK(cudaMemcpyAsync(rho, &inf, sizeof(double), cudaMemcpyHostToDevice, st));
         a.beta = (int)std::min<long long>(beta, 0x7fffffff);

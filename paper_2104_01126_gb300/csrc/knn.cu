@@ -37,6 +37,7 @@ struct KnnArgs {
     double eta;
     int *stack;
     int stack_cap;
+    double *wscratch;    // [warps][KL][32] FP64 candidate values
     double *cd64;
     float *cd32;
     int *rep_q;          // [n][KL-1] tree positions
@@ -78,13 +79,14 @@ __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
     extern __shared__ unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
     const int KL = a.KL;
-    // per-warp region: V sv[KL][32]; int sj[KL][32]; double sw[KL][32]
-    size_t per_warp = (size_t)KL * 32 * (sizeof(V) + sizeof(int) + sizeof(double));
+    // per-warp shared region: V sv[KL][32]; int sj[KL][32] (slot-major, one bank per lane);
+    // the FP64 candidate values of the epilogue live in global scratch: double sw[KL][32]
+    size_t per_warp = (size_t)KL * 32 * (sizeof(V) + sizeof(int));
     unsigned char *base = smem_raw + per_warp * wib;
-    double *sw = (double *)base;
-    V *sv = (V *)(base + (size_t)KL * 32 * sizeof(double));
-    int *sj = (int *)(base + (size_t)KL * 32 * (sizeof(double) + sizeof(V)));
+    V *sv = (V *)base;
+    int *sj = (int *)(base + (size_t)KL * 32 * sizeof(V));
     const int gw = blockIdx.x * nwb + wib, nw = gridDim.x * nwb;
+    double *sw = a.wscratch + (size_t)gw * KL * 32;
     int *stk = a.stack + (size_t)gw * a.stack_cap;
     const int n = a.n, d = a.d;
     unsigned long long n_ev = 0, n_re = 0;
@@ -392,6 +394,20 @@ __global__ void rep_emit_extra_kernel(const int *__restrict__ ep, const int *__r
     }
 }
 
+// order-preserving removal of repeated keys from a K-sorted array: flag, scan, scatter
+__global__ void first_of_run_kernel(const EdgeK *__restrict__ in, int m, int *__restrict__ flag)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x)
+        flag[t] = t == 0 || in[t - 1].hi != in[t].hi || in[t - 1].lo != in[t].lo;
+}
+
+__global__ void scatter_first_kernel(const EdgeK *__restrict__ in, int m, const int *__restrict__ pos,
+                                     EdgeK *__restrict__ out)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x)
+        if (t == 0 || in[t - 1].hi != in[t].hi || in[t - 1].lo != in[t].lo) out[pos[t]] = in[t];
+}
+
 __global__ void core_out_kernel(const double *__restrict__ cd64, const int *__restrict__ pid, int n, double *out)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[pid[i]] = sqrt(cd64[i]);
@@ -438,13 +454,14 @@ int core_distances(Points &P, Tree &T, int min_pts, bool fp64, HdbState &H, Aren
     cudaMemsetAsync(cnts, 0, 8 * sizeof(int), st);
     cudaMemsetAsync(a.stat, 0, 4 * sizeof(unsigned long long), st);
     // launch shape: warps per block limited by shared memory
-    size_t per_warp = (size_t)KL * 32 * ((fp64 ? 8 : 4) + 4 + 8);
+    size_t per_warp = (size_t)KL * 32 * ((fp64 ? 8 : 4) + 4);
     int wpb = (int)std::min<size_t>(8, std::max<size_t>(1, (96u << 10) / per_warp));
     size_t smem = per_warp * wpb;
     int blocks = 152 * std::max(1, 16 / wpb);
     int total_warps = blocks * wpb;
     a.stack = ar.get<int>((size_t)total_warps * a.stack_cap);
-    if (!a.stack) return WM_ENOMEM;
+    a.wscratch = ar.get<double>((size_t)total_warps * KL * 32);
+    if (!a.stack || !a.wscratch) return WM_ENOMEM;
 #define WM_KNN(DM)                                                                                           \
     do {                                                                                                     \
         if (fp64) {                                                                                          \
@@ -510,7 +527,20 @@ int core_distances(Points &P, Tree &T, int min_pts, bool fp64, HdbState &H, Aren
     EdgeK *sorted = rep;
     rc = radix_sort_edges(rep, tmp, nrep, st, ar, &sorted, pin + 4096);
     if (rc) return rc;
-    if (sorted != rep) cudaMemcpyAsync(rep, sorted, sizeof(EdgeK) * nrep, cudaMemcpyDeviceToDevice, st);
+    // (p,q) appears twice when p and q are in each other's core ball: keep one copy, in K order
+    if (nrep > 0) {
+        int *flag = ar.get<int>(nrep);
+        if (!flag) return WM_ENOMEM;
+        EdgeK *other = sorted == rep ? tmp : rep;
+        launch(first_of_run_kernel, grid_for(nrep, 256), 256, 0, st, sorted, nrep, flag);
+        rc = scan_exclusive_i32(flag, flag, nrep, cnts + 5, st, ar);
+        if (rc) return rc;
+        launch(scatter_first_kernel, grid_for(nrep, 256), 256, 0, st, sorted, nrep, flag, other);
+        cudaMemcpyAsync(pin, cnts + 5, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;
+        nrep = pin[0];
+        if (other != rep) cudaMemcpyAsync(rep, other, sizeof(EdgeK) * nrep, cudaMemcpyDeviceToDevice, st);
+    }
     H.rep = rep;
     H.nrep = nrep;
     ar.off = mark;

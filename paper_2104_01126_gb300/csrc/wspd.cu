@@ -157,8 +157,9 @@ __device__ inline void warp_emit(const TravArgs &a, bool has, const KMin &m)
 // links = {begin, end, left, right}; meta = {diam2 bound, cdmin, cdmax, 0};
 // box[node][2*DP] = lo[0..DP), hi[0..DP) with padded dimensions set to 0.
 template <int DP>
-__device__ inline void pair_bounds_packed(const TravArgs &a, int P, int Q, const int4 &lp, const int4 &lq, float &lbB,
-                                          float &ubB, bool &ws, float &dP, float &dQ)
+__device__ inline void pair_bounds_packed(const TravArgs &a, int P, int Q, const int4 &lp, const int4 &lq,
+                                          const float4 &mp, const float4 &mq, float &lbB, float &ubB, bool &ws,
+                                          float &dP, float &dQ)
 {
     const float4 *bp = (const float4 *)(a.box + (size_t)P * 2 * DP);
     const float4 *bq = (const float4 *)(a.box + (size_t)Q * 2 * DP);
@@ -177,7 +178,6 @@ __device__ inline void pair_bounds_packed(const TravArgs &a, int P, int Q, const
         }
     }
     float lb = lower_w2(s), ub = upper_w2(t);
-    float4 mp = a.meta[P], mq = a.meta[Q];
     dP = mp.x;
     dQ = mq.x;
     float dm = fmaxf(dP, dQ);
@@ -227,14 +227,17 @@ __global__ void __launch_bounds__(256) findpair_level_kernel(TravArgs a, const i
             const int4 lp = a.links[P], lq = a.links[Q];
             const int sp = lp.y - lp.x, sq = lq.y - lq.x;
             bool live = !(MODE == 0 && sp + sq <= a.beta);
+            float4 mp = make_float4(0.f, 0.f, 0.f, 0.f), mq = mp;
             if (live) {
-                int cp = a.comp[P];
-                if (cp >= 0 && cp == a.comp[Q]) live = false;
+                mp = a.meta[P];
+                mq = a.meta[Q];
+                int cp = __float_as_int(mp.w);
+                if (cp >= 0 && cp == __float_as_int(mq.w)) live = false;
             }
             if (live) {
                 float lbB, ubB, dP, dQ;
                 bool ws;
-                pair_bounds_packed<DP>(a, P, Q, lp, lq, lbB, ubB, ws, dP, dQ);
+                pair_bounds_packed<DP>(a, P, Q, lp, lq, mp, mq, lbB, ubB, ws, dP, dQ);
                 if (MODE == 0) {
                     double rho = *(volatile double *)a.rho_out;
                     if ((double)lbB >= rho) live = false;
@@ -399,11 +402,13 @@ __global__ void uf_flatten_kernel(int *uf, int n)
 // bottom-up: comp(leaf) = root of its point; comp(node) = common comp of the children or -1.
 __global__ void comp_labels_kernel(int N, const int *__restrict__ left, const int *__restrict__ right,
                                    const int *__restrict__ parent, const int *__restrict__ begin,
-                                   const int *__restrict__ pid, const int *__restrict__ uf, int *comp, int *arrive)
+                                   const int *__restrict__ pid, const int *__restrict__ uf, int *comp, int *arrive,
+                                   float4 *meta)
 {
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x) {
         if (left[x] >= 0) continue;
         comp[x] = uf[pid[begin[x]]];
+        if (meta) ((int *)(meta + x))[3] = comp[x];
         int cur = x;
         for (int it = 0; it < N; ++it) {
             int p = parent[cur];
@@ -413,6 +418,7 @@ __global__ void comp_labels_kernel(int N, const int *__restrict__ left, const in
             __threadfence();
             int cl = ((volatile int *)comp)[left[p]], cr = ((volatile int *)comp)[right[p]];
             comp[p] = (cl >= 0 && cl == cr) ? cl : -1;
+            if (meta) ((int *)(meta + p))[3] = comp[p];
             cur = p;
         }
     }
@@ -859,12 +865,12 @@ __global__ void __launch_bounds__(256) bccp_tile_kernel(TravArgs a, int m, const
 
 // ----------------------------------------------------------------------------- host side
 
-void launch_comp_labels(const Tree &T, const Points &P, int *uf, cudaStream_t st)
+void launch_comp_labels(const Tree &T, const Points &P, int *uf, float4 *meta, cudaStream_t st)
 {
     launch(uf_flatten_kernel, grid_for(P.n, 256), 256, 0, st, uf, P.n);
     cudaMemsetAsync(T.arrive, 0, sizeof(int) * T.N, st);
     launch(comp_labels_kernel, grid_for(T.N, 256), 256, 0, st, T.N, T.left, T.right, T.parent, T.begin, P.pid, uf,
-                                                         T.comp, T.arrive);
+                                                         T.comp, T.arrive, meta);
 }
 
 // ----------------------------------------------------------- bounded-memory traversal

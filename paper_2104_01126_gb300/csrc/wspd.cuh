@@ -47,7 +47,7 @@ struct TravArgs {
                                         // [3] tile evals, [4] GetPairs visits, [5] GetRho visits
 };
 
-void launch_comp_labels(const Tree &T, const Points &P, int *uf, cudaStream_t st);
+void launch_comp_labels(const Tree &T, const Points &P, int *uf, float4 *meta, cudaStream_t st);
 int run_traversal(int mode, TravArgs &a, int2 *stack, int2 *x, int *counters, int chunk, cudaStream_t st, int *pinned,
                   unsigned *overflow_out, int *steps_out);
 void traversal_init(int mode, TravArgs &a, int2 *stack, int *top, int *xcount, cudaStream_t st);
