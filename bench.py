@@ -445,7 +445,7 @@ def main():
                                                     "bccp_dual_evals", "knn_evals", "fp64_rechecks",
                                                     "candidate_edges", "tree_depth", "tile_launches",
                                                     "getpairs_launches", "getpairs_visits", "getrho_visits",
-                                                    "rho_shrinks")}
+                                                    "rho_shrinks", "max_pending_pairs")}
         line = {"metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",

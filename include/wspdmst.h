@@ -111,12 +111,13 @@ typedef struct {
     double ms_knn_kernel;          /* CUDA-event time of the k-NN kernel (one launch)   */
     double ms_tile_kernel;         /* CUDA-event time summed over BCCP tile launches    */
     int64_t tile_launches;         /* number of BCCP tile kernel launches               */
-    double ms_getpairs;            /* CUDA-event time summed over GetPairs level launches */
-    int64_t getpairs_launches;     /* number of GetPairs level launches                 */
+    double ms_getpairs;            /* CUDA-event time summed over GetPairs step launches  */
+    int64_t getpairs_launches;     /* number of GetPairs step launches                  */
     int64_t getpairs_visits;       /* node pairs examined by the GetPairs traversals     */
     int64_t getrho_visits;         /* node pairs examined by the GetRho traversals       */
     int64_t bccp_dual_evals;       /* distance evaluations in the pruned BCCP of huge pairs */
     int64_t rho_shrinks;           /* times a round lowered rho_hi to fit its edge batch  */
+    int64_t max_pending_pairs;     /* peak node pairs pending in a WSPD traversal         */
 } wm_stats;
 
 /* Options.  A zero-initialised struct (or NULL) gives the defaults. */

@@ -58,7 +58,8 @@ class _Stats(ctypes.Structure):
                 ("ms_tile_kernel", ctypes.c_double), ("tile_launches", ctypes.c_int64),
                 ("ms_getpairs", ctypes.c_double), ("getpairs_launches", ctypes.c_int64),
                 ("getpairs_visits", ctypes.c_int64), ("getrho_visits", ctypes.c_int64),
-                ("bccp_dual_evals", ctypes.c_int64), ("rho_shrinks", ctypes.c_int64)]
+                ("bccp_dual_evals", ctypes.c_int64), ("rho_shrinks", ctypes.c_int64),
+                ("max_pending_pairs", ctypes.c_int64)]
 
 
 class _Opts(ctypes.Structure):
@@ -114,6 +115,7 @@ class Stats:
     getrho_visits: int = 0
     bccp_dual_evals: int = 0
     rho_shrinks: int = 0
+    max_pending_pairs: int = 0
 
     @classmethod
     def _from(cls, s: _Stats) -> "Stats":

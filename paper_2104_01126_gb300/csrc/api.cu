@@ -85,7 +85,7 @@ static size_t estimate_bytes(long long n, int d, int min_pts, const Caps &c)
     b += (size_t)N * (8 * d + 48);          // tree arrays (+ build scratch counters)
     b += (size_t)n * 8;                     // small lists
     b += (size_t)N * (32 + 8 * dp);         // packed node records
-    b += (size_t)((N / 2 + 2 + (2 * depth + 4) * 2 * c.chunk) * c.frontier_scale + 2 * c.chunk) * 8;   // stack
+    b += (size_t)((N / 2 + 2 + (2 * depth + 4) * 2 * c.chunk) * c.frontier_scale + 4 * c.chunk) * 8;   // stack
     b += (size_t)c.chunk * (5 * 8 + 4 * 16 + 4);                                                       // lists, slots
     b += (size_t)152 * 64 * (depth + 4) * 4;                                                           // dual stacks
     b += (size_t)c.edges * 16 * 3 + (size_t)c.edges * 24;   // batch, filtered, sort tmp, kruskal
@@ -241,7 +241,8 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     const int chunk = (int)caps.chunk;
     const long long fcap = ((long long)T.N / 2 + 2 + (2LL * T.depth + 4) * 2 * chunk) * caps.frontier_scale;
     if (fcap > 0x7fffffffLL) { set_detail("WSPD stack capacity exceeds 2^31 pairs%s", ""); return WM_ENOMEM; }
-    int2 *stack = ar.get<int2>(fcap), *xbuf = ar.get<int2>(2LL * chunk);
+    int2 *stack = ar.get<int2>(fcap);
+    int2 *const xbuf[2] = {ar.get<int2>(2LL * chunk), ar.get<int2>(2LL * chunk)};   // step outputs
     // pair lists hold kListChunks chunks' worth of retrieved pairs; they are flushed (BCCP) when
     // one of them could overflow within the next poll interval, and when the traversal ends
     const int kPoll = 4, kListChunks = 8;
@@ -266,9 +267,9 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     unsigned *ovf = ar.get<unsigned>(2);
     unsigned long long *stat = ar.get<unsigned long long>(8);
     if (ar.failed) return WM_ENOMEM;
-    // counters: [0] stack top, [1] children count, [2..6] pair-list counts, [7] edge count,
-    // [8] filtered count, [9] repair lower bound, [10..11] / [12..13] 64-bit job totals
-    int *top = cnts + 0, *xcount = cnts + 1, *lcount = cnts + 2, *ecount = cnts + 7;
+    // counters: [2..6] pair-list counts, [7] edge count, [8] filtered count, [9] repair lower
+    // bound, [10..11] / [12..13] 64-bit job totals, [32..32+kTravCounters) traversal state
+    int *lcount = cnts + 2, *ecount = cnts + 7, *tcnt = cnts + 32;
     {
         Tree T2 = T;
         if (hdb) { T2.cdmin = hdb->cdmin; T2.cdmax = hdb->cdmax; }
@@ -316,7 +317,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         WM_CK(cudaMemcpyAsync(rho, &inf, sizeof(double), cudaMemcpyHostToDevice, st));
         a.beta = (int)std::min<long long>(beta, 0x7fffffff);
         unsigned ob = 0;
-        WM_TRY(run_traversal(0, a, stack, xbuf, cnts, chunk, st, C.pin, &ob, nullptr));
+        WM_TRY(run_traversal(a, stack, xbuf, tcnt, chunk, st, C.pin, &ob, nullptr));
         if (ob) { *overflow_bits = ob; return 0; }
         double rho_hi;
         WM_CK(cudaMemcpy(&rho_hi, rho, sizeof(double), cudaMemcpyDeviceToHost));
@@ -327,7 +328,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         a.edges = batch;
         spare = filt;
         WM_CK(cudaMemsetAsync(cnts + 2, 0, 6 * sizeof(int), st));
-        traversal_init(1, a, stack, top, xcount, st);
+        traversal_init(1, a, stack, tcnt, st);
         std::vector<cudaEvent_t> evs;   // (start, end) of traversal runs and BCCP flushes, summed per round
         auto mark_event = [&]() {
             if (!C.timing) return;
@@ -340,15 +341,16 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         int steps = 0;
         mark_event();
         while (true) {
-            for (int b = 0; b < kPoll; ++b, ++steps) traversal_step(1, a, stack, top, xbuf, xcount, chunk, st);
+            for (int b = 0; b < kPoll; ++b, ++steps) traversal_step(1, a, stack, xbuf, tcnt, steps, chunk, st);
             WM_CK(cudaMemcpyAsync(C.pin, cnts, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
             WM_CK(cudaMemcpyAsync(C.pin + 8, ovf, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+            WM_CK(cudaMemcpyAsync(C.pin + 16, tcnt, kTravCounters * sizeof(int), cudaMemcpyDeviceToHost, st));
             WM_CK(cudaStreamSynchronize(st));
             if (C.pin[8]) { *overflow_bits = (unsigned)C.pin[8]; return 0; }
-            const int tp = C.pin[0];
+            const bool empty = C.pin[16] == 0 && C.pin[17] == 0 && C.pin[18] == 0;
             int lc[5] = {C.pin[2], C.pin[3], C.pin[4], C.pin[5], C.pin[6]};
             int e = C.pin[7];
-            bool flush = tp == 0;
+            bool flush = empty;
             for (int c = 0; c < 5; ++c) flush = flush || lc[c] > lcap - (long long)kPoll * chunk;
             if (!flush) continue;
             mark_event();
@@ -389,7 +391,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
             if (lc[3] > 0 || lc[4] > 0) C.stats.tile_launches += 1;
             mark_event();
             ev_kind.push_back(1);
-            if (tp == 0) break;
+            if (empty) break;
             if (steps > 10000000) { set_detail("WSPD GetPairs traversal did not terminate%s", ""); return WM_EINTERNAL; }
         }
         WM_CK(cudaMemcpyAsync(C.pin, ecount, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -454,6 +456,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     C.stats.getpairs_visits = (int64_t)hs[4];
     C.stats.getrho_visits = (int64_t)hs[5];
     C.stats.bccp_dual_evals = (int64_t)hs[6];
+    C.stats.max_pending_pairs = (int64_t)hs[7];
     C.stats.rounds = rounds;
     C.stats.pairs_retrieved = (int64_t)hs[0];
     C.stats.bccp_evals = (int64_t)hs[1];

@@ -12,8 +12,9 @@
 //                  candidate inside the rigorous error band of the screened minimum, and the
 //                  K-minimum edge is emitted when its FP64 w2 lies in [rho_lo, rho_hi).
 //
-// Recursion-free form: each traversal keeps a frontier of node pairs; one kernel launch expands
-// one level of the FindPair recursion (children appended with warp-aggregated atomics).
+// Recursion-free form: each traversal keeps a stack of pending node pairs in HBM; one kernel
+// launch pops a chunk of it and every warp expands the pairs it takes depth first, on a stack of
+// its own in shared memory, for a bounded number of rounds (see findpair_dfs_kernel).
 //
 // Well-separation tests use boxes (the nodes' bounding volumes).  Geometric separation is
 // d(A,B) > max(diam A, diam B) with d and diam the box distance and box diagonal, made strict and
@@ -200,80 +201,164 @@ constexpr int kSmallMax = 64;    // 8 lanes per pair
 constexpr int kMediumMax = 1024; // one warp per pair
 constexpr long long kBigMax = 65536; // warp tiles (brute force); larger pairs: pruned dual-tree BCCP
 
-// One level of FindPair.  MODE 0 = GetRho, MODE 1 = GetPairs (classifies retrieved pairs).
+// One FindPair visit of the node pair me (Algorithm 1's recursion body).  MODE 0 = GetRho
+// (WriteMin candidates into rho_cand, pruned by rho_now), MODE 1 = GetPairs (classifies a
+// retrieved pair into cls).  Sets push = 2 with the two child pairs when the pair is split.
 template <int MODE, int DP>
-__global__ void __launch_bounds__(256) findpair_level_kernel(TravArgs a, const int2 *__restrict__ stack,
-                                                             const int *__restrict__ top, int chunk,
-                                                             int2 *__restrict__ out, int *out_count)
+__device__ inline void visit_pair(const TravArgs &a, int2 me, double rho_now, int &push, int2 &c0, int2 &c1, int &cls,
+                                  double &rho_cand)
 {
-    const int tp = *top;
-    const int m = tp < chunk ? tp : chunk;
-    const int2 *__restrict__ in = stack + (tp - m);
-    const int stride = gridDim.x * blockDim.x;
-    const int limit = (m + 31) & ~31;   // whole warps iterate together
+    const int P = me.x, Q = me.y;
+    const int4 lp = a.links[P], lq = a.links[Q];
+    const int sp = lp.y - lp.x, sq = lq.y - lq.x;
+    if (MODE == 0 && sp + sq <= a.beta) return;
+    const float4 mp = a.meta[P], mq = a.meta[Q];
+    const int cp = __float_as_int(mp.w);
+    if (cp >= 0 && cp == __float_as_int(mq.w)) return;   // all points already connected
+    float lbB, ubB, dP, dQ;
+    bool ws;
+    pair_bounds_packed<DP>(a, P, Q, lp, lq, mp, mq, lbB, ubB, ws, dP, dQ);
+    if (MODE == 0) {
+        if ((double)lbB >= rho_now) return;
+        if (ws) { rho_cand = fmin(rho_cand, (double)lbB); return; }
+    } else {
+        if ((double)lbB >= a.rho_hi || (double)ubB < a.rho_lo) return;
+        if (ws) {
+            long long prod = (long long)sp * sq;
+            cls = prod <= kTinyMax ? 0 : prod <= kSmallMax ? 1 : prod <= kMediumMax ? 2 : prod <= kBigMax ? 3 : 4;
+            return;
+        }
+    }
+    // split the node with the larger diameter (a leaf cannot be split)
+    const bool splitP = lp.z >= 0 && (lq.z < 0 || dP >= dQ);
+    const int O = splitP ? Q : P;
+    c0 = make_int2(splitP ? lp.z : lq.z, O);
+    c1 = make_int2(splitP ? lp.w : lq.w, O);
+    push = 2;
+}
+
+// one-per-lane warp append through a ballot; returns this lane's slot (valid where has)
+__device__ inline int warp_append1(int *counter, bool has)
+{
+    const unsigned b = __ballot_sync(0xffffffffu, has);
+    int base = 0;
+    if ((threadIdx.x & 31) == 0 && b) base = atomicAdd(counter, __popc(b));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    return base + __popc(b & lanemask_lt());
+}
+
+// One traversal step.  The pending pairs form a logical stack: the global stack S[0, top) with the
+// previous step's output xin[0, xin_count) on top of it.  The step pops the top min(size, chunk)
+// pairs, and every warp expands the pairs it takes depth first on a stack of its own in shared
+// memory, for at most `budget` rounds of up to 32 pairs; whatever is still pending then (its stack,
+// and pairs it took after the budget ran out) goes to xout.  Pairs of xin beyond one chunk are moved
+// onto S.  The last block to finish sets the new stack size and clears the counters it owns.
+template <int MODE, int DP>
+__global__ void __launch_bounds__(256) findpair_dfs_kernel(TravArgs a, DfsArgs s)
+{
+    __shared__ int2 wst[kDfsWarpsPerBlock][kDfsWarpCap];
     const int lane = threadIdx.x & 31;
-    unsigned long long n_vis = 0, n_ret = 0;
+    int2 *ws = wst[threadIdx.x >> 5];
+    // counts are clamped to the capacities, so that no access leaves the buffers even after an
+    // overflow (the host then discards the traversal)
+    const int tp = min(*s.top, a.frontier_cap), xc = min(*s.xin_count, s.xcap);
+    const int mx = xc < s.chunk ? xc : s.chunk;   // pairs taken from xin (its top part)
+    const int excess = xc - mx;                   // the rest of xin goes onto S
+    const int ms = excess > 0 ? 0 : (tp < s.chunk - mx ? tp : s.chunk - mx);   // pairs taken from S
+    const int m = mx + ms;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < excess; i += gridDim.x * blockDim.x) {
+        if (tp + i < a.frontier_cap) s.S[tp + i] = s.xin[i];
+        else atomicOr(a.overflow, 1u);
+    }
+    auto input = [&](int i) -> int2 { return i < mx ? s.xin[xc - mx + i] : s.S[tp - ms + (i - mx)]; };
     const bool stop = __shfl_sync(0xffffffffu, (int)(*(volatile unsigned *)a.overflow != 0), 0) != 0;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t - lane < limit && !stop; t += stride) {
-        int push = 0;
-        int2 c0 = make_int2(0, 0), c1 = make_int2(0, 0);
-        int cls = -1;   // retrieved pair class: 0 tiny, 1 small, 2 medium, 3 big
-        double rho_cand = INFINITY;
-        int2 me = make_int2(0, 0);
-        if (t < m) {
-            ++n_vis;
-            me = in[t];
-            const int P = me.x, Q = me.y;
-            const int4 lp = a.links[P], lq = a.links[Q];
-            const int sp = lp.y - lp.x, sq = lq.y - lq.x;
-            bool live = !(MODE == 0 && sp + sq <= a.beta);
-            float4 mp = make_float4(0.f, 0.f, 0.f, 0.f), mq = mp;
-            if (live) {
-                mp = a.meta[P];
-                mq = a.meta[Q];
-                int cp = __float_as_int(mp.w);
-                if (cp >= 0 && cp == __float_as_int(mq.w)) live = false;
+    unsigned long long n_vis = 0, n_ret = 0;
+    double rho_w = INFINITY;   // GetRho: smallest candidate this warp has written
+    int sp = 0, it = 0;        // warp stack size (warp-uniform), rounds done
+    bool fed = stop;           // no more input for this warp
+    while (!stop) {
+        if (sp < 32 && !fed) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(s.next, 32);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            const int cnt = base < m ? min(32, m - base) : 0;
+            if (cnt == 0) fed = true;
+            else {
+                if (lane < cnt) ws[sp + lane] = input(base + lane);
+                sp += cnt;
             }
-            if (live) {
-                float lbB, ubB, dP, dQ;
-                bool ws;
-                pair_bounds_packed<DP>(a, P, Q, lp, lq, mp, mq, lbB, ubB, ws, dP, dQ);
-                if (MODE == 0) {
-                    double rho = *(volatile double *)a.rho_out;
-                    if ((double)lbB >= rho) live = false;
-                    else if (ws) { rho_cand = (double)lbB; live = false; }
-                } else {
-                    if ((double)lbB >= a.rho_hi || (double)ubB < a.rho_lo) live = false;
-                    else if (ws) {
-                        long long prod = (long long)sp * sq;
-                        cls = prod <= kTinyMax ? 0 : prod <= kSmallMax ? 1 : prod <= kMediumMax ? 2 : prod <= kBigMax ? 3 : 4;
+            __syncwarp();
+        }
+        // before a round sp <= 63 + 32 * it: a refill happens only below 32 and a round adds at most 32
+        if (sp == 0 || it == s.budget) break;
+        const int k = sp < 32 ? sp : 32;
+        sp -= k;
+        const bool has = lane < k;
+        int2 me = make_int2(0, 0);
+        if (has) me = ws[sp + lane];
+        __syncwarp();
+        int push = 0, cls = -1;
+        int2 c0 = make_int2(0, 0), c1 = c0;
+        double rho_cand = INFINITY;
+        if (has) {
+            ++n_vis;
+            double rho_now = 0.0;
+            if (MODE == 0) rho_now = fmin(*(volatile double *)a.rho_out, rho_w);
+            visit_pair<MODE, DP>(a, me, rho_now, push, c0, c1, cls, rho_cand);
+        }
+        int x = push;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, x, 31);
+        if (push) { ws[sp + x - 2] = c0; ws[sp + x - 1] = c1; }
+        sp += total;
+        __syncwarp();
+        if (MODE == 0) {
+            for (int o = 16; o; o >>= 1) rho_cand = fmin(rho_cand, __shfl_xor_sync(0xffffffffu, rho_cand, o));
+            if (rho_cand < rho_w) {
+                rho_w = rho_cand;
+                if (lane == 0) atomicMinPosD(a.rho_out, rho_cand);
+            }
+        } else {
+            if (__any_sync(0xffffffffu, cls >= 0)) {
+#pragma unroll
+                for (int c = 0; c < 5; ++c) {
+                    int bs = warp_append1(a.list_count + c, cls == c);
+                    if (cls == c) {
                         ++n_ret;
-                        live = false;
+                        if (bs < a.list_cap[c]) a.list[c][bs] = me;
+                        else atomicOr(a.overflow, 4u);
                     }
-                }
-                if (live) {
-                    // split the node with the larger diameter (a leaf cannot be split)
-                    bool splitP = lp.z >= 0 && (lq.z < 0 || dP >= dQ);
-                    int O = splitP ? Q : P;
-                    c0 = make_int2(splitP ? lp.z : lq.z, O);
-                    c1 = make_int2(splitP ? lp.w : lq.w, O);
-                    push = 2;
                 }
             }
         }
-        int slot = warp_append(out_count, push);
-        if (push) { out[slot] = c0; out[slot + 1] = c1; }   // out holds 2 * chunk pairs
-        if (MODE == 0) {
-            for (int o = 16; o; o >>= 1) rho_cand = fmin(rho_cand, __shfl_xor_sync(0xffffffffu, rho_cand, o));
-            if (lane == 0 && rho_cand < INFINITY) atomicMinPosD(a.rho_out, rho_cand);
-        } else {
-#pragma unroll
-            for (int c = 0; c < 5; ++c) {
-                int bs = warp_append(a.list_count + c, cls == c ? 1 : 0);
-                if (cls == c) {
-                    if (bs < a.list_cap[c]) a.list[c][bs] = me;
-                    else atomicOr(a.overflow, 4u);
-                }
+        ++it;
+    }
+    if (!stop) {
+        // budget spent: the warp stack, then the input this warp still takes, go to xout
+        if (sp > 0) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(s.xout_count, sp);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            for (int i = lane; i < sp; i += 32) {
+                if (base + i < s.xcap) s.xout[base + i] = ws[i];
+                else atomicOr(a.overflow, 1u);
+            }
+        }
+        while (!fed) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(s.next, 32);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            const int cnt = base < m ? min(32, m - base) : 0;
+            if (cnt == 0) break;
+            int ob = 0;
+            if (lane == 0) ob = atomicAdd(s.xout_count, cnt);
+            ob = __shfl_sync(0xffffffffu, ob, 0);
+            if (lane < cnt) {
+                if (ob + lane < s.xcap) s.xout[ob + lane] = input(base + lane);
+                else atomicOr(a.overflow, 1u);
             }
         }
     }
@@ -282,6 +367,20 @@ __global__ void __launch_bounds__(256) findpair_level_kernel(TravArgs a, const i
     if (lane == 0 && n_vis) {
         atomicAdd(a.stat + (MODE == 0 ? 5 : 4), n_vis);
         if (n_ret) atomicAdd(a.stat + 0, n_ret);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(s.done, 1u);
+        if (t == gridDim.x - 1) {
+            const int nt = tp + excess - ms;
+            *s.top = nt < a.frontier_cap ? nt : a.frontier_cap;
+            atomicMax(a.stat + 7, (unsigned long long)nt + (unsigned long long)*(volatile int *)s.xout_count);
+            *s.xin_count = 0;   // xin is the next step's output buffer
+            *s.next = 0;
+            *s.done = 0;
+            __threadfence();
+        }
     }
 }
 
@@ -874,71 +973,69 @@ void launch_comp_labels(const Tree &T, const Points &P, int *uf, float4 *meta, c
 }
 
 // ----------------------------------------------------------- bounded-memory traversal
-// The frontier is a stack of node pairs.  One step pops the top min(top, chunk) pairs, expands
-// them (children into a scratch buffer of 2*chunk pairs) and pushes the children back: depth
-// first in chunks, so the stack never holds more than the initial pairs plus about 2*chunk per
-// recursion level.
-__global__ void stack_push_kernel(int2 *__restrict__ stack, const int *__restrict__ top, int chunk,
-                                  const int2 *__restrict__ x, const int *__restrict__ xcount, int cap, unsigned *overflow)
+// The pending pairs form a stack (S plus the previous step's output on top of it).  One step pops
+// at most `chunk` pairs and pushes back at most chunk + warps * kDfsWarpCap, so the stack grows by
+// a bounded amount per step while the traversal goes depth first.
+void traversal_init(int mode, TravArgs &a, int2 *stack, int *cnt, cudaStream_t st)
 {
-    const int tp = *top;
-    const int base = tp - (tp < chunk ? tp : chunk);
-    const int m = *xcount;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-        if (base + i < cap) stack[base + i] = x[i];
-        else atomicOr(overflow, 1u);
-    }
+    cudaMemsetAsync(cnt, 0, sizeof(int) * kTravCounters, st);
+    launch(frontier_init_kernel, grid_for(a.N, 256), 256, 0, st, a, mode, stack, cnt + 0);
 }
 
-__global__ void stack_top_kernel(int *top, int chunk, int *xcount, int cap)
+// Warps of a step: at most chunk / kDfsWarpCap, so that a step's output (at most the chunk it
+// popped plus every warp's full stack) fits in 2 * chunk pairs, and a step visits fewer than
+// chunk pairs (warps * 32 * kDfsBudget).
+int dfs_warps(int chunk)
 {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        int tp = *top;
-        int base = tp - (tp < chunk ? tp : chunk);
-        int nt = base + *xcount;
-        *top = nt < cap ? nt : cap;
-        *xcount = 0;
-    }
+    long long w = chunk / kDfsWarpCap;
+    w = w > 152 * 4 * kDfsWarpsPerBlock ? 152 * 4 * kDfsWarpsPerBlock : w;
+    w = w / kDfsWarpsPerBlock * kDfsWarpsPerBlock;
+    return (int)(w < kDfsWarpsPerBlock ? kDfsWarpsPerBlock : w);
 }
 
-void traversal_init(int mode, TravArgs &a, int2 *stack, int *top, int *xcount, cudaStream_t st)
-{
-    cudaMemsetAsync(top, 0, sizeof(int), st);
-    cudaMemsetAsync(xcount, 0, sizeof(int), st);
-    launch(frontier_init_kernel, grid_for(a.N, 256), 256, 0, st, a, mode, stack, top);
-}
+long long dfs_out_cap(int chunk) { return (long long)chunk + (long long)dfs_warps(chunk) * kDfsWarpCap; }
 
-void traversal_step(int mode, TravArgs &a, int2 *stack, int *top, int2 *x, int *xcount, int chunk, cudaStream_t st)
+void traversal_step(int mode, TravArgs &a, int2 *stack, int2 *const xbuf[2], int *cnt, int step, int chunk,
+                    cudaStream_t st)
 {
-    const int grid = grid_for((long long)chunk, 256, 152 * 8);
-#define WM_FP(DPV)                                                                                          \
-    do {                                                                                                    \
-        if (mode == 0) launch(findpair_level_kernel<0, DPV>, grid, 256, 0, st, a, stack, top, chunk, x, xcount); \
-        else launch(findpair_level_kernel<1, DPV>, grid, 256, 0, st, a, stack, top, chunk, x, xcount);           \
+    DfsArgs s;
+    const int cur = step & 1;
+    s.S = stack;
+    s.top = cnt + 0;
+    s.xin = xbuf[cur];
+    s.xin_count = cnt + (cur ? 2 : 1);
+    s.xout = xbuf[cur ^ 1];
+    s.xout_count = cnt + (cur ? 1 : 2);
+    s.next = cnt + 3;
+    s.done = (unsigned *)(cnt + 4);
+    s.chunk = chunk;
+    s.xcap = (int)std::min<long long>(dfs_out_cap(chunk), 2LL * chunk);   // the output buffers hold 2 * chunk pairs
+    s.budget = kDfsBudget;
+    const int grid = dfs_warps(chunk) / kDfsWarpsPerBlock;
+#define WM_FP(DPV)                                                                                \
+    do {                                                                                          \
+        if (mode == 0) launch(findpair_dfs_kernel<0, DPV>, grid, 32 * kDfsWarpsPerBlock, 0, st, a, s); \
+        else launch(findpair_dfs_kernel<1, DPV>, grid, 32 * kDfsWarpsPerBlock, 0, st, a, s);           \
     } while (0)
     if (a.dp == 4) WM_FP(4);
     else if (a.dp == 8) WM_FP(8);
     else WM_FP(16);
 #undef WM_FP
-    launch(stack_push_kernel, grid_for((long long)2 * chunk, 256), 256, 0, st, stack, top, chunk, x, xcount,
-           a.frontier_cap, a.overflow);
-    launch(stack_top_kernel, 1, 32, 0, st, top, chunk, xcount, a.frontier_cap);
 }
 
-// GetRho: the whole traversal, polling emptiness every 4 steps.
-int run_traversal(int mode, TravArgs &a, int2 *stack, int2 *x, int *counters, int chunk, cudaStream_t st, int *pinned,
+// GetRho: the whole traversal, polling emptiness every 2 steps.
+int run_traversal(TravArgs &a, int2 *stack, int2 *const xbuf[2], int *cnt, int chunk, cudaStream_t st, int *pinned,
                   unsigned *overflow_out, int *steps_out)
 {
-    int *top = counters, *xcount = counters + 1;
-    traversal_init(mode, a, stack, top, xcount, st);
+    traversal_init(0, a, stack, cnt, st);
     int steps = 0;
     while (true) {
-        for (int b = 0; b < 4; ++b, ++steps) traversal_step(mode, a, stack, top, x, xcount, chunk, st);
-        cudaMemcpyAsync(pinned, top, sizeof(int), cudaMemcpyDeviceToHost, st);
-        cudaMemcpyAsync(pinned + 1, a.overflow, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+        for (int b = 0; b < 2; ++b, ++steps) traversal_step(0, a, stack, xbuf, cnt, steps, chunk, st);
+        cudaMemcpyAsync(pinned, cnt, sizeof(int) * kTravCounters, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(pinned + kTravCounters, a.overflow, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
         if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;
-        if (pinned[1]) { *overflow_out = (unsigned)pinned[1]; return 0; }
-        if (pinned[0] == 0) break;
+        if (pinned[kTravCounters]) { *overflow_out = (unsigned)pinned[kTravCounters]; return 0; }
+        if (pinned[0] == 0 && pinned[1] == 0 && pinned[2] == 0) break;
         if (steps > 10000000) {
             set_error_detail("WSPD traversal did not terminate");
             return WM_EINTERNAL;

@@ -44,14 +44,40 @@ struct TravArgs {
     int edge_cap = 0;
     unsigned *overflow = nullptr;      // bit 0 frontier, bit 1 edges, bit 2 big pairs
     unsigned long long *stat = nullptr; // [0] pairs retrieved, [1] evals, [2] fp64 rechecks,
-                                        // [3] tile evals, [4] GetPairs visits, [5] GetRho visits
+                                        // [3] tile evals, [4] GetPairs visits, [5] GetRho visits,
+                                        // [6] dual-tree evals, [7] peak pending pairs
 };
 
+// Depth-first traversal step (see findpair_dfs_kernel): warps per block, rounds per warp and
+// the capacity of a warp's stack in shared memory (at most 63 + 32 * rounds pairs are pending).
+constexpr int kDfsWarpsPerBlock = 8;
+constexpr int kDfsBudget = 8;
+constexpr int kDfsWarpCap = 64 + 32 * kDfsBudget;
+// traversal counters: [0] stack size, [1] / [2] counts of the two step output buffers,
+// [3] input dispenser, [4] finished blocks
+constexpr int kTravCounters = 8;
+
+struct DfsArgs {
+    int2 *S = nullptr;            // the stack
+    int *top = nullptr;           // its size
+    const int2 *xin = nullptr;    // previous step's output (top of the logical stack)
+    int *xin_count = nullptr;
+    int2 *xout = nullptr;         // this step's output
+    int *xout_count = nullptr;
+    int *next = nullptr;
+    unsigned *done = nullptr;
+    int chunk = 0, xcap = 0, budget = 0;
+};
+
+int dfs_warps(int chunk);
+long long dfs_out_cap(int chunk);   // pairs one step can write to its output buffer
+
 void launch_comp_labels(const Tree &T, const Points &P, int *uf, float4 *meta, cudaStream_t st);
-int run_traversal(int mode, TravArgs &a, int2 *stack, int2 *x, int *counters, int chunk, cudaStream_t st, int *pinned,
+int run_traversal(TravArgs &a, int2 *stack, int2 *const xbuf[2], int *cnt, int chunk, cudaStream_t st, int *pinned,
                   unsigned *overflow_out, int *steps_out);
-void traversal_init(int mode, TravArgs &a, int2 *stack, int *top, int *xcount, cudaStream_t st);
-void traversal_step(int mode, TravArgs &a, int2 *stack, int *top, int2 *x, int *xcount, int chunk, cudaStream_t st);
+void traversal_init(int mode, TravArgs &a, int2 *stack, int *cnt, cudaStream_t st);
+void traversal_step(int mode, TravArgs &a, int2 *stack, int2 *const xbuf[2], int *cnt, int step, int chunk,
+                    cudaStream_t st);
 void sample_w2(const EdgeK *e, int m, int k, double *out, cudaStream_t st);
 void keep_below(const EdgeK *in, int m, double bound, EdgeK *out, int *count, cudaStream_t st);
 int run_bccp_tiles(TravArgs &a, int m, long long *jobs, long long *total, cudaStream_t st, Arena &ar, bool hdb,
