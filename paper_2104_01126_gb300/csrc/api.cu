@@ -81,7 +81,7 @@ static size_t estimate_bytes(long long n, int d, int min_pts, const Caps &c)
     size_t b = 0;
     b += (size_t)n * d * 8;                 // device copy of the input
     b += (size_t)n * d * 12 * 2;            // points + build scratch
-    b += (size_t)n * 16;                    // pid, pos, uf, R
+    b += (size_t)n * 24;                    // pid, pos, uf, R, component-label scratch
     b += (size_t)N * (8 * d + 48);          // tree arrays (+ build scratch counters)
     b += (size_t)n * 8;                     // small lists
     b += (size_t)N * (32 + 8 * dp);         // packed node records
@@ -266,6 +266,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     double *samples = ar.get<double>(4096);
     unsigned *ovf = ar.get<unsigned>(2);
     unsigned long long *stat = ar.get<unsigned long long>(8);
+    int *comp_scratch = ar.get<int>(2LL * n + 1);
     if (ar.failed) return WM_ENOMEM;
     // counters: [2..6] pair-list counts, [7] edge count, [8] filtered count, [9] repair lower
     // bound, [10..11] / [12..13] 64-bit job totals, [32..32+kTravCounters) traversal state
@@ -312,7 +313,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     while (nE < n - 1) {
         if (++rounds > 4096) { set_detail("MemoGFK made no progress%s (%lld rounds)", "", rounds); return WM_EINTERNAL; }
         Timer tw;
-        launch_comp_labels(T, P, uf, meta, st);
+        WM_TRY(launch_comp_labels(T, P, uf, links, meta, comp_scratch, ar, st));
         // ---- GetRho
         WM_CK(cudaMemcpyAsync(rho, &inf, sizeof(double), cudaMemcpyHostToDevice, st));
         a.beta = (int)std::min<long long>(beta, 0x7fffffff);

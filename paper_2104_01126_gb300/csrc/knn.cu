@@ -45,6 +45,7 @@ struct KnnArgs {
     int *rep_cnt;        // [n]
     int *slow;           // slow query list
     int *slow_cnt;
+    int *next_group;     // dispenser of 32-query groups
     unsigned long long *stat;   // [0] evals, [1] fp64 rechecks
 };
 
@@ -72,6 +73,17 @@ __device__ inline float knn_threshold(float s, double eta)
     return __double2float_ru(t);
 }
 
+// Upper bound of knn_threshold(s, 0) in FP32 with directed rounding: s (1 + 2^-17) + 1.6e-42, both
+// steps rounded up (1.6e-42 as a float exceeds 1.5e-42).  Any float >= the exact threshold is
+// >= its rounded-up value as well, so it can stand in for it as a pruning bound.
+__device__ inline float knn_threshold_fast(float s)
+{
+    return __fadd_ru(__fmul_ru(s, 1.0f + 4.0f / 524288.0f), 1.6e-42f);
+}
+
+// coordinates per leaf point in the shared-memory broadcast buffer (d rounded up to 4)
+template <int DM> constexpr int knn_dmp() { return (DM + 3) / 4 * 4; }
+
 template <int DM, bool FP64>
 __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
 {
@@ -79,26 +91,35 @@ __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
     extern __shared__ unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
     const int KL = a.KL;
-    // per-warp shared region: V sv[KL][32]; int sj[KL][32] (slot-major, one bank per lane);
-    // the FP64 candidate values of the epilogue live in global scratch: double sw[KL][32]
-    size_t per_warp = (size_t)KL * 32 * (sizeof(V) + sizeof(int));
+    // per-warp shared region: float4 leaf[32][DMP/4] (the scanned subtree's points, read as
+    // broadcasts); V sv[KL][32]; int sj[KL][32] (slot-major, one bank per lane); the FP64
+    // candidate values of the epilogue live in global scratch: double sw[KL][32]
+    constexpr int DMP = knn_dmp<DM>(), DQ = DMP / 4;
+    size_t per_warp = (size_t)32 * DMP * sizeof(float) + (size_t)KL * 32 * (sizeof(V) + sizeof(int));
     unsigned char *base = smem_raw + per_warp * wib;
-    V *sv = (V *)base;
-    int *sj = (int *)(base + (size_t)KL * 32 * sizeof(V));
-    const int gw = blockIdx.x * nwb + wib, nw = gridDim.x * nwb;
+    float4 *leaf = (float4 *)base;
+    V *sv = (V *)(base + (size_t)32 * DMP * sizeof(float));
+    int *sj = (int *)((unsigned char *)sv + (size_t)KL * 32 * sizeof(V));
+    const int gw = blockIdx.x * nwb + wib;
     double *sw = a.wscratch + (size_t)gw * KL * 32;
     int *stk = a.stack + (size_t)gw * a.stack_cap;
     const int n = a.n, d = a.d;
+    const bool exact32 = a.eta == 0.0;   // FP32 copy is exact: threshold in FP32
     unsigned long long n_ev = 0, n_re = 0;
-    for (int q0 = gw * 32; q0 < n; q0 += nw * 32) {
+    while (true) {
+        int q0 = 0;
+        if (lane == 0) q0 = atomicAdd(a.next_group, 32);
+        q0 = __shfl_sync(0xffffffffu, q0, 0);
+        if (q0 >= n) break;
         const int i = q0 + lane;
         const bool valid = i < n;
-        float qx[DM];
+        float qx[DMP];
         double qx64[DM];
+#pragma unroll
+        for (int k = 0; k < DMP; ++k) qx[k] = k < d && valid ? a.x32[(size_t)k * n + i] : 0.f;
 #pragma unroll
         for (int k = 0; k < DM; ++k) {
             if (k < d) {
-                qx[k] = valid ? a.x32[(size_t)k * n + i] : 0.f;
                 if (FP64) qx64[k] = valid ? a.x64[(size_t)k * n + i] : 0.0;
             }
         }
@@ -135,14 +156,23 @@ __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
             if (e - b <= 32) {
                 // scan the subtree's points
                 const int m = e - b;
-                float px[DM];
                 double px64[DM];
+                if (FP64) {
 #pragma unroll
-                for (int k = 0; k < DM; ++k) {
-                    if (k < d) {
-                        px[k] = lane < m ? a.x32[(size_t)k * n + b + lane] : 0.f;
-                        if (FP64) px64[k] = lane < m ? a.x64[(size_t)k * n + b + lane] : 0.0;
+                    for (int k = 0; k < DM; ++k)
+                        if (k < d) px64[k] = lane < m ? a.x64[(size_t)k * n + b + lane] : 0.0;
+                } else {
+                    if (lane < m) {
+#pragma unroll
+                        for (int c = 0; c < DQ; ++c) {
+                            float v[4];
+#pragma unroll
+                            for (int r = 0; r < 4; ++r)
+                                v[r] = 4 * c + r < d ? a.x32[(size_t)(4 * c + r) * n + b + lane] : 0.f;
+                            leaf[lane * DQ + c] = make_float4(v[0], v[1], v[2], v[3]);
+                        }
                     }
+                    __syncwarp();
                 }
                 for (int p = 0; p < m; ++p) {
                     V s;
@@ -157,11 +187,15 @@ __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
                         }
                         s = (V)acc;
                     } else {
+                        // padded coordinates are 0 on both sides and add nothing
                         float acc = 0.f;
 #pragma unroll
-                        for (int k = 0; k < DM; ++k) {
-                            if (k < d) {
-                                float t = qx[k] - __shfl_sync(0xffffffffu, px[k], p);
+                        for (int c = 0; c < DQ; ++c) {
+                            const float4 v = leaf[p * DQ + c];
+                            const float pv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) {
+                                float t = qx[4 * c + r] - pv[r];
                                 acc = fmaf(t, t, acc);
                             }
                         }
@@ -177,13 +211,16 @@ __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
                         sv[pos * 32 + lane] = s;
                         sj[pos * 32 + lane] = b + p;
                         if (cnt < KL) ++cnt;
-                        if (cnt == KL) thr = sv[(KL - 1) * 32 + lane];
                         if (cnt >= a.k && pos < a.k) {
                             V sk = sv[(a.k - 1) * 32 + lane];
-                            cut = FP64 ? sk : (V)knn_threshold((float)sk, a.eta);
+                            cut = FP64 ? sk : exact32 ? (V)knn_threshold_fast((float)sk) : (V)knn_threshold((float)sk, a.eta);
+                            // entries above the cut can never be candidates again: drop them
+                            while (cnt > a.k && sv[(cnt - 1) * 32 + lane] > cut) --cnt;
                         }
+                        thr = cnt == KL ? sv[(KL - 1) * 32 + lane] : (V)INFINITY;
                     }
                 }
+                if (!FP64) __syncwarp();   // the leaf buffer is reused by the next scan
                 n_ev += (unsigned long long)m;
             } else {
                 // push the farther child first so the nearer one is visited next
@@ -453,12 +490,15 @@ int core_distances(Points &P, Tree &T, int min_pts, bool fp64, HdbState &H, Aren
     if (ar.failed) return WM_ENOMEM;
     cudaMemsetAsync(cnts, 0, 8 * sizeof(int), st);
     cudaMemsetAsync(a.stat, 0, 4 * sizeof(unsigned long long), st);
-    // launch shape: warps per block limited by shared memory
-    size_t per_warp = (size_t)KL * 32 * ((fp64 ? 8 : 4) + 4);
-    int wpb = (int)std::min<size_t>(8, std::max<size_t>(1, (96u << 10) / per_warp));
+    // launch shape: warps per block limited by shared memory; 32-query groups are handed out
+    // dynamically, so the grid only has to fill the SMs
+    const int dmp = d <= 3 ? 4 : d <= 7 ? 8 : 16;
+    size_t per_warp = (size_t)32 * dmp * 4 + (size_t)KL * 32 * ((fp64 ? 8 : 4) + 4);
+    int wpb = (int)std::min<size_t>(8, std::max<size_t>(1, (48u << 10) / per_warp));
     size_t smem = per_warp * wpb;
-    int blocks = 152 * std::max(1, 16 / wpb);
+    int blocks = 152 * std::max(1, 32 / wpb);
     int total_warps = blocks * wpb;
+    a.next_group = cnts + 6;
     a.stack = ar.get<int>((size_t)total_warps * a.stack_cap);
     a.wscratch = ar.get<double>((size_t)total_warps * KL * 32);
     if (!a.stack || !a.wscratch) return WM_ENOMEM;

@@ -498,28 +498,28 @@ __global__ void uf_flatten_kernel(int *uf, int n)
     }
 }
 
-// bottom-up: comp(leaf) = root of its point; comp(node) = common comp of the children or -1.
-__global__ void comp_labels_kernel(int N, const int *__restrict__ left, const int *__restrict__ right,
-                                   const int *__restrict__ parent, const int *__restrict__ begin,
-                                   const int *__restrict__ pid, const int *__restrict__ uf, int *comp, int *arrive,
-                                   float4 *meta)
+// Component labels.  A node's points are the tree positions [begin, end); they all lie in one
+// component iff the per-position label (the union-find root of the point) does not change inside
+// the range.  With chg[i] = (lab[i] != lab[i-1]) and E its exclusive prefix sum, node x is in one
+// component iff E[end] == E[begin + 1].
+__global__ void pos_labels_kernel(const int *__restrict__ pid, const int *__restrict__ uf, int n, int *__restrict__ lab,
+                                  int *__restrict__ chg)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int l = uf[pid[i]];
+        lab[i] = l;
+        chg[i] = i > 0 && l != uf[pid[i - 1]];
+    }
+}
+
+__global__ void node_labels_kernel(int N, const int4 *__restrict__ links, const int *__restrict__ lab,
+                                   const int *__restrict__ E, int *__restrict__ comp, float4 *__restrict__ meta)
 {
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x) {
-        if (left[x] >= 0) continue;
-        comp[x] = uf[pid[begin[x]]];
-        if (meta) ((int *)(meta + x))[3] = comp[x];
-        int cur = x;
-        for (int it = 0; it < N; ++it) {
-            int p = parent[cur];
-            if (p < 0) break;
-            __threadfence();
-            if (atomicAdd(&arrive[p], 1) == 0) break;
-            __threadfence();
-            int cl = ((volatile int *)comp)[left[p]], cr = ((volatile int *)comp)[right[p]];
-            comp[p] = (cl >= 0 && cl == cr) ? cl : -1;
-            if (meta) ((int *)(meta + p))[3] = comp[p];
-            cur = p;
-        }
+        const int4 L = links[x];
+        const int c = E[L.y] == E[L.x + 1] ? lab[L.x] : -1;
+        comp[x] = c;
+        ((int *)(meta + x))[3] = c;
     }
 }
 
@@ -964,12 +964,17 @@ __global__ void __launch_bounds__(256) bccp_tile_kernel(TravArgs a, int m, const
 
 // ----------------------------------------------------------------------------- host side
 
-void launch_comp_labels(const Tree &T, const Points &P, int *uf, float4 *meta, cudaStream_t st)
+int launch_comp_labels(const Tree &T, const Points &P, int *uf, const int4 *links, float4 *meta, int *scratch,
+                       Arena &ar, cudaStream_t st)
 {
-    launch(uf_flatten_kernel, grid_for(P.n, 256), 256, 0, st, uf, P.n);
-    cudaMemsetAsync(T.arrive, 0, sizeof(int) * T.N, st);
-    launch(comp_labels_kernel, grid_for(T.N, 256), 256, 0, st, T.N, T.left, T.right, T.parent, T.begin, P.pid, uf,
-                                                         T.comp, T.arrive, meta);
+    const int n = P.n;
+    int *lab = scratch, *E = scratch + n;   // E holds n + 1 entries
+    launch(uf_flatten_kernel, grid_for(n, 256), 256, 0, st, uf, n);
+    launch(pos_labels_kernel, grid_for(n, 256), 256, 0, st, P.pid, uf, n, lab, E);
+    int rc = scan_exclusive_i32(E, E, n, E + n, st, ar);
+    if (rc) return rc;
+    launch(node_labels_kernel, grid_for(T.N, 256), 256, 0, st, T.N, links, lab, E, T.comp, meta);
+    return 0;
 }
 
 // ----------------------------------------------------------- bounded-memory traversal

@@ -72,7 +72,10 @@ struct DfsArgs {
 int dfs_warps(int chunk);
 long long dfs_out_cap(int chunk);   // pairs one step can write to its output buffer
 
-void launch_comp_labels(const Tree &T, const Points &P, int *uf, float4 *meta, cudaStream_t st);
+// component label of every node (-1 when its points span several components), into T.comp and
+// meta[x].w; scratch holds 2 n + 1 ints
+int launch_comp_labels(const Tree &T, const Points &P, int *uf, const int4 *links, float4 *meta, int *scratch,
+                       Arena &ar, cudaStream_t st);
 int run_traversal(TravArgs &a, int2 *stack, int2 *const xbuf[2], int *cnt, int chunk, cudaStream_t st, int *pinned,
                   unsigned *overflow_out, int *steps_out);
 void traversal_init(int mode, TravArgs &a, int2 *stack, int *cnt, cudaStream_t st);
