@@ -26,8 +26,8 @@ int ingest_points(const void *dev_src, int n, int d, int dtype, int layout, Poin
                   unsigned *pinned);
 int build_tree(Points &P, Tree &T, Arena &ar, cudaStream_t st, int *pinned);
 int filter_connected(const EdgeK *in, int m, const int *uf, EdgeK *out, int *count_dev, cudaStream_t st);
-int batch_kruskal(const EdgeK *e, int m, int n, int *uf, int *R, EdgeK *out, int out_base, int *accepted, Arena &ar,
-                  cudaStream_t st, int *pinned);
+int batch_kruskal(const EdgeK *e, int m, int n, int *uf, unsigned long long *R, EdgeK *out, int out_base, int *accepted,
+                  Arena &ar, cudaStream_t st, int *pinned);
 
 // ----------------------------------------------------------------------------- error state
 static thread_local std::string g_detail;
@@ -81,7 +81,7 @@ static size_t estimate_bytes(long long n, int d, int min_pts, const Caps &c)
     size_t b = 0;
     b += (size_t)n * d * 8;                 // device copy of the input
     b += (size_t)n * d * 12 * 2;            // points + build scratch
-    b += (size_t)n * 24;                    // pid, pos, uf, R, component-label scratch
+    b += (size_t)n * 36;                    // pid, pos, uf, R (2 x 8 B), component-label scratch
     b += (size_t)N * (8 * d + 48);          // tree arrays (+ build scratch counters)
     b += (size_t)n * 8;                     // small lists
     b += (size_t)N * (32 + 8 * dp);         // packed node records
@@ -112,11 +112,12 @@ static Caps default_caps(long long n, int min_pts)
 // ------------------------------------------------------------------------------- kernels
 namespace {
 
-__global__ void init_uf_kernel(int *uf, int *R, int n)
+__global__ void init_uf_kernel(int *uf, unsigned long long *R, int n)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         uf[i] = i;
-        R[i] = 0x7fffffff;
+        R[i] = ~0ull;
+        R[n + i] = ~0ull;
     }
 }
 
@@ -230,7 +231,7 @@ struct Timer {
 // MemoGFK rounds (Algorithm 3).  On return E_out holds the n-1 tree edges in K order.
 // hdb: optional HDBSCAN* state (node cd bounds, per-position cd2, sorted repair edges).
 static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps &caps, EdgeK *E_out, int *uf,
-                   int *R, unsigned *overflow_bits)
+                   unsigned long long *R, unsigned *overflow_bits)
 {
     const int n = P.n;
     cudaStream_t st = C.st;
@@ -437,9 +438,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
             WM_CK(cudaStreamSynchronize(st));
             int mf = C.pin[0];
             C.stats.candidate_edges += mf;
-            EdgeK *sorted = fout;
-            WM_TRY(radix_sort_edges(fout, tmp, mf, st, ar, &sorted, C.pin + 4096));
-            WM_TRY(batch_kruskal(sorted, mf, n, uf, R, E_out, nE, &accepted, ar, st, C.pin));
+            WM_TRY(batch_kruskal(fout, mf, n, uf, R, E_out, nE, &accepted, ar, st, C.pin));
         }
         C.stats.ms_kruskal += tk.ms();
         nE += accepted;
@@ -449,6 +448,15 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         }
         rho_lo = rho_hi;
         beta *= 2;
+    }
+    {
+        // every round appended its tree edges unordered: put the tree in K order
+        Timer ts;
+        EdgeK *sorted = E_out;
+        WM_TRY(radix_sort_edges(E_out, tmp, n - 1, st, ar, &sorted, C.pin + 4096));
+        if (sorted != E_out) WM_CK(cudaMemcpyAsync(E_out, sorted, sizeof(EdgeK) * (n - 1), cudaMemcpyDeviceToDevice, st));
+        WM_CK(cudaStreamSynchronize(st));
+        C.stats.ms_kruskal += ts.ms();
     }
     WM_CK(cudaMemcpyAsync(C.pin, stat, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     WM_CK(cudaStreamSynchronize(st));
@@ -632,7 +640,8 @@ static int emst_body(Call &C, void *vctx, const Caps &caps, unsigned *ovf)
     Prepared S;
     WM_TRY(prepare(C, x.pts, x.n, x.d, x.dtype, x.layout, S));
     const int n = (int)x.n;
-    int *uf = C.ar.get<int>(n), *R = C.ar.get<int>(n);
+    int *uf = C.ar.get<int>(n);
+    unsigned long long *R = C.ar.get<unsigned long long>(2LL * n);
     EdgeK *E = C.ar.get<EdgeK>(n);
     if (C.ar.failed) return WM_ENOMEM;
     launch(init_uf_kernel, grid_for(n, 256), 256, 0, C.st, uf, R, n);
@@ -662,7 +671,8 @@ static int hdbscan_body(Call &C, void *vctx, const Caps &caps, unsigned *ovf)
     Timer tc;
     WM_TRY(core_distances(S.P, S.T, x.min_pts, C.precision == WM_PREC_FP64, H, C.ar, C.st, C.pin, &C.stats));
     C.stats.ms_core_dist = tc.ms();
-    int *uf = C.ar.get<int>(n), *R = C.ar.get<int>(n);
+    int *uf = C.ar.get<int>(n);
+    unsigned long long *R = C.ar.get<unsigned long long>(2LL * n);
     EdgeK *E = C.ar.get<EdgeK>(n);
     if (C.ar.failed) return WM_ENOMEM;
     launch(init_uf_kernel, grid_for(n, 256), 256, 0, C.st, uf, R, n);

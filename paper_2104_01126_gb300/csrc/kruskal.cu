@@ -1,13 +1,17 @@
 // kruskal.cu -- batched Kruskal over a union-find shared across rounds (Sec. 3.1.2
 // "ParallelKruskal", Algorithms 2 and 3), made deterministic with reservations.
 //
-// A batch of edges sorted by K is accepted exactly as sequential Kruskal would accept it: edge i
-// (its index in the sorted batch is its priority) finds the roots of its endpoints; equal roots
-// reject it.  Otherwise it reserves both roots with a WriteMin of its priority.  An edge that
-// holds the reservation of a root links that root under the other root and is accepted; edges
-// that hold neither retry in the next step.  The lowest-priority edge touching a root always
-// wins it, so every step accepts or rejects at least one edge, and an edge is accepted only when
-// no earlier pending edge touches the component it links, which is the sequential condition.
+// A batch of edges is accepted exactly as sequential Kruskal would accept it in the order of the
+// key K = (w2, min id, max id), without sorting the batch: every pending edge finds the roots of
+// its endpoints; equal roots reject it.  Otherwise it reserves both roots with a WriteMin of its
+// key (two 64-bit WriteMins: the w2 bits, then, among the edges with the winning w2, the id
+// pair).  An edge that holds the reservation of a root links that root under the other root and
+// is accepted; edges that hold neither retry in the next step.  The K-smallest pending edge
+// touching a root always wins it, so every step accepts or rejects at least one edge, and an
+// edge is accepted only when no K-smaller pending edge touches the component it links, which is
+// the sequential condition.  Exact copies of an edge (the same key twice in a batch) all win the
+// same root; the link is a compare-and-swap, so one copy links and the others are rejected in
+// the next step.
 #include <cstdio>
 
 #include "wm_internal.cuh"
@@ -66,15 +70,6 @@ __global__ void filter_connected_kernel(const EdgeK *__restrict__ in, int m, con
     }
 }
 
-// Every edge handed to Kruskal must have 0 <= u < v < n.
-__global__ void validate_edges_kernel(const EdgeK *__restrict__ e, int m, int n, int *bad)
-{
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-        int u = edge_u(e[i]), v = edge_v(e[i]);
-        if (u < 0 || u >= v || v >= n) atomicOr(bad, 1);
-    }
-}
-
 __global__ void init_list_kernel(int *list, int m, int *status)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
@@ -83,41 +78,96 @@ __global__ void init_list_kernel(int *list, int m, int *status)
     }
 }
 
-__global__ void reserve_kernel(const EdgeK *__restrict__ e, const int *__restrict__ list, const int *__restrict__ cnt,
-                               int *uf, int *R, int2 *__restrict__ roots, int *__restrict__ status)
+// Finds the roots; rejects edges inside one component (and invalid edges, flagged in *bad: every
+// edge must have 0 <= u < v < n); WriteMin of the w2 bits on both roots.
+__global__ void reserve_hi_kernel(const EdgeK *__restrict__ e, const int *__restrict__ list, const int *__restrict__ cnt,
+                                  int n, int *uf, unsigned long long *Rhi, int2 *__restrict__ roots,
+                                  int *__restrict__ status, int *bad)
 {
     const int m = *cnt;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
-        int i = list[j];
-        EdgeK x = e[i];
-        int ru = uf_find_halving(uf, edge_u(x)), rv = uf_find_halving(uf, edge_v(x));
+        const int i = list[j];
+        const EdgeK x = e[i];
+        const int u = edge_u(x), v = edge_v(x);
+        if (u < 0 || u >= v || v >= n) {
+            atomicOr(bad, 1);
+            status[i] = kReject;
+            roots[j] = make_int2(-1, -1);
+            continue;
+        }
+        const int ru = uf_find_halving(uf, u), rv = uf_find_halving(uf, v);
         if (ru == rv) {
             status[i] = kReject;
             roots[j] = make_int2(-1, -1);
         } else {
             roots[j] = make_int2(ru, rv);
-            atomicMin(&R[ru], i);
-            atomicMin(&R[rv], i);
+            atomicMin(&Rhi[ru], x.hi);
+            atomicMin(&Rhi[rv], x.hi);
         }
     }
 }
 
-__global__ void commit_kernel(const int *__restrict__ list, const int *__restrict__ cnt, int *uf, const int *__restrict__ R,
-                              const int2 *__restrict__ roots, int *__restrict__ status)
+// Among the edges that won the w2 WriteMin of a root: WriteMin of the id pair.
+__global__ void reserve_lo_kernel(const EdgeK *__restrict__ e, const int *__restrict__ list, const int *__restrict__ cnt,
+                                  const unsigned long long *__restrict__ Rhi, unsigned long long *Rlo,
+                                  const int2 *__restrict__ roots)
 {
     const int m = *cnt;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
-        int2 r = roots[j];
+        const int2 r = roots[j];
         if (r.x < 0) continue;
-        int i = list[j];
-        if (R[r.y] == i) { uf[r.y] = r.x; status[i] = kAccept; }
-        else if (R[r.x] == i) { uf[r.x] = r.y; status[i] = kAccept; }
+        const EdgeK x = e[list[j]];
+        if (Rhi[r.x] == x.hi) atomicMin(&Rlo[r.x], x.lo);
+        if (Rhi[r.y] == x.hi) atomicMin(&Rlo[r.y], x.lo);
     }
 }
 
-__global__ void reset_compact_kernel(const int *__restrict__ list, const int *__restrict__ cnt, int *R,
-                                     const int2 *__restrict__ roots, const int *__restrict__ status,
-                                     int *__restrict__ next, int *next_cnt, int *zero_me)
+__device__ inline void append_edge(const EdgeK &x, bool has, EdgeK *out, int *out_count, int out_cap, int *bad)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned b = __ballot_sync(0xffffffffu, has);
+    int base = 0;
+    if (lane == 0 && b) base = atomicAdd(out_count, __popc(b));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (has) {
+        const int k = base + __popc(b & lanemask_lt());
+        if (k < out_cap) out[k] = x;
+        else atomicOr(bad, 2);
+    }
+}
+
+// The holder of a root's reservation links that root under the other root and is accepted.
+// Accepted edges are appended to the output (in no particular order).
+__global__ void commit_kernel(const EdgeK *__restrict__ e, const int *__restrict__ list, const int *__restrict__ cnt,
+                              int *uf, const unsigned long long *__restrict__ Rhi,
+                              const unsigned long long *__restrict__ Rlo, const int2 *__restrict__ roots,
+                              int *__restrict__ status, EdgeK *__restrict__ out, int *out_count, int out_cap, int *bad)
+{
+    const int m = *cnt;
+    const int lane = threadIdx.x & 31;
+    const int limit = (m + 31) & ~31;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j - lane < limit; j += gridDim.x * blockDim.x) {
+        bool acc = false;
+        EdgeK x;
+        x.hi = 0; x.lo = 0;
+        if (j < m) {
+            const int2 r = roots[j];
+            if (r.x >= 0) {
+                const int i = list[j];
+                x = e[i];
+                if (Rhi[r.y] == x.hi && Rlo[r.y] == x.lo) acc = atomicCAS(&uf[r.y], r.y, r.x) == r.y;
+                else if (Rhi[r.x] == x.hi && Rlo[r.x] == x.lo) acc = atomicCAS(&uf[r.x], r.x, r.y) == r.x;
+                if (acc) status[i] = kAccept;
+            }
+        }
+        append_edge(x, acc, out, out_count, out_cap, bad);
+    }
+}
+
+// Clears the reservations that were made and compacts the pending edges.
+__global__ void reset_compact_kernel(const int *__restrict__ list, const int *__restrict__ cnt, unsigned long long *Rhi,
+                                     unsigned long long *Rlo, const int2 *__restrict__ roots,
+                                     const int *__restrict__ status, int *__restrict__ next, int *next_cnt)
 {
     const int m = *cnt;
     const int lane = threadIdx.x & 31;
@@ -126,36 +176,20 @@ __global__ void reset_compact_kernel(const int *__restrict__ list, const int *__
         bool keep = false;
         int i = 0;
         if (j < m) {
-            int2 r = roots[j];
-            if (r.x >= 0) { R[r.x] = 0x7fffffff; R[r.y] = 0x7fffffff; }
+            const int2 r = roots[j];
+            if (r.x >= 0) {
+                Rhi[r.x] = ~0ull; Rhi[r.y] = ~0ull;
+                Rlo[r.x] = ~0ull; Rlo[r.y] = ~0ull;
+            }
             i = list[j];
             keep = status[i] == kPending;
         }
-        unsigned b = __ballot_sync(0xffffffffu, keep);
+        const unsigned b = __ballot_sync(0xffffffffu, keep);
         int base = 0;
         if (lane == 0 && b) base = atomicAdd(next_cnt, __popc(b));
         base = __shfl_sync(0xffffffffu, base, 0);
         if (keep) next[base + __popc(b & lanemask_lt())] = i;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0 && zero_me) *zero_me = 0;
-}
-
-// Appends the accepted edges of the batch, in batch (K) order, to the output tree.
-__global__ void flag_accept_kernel(const int *__restrict__ status, int m, int *__restrict__ flag)
-{
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) flag[i] = status[i] == kAccept;
-}
-
-__global__ void append_accept_kernel(const EdgeK *__restrict__ e, const int *__restrict__ status,
-                                     const int *__restrict__ pre, int m, EdgeK *__restrict__ out, int out_base,
-                                     int out_cap, int *bad)
-{
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
-        if (status[i] == kAccept) {
-            int k = out_base + pre[i];
-            if (k < out_cap) out[k] = e[i];
-            else atomicOr(bad, 2);
-        }
 }
 
 }  // namespace
@@ -167,67 +201,58 @@ int filter_connected(const EdgeK *in, int m, const int *uf, EdgeK *out, int *cou
     return 0;
 }
 
-// Kruskal over a K-sorted batch e[0..m).  R[n] must hold INT_MAX everywhere on entry (kept so).
-// Accepted edges are appended to out at out_base; *accepted receives their number.
-int batch_kruskal(const EdgeK *e, int m, int n, int *uf, int *R, EdgeK *out, int out_base, int *accepted, Arena &ar,
-                  cudaStream_t st, int *pinned)
+// Kruskal over the batch e[0..m) (any order).  R holds 2 n 64-bit reservation words, all ~0 on
+// entry (kept so).  Accepted edges are appended to out at out_base (in no particular order);
+// *accepted receives their number.
+int batch_kruskal(const EdgeK *e, int m, int n, int *uf, unsigned long long *R, EdgeK *out, int out_base, int *accepted,
+                  Arena &ar, cudaStream_t st, int *pinned)
 {
     *accepted = 0;
     if (m <= 0) return 0;
     size_t mark = ar.off;
-    int *listA = ar.get<int>(m), *listB = ar.get<int>(m), *status = ar.get<int>(m + 1), *pre = ar.get<int>(m + 1);
+    int *listA = ar.get<int>(m), *listB = ar.get<int>(m), *status = ar.get<int>(m);
     int2 *roots = ar.get<int2>(m);
-    int *cnt = ar.get<int>(4);
-    int *bad = ar.get<int>(1);
+    int *cnt = ar.get<int>(4);   // [0] / [1] pending counts, [2] accepted, [3] bad
     if (ar.failed) return WM_ENOMEM;
-    cudaMemsetAsync(bad, 0, sizeof(int), st);
-    launch(validate_edges_kernel, grid_for(m, 256), 256, 0, st, e, m, n, bad);
-    cudaMemcpyAsync(pinned, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;
-    if (pinned[0]) {
-        set_error_detail("a candidate edge handed to Kruskal has an endpoint outside [0, n) or u >= v");
-        return WM_EINTERNAL;
-    }
+    unsigned long long *Rhi = R, *Rlo = R + n;
     launch(init_list_kernel, grid_for(m, 256), 256, 0, st, listA, m, status);
-    int hm = m;
-    cudaMemcpyAsync(cnt, &hm, sizeof(int), cudaMemcpyHostToDevice, st);
-    cudaMemsetAsync(cnt + 1, 0, sizeof(int), st);
+    const int init[4] = {m, 0, 0, 0};   // pageable source: copied out before the call returns
+    cudaMemcpyAsync(cnt, init, sizeof init, cudaMemcpyHostToDevice, st);
     int step = 0;
     const int grid = grid_for(m, 256);
     while (true) {
         for (int b = 0; b < 4; ++b, ++step) {
             int *lin = (step & 1) ? listB : listA, *lout = (step & 1) ? listA : listB;
             int *cin = cnt + (step & 1), *cout = cnt + ((step + 1) & 1);
-            launch(reserve_kernel, grid, 256, 0, st, e, lin, cin, uf, R, roots, status);
-            launch(commit_kernel, grid, 256, 0, st, lin, cin, uf, R, roots, status);
+            launch(reserve_hi_kernel, grid, 256, 0, st, e, lin, cin, n, uf, Rhi, roots, status, cnt + 3);
+            launch(reserve_lo_kernel, grid, 256, 0, st, e, lin, cin, Rhi, Rlo, roots);
+            launch(commit_kernel, grid, 256, 0, st, e, lin, cin, uf, Rhi, Rlo, roots, status, out + out_base,
+                   cnt + 2, n - 1 - out_base, cnt + 3);
             // cout must be zero before this kernel appends into it: it was consumed two steps ago
-            launch(reset_compact_kernel, grid, 256, 0, st, lin, cin, R, roots, status, lout, cout, nullptr);
+            launch(reset_compact_kernel, grid, 256, 0, st, lin, cin, Rhi, Rlo, roots, status, lout, cout);
             // the consumed input counter becomes the next output counter: zero it now
             cudaMemsetAsync(cin, 0, sizeof(int), st);
         }
-        cudaMemcpyAsync(pinned, cnt + (step & 1), sizeof(int), cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(pinned, cnt, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
         if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;
-        if (pinned[0] == 0) break;
+        if (pinned[3] & 1) {
+            set_error_detail("a candidate edge handed to Kruskal has an endpoint outside [0, n) or u >= v");
+            return WM_EINTERNAL;
+        }
+        if (pinned[3] & 2) {
+            set_error_detail("Kruskal accepted more than n-1 edges in total");
+            return WM_EINTERNAL;
+        }
+        if (pinned[step & 1] == 0) break;
         if (step > 4 * (m + 8)) {
             char msg[160];
             snprintf(msg, sizeof msg, "batched Kruskal made no progress (reservations): %d of %d edges pending",
-                     pinned[0], m);
+                     pinned[step & 1], m);
             set_error_detail(msg);
             return WM_EINTERNAL;
         }
     }
-    launch(flag_accept_kernel, grid, 256, 0, st, status, m, pre);
-    int rc = scan_exclusive_i32(pre, pre, m, cnt + 2, st, ar);
-    if (rc) return rc;
-    launch(append_accept_kernel, grid, 256, 0, st, e, status, pre, m, out, out_base, n - 1, bad);
-    cudaMemcpyAsync(pinned, cnt + 2, sizeof(int), cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(pinned + 1, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;
-    *accepted = pinned[0];
-    if (pinned[1]) {
-        set_error_detail("Kruskal accepted more than n-1 edges in total");
-        return WM_EINTERNAL;
-    }
+    *accepted = pinned[2];
     ar.off = mark;
     return 0;
 }
