@@ -228,6 +228,22 @@ struct Timer {
     double ms() const { return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count(); }
 };
 
+// the smallest float >= r (r >= 0 or +inf)
+static float float_ru(double r)
+{
+    float f = (float)r;
+    if ((double)f < r) f = std::nextafter(f, INFINITY);
+    return f;
+}
+
+static void set_rho(TravArgs &a, double lo, double hi)
+{
+    a.rho_lo = lo;
+    a.rho_hi = hi;
+    a.rho_lo_f = float_ru(lo);
+    a.rho_hi_f = float_ru(hi);
+}
+
 // MemoGFK rounds (Algorithm 3).  On return E_out holds the n-1 tree edges in K order.
 // hdb: optional HDBSCAN* state (node cd bounds, per-position cd2, sorted repair edges).
 static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps &caps, EdgeK *E_out, int *uf,
@@ -263,7 +279,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     float *box = ar.get<float>((size_t)T.N * 2 * dp);
     EdgeK *batch = ar.get<EdgeK>(caps.edges), *filt = ar.get<EdgeK>(caps.edges), *tmp = ar.get<EdgeK>(caps.edges);
     int *cnts = ar.get<int>(64);
-    double *rho = ar.get<double>(2);
+    unsigned *rho = ar.get<unsigned>(2);
     double *samples = ar.get<double>(4096);
     unsigned *ovf = ar.get<unsigned>(2);
     unsigned long long *stat = ar.get<unsigned long long>(8);
@@ -302,7 +318,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     a.edges = batch; a.edge_count = ecount; a.edge_cap = (int)caps.edges;
     a.overflow = ovf;
     a.stat = stat;
-    a.rho_out = rho;
+    a.rho_bits = rho;
     EdgeK *spare = filt;   // second edge buffer for compaction when rho_hi shrinks
 
     int nE = 0;
@@ -316,17 +332,19 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         Timer tw;
         WM_TRY(launch_comp_labels(T, P, uf, links, meta, comp_scratch, ar, st));
         // ---- GetRho
-        WM_CK(cudaMemcpyAsync(rho, &inf, sizeof(double), cudaMemcpyHostToDevice, st));
+        fill_i32((int *)rho, 0x7f800000, 1, st);   // +inf
         a.beta = (int)std::min<long long>(beta, 0x7fffffff);
         unsigned ob = 0;
         WM_TRY(run_traversal(a, stack, xbuf, tcnt, chunk, st, C.pin, &ob, nullptr));
         if (ob) { *overflow_bits = ob; return 0; }
-        double rho_hi;
-        WM_CK(cudaMemcpy(&rho_hi, rho, sizeof(double), cudaMemcpyDeviceToHost));
+        WM_CK(cudaMemcpyAsync(C.pin, rho, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        WM_CK(cudaStreamSynchronize(st));
+        float rho_f;
+        memcpy(&rho_f, C.pin, sizeof rho_f);
+        double rho_hi = rho_f;
         if (rho_hi < rho_lo) rho_hi = rho_lo;
         // ---- GetPairs in chunks; the retrieved pairs of every chunk get their BCCP right away
-        a.rho_lo = rho_lo;
-        a.rho_hi = rho_hi;
+        set_rho(a, rho_lo, rho_hi);
         a.edges = batch;
         spare = filt;
         WM_CK(cudaMemsetAsync(cnts + 2, 0, 6 * sizeof(int), st));
@@ -385,7 +403,8 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
                 if (!(nh < a.rho_hi)) { *overflow_bits = 2; return 0; }   // cannot shrink: grow and restart
                 keep_below(a.edges, e_before, nh, spare, ecount, st);
                 std::swap(a.edges, spare);
-                a.rho_hi = rho_hi = nh;
+                rho_hi = nh;
+                set_rho(a, rho_lo, rho_hi);
                 WM_CK(cudaMemsetAsync(ovf, 0, sizeof(unsigned), st));
                 C.stats.rho_shrinks += 1;
             }

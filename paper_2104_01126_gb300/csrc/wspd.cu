@@ -52,9 +52,12 @@ __device__ inline void pair_bounds(const TravArgs &a, int P, int Q, float &lbB, 
 }
 
 // threshold of the FP32 screen: any candidate whose screened value exceeds T cannot beat the
-// screened minimum s once both are evaluated exactly in FP64.
+// screened minimum s once both are evaluated exactly in FP64.  With an exact FP32 copy (eta = 0)
+// T = s (1 + 4 eps32) + 1.5e-42, bounded from above in FP32 with directed rounding (a float
+// >= the exact value is >= its rounded-up value too); otherwise in FP64.
 __device__ inline float screen_threshold(float s, double eta)
 {
+    if (eta == 0.0) return __fadd_ru(__fmul_ru(s, 1.0f + 4.0f / 524288.0f), 1.6e-42f);
     double t;
     if (eta == 0.0) {
         t = (double)s * (1.0 + 4.0 * kEps32) + 1.5e-42;
@@ -87,14 +90,20 @@ __device__ inline double dist64(const double *__restrict__ x64, int n, int d, in
     return s;
 }
 
+// max of two non-negative doubles through their bit patterns (integer compare, no FP64 op)
+__device__ inline double pos_dmax(double x, double y)
+{
+    return __double_as_longlong(x) >= __double_as_longlong(y) ? x : y;
+}
+
 // exact FP64 weight of positions (i,j), skipping the distance when core distances dominate
 __device__ inline double exact_w2(const TravArgs &a, int i, int j, float s32)
 {
     if (a.cd64) {
-        double c = fmax(a.cd64[i], a.cd64[j]);
+        double c = pos_dmax(a.cd64[i], a.cd64[j]);
         if (a.eta == 0.0 && s32 * (1.0f + 1.0f / 131072.0f) < fmaxf(a.cd32[i], a.cd32[j]) * (1.0f - 1.0f / 4194304.0f))
             return c;
-        return fmax(c, dist64(a.x64, a.n, a.d, i, j));
+        return pos_dmax(c, dist64(a.x64, a.n, a.d, i, j));
     }
     return dist64(a.x64, a.n, a.d, i, j);
 }
@@ -128,8 +137,9 @@ __device__ inline int warp_append(int *counter, int cnt)
 
 __device__ inline bool in_range(const TravArgs &a, const KMin &m)
 {
-    double w2 = __longlong_as_double((long long)m.hi);
-    return m.hi != ~0ull && w2 >= a.rho_lo && w2 < a.rho_hi;
+    // non-negative doubles (and +inf) order like their bit patterns
+    return m.hi != ~0ull && m.hi >= (unsigned long long)__double_as_longlong(a.rho_lo) &&
+           m.hi < (unsigned long long)__double_as_longlong(a.rho_hi);
 }
 
 __device__ inline unsigned long long warp_sum_u64(unsigned long long v)
@@ -205,8 +215,8 @@ constexpr long long kBigMax = 65536; // warp tiles (brute force); larger pairs: 
 // (WriteMin candidates into rho_cand, pruned by rho_now), MODE 1 = GetPairs (classifies a
 // retrieved pair into cls).  Sets push = 2 with the two child pairs when the pair is split.
 template <int MODE, int DP>
-__device__ inline void visit_pair(const TravArgs &a, int2 me, double rho_now, int &push, int2 &c0, int2 &c1, int &cls,
-                                  double &rho_cand)
+__device__ inline void visit_pair(const TravArgs &a, int2 me, float rho_now, int &push, int2 &c0, int2 &c1, int &cls,
+                                  float &rho_cand)
 {
     const int P = me.x, Q = me.y;
     const int4 lp = a.links[P], lq = a.links[Q];
@@ -218,11 +228,12 @@ __device__ inline void visit_pair(const TravArgs &a, int2 me, double rho_now, in
     float lbB, ubB, dP, dQ;
     bool ws;
     pair_bounds_packed<DP>(a, P, Q, lp, lq, mp, mq, lbB, ubB, ws, dP, dQ);
+    // (double)x >= r  <=>  x >= (smallest float >= r), for a float x; likewise for <
     if (MODE == 0) {
-        if ((double)lbB >= rho_now) return;
-        if (ws) { rho_cand = fmin(rho_cand, (double)lbB); return; }
+        if (lbB >= rho_now) return;
+        if (ws) { rho_cand = fminf(rho_cand, lbB); return; }
     } else {
-        if ((double)lbB >= a.rho_hi || (double)ubB < a.rho_lo) return;
+        if (lbB >= a.rho_hi_f || ubB < a.rho_lo_f) return;
         if (ws) {
             long long prod = (long long)sp * sq;
             cls = prod <= kTinyMax ? 0 : prod <= kSmallMax ? 1 : prod <= kMediumMax ? 2 : prod <= kBigMax ? 3 : 4;
@@ -273,7 +284,7 @@ __global__ void __launch_bounds__(256) findpair_dfs_kernel(TravArgs a, DfsArgs s
     auto input = [&](int i) -> int2 { return i < mx ? s.xin[xc - mx + i] : s.S[tp - ms + (i - mx)]; };
     const bool stop = __shfl_sync(0xffffffffu, (int)(*(volatile unsigned *)a.overflow != 0), 0) != 0;
     unsigned long long n_vis = 0, n_ret = 0;
-    double rho_w = INFINITY;   // GetRho: smallest candidate this warp has written
+    float rho_w = INFINITY;    // GetRho: smallest candidate this warp has written
     int sp = 0, it = 0;        // warp stack size (warp-uniform), rounds done
     bool fed = stop;           // no more input for this warp
     while (!stop) {
@@ -299,11 +310,11 @@ __global__ void __launch_bounds__(256) findpair_dfs_kernel(TravArgs a, DfsArgs s
         __syncwarp();
         int push = 0, cls = -1;
         int2 c0 = make_int2(0, 0), c1 = c0;
-        double rho_cand = INFINITY;
+        float rho_cand = INFINITY;
         if (has) {
             ++n_vis;
-            double rho_now = 0.0;
-            if (MODE == 0) rho_now = fmin(*(volatile double *)a.rho_out, rho_w);
+            float rho_now = 0.f;
+            if (MODE == 0) rho_now = fminf(__uint_as_float(*(volatile unsigned *)a.rho_bits), rho_w);
             visit_pair<MODE, DP>(a, me, rho_now, push, c0, c1, cls, rho_cand);
         }
         int x = push;
@@ -316,10 +327,11 @@ __global__ void __launch_bounds__(256) findpair_dfs_kernel(TravArgs a, DfsArgs s
         sp += total;
         __syncwarp();
         if (MODE == 0) {
-            for (int o = 16; o; o >>= 1) rho_cand = fmin(rho_cand, __shfl_xor_sync(0xffffffffu, rho_cand, o));
+            for (int o = 16; o; o >>= 1) rho_cand = fminf(rho_cand, __shfl_xor_sync(0xffffffffu, rho_cand, o));
             if (rho_cand < rho_w) {
                 rho_w = rho_cand;
-                if (lane == 0) atomicMinPosD(a.rho_out, rho_cand);
+                // non-negative floats order like their bit patterns
+                if (lane == 0) atomicMin(a.rho_bits, __float_as_uint(rho_cand));
             }
         } else {
             if (__any_sync(0xffffffffu, cls >= 0)) {
@@ -414,7 +426,7 @@ __global__ void __launch_bounds__(256) bccp_group_kernel(TravArgs a, const int2 
             for (int e = g; e < tot; e += G) {
                 int i = pb + e / nb, j = qb + e % nb;
                 double w = dist64(a.x64, n, d, i, j);
-                if (a.cd64) w = fmax(w, fmax(a.cd64[i], a.cd64[j]));
+                if (a.cd64) w = pos_dmax(w, pos_dmax(a.cd64[i], a.cd64[j]));
                 kmin_update(best, w, a.pid[i], a.pid[j]);
             }
         } else {
@@ -579,7 +591,7 @@ __global__ void __launch_bounds__(256) bccp_dual_kernel(TravArgs a, int m, const
     int *stk = a.stack + (size_t)gw * a.stack_cap;
     const long long TI = *total_items;
     const int n = a.n, d = a.d;
-    const float rho_hi_f = __double2float_ru(a.rho_hi);
+    const float rho_hi_f = a.rho_hi_f;
     unsigned long long n_ev = 0, n_re = 0;
     for (long long item = gw; item < TI; item += nw) {
         int lo = 0, hi = m - 1;
@@ -668,7 +680,7 @@ __global__ void __launch_bounds__(256) bccp_dual_kernel(TravArgs a, int m, const
                             }
                         }
                         int bp = __shfl_sync(0xffffffffu, ppid, p);
-                        if (HDB) acc = fmax(acc, fmax(a.cd64[ii], a.cd64[b0 + p]));
+                        if (HDB) acc = pos_dmax(acc, pos_dmax(a.cd64[ii], a.cd64[b0 + p]));
                         if (valid) kmin_update(best, acc, qpid, bp);
                     }
                     n_ev += (unsigned long long)bsz;
@@ -927,7 +939,7 @@ __global__ void __launch_bounds__(256) bccp_tile_kernel(TravArgs a, int m, const
                 int i = a0 + lane + 32 * it;
                 for (int jj = 0; jj < nb; ++jj) {
                     double w = dist64(a.x64, n, d, i, b0 + jj);
-                    if (HDB) w = fmax(w, fmax(a.cd64[i], a.cd64[b0 + jj]));
+                    if (HDB) w = pos_dmax(w, pos_dmax(a.cd64[i], a.cd64[b0 + jj]));
                     kmin_update(best, w, a.pid[i], a.pid[b0 + jj]);
                 }
             }

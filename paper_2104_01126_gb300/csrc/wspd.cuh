@@ -20,7 +20,8 @@ struct TravArgs {
     int fp64 = 0;              // plain FP64 form
     int beta = 2;
     double rho_lo = 0.0, rho_hi = 0.0;
-    double *rho_out = nullptr; // GetRho result (WriteMin target)
+    float rho_lo_f = 0.f, rho_hi_f = 0.f;   // the smallest floats >= rho_lo, rho_hi
+    unsigned *rho_bits = nullptr;           // GetRho result: bits of a non-negative float (WriteMin)
     int frontier_cap = 0;
     // packed node records used by the traversals (see wspd.cu)
     const int4 *links = nullptr;
