@@ -86,7 +86,7 @@ static size_t estimate_bytes(long long n, int d, int min_pts, const Caps &c)
     b += (size_t)n * 8;                     // small lists
     b += (size_t)N * (32 + 8 * dp);         // packed node records
     b += (size_t)((N / 2 + 2 + (2 * depth + 4) * 2 * c.chunk) * c.frontier_scale + 4 * c.chunk) * 8;   // stack
-    b += (size_t)c.chunk * (5 * 8 + 4 * 16 + 4);                                                       // lists, slots
+    b += (size_t)8 * (c.chunk + 1) * (5 * 8 + 16 + 4 + 8);   // pair lists (8 chunks each), huge-pair slots
     b += (size_t)152 * 64 * (depth + 4) * 4;                                                           // dual stacks
     b += (size_t)c.edges * 16 * 3 + (size_t)c.edges * 24;   // batch, filtered, sort tmp, kruskal
     b += (size_t)n * 16 * 2;                // output tree + conversion
@@ -266,8 +266,6 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     const long long lcap = (long long)kListChunks * chunk;
     int2 *lists[5];
     for (int c = 0; c < 5; ++c) lists[c] = ar.get<int2>(lcap);
-    long long *jobs = ar.get<long long>(lcap + 1);
-    EdgeK *pair_best = ar.get<EdgeK>(lcap + 1);
     EdgeK *huge_best = ar.get<EdgeK>(lcap + 1);
     unsigned *huge_sbest = ar.get<unsigned>(lcap + 1);
     long long *huge_items = ar.get<long long>(lcap + 1);
@@ -286,7 +284,8 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     int *comp_scratch = ar.get<int>(2LL * n + 1);
     if (ar.failed) return WM_ENOMEM;
     // counters: [2..6] pair-list counts, [7] edge count, [8] filtered count, [9] repair lower
-    // bound, [10..11] / [12..13] 64-bit job totals, [32..32+kTravCounters) traversal state
+    // bound, [12..13] 64-bit huge-pair item total, [16..17] tile-kernel pair dispensers,
+    // [32..32+kTravCounters) traversal state
     int *lcount = cnts + 2, *ecount = cnts + 7, *tcnt = cnts + 32;
     {
         Tree T2 = T;
@@ -312,7 +311,6 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     for (int c = 0; c < 5; ++c) { a.list[c] = lists[c]; a.list_cap[c] = (int)lcap; }
     a.list_count = lcount;
     a.big = lists[3]; a.big_count = lcount + 3;
-    a.pair_best = pair_best;
     a.huge_best = huge_best; a.huge_sbest = huge_sbest;
     a.stack = dual_stack; a.stack_cap = T.depth + 4;
     a.edges = batch; a.edge_count = ecount; a.edge_cap = (int)caps.edges;
@@ -382,7 +380,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
             const int e_before = e;
             for (int attempt = 0;; ++attempt) {
                 run_bccp_groups(a, lc, st);
-                WM_TRY(run_bccp_tiles(a, lc[3], jobs, (long long *)(cnts + 10), st, ar, hdb != nullptr, a.fp64 != 0));
+                run_bccp_tiles(a, lc, cnts + 16, st, hdb != nullptr, a.fp64 != 0);
                 WM_TRY(run_bccp_huge(a, lc[4], huge_items, (long long *)(cnts + 12), st, ar, hdb != nullptr,
                                      a.fp64 != 0, stack_warps));
                 WM_CK(cudaMemcpyAsync(C.pin, ecount, sizeof(int), cudaMemcpyDeviceToHost, st));

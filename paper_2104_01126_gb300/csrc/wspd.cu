@@ -541,31 +541,6 @@ constexpr int kTileA = 32 * kItems;
 // points of the smaller side staged per warp (8 warps per block, static shared memory < 48 KB)
 __host__ __device__ constexpr int tile_q(int dd) { return dd <= 8 ? 128 : 64; }
 
-__global__ void tile_jobs_kernel(const TravArgs a, int m, int tq, long long *__restrict__ jobs)
-{
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < m) {
-        EdgeK none;
-        none.hi = ~0ull;
-        none.lo = ~0ull;
-        a.pair_best[j] = none;
-        int P = a.big[j].x, Q = a.big[j].y;
-        int sp = nsize(a, P), sq = nsize(a, Q);
-        int big = max(sp, sq), small = min(sp, sq);
-        jobs[j] = (long long)((big + kTileA - 1) / kTileA) * ((small + tq - 1) / tq);
-    }
-}
-
-// ---------------------------------------------------------- pruned BCCP of huge pairs
-// A huge well-separated pair (A,B) is split into work items of 32 consecutive points of its larger
-// side A; a warp holds one item (a point per lane) and walks B's subtree depth first, nearer child
-// first.  A node is skipped when, for every lane, its box bound (BCCP*: also the cd bounds)
-// exceeds the pair's current threshold: the band threshold of the pair's screened minimum so far
-// (shared by all items of the pair through a WriteMin on its FP32 bits) and rho_hi (an edge at or
-// above rho_hi would not be emitted).  A subtree of <= 32 points is screened in FP32, its warp
-// minimum lowers the shared bound, and every pair screened at or below the threshold is
-// re-evaluated in FP64 and folded into the pair's 16-byte K-minimum slot.  The K-minimum itself
-// is never skipped: its FP64 weight is below the band threshold of any screened value seen.
 __global__ void huge_items_kernel(const TravArgs a, int m, long long *__restrict__ items)
 {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -809,31 +784,14 @@ __global__ void huge_emit_kernel(TravArgs a, int m)
     }
 }
 
-// one edge per big pair: its K-minimum, when in [rho_lo, rho_hi)
-__global__ void big_emit_kernel(TravArgs a, int m)
-{
-    const int lane = threadIdx.x & 31;
-    const int limit = (m + 31) & ~31;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j - lane < limit; j += gridDim.x * blockDim.x) {
-        KMin b{~0ull, ~0ull};
-        if (j < m) { b.hi = a.pair_best[j].hi; b.lo = a.pair_best[j].lo; }
-        warp_emit(a, j < m && in_range(a, b), b);
-    }
-}
-
-__device__ inline int find_job_pair(const long long *__restrict__ off, int m, long long u)
-{
-    int lo = 0, hi = m - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (off[mid] <= u) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
+// BCCP of one medium or big pair per warp (pairs handed out through *next): the larger side A
+// on the lanes (kItems points each), the smaller side B staged in shared memory in chunks of
+// kTileQ.  FP32 screen against a running warp minimum, FP64 re-evaluation of every candidate
+// inside the band of the running minimum (the threshold only decreases, so every candidate of
+// the final band is re-evaluated), warp K-minimum, emitted when its FP64 w2 lies in
+// [rho_lo, rho_hi).
 template <int D, bool HDB, bool FP64>
-__global__ void __launch_bounds__(256) bccp_tile_kernel(TravArgs a, int m, const long long *__restrict__ job_off,
-                                                        const long long *__restrict__ total_jobs)
+__global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const int2 *__restrict__ pairs, int m, int *next)
 {
     constexpr int DD = D > 0 ? D : kMaxDim;
     constexpr int kTileQ = tile_q(DD);
@@ -841,130 +799,123 @@ __global__ void __launch_bounds__(256) bccp_tile_kernel(TravArgs a, int m, const
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     float *q = qs[wib];
     const int d = D > 0 ? D : a.d;
-    const long long TJ = *total_jobs;
     const int n = a.n;
     unsigned long long n_ev = 0, n_re = 0;
-    for (long long job = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; job < TJ; job += (gridDim.x * blockDim.x) >> 5) {
-        int j = find_job_pair(job_off, m, job);
-        int P = a.big[j].x, Q = a.big[j].y;
-        int sp = nsize(a, P), sq = nsize(a, Q);
-        int A = sp >= sq ? P : Q, B = sp >= sq ? Q : P;   // A: larger side on the lanes
-        int sa = max(sp, sq), sb = min(sp, sq);
-        int nbq = (sb + kTileQ - 1) / kTileQ;
-        long long r = job - job_off[j];
-        int ta = (int)(r / nbq), tb = (int)(r % nbq);
-        int a0 = a.begin[A] + ta * kTileA, a1 = min(a0 + kTileA, a.begin[A] + sa);
-        int b0 = a.begin[B] + tb * kTileQ, b1 = min(b0 + kTileQ, a.begin[B] + sb);
-        int nb = b1 - b0;
-        __syncwarp();
-        // stage the B chunk: q[jj*(DD+1) + k], last slot = cd (HDB)
-        for (int jj = lane; jj < nb; jj += 32) {
-#pragma unroll
-            for (int k = 0; k < DD; ++k)
-                if (D > 0 || k < d) q[jj * (DD + 1) + k] = a.x32[(size_t)k * n + b0 + jj];
-            q[jj * (DD + 1) + DD] = HDB ? a.cd32[b0 + jj] : 0.f;
-        }
-        __syncwarp();
-        float ax[kItems][DD];
-        float acd[kItems];
-        bool av[kItems];
-#pragma unroll
-        for (int it = 0; it < kItems; ++it) {
-            int i = a0 + lane + 32 * it;
-            av[it] = i < a1;
-            int ii = av[it] ? i : a0;
-#pragma unroll
-            for (int k = 0; k < DD; ++k)
-                if (D > 0 || k < d) ax[it][k] = a.x32[(size_t)k * n + ii];
-            acd[it] = HDB ? a.cd32[ii] : 0.f;
-        }
+    while (true) {
+        int j = 0;
+        if (lane == 0) j = atomicAdd(next, 1);
+        j = __shfl_sync(0xffffffffu, j, 0);
+        if (j >= m) break;
+        const int2 pr = pairs[j];
+        const int4 lp = a.links[pr.x], lq = a.links[pr.y];
+        const bool pa = lp.y - lp.x >= lq.y - lq.x;   // A: the larger side, on the lanes
+        const int abeg = pa ? lp.x : lq.x, aend = pa ? lp.y : lq.y;
+        const int bbeg = pa ? lq.x : lp.x, bend = pa ? lq.y : lp.y;
         KMin best{~0ull, ~0ull};
-        if (!FP64) {
-            float mn[kItems];
+        float run_min = INFINITY;   // screened minimum over the chunks done so far
+        for (int a0 = abeg; a0 < aend; a0 += kTileA) {
+            const int a1 = min(a0 + kTileA, aend);
+            float ax[kItems][DD];
+            float acd[kItems];
+            bool av[kItems];
 #pragma unroll
-            for (int it = 0; it < kItems; ++it) mn[it] = INFINITY;
-            for (int jj = 0; jj < nb; ++jj) {
-                const float *qq = q + jj * (DD + 1);
-                float qv[DD];
+            for (int it = 0; it < kItems; ++it) {
+                const int i = a0 + lane + 32 * it;
+                av[it] = i < a1;
+                const int ii = av[it] ? i : a0;
 #pragma unroll
                 for (int k = 0; k < DD; ++k)
-                    if (D > 0 || k < d) qv[k] = qq[k];
+                    if (D > 0 || k < d) ax[it][k] = a.x32[(size_t)k * n + ii];
+                acd[it] = HDB ? a.cd32[ii] : 0.f;
+            }
+            for (int b0 = bbeg; b0 < bend; b0 += kTileQ) {
+                const int nb = min(kTileQ, bend - b0);
+                __syncwarp();
+                // stage the B chunk: q[jj*(DD+1) + k], last slot = cd (HDB)
+                for (int jj = lane; jj < nb; jj += 32) {
 #pragma unroll
-                for (int it = 0; it < kItems; ++it) {
-                    float s = 0.f;
+                    for (int k = 0; k < DD; ++k)
+                        if (D > 0 || k < d) q[jj * (DD + 1) + k] = a.x32[(size_t)k * n + b0 + jj];
+                    q[jj * (DD + 1) + DD] = HDB ? a.cd32[b0 + jj] : 0.f;
+                }
+                __syncwarp();
+                if (!FP64) {
+                    float mn[kItems];
 #pragma unroll
-                    for (int k = 0; k < DD; ++k) {
-                        if (D > 0 || k < d) {
-                            float t = ax[it][k] - qv[k];
-                            s = fmaf(t, t, s);
+                    for (int it = 0; it < kItems; ++it) mn[it] = INFINITY;
+                    for (int jj = 0; jj < nb; ++jj) {
+                        const float *qq = q + jj * (DD + 1);
+                        float qv[DD];
+#pragma unroll
+                        for (int k = 0; k < DD; ++k)
+                            if (D > 0 || k < d) qv[k] = qq[k];
+#pragma unroll
+                        for (int it = 0; it < kItems; ++it) {
+                            float s = 0.f;
+#pragma unroll
+                            for (int k = 0; k < DD; ++k) {
+                                if (D > 0 || k < d) {
+                                    float t = ax[it][k] - qv[k];
+                                    s = fmaf(t, t, s);
+                                }
+                            }
+                            if (HDB) s = fmaxf(s, fmaxf(acd[it], qq[DD]));
+                            mn[it] = fminf(mn[it], s);
                         }
                     }
-                    if (HDB) s = fmaxf(s, fmaxf(acd[it], qq[DD]));
-                    mn[it] = fminf(mn[it], s);
-                }
-            }
-            float wmn = INFINITY;
+                    float wmn = INFINITY;
 #pragma unroll
-            for (int it = 0; it < kItems; ++it) if (av[it]) wmn = fminf(wmn, mn[it]);
-            for (int o = 16; o; o >>= 1) wmn = fminf(wmn, __shfl_xor_sync(0xffffffffu, wmn, o));
-            float T = screen_threshold(wmn, a.eta);
-            int nre = 0;
+                    for (int it = 0; it < kItems; ++it) if (av[it]) wmn = fminf(wmn, mn[it]);
+                    for (int o = 16; o; o >>= 1) wmn = fminf(wmn, __shfl_xor_sync(0xffffffffu, wmn, o));
+                    run_min = fminf(run_min, wmn);
+                    const float T = screen_threshold(run_min, a.eta);
+                    int nre = 0;
 #pragma unroll
-            for (int it = 0; it < kItems; ++it) {
-                if (!av[it] || mn[it] > T) continue;
-                int i = a0 + lane + 32 * it;
-                for (int jj = 0; jj < nb; ++jj) {
-                    const float *qq = q + jj * (DD + 1);
-                    float s = 0.f;
+                    for (int it = 0; it < kItems; ++it) {
+                        if (!av[it] || mn[it] > T) continue;
+                        const int i = a0 + lane + 32 * it;
+                        for (int jj = 0; jj < nb; ++jj) {
+                            const float *qq = q + jj * (DD + 1);
+                            float s = 0.f;
 #pragma unroll
-                    for (int k = 0; k < DD; ++k) {
-                        if (D > 0 || k < d) {
-                            float t = ax[it][k] - qq[k];
-                            s = fmaf(t, t, s);
+                            for (int k = 0; k < DD; ++k) {
+                                if (D > 0 || k < d) {
+                                    float t = ax[it][k] - qq[k];
+                                    s = fmaf(t, t, s);
+                                }
+                            }
+                            if (HDB) s = fmaxf(s, fmaxf(acd[it], qq[DD]));
+                            if (s <= T) {
+                                kmin_update(best, exact_w2(a, i, b0 + jj, s), a.pid[i], a.pid[b0 + jj]);
+                                ++nre;
+                            }
                         }
                     }
-                    if (HDB) s = fmaxf(s, fmaxf(acd[it], qq[DD]));
-                    if (s <= T) {
-                        kmin_update(best, exact_w2(a, i, b0 + jj, s), a.pid[i], a.pid[b0 + jj]);
-                        ++nre;
+                    n_re += (unsigned long long)nre;
+                } else {
+#pragma unroll
+                    for (int it = 0; it < kItems; ++it) {
+                        if (!av[it]) continue;
+                        const int i = a0 + lane + 32 * it;
+                        for (int jj = 0; jj < nb; ++jj) {
+                            double w = dist64(a.x64, n, d, i, b0 + jj);
+                            if (HDB) w = pos_dmax(w, pos_dmax(a.cd64[i], a.cd64[b0 + jj]));
+                            kmin_update(best, w, a.pid[i], a.pid[b0 + jj]);
+                        }
                     }
                 }
-            }
-            for (int o = 16; o; o >>= 1) nre += __shfl_xor_sync(0xffffffffu, nre, o);
-            n_re += (unsigned long long)nre;
-        } else {
-#pragma unroll
-            for (int it = 0; it < kItems; ++it) {
-                if (!av[it]) continue;
-                int i = a0 + lane + 32 * it;
-                for (int jj = 0; jj < nb; ++jj) {
-                    double w = dist64(a.x64, n, d, i, b0 + jj);
-                    if (HDB) w = pos_dmax(w, pos_dmax(a.cd64[i], a.cd64[b0 + jj]));
-                    kmin_update(best, w, a.pid[i], a.pid[b0 + jj]);
-                }
+                n_ev += (unsigned long long)((a1 - a0) * nb);
             }
         }
-        // warp K-minimum
+        // warp K-minimum of the pair
         for (int o = 16; o; o >>= 1) {
             unsigned long long oh = __shfl_xor_sync(0xffffffffu, best.hi, o);
             unsigned long long ol = __shfl_xor_sync(0xffffffffu, best.lo, o);
             if (oh < best.hi || (oh == best.hi && ol < best.lo)) { best.hi = oh; best.lo = ol; }
         }
-        n_ev += (unsigned long long)((a1 - a0) * nb);
-        if (lane == 0 && best.hi != ~0ull) {
-            // WriteMin of the tile's K-minimum into the pair's 16-byte slot
-            EdgeK *slot = a.pair_best + j;
-            EdgeK mine;
-            mine.hi = best.hi;
-            mine.lo = best.lo;
-            EdgeK cur = *slot;
-            for (int it = 0; it < (1 << 20) && edge_less(mine, cur); ++it) {
-                EdgeK old = atomicCAS(slot, cur, mine);
-                if (old.hi == cur.hi && old.lo == cur.lo) break;
-                cur = old;
-            }
-        }
+        warp_emit(a, lane == 0 && in_range(a, best), best);
     }
+    n_re = warp_sum_u64(n_re);
     if (lane == 0 && n_ev) {
         atomicAdd(a.stat + 1, n_ev);
         atomicAdd(a.stat + 3, n_ev);
@@ -1104,8 +1055,6 @@ void run_bccp_groups(TravArgs &a, const int *counts_host, cudaStream_t st)
         launch(bccp_group_kernel<1>, grid_for((long long)counts_host[0], 256), 256, 0, st, a, a.list[0], a.list_count + 0);
     if (counts_host[1] > 0)
         launch(bccp_group_kernel<8>, grid_for((long long)counts_host[1] * 8, 256), 256, 0, st, a, a.list[1], a.list_count + 1);
-    if (counts_host[2] > 0)
-        launch(bccp_group_kernel<32>, grid_for((long long)counts_host[2] * 32, 256), 256, 0, st, a, a.list[2], a.list_count + 2);
 }
 
 void pack_nodes(const Tree &T, int d, int dp, int4 *links, float4 *meta, float *box, cudaStream_t st)
@@ -1143,36 +1092,35 @@ int run_bccp_huge(TravArgs &a, int m, long long *items, long long *total, cudaSt
     return 0;
 }
 
-// BCCP tile kernel over the queued big pairs (m of them, count known on host).
-int run_bccp_tiles(TravArgs &a, int m, long long *jobs, long long *total, cudaStream_t st, Arena &ar, bool hdb,
-                   bool fp64)
+// BCCP of the medium and big pair lists: one warp per pair.  next: two device counters.
+void run_bccp_tiles(TravArgs &a, const int *counts_host, int *next, cudaStream_t st, bool hdb, bool fp64)
 {
-    if (m <= 0) return 0;
-    int dd = (a.d == 2 || a.d == 3 || a.d == 5 || a.d == 7) ? a.d : kMaxDim;
-    launch(tile_jobs_kernel, grid_for(m, 256, 1 << 20), 256, 0, st, a, m, tile_q(dd), jobs);
-    int rc = scan_exclusive_i64(jobs, jobs, m, total, st, ar);
-    if (rc) return rc;
-    const int grid = 152 * 4;
-#define WM_TILE(DV)                                                                                     \
-    do {                                                                                                \
-        if (fp64) {                                                                                     \
-            if (hdb) launch(bccp_tile_kernel<DV, true, true>, grid, 256, 0, st, a, m, jobs, total);          \
-            else launch(bccp_tile_kernel<DV, false, true>, grid, 256, 0, st, a, m, jobs, total);             \
-        } else {                                                                                        \
-            if (hdb) launch(bccp_tile_kernel<DV, true, false>, grid, 256, 0, st, a, m, jobs, total);         \
-            else launch(bccp_tile_kernel<DV, false, false>, grid, 256, 0, st, a, m, jobs, total);            \
-        }                                                                                               \
+    cudaMemsetAsync(next, 0, 2 * sizeof(int), st);
+    for (int c = 2; c <= 3; ++c) {
+        const int m = counts_host[c];
+        if (m <= 0) continue;
+        const int grid = (int)std::min<long long>(152 * 4, ((long long)m + 7) / 8);
+        const int2 *pl = a.list[c];
+        int *nx = next + (c - 2);
+#define WM_TILE(DV)                                                                                                \
+    do {                                                                                                           \
+        if (fp64) {                                                                                                \
+            if (hdb) launch(bccp_pair_tile_kernel<DV, true, true>, grid, 256, 0, st, a, pl, m, nx);               \
+            else launch(bccp_pair_tile_kernel<DV, false, true>, grid, 256, 0, st, a, pl, m, nx);                  \
+        } else {                                                                                                   \
+            if (hdb) launch(bccp_pair_tile_kernel<DV, true, false>, grid, 256, 0, st, a, pl, m, nx);              \
+            else launch(bccp_pair_tile_kernel<DV, false, false>, grid, 256, 0, st, a, pl, m, nx);                 \
+        }                                                                                                          \
     } while (0)
-    switch (a.d) {
-    case 2: WM_TILE(2); break;
-    case 3: WM_TILE(3); break;
-    case 5: WM_TILE(5); break;
-    case 7: WM_TILE(7); break;
-    default: WM_TILE(0); break;
-    }
+        switch (a.d) {
+        case 2: WM_TILE(2); break;
+        case 3: WM_TILE(3); break;
+        case 5: WM_TILE(5); break;
+        case 7: WM_TILE(7); break;
+        default: WM_TILE(0); break;
+        }
 #undef WM_TILE
-    launch(big_emit_kernel, grid_for(m, 256), 256, 0, st, a, m);
-    return 0;
+    }
 }
 
 }  // namespace wm

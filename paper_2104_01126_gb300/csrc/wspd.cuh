@@ -34,7 +34,6 @@ struct TravArgs {
     int *list_count = nullptr;          // [5]
     int list_cap[5] = {0, 0, 0, 0, 0};
     int2 *big = nullptr;                // = list[3]
-    EdgeK *pair_best = nullptr;         // per big pair: K-minimum over its tiles
     EdgeK *huge_best = nullptr;         // per huge pair: K-minimum
     unsigned *huge_sbest = nullptr;     // per huge pair: screened minimum (FP32 bits), WriteMin
     int *stack = nullptr;               // per-warp traversal stacks of the dual-tree kernel
@@ -84,8 +83,7 @@ void traversal_step(int mode, TravArgs &a, int2 *stack, int2 *const xbuf[2], int
                     cudaStream_t st);
 void sample_w2(const EdgeK *e, int m, int k, double *out, cudaStream_t st);
 void keep_below(const EdgeK *in, int m, double bound, EdgeK *out, int *count, cudaStream_t st);
-int run_bccp_tiles(TravArgs &a, int m, long long *jobs, long long *total, cudaStream_t st, Arena &ar, bool hdb,
-                   bool fp64);
+void run_bccp_tiles(TravArgs &a, const int *counts_host, int *next, cudaStream_t st, bool hdb, bool fp64);
 void run_bccp_groups(TravArgs &a, const int *counts_host, cudaStream_t st);
 int run_bccp_huge(TravArgs &a, int m, long long *items, long long *total, cudaStream_t st, Arena &ar, bool hdb,
                   bool fp64, int stack_warps);
