@@ -331,6 +331,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         WM_TRY(launch_comp_labels(T, P, uf, links, meta, comp_scratch, ar, st));
         // ---- GetRho
         fill_i32((int *)rho, 0x7f800000, 1, st);   // +inf
+        set_rho(a, rho_lo, inf);
         a.beta = (int)std::min<long long>(beta, 0x7fffffff);
         unsigned ob = 0;
         WM_TRY(run_traversal(a, stack, xbuf, tcnt, chunk, st, C.pin, &ob, nullptr));

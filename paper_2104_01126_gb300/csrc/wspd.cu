@@ -230,7 +230,8 @@ __device__ inline void visit_pair(const TravArgs &a, int2 me, float rho_now, int
     pair_bounds_packed<DP>(a, P, Q, lp, lq, mp, mq, lbB, ubB, ws, dP, dQ);
     // (double)x >= r  <=>  x >= (smallest float >= r), for a float x; likewise for <
     if (MODE == 0) {
-        if (lbB >= rho_now) return;
+        // pairs whose BCCP is certainly below rho_lo were handled by earlier rounds
+        if (lbB >= rho_now || ubB < a.rho_lo_f) return;
         if (ws) { rho_cand = fminf(rho_cand, lbB); return; }
     } else {
         if (lbB >= a.rho_hi_f || ubB < a.rho_lo_f) return;
@@ -547,8 +548,8 @@ __global__ void huge_items_kernel(const TravArgs a, int m, long long *__restrict
     if (j < m) {
         int P = a.list[4][j].x, Q = a.list[4][j].y;
         int4 lp = a.links[P], lq = a.links[Q];
-        int big = max(lp.y - lp.x, lq.y - lq.x);
-        items[j] = (big + 31) / 32;
+        int small = min(lp.y - lp.x, lq.y - lq.x);   // the query side
+        items[j] = (small + 31) / 32;
         EdgeK none;
         none.hi = ~0ull;
         none.lo = ~0ull;
@@ -577,12 +578,14 @@ __global__ void __launch_bounds__(256) bccp_dual_kernel(TravArgs a, int m, const
         const int j = lo;
         const int P = a.list[4][j].x, Q = a.list[4][j].y;
         const int4 lp = a.links[P], lq = a.links[Q];
-        const bool pbig = lp.y - lp.x >= lq.y - lq.x;
-        const int Aend = pbig ? lp.y : lq.y;
-        const int Broot = pbig ? Q : P;
-        const int i = (pbig ? lp.x : lq.x) + (int)(item - item_off[j]) * 32 + lane;
+        // queries: the smaller side; its points far from the other side are pruned at the other
+        // tree's root, the rest run a nearest-first descent into it
+        const bool pq = lp.y - lp.x <= lq.y - lq.x;   // P is the query side
+        const int Aend = pq ? lp.y : lq.y;
+        const int Broot = pq ? Q : P;
+        const int i = (pq ? lp.x : lq.x) + (int)(item - item_off[j]) * 32 + lane;
         const bool valid = i < Aend;
-        const int ii = valid ? i : (pbig ? lp.x : lq.x);
+        const int ii = valid ? i : (pq ? lp.x : lq.x);
         float qx[DM];
         double qx64[DM];
 #pragma unroll
@@ -1063,7 +1066,7 @@ void pack_nodes(const Tree &T, int d, int dp, int4 *links, float4 *meta, float *
            T.diam2, T.cdmin, T.cdmax, links, meta, box);
 }
 
-// Pruned BCCP of the huge pairs (m of them): one warp per 32 points of a pair's larger side.
+// Pruned BCCP of the huge pairs (m of them): one warp per 32 points of a pair's smaller side.
 int run_bccp_huge(TravArgs &a, int m, long long *items, long long *total, cudaStream_t st, Arena &ar, bool hdb,
                   bool fp64, int stack_warps)
 {
