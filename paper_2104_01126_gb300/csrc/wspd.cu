@@ -249,16 +249,6 @@ __device__ inline void visit_pair(const TravArgs &a, int2 me, float rho_now, int
     push = 2;
 }
 
-// one-per-lane warp append through a ballot; returns this lane's slot (valid where has)
-__device__ inline int warp_append1(int *counter, bool has)
-{
-    const unsigned b = __ballot_sync(0xffffffffu, has);
-    int base = 0;
-    if ((threadIdx.x & 31) == 0 && b) base = atomicAdd(counter, __popc(b));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    return base + __popc(b & lanemask_lt());
-}
-
 // One traversal step.  The pending pairs form a logical stack: the global stack S[0, top) with the
 // previous step's output xin[0, xin_count) on top of it.  The step pops the top min(size, chunk)
 // pairs, and every warp expands the pairs it takes depth first on a stack of its own in shared
@@ -336,14 +326,24 @@ __global__ void __launch_bounds__(256) findpair_dfs_kernel(TravArgs a, DfsArgs s
             }
         } else {
             if (__any_sync(0xffffffffu, cls >= 0)) {
+                // one ballot per class; lanes 0..4 reserve the five lists' slots concurrently
+                unsigned bal[5];
+#pragma unroll
+                for (int c = 0; c < 5; ++c) bal[c] = __ballot_sync(0xffffffffu, cls == c);
+                unsigned lb = 0, mine = 0;
 #pragma unroll
                 for (int c = 0; c < 5; ++c) {
-                    int bs = warp_append1(a.list_count + c, cls == c);
-                    if (cls == c) {
-                        ++n_ret;
-                        if (bs < a.list_cap[c]) a.list[c][bs] = me;
-                        else atomicOr(a.overflow, 4u);
-                    }
+                    if (lane == c) lb = bal[c];
+                    if (cls == c) mine = bal[c];
+                }
+                int base = 0;
+                if (lane < 5 && lb) base = atomicAdd(a.list_count + lane, __popc(lb));
+                base = __shfl_sync(0xffffffffu, base, cls >= 0 ? cls : 0);
+                if (cls >= 0) {
+                    ++n_ret;
+                    const int bs = base + __popc(mine & lanemask_lt());
+                    if (bs < a.list_cap[cls]) a.list[cls][bs] = me;
+                    else atomicOr(a.overflow, 4u);
                 }
             }
         }
