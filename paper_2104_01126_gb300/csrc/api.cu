@@ -303,6 +303,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     a.x32 = P.x32; a.x64 = P.x64; a.pid = P.pid;
     a.fp64 = C.precision == WM_PREC_FP64;
     a.eta = a.fp64 ? 0.0 : 2.0 * (double)P.delta * std::sqrt((double)P.d) * (1.0 + 1e-6);
+    a.exact32 = a.eta == 0.0;
     if (hdb) {
         a.cdmin = hdb->cdmin; a.cdmax = hdb->cdmax; a.cd32 = hdb->cd32; a.cd64 = hdb->cd64;
     }

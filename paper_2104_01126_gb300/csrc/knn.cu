@@ -262,7 +262,8 @@ __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
                 ++ncand;
             }
         } else {
-            float T = knn_threshold((float)sv[(k - 1) * 32 + lane], a.eta);
+            const float sk = (float)sv[(k - 1) * 32 + lane];
+            const float T = exact32 ? knn_threshold_fast(sk) : knn_threshold(sk, a.eta);
             complete = cnt < KL || (float)sv[(KL - 1) * 32 + lane] > T;
             ncand = 0;
             while (ncand < cnt && (float)sv[ncand * 32 + lane] <= T) ++ncand;
@@ -270,9 +271,9 @@ __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
                 for (int c = 0; c < ncand; ++c) {
                     int j = sj[c * 32 + lane];
                     double w = j == i ? 0.0 : d64(a.x64, n, d, i, j);
-                    // insertion sort by (w, position)
+                    // insertion sort by w (non-negative doubles compared through their bit patterns)
                     int pos = c;
-                    while (pos > 0 && sw[(pos - 1) * 32 + lane] > w) {
+                    while (pos > 0 && __double_as_longlong(sw[(pos - 1) * 32 + lane]) > __double_as_longlong(w)) {
                         sw[pos * 32 + lane] = sw[(pos - 1) * 32 + lane];
                         sj[pos * 32 + lane] = sj[(pos - 1) * 32 + lane];
                         --pos;
@@ -295,7 +296,7 @@ __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
         for (int c = 0; c < ncand && r < KL - 1; ++c) {
             int j = sj[c * 32 + lane];
             double w = sw[c * 32 + lane];
-            if (j != i && w <= cd2) {
+            if (j != i && __double_as_longlong(w) <= __double_as_longlong(cd2)) {
                 a.rep_q[(size_t)i * (KL - 1) + r] = j;
                 a.rep_d[(size_t)i * (KL - 1) + r] = w;
                 ++r;

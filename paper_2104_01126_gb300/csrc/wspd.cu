@@ -55,19 +55,14 @@ __device__ inline void pair_bounds(const TravArgs &a, int P, int Q, float &lbB, 
 // screened minimum s once both are evaluated exactly in FP64.  With an exact FP32 copy (eta = 0)
 // T = s (1 + 4 eps32) + 1.5e-42, bounded from above in FP32 with directed rounding (a float
 // >= the exact value is >= its rounded-up value too); otherwise in FP64.
-__device__ inline float screen_threshold(float s, double eta)
+__device__ inline float screen_threshold(float s, const TravArgs &a)
 {
-    if (eta == 0.0) return __fadd_ru(__fmul_ru(s, 1.0f + 4.0f / 524288.0f), 1.6e-42f);
-    double t;
-    if (eta == 0.0) {
-        t = (double)s * (1.0 + 4.0 * kEps32) + 1.5e-42;
-    } else {
-        double r = sqrt((double)s * (1.0 + 2.0 * kEps32)) + eta;
-        double U = r * r * (1.0 + 2.0 * kGam64);
-        double q = sqrt(U * (1.0 + 2.0 * kGam64)) + eta;
-        t = q * q * (1.0 + 2.0 * kEps32) + 1.5e-42;
-    }
-    return __double2float_ru(t);
+    if (a.exact32) return __fadd_ru(__fmul_ru(s, 1.0f + 4.0f / 524288.0f), 1.6e-42f);
+    const double eta = a.eta;
+    double r = sqrt((double)s * (1.0 + 2.0 * kEps32)) + eta;
+    double U = r * r * (1.0 + 2.0 * kGam64);
+    double q = sqrt(U * (1.0 + 2.0 * kGam64)) + eta;
+    return __double2float_ru(q * q * (1.0 + 2.0 * kEps32) + 1.5e-42);
 }
 
 __device__ inline float dist32(const float *__restrict__ x32, int n, int d, int i, int j)
@@ -96,13 +91,15 @@ __device__ inline double pos_dmax(double x, double y)
     return __double_as_longlong(x) >= __double_as_longlong(y) ? x : y;
 }
 
-// exact FP64 weight of positions (i,j), skipping the distance when core distances dominate
-__device__ inline double exact_w2(const TravArgs &a, int i, int j, float s32)
+// exact FP64 weight of positions (i,j).  d32: the FP32 squared distance alone; c32: the larger
+// FP32 core distance (HDBSCAN*).  When d32 is provably below the larger core distance (d32 is
+// within 2^-19 of the true distance, a stored cd32 within 2^-24 of its FP64 value), the weight
+// is that core distance and the FP64 distance is skipped.
+__device__ inline double exact_w2(const TravArgs &a, int i, int j, float d32, float c32)
 {
     if (a.cd64) {
         double c = pos_dmax(a.cd64[i], a.cd64[j]);
-        if (a.eta == 0.0 && s32 * (1.0f + 1.0f / 131072.0f) < fmaxf(a.cd32[i], a.cd32[j]) * (1.0f - 1.0f / 4194304.0f))
-            return c;
+        if (a.exact32 && d32 * (1.0f + 1.0f / 131072.0f) < c32 * (1.0f - 1.0f / 4194304.0f)) return c;
         return pos_dmax(c, dist64(a.x64, a.n, a.d, i, j));
     }
     return dist64(a.x64, a.n, a.d, i, j);
@@ -431,23 +428,31 @@ __global__ void __launch_bounds__(256) bccp_group_kernel(TravArgs a, const int2 
                 kmin_update(best, w, a.pid[i], a.pid[j]);
             }
         } else {
+            // lane g visits e = g, g + G, ... of the na x nb grid; (i, j) advance without division
             float smin = INFINITY;
-            for (int e = g; e < tot; e += G) {
-                int i = pb + e / nb, j = qb + e % nb;
-                float s = dist32(a.x32, n, d, i, j);
-                if (a.cd32) s = fmaxf(s, fmaxf(a.cd32[i], a.cd32[j]));
-                smin = fminf(smin, s);
+            {
+                int i = pb + (nb > 0 ? g / nb : 0), j = qb + (nb > 0 ? g % nb : 0);
+                for (int e = g; e < tot; e += G) {
+                    const float sd = dist32(a.x32, n, d, i, j);
+                    smin = fminf(smin, a.cd32 ? fmaxf(sd, fmaxf(a.cd32[i], a.cd32[j])) : sd);
+                    j += G;
+                    while (j >= qb + nb) { j -= nb; ++i; }
+                }
             }
 #pragma unroll
             for (int o = G / 2; o; o >>= 1) smin = fminf(smin, __shfl_xor_sync(0xffffffffu, smin, o));
-            const float T = screen_threshold(smin, a.eta);
-            for (int e = g; e < tot; e += G) {
-                int i = pb + e / nb, j = qb + e % nb;
-                float s = dist32(a.x32, n, d, i, j);
-                if (a.cd32) s = fmaxf(s, fmaxf(a.cd32[i], a.cd32[j]));
-                if (s <= T) {
-                    kmin_update(best, exact_w2(a, i, j, s), a.pid[i], a.pid[j]);
-                    ++n_re;
+            const float T = screen_threshold(smin, a);
+            {
+                int i = pb + (nb > 0 ? g / nb : 0), j = qb + (nb > 0 ? g % nb : 0);
+                for (int e = g; e < tot; e += G) {
+                    const float sd = dist32(a.x32, n, d, i, j);
+                    const float c32 = a.cd32 ? fmaxf(a.cd32[i], a.cd32[j]) : 0.f;
+                    if (fmaxf(sd, c32) <= T) {
+                        kmin_update(best, exact_w2(a, i, j, sd, c32), a.pid[i], a.pid[j]);
+                        ++n_re;
+                    }
+                    j += G;
+                    while (j >= qb + nb) { j -= nb; ++i; }
                 }
             }
         }
@@ -606,7 +611,7 @@ __global__ void __launch_bounds__(256) bccp_dual_kernel(TravArgs a, int m, const
                 t = hb == ~0ull ? INFINITY : __double2float_ru(__longlong_as_double((long long)hb));
             } else {
                 float sb = __uint_as_float(((volatile unsigned *)a.huge_sbest)[j]);
-                t = sb == INFINITY ? INFINITY : screen_threshold(sb, a.eta);
+                t = sb == INFINITY ? INFINITY : screen_threshold(sb, a);
             }
             return fminf(t, rho_hi_f);
         };
@@ -698,7 +703,7 @@ __global__ void __launch_bounds__(256) bccp_dual_kernel(TravArgs a, int m, const
                     }
                     for (int o = 16; o; o >>= 1) smin = fminf(smin, __shfl_xor_sync(0xffffffffu, smin, o));
                     if (lane == 0 && smin < INFINITY) atomicMin(a.huge_sbest + j, __float_as_uint(smin));
-                    thr = fminf(thr, fminf(screen_threshold(smin, a.eta), rho_hi_f));
+                    thr = fminf(thr, fminf(screen_threshold(smin, a), rho_hi_f));
                     thr = fminf(thr, cur_thr());
                     for (int p = 0; p < bsz; ++p) {
                         float acc = 0.f;
@@ -709,10 +714,12 @@ __global__ void __launch_bounds__(256) bccp_dual_kernel(TravArgs a, int m, const
                                 acc = fmaf(t, t, acc);
                             }
                         }
-                        if (HDB) acc = fmaxf(acc, fmaxf(qcd, __shfl_sync(0xffffffffu, pcd, p)));
+                        const float c32 = HDB ? fmaxf(qcd, __shfl_sync(0xffffffffu, pcd, p)) : 0.f;
+                        const float sd = acc;
+                        if (HDB) acc = fmaxf(acc, c32);
                         int bp = __shfl_sync(0xffffffffu, ppid, p);
                         if (valid && acc <= thr) {
-                            kmin_update(best, exact_w2(a, ii, b0 + p, acc), qpid, bp);
+                            kmin_update(best, exact_w2(a, ii, b0 + p, sd, c32), qpid, bp);
                             ++n_re;
                         }
                     }
@@ -871,7 +878,7 @@ __global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const i
                     for (int it = 0; it < kItems; ++it) if (av[it]) wmn = fminf(wmn, mn[it]);
                     for (int o = 16; o; o >>= 1) wmn = fminf(wmn, __shfl_xor_sync(0xffffffffu, wmn, o));
                     run_min = fminf(run_min, wmn);
-                    const float T = screen_threshold(run_min, a.eta);
+                    const float T = screen_threshold(run_min, a);
                     int nre = 0;
 #pragma unroll
                     for (int it = 0; it < kItems; ++it) {
@@ -887,9 +894,11 @@ __global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const i
                                     s = fmaf(t, t, s);
                                 }
                             }
-                            if (HDB) s = fmaxf(s, fmaxf(acd[it], qq[DD]));
+                            const float c32 = HDB ? fmaxf(acd[it], qq[DD]) : 0.f;
+                            const float sd = s;
+                            if (HDB) s = fmaxf(s, c32);
                             if (s <= T) {
-                                kmin_update(best, exact_w2(a, i, b0 + jj, s), a.pid[i], a.pid[b0 + jj]);
+                                kmin_update(best, exact_w2(a, i, b0 + jj, sd, c32), a.pid[i], a.pid[b0 + jj]);
                                 ++nre;
                             }
                         }

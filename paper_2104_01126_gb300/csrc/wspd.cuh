@@ -17,6 +17,7 @@ struct TravArgs {
     const float *cd32 = nullptr;                       // HDBSCAN* cd2 per tree position
     const double *cd64 = nullptr;
     double eta = 0.0;          // absolute distance error of the FP32 copy (FP64 input), else 0
+    int exact32 = 1;           // eta == 0: the FP32 copy is exact
     int fp64 = 0;              // plain FP64 form
     int beta = 2;
     double rho_lo = 0.0, rho_hi = 0.0;
