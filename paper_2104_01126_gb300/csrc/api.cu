@@ -85,7 +85,7 @@ static size_t estimate_bytes(long long n, int d, int min_pts, const Caps &c)
     b += (size_t)N * (8 * d + 48);          // tree arrays (+ build scratch counters)
     b += (size_t)n * 8;                     // small lists
     b += (size_t)N * (32 + 8 * dp);         // packed node records
-    b += (size_t)((N / 2 + 2 + (2 * depth + 4) * 2 * c.chunk) * c.frontier_scale + 4 * c.chunk) * 8;   // stack
+    b += (size_t)((N / 2 + 2 + (2 * depth + 4) * 2 * c.chunk) * c.frontier_scale + 8 * c.chunk) * 8;   // stack, step outputs
     b += (size_t)8 * (c.chunk + 1) * (5 * 8 + 16 + 4 + 8);   // pair lists (8 chunks each), huge-pair slots
     b += (size_t)152 * 64 * (depth + 4) * 4;                                                           // dual stacks
     b += (size_t)c.edges * 16 * 3 + (size_t)c.edges * 24;   // batch, filtered, sort tmp, kruskal
@@ -259,10 +259,10 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     const long long fcap = ((long long)T.N / 2 + 2 + (2LL * T.depth + 4) * 2 * chunk) * caps.frontier_scale;
     if (fcap > 0x7fffffffLL) { set_detail("WSPD stack capacity exceeds 2^31 pairs%s", ""); return WM_ENOMEM; }
     int2 *stack = ar.get<int2>(fcap);
-    int2 *const xbuf[2] = {ar.get<int2>(2LL * chunk), ar.get<int2>(2LL * chunk)};   // step outputs
+    int2 *const xbuf[2] = {ar.get<int2>(4LL * chunk), ar.get<int2>(4LL * chunk)};   // step outputs
     // pair lists hold kListChunks chunks' worth of retrieved pairs; they are flushed (BCCP) when
     // one of them could overflow within the next poll interval, and when the traversal ends
-    const int kPoll = 4, kListChunks = 8;
+    const int kPoll = 3, kListChunks = 8;
     const long long lcap = (long long)kListChunks * chunk;
     int2 *lists[5];
     for (int c = 0; c < 5; ++c) lists[c] = ar.get<int2>(lcap);
@@ -371,7 +371,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
             int lc[5] = {C.pin[2], C.pin[3], C.pin[4], C.pin[5], C.pin[6]};
             int e = C.pin[7];
             bool flush = empty;
-            for (int c = 0; c < 5; ++c) flush = flush || lc[c] > lcap - (long long)kPoll * chunk;
+            for (int c = 0; c < 5; ++c) flush = flush || lc[c] > lcap - (long long)kPoll * dfs_step_visits(chunk);
             if (!flush) continue;
             mark_event();
             ev_kind.push_back(0);

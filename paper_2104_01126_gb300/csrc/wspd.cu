@@ -248,10 +248,11 @@ __device__ inline void visit_pair(const TravArgs &a, int2 me, float rho_now, int
 
 // One traversal step.  The pending pairs form a logical stack: the global stack S[0, top) with the
 // previous step's output xin[0, xin_count) on top of it.  The step pops the top min(size, chunk)
-// pairs, and every warp expands the pairs it takes depth first on a stack of its own in shared
-// memory, for at most `budget` rounds of up to 32 pairs; whatever is still pending then (its stack,
-// and pairs it took after the budget ran out) goes to xout.  Pairs of xin beyond one chunk are moved
-// onto S.  The last block to finish sets the new stack size and clears the counters it owns.
+// pairs; warps take them 32 at a time and visit each (breadth first over the popped pairs), keeping
+// the children on a stack of their own in shared memory (spilled to the step output xout when it
+// is full); when the popped pairs are exhausted, every warp expands its own stack depth first for
+// at most `budget` rounds and then writes what is left to xout.  Pairs of xin beyond one chunk are
+// moved onto S.  The last block to finish sets the new stack size and clears the counters it owns.
 template <int MODE, int DP>
 __global__ void __launch_bounds__(256) findpair_dfs_kernel(TravArgs a, DfsArgs s)
 {
@@ -273,29 +274,34 @@ __global__ void __launch_bounds__(256) findpair_dfs_kernel(TravArgs a, DfsArgs s
     const bool stop = __shfl_sync(0xffffffffu, (int)(*(volatile unsigned *)a.overflow != 0), 0) != 0;
     unsigned long long n_vis = 0, n_ret = 0;
     float rho_w = INFINITY;    // GetRho: smallest candidate this warp has written
-    int sp = 0, it = 0;        // warp stack size (warp-uniform), rounds done
+    int sp = 0, it = 0;        // warp stack size (warp-uniform), rounds on the warp's own stack
     bool fed = stop;           // no more input for this warp
     while (!stop) {
-        if (sp < 32 && !fed) {
+        // one round: the next 32 popped pairs while there are any (every popped pair is visited
+        // in this step, breadth first), then up to `budget` rounds of the warp's own stack
+        int2 me = make_int2(0, 0);
+        int k = 0;
+        bool from_input = false;
+        if (!fed) {
             int base = 0;
             if (lane == 0) base = atomicAdd(s.next, 32);
             base = __shfl_sync(0xffffffffu, base, 0);
-            const int cnt = base < m ? min(32, m - base) : 0;
-            if (cnt == 0) fed = true;
+            k = base < m ? min(32, m - base) : 0;
+            if (k == 0) fed = true;
             else {
-                if (lane < cnt) ws[sp + lane] = input(base + lane);
-                sp += cnt;
+                from_input = true;
+                if (lane < k) me = input(base + lane);
             }
-            __syncwarp();
         }
-        // before a round sp <= 63 + 32 * it: a refill happens only below 32 and a round adds at most 32
-        if (sp == 0 || it == s.budget) break;
-        const int k = sp < 32 ? sp : 32;
-        sp -= k;
+        if (!from_input) {
+            if (sp == 0 || it == s.budget) break;
+            k = sp < 32 ? sp : 32;
+            sp -= k;
+            if (lane < k) me = ws[sp + lane];
+            __syncwarp();
+            ++it;
+        }
         const bool has = lane < k;
-        int2 me = make_int2(0, 0);
-        if (has) me = ws[sp + lane];
-        __syncwarp();
         int push = 0, cls = -1;
         int2 c0 = make_int2(0, 0), c1 = c0;
         float rho_cand = INFINITY;
@@ -311,8 +317,19 @@ __global__ void __launch_bounds__(256) findpair_dfs_kernel(TravArgs a, DfsArgs s
             if (lane >= o) x += y;
         }
         const int total = __shfl_sync(0xffffffffu, x, 31);
-        if (push) { ws[sp + x - 2] = c0; ws[sp + x - 1] = c1; }
-        sp += total;
+        // children onto the warp stack while it has room, else into the step output
+        if (sp + total <= kDfsWarpCap) {
+            if (push) { ws[sp + x - 2] = c0; ws[sp + x - 1] = c1; }
+            sp += total;
+        } else {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(s.xout_count, total);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (push) {
+                if (base + x <= s.xcap) { s.xout[base + x - 2] = c0; s.xout[base + x - 1] = c1; }
+                else atomicOr(a.overflow, 1u);
+            }
+        }
         __syncwarp();
         if (MODE == 0) {
             for (int o = 16; o; o >>= 1) rho_cand = fminf(rho_cand, __shfl_xor_sync(0xffffffffu, rho_cand, o));
@@ -344,32 +361,15 @@ __global__ void __launch_bounds__(256) findpair_dfs_kernel(TravArgs a, DfsArgs s
                 }
             }
         }
-        ++it;
     }
-    if (!stop) {
-        // budget spent: the warp stack, then the input this warp still takes, go to xout
-        if (sp > 0) {
-            int base = 0;
-            if (lane == 0) base = atomicAdd(s.xout_count, sp);
-            base = __shfl_sync(0xffffffffu, base, 0);
-            for (int i = lane; i < sp; i += 32) {
-                if (base + i < s.xcap) s.xout[base + i] = ws[i];
-                else atomicOr(a.overflow, 1u);
-            }
-        }
-        while (!fed) {
-            int base = 0;
-            if (lane == 0) base = atomicAdd(s.next, 32);
-            base = __shfl_sync(0xffffffffu, base, 0);
-            const int cnt = base < m ? min(32, m - base) : 0;
-            if (cnt == 0) break;
-            int ob = 0;
-            if (lane == 0) ob = atomicAdd(s.xout_count, cnt);
-            ob = __shfl_sync(0xffffffffu, ob, 0);
-            if (lane < cnt) {
-                if (ob + lane < s.xcap) s.xout[ob + lane] = input(base + lane);
-                else atomicOr(a.overflow, 1u);
-            }
+    // what is left on the warp stack goes to the step output (every popped pair was visited)
+    if (!stop && sp > 0) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(s.xout_count, sp);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        for (int i = lane; i < sp; i += 32) {
+            if (base + i < s.xcap) s.xout[base + i] = ws[i];
+            else atomicOr(a.overflow, 1u);
         }
     }
     n_vis = warp_sum_u64(n_vis);
@@ -962,18 +962,23 @@ void traversal_init(int mode, TravArgs &a, int2 *stack, int *cnt, cudaStream_t s
     launch(frontier_init_kernel, grid_for(a.N, 256), 256, 0, st, a, mode, stack, cnt + 0);
 }
 
-// Warps of a step: at most chunk / kDfsWarpCap, so that a step's output (at most the chunk it
-// popped plus every warp's full stack) fits in 2 * chunk pairs, and a step visits fewer than
-// chunk pairs (warps * 32 * kDfsBudget).
+// Warps of a step: at most 2 chunk / (64 kDfsBudget + kDfsWarpCap), so that a step's output
+// (children of at most chunk + warps * 32 * kDfsBudget visits, plus every warp's full stack) fits
+// in 4 * chunk pairs.
 int dfs_warps(int chunk)
 {
-    long long w = chunk / kDfsWarpCap;
+    long long w = 2LL * chunk / (64 * kDfsBudget + kDfsWarpCap);
     w = w > 152 * 4 * kDfsWarpsPerBlock ? 152 * 4 * kDfsWarpsPerBlock : w;
     w = w / kDfsWarpsPerBlock * kDfsWarpsPerBlock;
     return (int)(w < kDfsWarpsPerBlock ? kDfsWarpsPerBlock : w);
 }
 
-long long dfs_out_cap(int chunk) { return (long long)chunk + (long long)dfs_warps(chunk) * kDfsWarpCap; }
+long long dfs_out_cap(int chunk)
+{
+    return 2LL * chunk + (long long)dfs_warps(chunk) * (64 * kDfsBudget + kDfsWarpCap);
+}
+
+long long dfs_step_visits(int chunk) { return (long long)chunk + (long long)dfs_warps(chunk) * 32 * kDfsBudget; }
 
 void traversal_step(int mode, TravArgs &a, int2 *stack, int2 *const xbuf[2], int *cnt, int step, int chunk,
                     cudaStream_t st)
@@ -989,7 +994,7 @@ void traversal_step(int mode, TravArgs &a, int2 *stack, int2 *const xbuf[2], int
     s.next = cnt + 3;
     s.done = (unsigned *)(cnt + 4);
     s.chunk = chunk;
-    s.xcap = (int)std::min<long long>(dfs_out_cap(chunk), 2LL * chunk);   // the output buffers hold 2 * chunk pairs
+    s.xcap = (int)std::min<long long>(dfs_out_cap(chunk), 4LL * chunk);   // the output buffers hold 4 * chunk pairs
     s.budget = kDfsBudget;
     const int grid = dfs_warps(chunk) / kDfsWarpsPerBlock;
 #define WM_FP(DPV)                                                                                \

@@ -49,11 +49,11 @@ struct TravArgs {
                                         // [6] dual-tree evals, [7] peak pending pairs
 };
 
-// Depth-first traversal step (see findpair_dfs_kernel): warps per block, rounds per warp and
-// the capacity of a warp's stack in shared memory (at most 63 + 32 * rounds pairs are pending).
+// Traversal step (see findpair_dfs_kernel): warps per block, depth-first rounds per warp on its
+// own stack, and the capacity of that stack in shared memory.
 constexpr int kDfsWarpsPerBlock = 8;
 constexpr int kDfsBudget = 8;
-constexpr int kDfsWarpCap = 64 + 32 * kDfsBudget;
+constexpr int kDfsWarpCap = 320;
 // traversal counters: [0] stack size, [1] / [2] counts of the two step output buffers,
 // [3] input dispenser, [4] finished blocks
 constexpr int kTravCounters = 8;
@@ -71,7 +71,8 @@ struct DfsArgs {
 };
 
 int dfs_warps(int chunk);
-long long dfs_out_cap(int chunk);   // pairs one step can write to its output buffer
+long long dfs_out_cap(int chunk);       // pairs one step can write to its output buffer
+long long dfs_step_visits(int chunk);   // pairs one step can visit
 
 // component label of every node (-1 when its points span several components), into T.comp and
 // meta[x].w; scratch holds 2 n + 1 ints
