@@ -332,13 +332,13 @@ def main():
     dp = 4 if d <= 4 else 8 if d <= 8 else 16
     kernels = []
     if s0.ms_getpairs > 0 and s0.getpairs_visits > 0:
-        per = 8 + 2 * 16 + 2 * 4 + 2 * (16 + 8 * dp) + 16
+        per = 8 + 2 * 16 + 2 * 16 + 2 * 8 * dp + 16
         gbs = s0.getpairs_visits * per / (s0.ms_getpairs * 1e-3) / 1e9
-        kernels.append({"kernel": "findpair_level_kernel<1> (GetPairs traversal)", "bound": "hbm",
+        kernels.append({"kernel": "findpair_dfs_kernel<1> (GetPairs traversal)", "bound": "hbm",
                         "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
                         "traffic": None, "ms": s0.ms_getpairs, "launches": s0.getpairs_launches,
-                        "work": f"{s0.getpairs_visits} visited node pairs x {per} B (pair, two links, two comp "
-                                f"labels, two meta+box records, two child pairs)",
+                        "work": f"{s0.getpairs_visits} visited node pairs x {per} B (pair, two links, two meta "
+                                f"records holding the component labels, two boxes, two child pairs)",
                         "peak_basis": peaks["hbm_basis"]})
     if s0.ms_knn_kernel > 0:
         fl = s0.knn_evals * (3 * d - 1)
@@ -350,7 +350,7 @@ def main():
     if s0.ms_bccp > 0 and s0.bccp_evals > 0:
         per = 3 * d - 1 + (2 if w["problem"] == "hdbscan" else 0)
         tf = s0.bccp_evals * per / (s0.ms_bccp * 1e-3) / 1e12
-        kernels.append({"kernel": "bccp_group/tile/dual kernels (all BCCP classes)", "bound": "alu", "achieved": tf,
+        kernels.append({"kernel": "bccp_group/pair_tile/dual kernels (all BCCP classes)", "bound": "alu", "achieved": tf,
                         "peak": fp32_peak, "unit": "TFLOP/s", "frac": tf / fp32_peak, "traffic": None,
                         "ms": s0.ms_bccp, "launches": s0.tile_launches,
                         "work": f"{s0.bccp_evals} distance evaluations x {per} flop",
