@@ -162,6 +162,41 @@ int wm_hdbscan(const void *pts, int64_t n, int32_t d, int32_t dtype, int32_t lay
                int32_t *out_order, double *out_reach, int32_t start, const wm_opts *opts);
 
 /*
+ * wm_batch -- many independent EMST / HDBSCAN* instances in one call (the problems of Sec. 2.1,
+ * solved as above).  Instances with the same dimension and minPts run as one problem: their
+ * points share one k-d forest, one WSPD traversal per round, one set of BCCP kernels and one
+ * Kruskal, with no pair or edge ever joining two instances; each instance's results are exactly
+ * those of its own wm_emst / wm_hdbscan call (bit for bit).
+ *   inst    count instances; every pointer in them may be host or device
+ *   count   >= 1
+ *   dtype, layout  as for wm_emst, for every instance
+ * Per instance (wm_instance):
+ *   pts, n, d         n >= 1, 1 <= d <= 15 (one coordinate is taken to separate instances)
+ *   min_pts           0 or 1: EMST (out_edges, out_total_weight); 2..min(n, 256): HDBSCAN*
+ *                     (out_edges = MST of G_MR, out_core_dist, out_dendro, out_order, out_reach
+ *                     as for wm_hdbscan); NULL outputs are skipped
+ *   start             HDBSCAN*: the start point of the dendrogram and plot, 0 <= start < n
+ * Returns WM_OK, or the first error of any group (WM_EINVAL names the instance in
+ * wm_last_error_detail()).  opts as for wm_emst; opts->stats sums the groups.
+ */
+typedef struct {
+    const void *pts;
+    int64_t n;
+    int32_t d;
+    int32_t min_pts;
+    int32_t start;
+    int32_t reserved;
+    wm_edge *out_edges;
+    double *out_total_weight;
+    double *out_core_dist;
+    wm_dnode *out_dendro;
+    int32_t *out_order;
+    double *out_reach;
+} wm_instance;
+
+int wm_batch(const wm_instance *inst, int32_t count, int32_t dtype, int32_t layout, const wm_opts *opts);
+
+/*
  * wm_single_linkage -- ordered dendrogram and reachability plot of any weighted spanning tree
  * (Sec. 4: with the EMST as input this is single-linkage clustering).
  *   tree       n-1 wm_edge forming a spanning tree of 0..n-1 (any order; the library orders

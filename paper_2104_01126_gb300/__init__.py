@@ -21,7 +21,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["emst", "hdbscan", "single_linkage", "query_footprint", "library_path", "load",
-           "WMError", "Stats", "version"]
+           "WMError", "Stats", "version", "batch"]
 
 WM_F32, WM_F64 = 0, 1
 WM_AOS, WM_SOA = 0, 1
@@ -66,6 +66,13 @@ class _Opts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("precision", ctypes.c_int32),
                 ("reserved0", ctypes.c_int32), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t), ("stats", ctypes.POINTER(_Stats))]
+
+
+class _Instance(ctypes.Structure):
+    _fields_ = [("pts", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int32), ("min_pts", ctypes.c_int32),
+                ("start", ctypes.c_int32), ("reserved", ctypes.c_int32), ("out_edges", ctypes.c_void_p),
+                ("out_total_weight", ctypes.c_void_p), ("out_core_dist", ctypes.c_void_p),
+                ("out_dendro", ctypes.c_void_p), ("out_order", ctypes.c_void_p), ("out_reach", ctypes.c_void_p)]
 
 
 class _Job(ctypes.Structure):
@@ -170,6 +177,8 @@ def load(build_if_missing: bool = True):
         lib.wm_server_counters.restype = ctypes.c_int
         lib.wm_server_counters.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_size_t),
                                            ctypes.POINTER(ctypes.c_int32)]
+        lib.wm_batch.restype = ctypes.c_int
+        lib.wm_batch.argtypes = [ctypes.POINTER(_Instance), i32, i32, i32, ctypes.POINTER(_Opts)]
         lib.wm_emst_noalloc.restype = ctypes.c_int
         lib.wm_emst_noalloc.argtypes = [P, i64, i32, i32, i32, P, P, ctypes.POINTER(_Opts)]
         _lib = lib
@@ -350,6 +359,78 @@ def hdbscan(points, min_pts: int = 10, start: int = 0, precision: str = "fp32", 
     if return_stats:
         out["stats"] = Stats._from(st)
     del keep
+    return out
+
+
+def batch(instances, precision: str = "fp32", stream=None, return_stats: bool = False):
+    """Many independent instances in one call (wm_batch).
+
+    instances: a list of (points, min_pts, start) with min_pts <= 1 for an EMST; all points torch
+    CUDA tensors or all host arrays, of one dtype.  Returns a list of dicts: (u, v, w, total) for
+    an EMST, the wm_hdbscan fields for an HDBSCAN* instance; the results of each instance are those
+    of its own emst() / hdbscan() call."""
+    lib = load()
+    t = _torch()
+    pts = [_points(p) for p, _, _ in instances]
+    codes = {q[4] for q in pts}
+    if len(codes) != 1:
+        # one dtype per call: widen to FP64 (exact for FP32 values)
+        pts = [_points(q[0].to(t.float64) if q[5] else np.asarray(q[0], dtype=np.float64)) for q in pts]
+    code = pts[0][4]
+    dev = next((q[6] for q in pts if q[6] is not None), None)
+    k = len(instances)
+    arr = (_Instance * k)()
+    ns = [q[2] for q in pts]
+    ms = [max(n - 1, 0) for n in ns]
+    hd = [int(mp) >= 2 for _, mp, _ in instances]
+    eoff = np.concatenate([[0], np.cumsum(ms)]).astype(np.int64)
+    poff = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+    ebuf, eptr = _out_buffer(16 * int(eoff[-1]), dev)
+    cbuf, cptr = _out_buffer(8 * int(poff[-1]), dev)
+    dbuf, dptr = _out_buffer(24 * int(eoff[-1]), dev)
+    obuf, optr = _out_buffer(4 * int(poff[-1]), dev)
+    rbuf, rptr = _out_buffer(8 * int(poff[-1]), dev)
+    totals = (ctypes.c_double * k)()
+    for j, (q, (_, mp, s)) in enumerate(zip(pts, instances)):
+        a = arr[j]
+        a.pts, a.n, a.d, a.min_pts, a.start = q[1], q[2], q[3], int(mp), int(s)
+        a.out_edges = eptr + 16 * int(eoff[j]) if ms[j] else None
+        if hd[j]:
+            a.out_core_dist = cptr + 8 * int(poff[j])
+            a.out_dendro = dptr + 24 * int(eoff[j]) if ms[j] else None
+            a.out_order = optr + 4 * int(poff[j])
+            a.out_reach = rptr + 8 * int(poff[j])
+        else:
+            a.out_total_weight = ctypes.addressof(totals) + 8 * j
+    st = _Stats()
+    if stream is None and dev is not None:
+        stream = _current_stream(dev)
+    o = _opts(precision, stream, st)
+    rc = lib.wm_batch(arr, k, code, WM_AOS, ctypes.byref(o))
+    _check(rc, "wm_batch")
+    out = []
+    for j in range(k):
+        m, n = ms[j], ns[j]
+        e0, p0 = int(eoff[j]), int(poff[j])
+        u, v, w = _edges_result(ebuf[16 * e0:], m, dev)
+        r = {"u": u, "v": v, "w": w}
+        if hd[j]:
+            left, right, height, size = _dnode_result(dbuf[24 * e0:], m, dev)
+            if dev is not None:
+                cd = cbuf[8 * p0: 8 * (p0 + n)].view(t.float64).clone()
+                order = obuf[4 * p0: 4 * (p0 + n)].view(t.int32).clone()
+                reach = rbuf[8 * p0: 8 * (p0 + n)].view(t.float64).clone()
+            else:
+                cd = np.frombuffer(cbuf, dtype=np.float64, count=n, offset=8 * p0).copy()
+                order = np.frombuffer(obuf, dtype=np.int32, count=n, offset=4 * p0).copy()
+                reach = np.frombuffer(rbuf, dtype=np.float64, count=n, offset=8 * p0).copy()
+            r.update(cd=cd, left=left, right=right, height=height, size=size, order=order, reach=reach)
+        else:
+            r["total"] = totals[j]
+        out.append(r)
+    del pts
+    if return_stats:
+        return out, Stats._from(st)
     return out
 
 

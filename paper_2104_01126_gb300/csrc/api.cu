@@ -16,6 +16,7 @@
 
 #include "wm_internal.cuh"
 #include "wspd.cuh"
+#include "batch.cuh"
 #include "hdb.cuh"
 
 namespace wm {
@@ -244,12 +245,15 @@ static void set_rho(TravArgs &a, double lo, double hi)
     a.rho_hi_f = float_ru(hi);
 }
 
-// MemoGFK rounds (Algorithm 3).  On return E_out holds the n-1 tree edges in K order.
+// MemoGFK rounds (Algorithm 3).  On return E_out holds the tree edges in K order: n-1 of them, or
+// `target` when the points form several instances that must not be joined (a batch): then every
+// edge weight is below rho_cap, rho_hi never exceeds it, and no pair at or above it is retrieved.
 // hdb: optional HDBSCAN* state (node cd bounds, per-position cd2, sorted repair edges).
 static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps &caps, EdgeK *E_out, int *uf,
-                   unsigned long long *R, unsigned *overflow_bits)
+                   unsigned long long *R, unsigned *overflow_bits, long long target = -1, double rho_cap = INFINITY)
 {
     const int n = P.n;
+    if (target < 0) target = (long long)n - 1;
     cudaStream_t st = C.st;
     Arena &ar = C.ar;
     *overflow_bits = 0;
@@ -326,7 +330,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     int rpos = 0;   // HDBSCAN*: next unconsumed repair edge
     const double inf = INFINITY;
     int rounds = 0;
-    while (nE < n - 1) {
+    while (nE < target) {
         if (++rounds > 4096) { set_detail("MemoGFK made no progress%s (%lld rounds)", "", rounds); return WM_EINTERNAL; }
         Timer tw;
         WM_TRY(launch_comp_labels(T, P, uf, links, meta, comp_scratch, ar, st));
@@ -341,7 +345,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         WM_CK(cudaStreamSynchronize(st));
         float rho_f;
         memcpy(&rho_f, C.pin, sizeof rho_f);
-        double rho_hi = rho_f;
+        double rho_hi = std::min<double>(rho_f, rho_cap);
         if (rho_hi < rho_lo) rho_hi = rho_lo;
         // ---- GetPairs in chunks; the retrieved pairs of every chunk get their BCCP right away
         set_rho(a, rho_lo, rho_hi);
@@ -461,8 +465,8 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         }
         C.stats.ms_kruskal += tk.ms();
         nE += accepted;
-        if (rho_hi == inf && nE < n - 1) {
-            set_detail("MemoGFK round with rho_hi = inf left the forest incomplete%s (%lld edges)", "", nE);
+        if (rho_hi >= rho_cap && nE < target) {
+            set_detail("MemoGFK round with rho_hi = its cap left the forest incomplete%s (%lld edges)", "", nE);
             return WM_EINTERNAL;
         }
         rho_lo = rho_hi;
@@ -472,8 +476,8 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         // every round appended its tree edges unordered: put the tree in K order
         Timer ts;
         EdgeK *sorted = E_out;
-        WM_TRY(radix_sort_edges(E_out, tmp, n - 1, st, ar, &sorted, C.pin + 4096));
-        if (sorted != E_out) WM_CK(cudaMemcpyAsync(E_out, sorted, sizeof(EdgeK) * (n - 1), cudaMemcpyDeviceToDevice, st));
+        WM_TRY(radix_sort_edges(E_out, tmp, (int)target, st, ar, &sorted, C.pin + 4096));
+        if (sorted != E_out) WM_CK(cudaMemcpyAsync(E_out, sorted, sizeof(EdgeK) * target, cudaMemcpyDeviceToDevice, st));
         WM_CK(cudaStreamSynchronize(st));
         C.stats.ms_kruskal += ts.ms();
     }
@@ -558,7 +562,8 @@ static int write_edges(Call &C, const EdgeK *E, int m, wm_edge *out, double *tot
 // ------------------------------------------------------------------------ the call driver
 typedef int (*Body)(Call &C, void *ctx, const Caps &caps, unsigned *overflow);
 
-static int run_call(const wm_opts *opts, long long n, int d, int min_pts, Body body, void *ctx)
+static int run_call(const wm_opts *opts, long long n, int d, int min_pts, Body body, void *ctx,
+                    long long extra_bytes = 0)
 {
     g_detail.clear();
     Timer total;
@@ -574,6 +579,7 @@ static int run_call(const wm_opts *opts, long long n, int d, int min_pts, Body b
     C.pin = pinned_scratch();
     if (!C.pin) { set_detail("cudaMallocHost failed%s", ""); return WM_ENOMEM; }
     Caps caps = default_caps(n, min_pts);
+    caps.extra_bytes = extra_bytes;
     const bool user_ws = opts && opts->workspace;
     int rc = 0;
     unsigned ovf_seen = 0;   // capacities that overflowed in earlier attempts
@@ -746,6 +752,197 @@ static int sl_body(Call &C, void *vctx, const Caps &, unsigned *ovf)
     return 0;
 }
 
+// ------------------------------------------------------------------------------ batches
+// Instances of one group (same d, same minPts) solved as one point set; see batch.cu.
+struct BatchCtx {
+    const wm_instance *inst;
+    const std::vector<int> *idx;
+    int d, min_pts, dtype, layout;
+};
+
+// copy stage[off[j], off[j+1]) to every instance's output dst[j]: device outputs by one kernel,
+// host outputs through one device-to-host copy of the whole stage
+template <typename T>
+static int scatter_outputs(Call &C, const T *stage, const std::vector<long long> &off, const long long *off_d,
+                           const std::vector<T *> &dst)
+{
+    const int k = (int)dst.size();
+    const long long cnt = off[k];
+    std::vector<T *> dev(k, nullptr);
+    bool any_host = false, any_dev = false;
+    for (int j = 0; j < k; ++j) {
+        if (!dst[j] || off[j + 1] == off[j]) continue;
+        if (is_device_ptr(dst[j])) { dev[j] = dst[j]; any_dev = true; }
+        else any_host = true;
+    }
+    if (any_dev) {
+        T **dt = (T **)C.ar.take(sizeof(T *) * k);
+        if (!dt) return WM_ENOMEM;
+        WM_CK(cudaMemcpyAsync(dt, dev.data(), sizeof(T *) * k, cudaMemcpyHostToDevice, C.st));
+        batch_scatter<T>(stage, cnt, off_d, k, dt, C.st);
+    }
+    if (any_host && cnt > 0) {
+        std::vector<T> h((size_t)cnt);
+        WM_CK(cudaMemcpyAsync(h.data(), stage, sizeof(T) * cnt, cudaMemcpyDeviceToHost, C.st));
+        WM_CK(cudaStreamSynchronize(C.st));
+        for (int j = 0; j < k; ++j)
+            if (dst[j] && !dev[j] && off[j + 1] > off[j])
+                memcpy(dst[j], h.data() + off[j], sizeof(T) * (off[j + 1] - off[j]));
+    }
+    return 0;
+}
+
+static int batch_body(Call &C, void *vctx, const Caps &caps, unsigned *ovf)
+{
+    BatchCtx &x = *(BatchCtx *)vctx;
+    cudaStream_t st = C.st;
+    Arena &ar = C.ar;
+    *ovf = 0;
+    const std::vector<int> &idx = *x.idx;
+    const int k = (int)idx.size();
+    const int d = x.d, D = d + 1;
+    const bool hdb = x.min_pts >= 2;
+    auto I = [&](int j) -> const wm_instance & { return x.inst[idx[j]]; };
+    std::vector<long long> base(k + 1, 0), eoff(k + 1, 0);
+    for (int j = 0; j < k; ++j) base[j + 1] = base[j] + I(j).n;
+    for (int j = 0; j <= k; ++j) eoff[j] = base[j] - j;   // tree edges of the instances before j
+    const long long total = base[k];
+    const int n = (int)total;
+    const long long m = total - k;
+    // ---- inputs: device pointers as given, host ones packed into one device buffer
+    const size_t esz = x.dtype == WM_F32 ? 4 : 8;
+    std::vector<const void *> src(k);
+    std::vector<char> on_dev(k);
+    size_t host_bytes = 0;
+    for (int j = 0; j < k; ++j) {
+        on_dev[j] = is_device_ptr(I(j).pts);
+        if (!on_dev[j]) host_bytes += (size_t)I(j).n * d * esz;
+        else src[j] = I(j).pts;
+    }
+    if (host_bytes) {
+        char *hb = (char *)ar.take(host_bytes);
+        if (!hb) return WM_ENOMEM;
+        std::vector<char> pack(host_bytes);
+        size_t off = 0;
+        for (int j = 0; j < k; ++j) {
+            if (on_dev[j]) continue;
+            const size_t b = (size_t)I(j).n * d * esz;
+            memcpy(pack.data() + off, I(j).pts, b);
+            src[j] = hb + off;
+            off += b;
+        }
+        WM_CK(cudaMemcpyAsync(hb, pack.data(), host_bytes, cudaMemcpyHostToDevice, st));
+        WM_CK(cudaStreamSynchronize(st));
+    }
+    long long *base_d = ar.get<long long>(k + 1), *eoff_d = ar.get<long long>(k + 1);
+    const void **src_d = (const void **)ar.take(sizeof(void *) * k);
+    unsigned *maxabs = ar.get<unsigned>(1);
+    int *bad = ar.get<int>(1);
+    double *raw = ar.get<double>((size_t)total * D);
+    if (ar.failed || !src_d) return WM_ENOMEM;
+    WM_CK(cudaMemcpyAsync(base_d, base.data(), sizeof(long long) * (k + 1), cudaMemcpyHostToDevice, st));
+    WM_CK(cudaMemcpyAsync(eoff_d, eoff.data(), sizeof(long long) * (k + 1), cudaMemcpyHostToDevice, st));
+    WM_CK(cudaMemcpyAsync(src_d, src.data(), sizeof(void *) * k, cudaMemcpyHostToDevice, st));
+    WM_CK(cudaMemsetAsync(maxabs, 0, sizeof(unsigned), st));
+    WM_CK(cudaMemsetAsync(bad, 0, sizeof(int), st));
+    batch_gather(src_d, base_d, k, total, d, x.dtype, x.layout, raw, maxabs, st);
+    WM_CK(cudaMemcpyAsync(C.pin, maxabs, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    WM_CK(cudaStreamSynchronize(st));
+    float mabs;
+    memcpy(&mabs, C.pin, sizeof mabs);
+    if (!(mabs <= 1.2e18f)) { set_detail("non-finite coordinate or |coordinate| > 2^60%s", ""); return WM_EINVAL; }
+    // separation L: a power of two with L^2 / 4 above every squared distance inside an instance
+    // (at most d (2 max|x|)^2), so the cap rho_cap = L^2 / 4 sits between the two kinds of pairs
+    double L = 1.0;
+    const double need = 4.0 * std::sqrt((double)D) * (double)mabs * (1.0 + 1e-6);
+    while (L <= need) L *= 2.0;
+    batch_scale(raw + (size_t)d * total, total, L, st);
+    // ---- the joint problem
+    Prepared S;
+    WM_TRY(prepare(C, raw, total, D, WM_F64, WM_SOA, S));
+    HdbState H;
+    if (hdb) {
+        Timer tc;
+        WM_TRY(core_distances(S.P, S.T, x.min_pts, C.precision == WM_PREC_FP64, H, ar, st, C.pin, &C.stats));
+        C.stats.ms_core_dist = tc.ms();
+    }
+    int *uf = ar.get<int>(n);
+    unsigned long long *R = ar.get<unsigned long long>(2LL * n);
+    EdgeK *E = ar.get<EdgeK>(n);
+    if (ar.failed) return WM_ENOMEM;
+    launch(init_uf_kernel, grid_for(n, 256), 256, 0, st, uf, R, n);
+    WM_TRY(memogfk(C, S.P, S.T, hdb ? &H : nullptr, caps, E, uf, R, ovf, m, L * L / 4));
+    if (*ovf) return 0;
+    // ---- tree edges grouped by instance, K order inside each
+    EdgeK *keys = ar.get<EdgeK>(m + 1), *ktmp = ar.get<EdgeK>(m + 1);
+    int *local = ar.get<int>(m + 1);
+    wm_edge *se = ar.get<wm_edge>(m + 1);
+    if (ar.failed) return WM_ENOMEM;
+    batch_edge_inst(E, (int)m, base_d, k, keys, st);
+    EdgeK *grouped = keys;
+    WM_TRY(radix_sort_edges(keys, ktmp, (int)m, st, ar, &grouped, C.pin + 4096));
+    batch_edge_place(grouped, E, (int)m, base_d, local, se, bad, st);
+    {
+        std::vector<wm_edge *> dst(k);
+        for (int j = 0; j < k; ++j) dst[j] = I(j).out_edges;
+        WM_TRY(scatter_outputs<wm_edge>(C, se, eoff, eoff_d, dst));
+    }
+    if (!hdb) {
+        double *tot = ar.get<double>(k);
+        if (!tot) return WM_ENOMEM;
+        batch_totals(se, base_d, k, tot, st);
+        std::vector<double> ht(k);
+        WM_CK(cudaMemcpyAsync(ht.data(), tot, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+        WM_CK(cudaStreamSynchronize(st));
+        for (int j = 0; j < k; ++j)
+            if (I(j).out_total_weight) *I(j).out_total_weight = ht[j];
+    } else {
+        double *scd = ar.get<double>(n);
+        if (!scd) return WM_ENOMEM;
+        batch_cd(H.cd64, S.P.pid, n, scd, st);
+        {
+            std::vector<double *> dst(k);
+            for (int j = 0; j < k; ++j) dst[j] = I(j).out_core_dist;
+            WM_TRY(scatter_outputs<double>(C, scd, base, base_d, dst));
+        }
+        bool want = false;
+        for (int j = 0; j < k; ++j) want = want || I(j).out_dendro || I(j).out_order || I(j).out_reach;
+        if (want) {
+            Timer td;
+            // the instances chained by bridges between consecutive start points
+            std::vector<int> starts(k);
+            for (int j = 0; j < k; ++j) starts[j] = (int)(base[j] + I(j).start);
+            int *starts_d = ar.get<int>(k);
+            EdgeK *Eall = ar.get<EdgeK>(n);
+            wm_dnode *jd = ar.get<wm_dnode>(n), *sd = ar.get<wm_dnode>(m + 1);
+            int *jo = ar.get<int>(n), *so = ar.get<int>(n);
+            double *jr = ar.get<double>(n), *sr = ar.get<double>(n);
+            if (ar.failed) return WM_ENOMEM;
+            WM_CK(cudaMemcpyAsync(starts_d, starts.data(), sizeof(int) * k, cudaMemcpyHostToDevice, st));
+            if (m > 0) WM_CK(cudaMemcpyAsync(Eall, E, sizeof(EdgeK) * m, cudaMemcpyDeviceToDevice, st));
+            batch_bridges(starts_d, k, Eall + m, st);
+            WM_TRY(dendrogram_impl(Eall, n, starts[0], 1, jd, jo, jr, ar, st, C.pin));
+            batch_dendro(jd, E, (int)m, total, base_d, k, local, sd, bad, st);
+            batch_order(jo, jr, total, base_d, k, so, sr, bad, st);
+            std::vector<wm_dnode *> dd(k);
+            std::vector<int *> od(k);
+            std::vector<double *> rd(k);
+            for (int j = 0; j < k; ++j) { dd[j] = I(j).out_dendro; od[j] = I(j).out_order; rd[j] = I(j).out_reach; }
+            WM_TRY(scatter_outputs<wm_dnode>(C, sd, eoff, eoff_d, dd));
+            WM_TRY(scatter_outputs<int>(C, so, base, base_d, od));
+            WM_TRY(scatter_outputs<double>(C, sr, base, base_d, rd));
+            C.stats.ms_dendrogram = td.ms();
+        }
+    }
+    WM_CK(cudaMemcpyAsync(C.pin, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    WM_CK(cudaStreamSynchronize(st));
+    if (C.pin[0]) {
+        set_detail("batch: an output crossed two instances%s (flags %lld)", "", C.pin[0]);
+        return WM_EINTERNAL;
+    }
+    return 0;
+}
+
 }  // namespace wm
 
 // =========================================================================== C ABI
@@ -790,6 +987,81 @@ int wm_single_linkage(const wm_edge *tree, int64_t n, int32_t start, wm_dnode *o
     }
     SlCtx c{tree, n, start, out_dendro, out_order, out_reach};
     return run_call(opts, n, 1, 1, sl_body, &c);
+}
+
+int wm_batch(const wm_instance *inst, int32_t count, int32_t dtype, int32_t layout, const wm_opts *opts)
+{
+    g_detail.clear();
+    if (!inst || count < 1 || (dtype != WM_F32 && dtype != WM_F64) || (layout != WM_AOS && layout != WM_SOA)) {
+        set_detail("invalid argument to wm_batch%s (count=%lld)", "", (long long)count);
+        return WM_EINVAL;
+    }
+    // groups of equal (d, minPts class); EMST instances form the class minPts <= 1
+    std::vector<std::pair<long long, int>> keyed;
+    for (int i = 0; i < count; ++i) {
+        const wm_instance &q = inst[i];
+        const int mp = q.min_pts <= 1 ? 1 : q.min_pts;
+        if (!q.pts || q.n < 1 || q.n > 0x3fffffff || q.d < 1 || q.d > kMaxDim - 1 || q.min_pts < 0 ||
+            (mp > 1 && (mp > q.n || mp > 256 || q.start < 0 || q.start >= q.n))) {
+            set_detail("wm_batch: invalid instance %s%lld", "", (long long)i);
+            return WM_EINVAL;
+        }
+        keyed.push_back({(long long)q.d * 1024 + mp, i});
+    }
+    std::stable_sort(keyed.begin(), keyed.end(),
+                     [](const std::pair<long long, int> &a, const std::pair<long long, int> &b) { return a.first < b.first; });
+    wm_stats sum{};
+    int rc = WM_OK;
+    for (size_t a = 0; a < keyed.size() && rc == WM_OK;) {
+        size_t b = a;
+        std::vector<int> idx;
+        long long total = 0;
+        while (b < keyed.size() && keyed[b].first == keyed[a].first) {
+            idx.push_back(keyed[b].second);
+            total += inst[keyed[b].second].n;
+            ++b;
+        }
+        // one group: at most 2^30 points (split longer runs)
+        std::vector<int> part;
+        long long ptotal = 0;
+        for (size_t t = 0; t <= idx.size() && rc == WM_OK; ++t) {
+            if (t < idx.size() && ptotal + inst[idx[t]].n <= 0x3fffffff) {
+                part.push_back(idx[t]);
+                ptotal += inst[idx[t]].n;
+                continue;
+            }
+            if (!part.empty()) {
+                const int d = inst[part[0]].d;
+                const int mp = inst[part[0]].min_pts <= 1 ? 1 : inst[part[0]].min_pts;
+                BatchCtx c{inst, &part, d, mp, dtype, layout};
+                wm_stats gs{};
+                wm_opts o = opts ? *opts : wm_opts{};
+                o.stats = &gs;
+                const long long extra = ptotal * (8LL * (d + 1) + 200) + (long long)part.size() * 64;
+                rc = run_call(&o, ptotal, d + 1, mp > 1 ? mp : 0, batch_body, &c, extra);
+                sum.ms_total += gs.ms_total; sum.ms_ingest += gs.ms_ingest; sum.ms_build_tree += gs.ms_build_tree;
+                sum.ms_core_dist += gs.ms_core_dist; sum.ms_wspd += gs.ms_wspd; sum.ms_bccp += gs.ms_bccp;
+                sum.ms_kruskal += gs.ms_kruskal; sum.ms_dendrogram += gs.ms_dendrogram; sum.rounds += gs.rounds;
+                sum.pairs_retrieved += gs.pairs_retrieved; sum.bccp_evals += gs.bccp_evals;
+                sum.bccp_tile_evals += gs.bccp_tile_evals; sum.knn_evals += gs.knn_evals;
+                sum.fp64_rechecks += gs.fp64_rechecks; sum.candidate_edges += gs.candidate_edges;
+                sum.tree_nodes += gs.tree_nodes; sum.tree_depth = std::max(sum.tree_depth, gs.tree_depth);
+                sum.workspace_bytes_used = std::max(sum.workspace_bytes_used, gs.workspace_bytes_used);
+                sum.getpairs_visits += gs.getpairs_visits; sum.getrho_visits += gs.getrho_visits;
+                sum.getpairs_launches += gs.getpairs_launches; sum.bccp_dual_evals += gs.bccp_dual_evals;
+                sum.rho_shrinks += gs.rho_shrinks; sum.tile_launches += gs.tile_launches;
+                sum.ms_knn_kernel += gs.ms_knn_kernel; sum.ms_tile_kernel += gs.ms_tile_kernel;
+                sum.ms_getpairs += gs.ms_getpairs;
+                sum.max_pending_pairs = std::max(sum.max_pending_pairs, gs.max_pending_pairs);
+            }
+            part.clear();
+            ptotal = 0;
+            if (t < idx.size()) { part.push_back(idx[t]); ptotal = inst[idx[t]].n; }
+        }
+        a = b;
+    }
+    if (opts && opts->stats) *opts->stats = sum;
+    return rc;
 }
 
 int wm_query_footprint(int64_t n, int32_t d, int32_t min_pts, size_t *bytes)

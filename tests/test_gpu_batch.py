@@ -1,0 +1,119 @@
+"""wm_batch (many independent instances in one call) against the single-instance calls and the oracle.
+
+Every instance's edges, core distances, dendrogram, order and bars must equal those of its own
+wm_emst / wm_hdbscan call element for element (the batch shares the k-d forest, the traversals,
+the BCCP kernels and Kruskal across instances, but no pair or edge may join two instances), and
+the small instances must equal the FP64 oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synthdata
+import paper_2104_01126_gb300 as wm
+from gpu_common import require_gpu, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+    wm.load()
+
+
+def _instances(seed, count, nmin, nmax, dims=(2, 3, 5), mps=(1, 5, 10)):
+    rng = np.random.default_rng(seed)
+    out = []
+    for j in range(count):
+        n = int(np.exp(rng.uniform(np.log(nmin), np.log(nmax))))
+        d = int(rng.choice(dims))
+        mp = int(rng.choice(mps))
+        if mp > n:
+            mp = 1
+        kind = "uniform" if rng.random() < 0.5 else "gmm"
+        x = synthdata.generate(kind, n, d, seed=seed * 1000 + j)
+        start = int(rng.integers(0, n))
+        out.append((x, mp, start))
+    return out
+
+
+def _same(a, b):
+    return np.array_equal(to_np(a), to_np(b))
+
+
+def _check_against_single(inst, res, device):
+    import torch
+    for (x, mp, s), r in zip(inst, res):
+        xx = torch.from_numpy(x).cuda() if device else x
+        if mp <= 1:
+            one = wm.emst(xx)
+            assert _same(r["u"], one["u"]) and _same(r["v"], one["v"]) and _same(r["w"], one["w"])
+            assert math.isclose(r["total"], one["total"], rel_tol=1e-12, abs_tol=1e-300)
+        else:
+            one = wm.hdbscan(xx, min_pts=mp, start=s)
+            for key in ("u", "v", "w", "cd", "left", "right", "height", "size", "order", "reach"):
+                assert _same(r[key], one[key]), (len(x), mp, key)
+
+
+def test_batch_matches_single_calls_device():
+    import torch
+    inst = _instances(1, 40, 1, 4000)
+    inst[0] = (inst[0][0][:1], 1, 0)                         # a one-point EMST instance
+    inst[1] = (synthdata.generate("uniform", 2, 3, seed=5), 2, 1)
+    dev = [(torch.from_numpy(x).cuda(), mp, s) for x, mp, s in inst]
+    res = wm.batch(dev)
+    _check_against_single(inst, res, device=True)
+
+
+def test_batch_matches_single_calls_host_inputs():
+    inst = _instances(2, 16, 30, 3000)
+    res = wm.batch(inst)
+    _check_against_single(inst, res, device=False)
+
+
+def test_batch_matches_oracle_small():
+    import torch
+    inst = _instances(3, 24, 20, 600)
+    res = wm.batch([(torch.from_numpy(x).cuda(), mp, s) for x, mp, s in inst])
+    for (x, mp, s), r in zip(inst, res):
+        if mp <= 1:
+            o = oracle.emst(x)
+            assert np.array_equal(to_np(r["u"]), o["u"]) and np.array_equal(to_np(r["v"]), o["v"])
+            assert np.array_equal(to_np(r["w"]), o["w"])
+        else:
+            o = oracle.hdbscan(x, mp, s)
+            if o["tie"]:
+                # equal-weight alternatives: the batch must still return a minimum tree of that weight
+                assert math.isclose(float(np.sum(to_np(r["w"]))), o["total"], rel_tol=1e-12)
+                continue
+            for key in ("u", "v", "w", "cd", "left", "right", "height", "size", "order", "reach"):
+                assert np.array_equal(to_np(r[key]), o[key]), (len(x), mp, key)
+
+
+def test_batch_duplicates_and_ties():
+    import torch
+    g = synthdata.unit_grid(12, 2).astype(np.float32)             # many equal distances
+    dup = np.repeat(synthdata.generate("uniform", 50, 3, seed=9), 3, axis=0)
+    inst = [(g, 1, 0), (g, 5, 7), (dup, 4, 3), (dup, 1, 0)]
+    res = wm.batch([(torch.from_numpy(x).cuda(), mp, s) for x, mp, s in inst])
+    _check_against_single(inst, res, device=True)
+
+
+def test_batch_many_small_instances():
+    import torch
+    inst = _instances(4, 600, 64, 2048, mps=(1, 5, 10, 50))
+    res = wm.batch([(torch.from_numpy(x).cuda(), mp, s) for x, mp, s in inst])
+    rng = np.random.default_rng(0)
+    pick = rng.choice(len(inst), size=30, replace=False)
+    _check_against_single([inst[i] for i in pick], [res[i] for i in pick], device=True)
+
+
+def test_batch_rejects_bad_instance():
+    x = synthdata.generate("uniform", 10, 2, seed=0)
+    with pytest.raises(wm.WMError):
+        wm.batch([(x, 20, 0)])          # minPts > n
+    with pytest.raises(wm.WMError):
+        wm.batch([(x, 5, 10)])          # start out of range
