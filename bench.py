@@ -135,6 +135,68 @@ def serving_mix(count, seed=0, n_lo=1_000, n_hi=200_000):
     return jobs
 
 
+def batched_mix(count, seed=0, n_lo=64, n_hi=65536):
+    """Instances shaped like the batched configuration: n log-uniform in [n_lo, n_hi], d in {2,3,5},
+    half EMST and half HDBSCAN* (minPts in {5,10,50}), uniform or Gaussian-mixture points."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(count):
+        n = int(np.exp(g.uniform(np.log(n_lo), np.log(n_hi))))
+        d = int(g.choice([2, 3, 5]))
+        mp = 1 if i % 2 == 0 else int(g.choice([5, 10, 50]))
+        if g.random() < 0.5:
+            x = synthdata.gaussian_mixture(n, d, seed=seed * 100003 + i)
+        else:
+            x = synthdata.uniform(n, d, seed=seed * 100003 + i, dtype=np.float32)
+        out.append((x, min(mp, n), 0))
+    return out
+
+
+def run_batched(wm, torch, count, seed):
+    """The batched configuration: all instances in one wm_batch call (device-resident inputs),
+    and, on a 64-instance subset, one call per instance against one batched call."""
+    inst = batched_mix(count, seed=seed)
+    dev = [(torch.from_numpy(x).cuda(), mp, s) for x, mp, s in inst]
+    pts = sum(len(x) for x, _, _ in inst)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return sum(ts) / len(ts)
+
+    wm.batch(dev, raw=True)                                           # warm-up (arenas, caches)
+    ms = timed(lambda: wm.batch(dev, raw=True), 2)
+    sub = [dev[i] for i in np.random.default_rng(seed).choice(len(dev), size=min(64, len(dev)), replace=False)]
+    sub_pts = sum(int(x.shape[0]) for x, _, _ in sub)
+
+    def one_at_a_time():
+        for x, mp, s in sub:
+            if mp <= 1:
+                wm.emst(x)
+            else:
+                wm.hdbscan(x, min_pts=mp, start=s)
+
+    one_at_a_time()
+    ms_single = timed(one_at_a_time, 1)
+    ms_sub = timed(lambda: wm.batch(sub, raw=True), 2)
+    return {"instances": len(inst), "points": pts, "ms": ms, "instances_per_s": len(inst) / (ms * 1e-3),
+            "mpoints_per_s": pts / (ms * 1e-3) / 1e6,
+            "subset": {"instances": len(sub), "points": sub_pts, "one_call_per_instance_ms": ms_single,
+                       "batched_ms": ms_sub, "speedup": ms_single / ms_sub},
+            "mix": "n log-uniform [64, 65536], d in {2,3,5}, half EMST and half HDBSCAN* (minPts in {5,10,50}), "
+                   "uniform or gmm points; instances with equal minPts share one k-d forest and one set of "
+                   "MemoGFK rounds (split by d where a dimension holds >= 2^20 points)"}
+
+
 def run_serving(wm, jobs, workers, budget, rate_hz=None, seed=1):
     """Submits the jobs (all at once, or as a Poisson stream at rate_hz); returns latencies (ms)
     and the wall time (s)."""
@@ -269,6 +331,7 @@ def main():
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--batch-instances", type=int, default=4096)
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     ws, rank, local = dist_setup()
@@ -428,6 +491,10 @@ def main():
                   "mix": "n log-uniform [1e3, 2e5], d in {2,3,5,7}, minPts in {10,50}, gmm or uniform, "
                          "EMST or HDBSCAN*; Poisson arrivals at half the measured saturation rate"}
 
+    batched = None
+    if args.batch_instances > 0:
+        batched = run_batched(wm, torch, args.batch_instances, seed=rank)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, args.cpu_sample)
@@ -450,7 +517,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
                 "config": cfg, "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
-                "cpu_baseline": cpu, "plain_form": plain, "served": served, "phases_ms": phases,
+                "cpu_baseline": cpu, "plain_form": plain, "served": served, "batched": batched,
+                "phases_ms": phases,
                 "counters": counters,
                 "step_ms": [round(t, 3) for t in times]}
         print(json.dumps(line), flush=True)

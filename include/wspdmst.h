@@ -163,10 +163,12 @@ int wm_hdbscan(const void *pts, int64_t n, int32_t d, int32_t dtype, int32_t lay
 
 /*
  * wm_batch -- many independent EMST / HDBSCAN* instances in one call (the problems of Sec. 2.1,
- * solved as above).  Instances with the same dimension and minPts run as one problem: their
+ * solved as above).  Instances with the same minPts run as one problem (in the dimension of the
+ * largest, missing coordinates being 0, which adds exactly 0 to every distance): their
  * points share one k-d forest, one WSPD traversal per round, one set of BCCP kernels and one
- * Kruskal, with no pair or edge ever joining two instances; each instance's results are exactly
- * those of its own wm_emst / wm_hdbscan call (bit for bit).
+ * Kruskal, with no pair or edge ever joining two instances; each instance's edges, core
+ * distances, dendrogram, order and bars are exactly those of its own wm_emst / wm_hdbscan call
+ * (bit for bit; the total weight is summed in another order).
  *   inst    count instances; every pointer in them may be host or device
  *   count   >= 1
  *   dtype, layout  as for wm_emst, for every instance

@@ -362,7 +362,7 @@ def hdbscan(points, min_pts: int = 10, start: int = 0, precision: str = "fp32", 
     return out
 
 
-def batch(instances, precision: str = "fp32", stream=None, return_stats: bool = False):
+def batch(instances, precision: str = "fp32", stream=None, return_stats: bool = False, raw: bool = False):
     """Many independent instances in one call (wm_batch).
 
     instances: a list of (points, min_pts, start) with min_pts <= 1 for an EMST; all points torch
@@ -408,6 +408,11 @@ def batch(instances, precision: str = "fp32", stream=None, return_stats: bool = 
     o = _opts(precision, stream, st)
     rc = lib.wm_batch(arr, k, code, WM_AOS, ctypes.byref(o))
     _check(rc, "wm_batch")
+    if raw:
+        # concatenated outputs (instance j's slices start at edge_offsets[j] / point_offsets[j])
+        res = {"edges": ebuf, "core_dist": cbuf, "dendro": dbuf, "order": obuf, "reach": rbuf,
+               "edge_offsets": eoff, "point_offsets": poff, "totals": list(totals)}
+        return (res, Stats._from(st)) if return_stats else res
     out = []
     for j in range(k):
         m, n = ms[j], ns[j]

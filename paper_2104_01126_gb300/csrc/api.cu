@@ -814,9 +814,11 @@ static int batch_body(Call &C, void *vctx, const Caps &caps, unsigned *ovf)
     std::vector<const void *> src(k);
     std::vector<char> on_dev(k);
     size_t host_bytes = 0;
+    std::vector<int> dims(k);
     for (int j = 0; j < k; ++j) {
+        dims[j] = I(j).d;
         on_dev[j] = is_device_ptr(I(j).pts);
-        if (!on_dev[j]) host_bytes += (size_t)I(j).n * d * esz;
+        if (!on_dev[j]) host_bytes += (size_t)I(j).n * I(j).d * esz;
         else src[j] = I(j).pts;
     }
     if (host_bytes) {
@@ -826,7 +828,7 @@ static int batch_body(Call &C, void *vctx, const Caps &caps, unsigned *ovf)
         size_t off = 0;
         for (int j = 0; j < k; ++j) {
             if (on_dev[j]) continue;
-            const size_t b = (size_t)I(j).n * d * esz;
+            const size_t b = (size_t)I(j).n * I(j).d * esz;
             memcpy(pack.data() + off, I(j).pts, b);
             src[j] = hb + off;
             off += b;
@@ -835,6 +837,7 @@ static int batch_body(Call &C, void *vctx, const Caps &caps, unsigned *ovf)
         WM_CK(cudaStreamSynchronize(st));
     }
     long long *base_d = ar.get<long long>(k + 1), *eoff_d = ar.get<long long>(k + 1);
+    int *dims_d = ar.get<int>(k);
     const void **src_d = (const void **)ar.take(sizeof(void *) * k);
     unsigned *maxabs = ar.get<unsigned>(1);
     int *bad = ar.get<int>(1);
@@ -843,9 +846,10 @@ static int batch_body(Call &C, void *vctx, const Caps &caps, unsigned *ovf)
     WM_CK(cudaMemcpyAsync(base_d, base.data(), sizeof(long long) * (k + 1), cudaMemcpyHostToDevice, st));
     WM_CK(cudaMemcpyAsync(eoff_d, eoff.data(), sizeof(long long) * (k + 1), cudaMemcpyHostToDevice, st));
     WM_CK(cudaMemcpyAsync(src_d, src.data(), sizeof(void *) * k, cudaMemcpyHostToDevice, st));
+    WM_CK(cudaMemcpyAsync(dims_d, dims.data(), sizeof(int) * k, cudaMemcpyHostToDevice, st));
     WM_CK(cudaMemsetAsync(maxabs, 0, sizeof(unsigned), st));
     WM_CK(cudaMemsetAsync(bad, 0, sizeof(int), st));
-    batch_gather(src_d, base_d, k, total, d, x.dtype, x.layout, raw, maxabs, st);
+    batch_gather(src_d, dims_d, base_d, k, total, d, x.dtype, x.layout, raw, maxabs, st);
     WM_CK(cudaMemcpyAsync(C.pin, maxabs, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     WM_CK(cudaStreamSynchronize(st));
     float mabs;
@@ -996,7 +1000,10 @@ int wm_batch(const wm_instance *inst, int32_t count, int32_t dtype, int32_t layo
         set_detail("invalid argument to wm_batch%s (count=%lld)", "", (long long)count);
         return WM_EINVAL;
     }
-    // groups of equal (d, minPts class); EMST instances form the class minPts <= 1
+    // groups of equal minPts class (EMST instances form the class minPts <= 1); within a class,
+    // the instances of one dimension form a group of their own when they hold at least
+    // kBatchSplit points, the rest share one group in the dimension of its largest instance
+    // (fewer groups, fewer rounds; at scale, the narrower arithmetic of one dimension wins)
     std::vector<std::pair<long long, int>> keyed;
     for (int i = 0; i < count; ++i) {
         const wm_instance &q = inst[i];
@@ -1006,7 +1013,14 @@ int wm_batch(const wm_instance *inst, int32_t count, int32_t dtype, int32_t layo
             set_detail("wm_batch: invalid instance %s%lld", "", (long long)i);
             return WM_EINVAL;
         }
-        keyed.push_back({(long long)q.d * 1024 + mp, i});
+        keyed.push_back({(long long)mp * 64 + q.d, i});
+    }
+    {
+        const long long kBatchSplit = 1 << 20;
+        std::unordered_map<long long, long long> pts;
+        for (auto &e : keyed) pts[e.first] += inst[e.second].n;
+        for (auto &e : keyed)
+            if (pts[e.first] < kBatchSplit) e.first = e.first / 64 * 64;   // merged: dimension 0 marks it
     }
     std::stable_sort(keyed.begin(), keyed.end(),
                      [](const std::pair<long long, int> &a, const std::pair<long long, int> &b) { return a.first < b.first; });
@@ -1031,7 +1045,8 @@ int wm_batch(const wm_instance *inst, int32_t count, int32_t dtype, int32_t layo
                 continue;
             }
             if (!part.empty()) {
-                const int d = inst[part[0]].d;
+                int d = 0;
+                for (int i : part) d = std::max(d, (int)inst[i].d);
                 const int mp = inst[part[0]].min_pts <= 1 ? 1 : inst[part[0]].min_pts;
                 BatchCtx c{inst, &part, d, mp, dtype, layout};
                 wm_stats gs{};

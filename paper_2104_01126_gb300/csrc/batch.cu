@@ -1,7 +1,8 @@
 // batch.cu -- kernels of wm_batch: several independent instances solved as one point set.
 //
-// The instances of a group (same d, same minPts) are concatenated; coordinate d (an extra one)
-// holds j * L for instance j, with L a power of two larger than twice the diameter bound of every
+// The instances of a group (same minPts) are concatenated, with the coordinates an instance does
+// not have set to 0 (they add exactly 0 to every distance); coordinate d (an extra one) holds
+// j * L for instance j, with L a power of two larger than twice the diameter bound of every
 // instance.  Two points of one instance differ by exactly 0 in that coordinate, so every FP32
 // screen value and every FP64 key of a pair inside an instance is bit for bit the instance's own;
 // two points of different instances are at least L apart, and the rounds cap rho_hi below L^2,
@@ -27,18 +28,23 @@ __device__ inline int inst_of(const long long *__restrict__ off, int k, long lon
     return lo;
 }
 
-__global__ void gather_kernel(const void *const *__restrict__ src, const long long *__restrict__ base, int k,
-                              long long total, int d, int dtype, int layout, double *__restrict__ raw,
-                              unsigned *__restrict__ maxabs)
+// instance j has dims[j] <= d coordinates; the others are 0 (they add exactly 0 to every distance)
+__global__ void gather_kernel(const void *const *__restrict__ src, const int *__restrict__ dims,
+                              const long long *__restrict__ base, int k, long long total, int d, int dtype, int layout,
+                              double *__restrict__ raw, unsigned *__restrict__ maxabs)
 {
     float mx = 0.f;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         const int j = inst_of(base, k, t);
         const long long i = t - base[j], nj = base[j + 1] - base[j];
+        const int dj = dims[j];
         for (int c = 0; c < d; ++c) {
-            const size_t s = layout == WM_SOA ? (size_t)c * nj + i : (size_t)i * d + c;
-            const double v = dtype == WM_F32 ? (double)((const float *)src[j])[s] : ((const double *)src[j])[s];
+            double v = 0.0;
+            if (c < dj) {
+                const size_t s = layout == WM_SOA ? (size_t)c * nj + i : (size_t)i * dj + c;
+                v = dtype == WM_F32 ? (double)((const float *)src[j])[s] : ((const double *)src[j])[s];
+            }
             raw[(size_t)c * total + t] = v;
             const float a = (float)fabs(v);
             if (a > mx) mx = a;   // NaN never raises it; ingest rejects non-finite input
@@ -177,10 +183,10 @@ __global__ void scatter_out_kernel(const T *__restrict__ stage, long long cnt, c
 
 }  // namespace
 
-void batch_gather(const void *const *src, const long long *base, int k, long long total, int d, int dtype, int layout,
-                  double *raw, unsigned *maxabs, cudaStream_t st)
+void batch_gather(const void *const *src, const int *dims, const long long *base, int k, long long total, int d,
+                  int dtype, int layout, double *raw, unsigned *maxabs, cudaStream_t st)
 {
-    launch(gather_kernel, grid_for(total, 256), 256, 0, st, src, base, k, total, d, dtype, layout, raw, maxabs);
+    launch(gather_kernel, grid_for(total, 256), 256, 0, st, src, dims, base, k, total, d, dtype, layout, raw, maxabs);
 }
 
 void batch_scale(double *x, long long total, double L, cudaStream_t st)

@@ -7,10 +7,11 @@
 
 namespace wm {
 
-// raw[c * total + t] (SoA, d + 1 coordinates) from the instances' inputs src[j] (device), base[j]
-// = first combined index of instance j (base[k] = total); coordinate d = j; *maxabs = max |x| bits
-void batch_gather(const void *const *src, const long long *base, int k, long long total, int d, int dtype, int layout,
-                  double *raw, unsigned *maxabs, cudaStream_t st);
+// raw[c * total + t] (SoA, d + 1 coordinates) from the instances' inputs src[j] (device, dims[j]
+// <= d coordinates each, the rest 0), base[j] = first combined index of instance j (base[k] =
+// total); coordinate d = j; *maxabs = max |x| bits
+void batch_gather(const void *const *src, const int *dims, const long long *base, int k, long long total, int d,
+                  int dtype, int layout, double *raw, unsigned *maxabs, cudaStream_t st);
 void batch_scale(double *x, long long total, double L, cudaStream_t st);
 void batch_edge_inst(const EdgeK *E, int m, const long long *base, int k, EdgeK *keys, cudaStream_t st);
 void batch_edge_place(const EdgeK *keys, const EdgeK *E, int m, const long long *base, int *local, wm_edge *stage,
