@@ -48,13 +48,22 @@ static void set_detail(const char *fmt, long long b, const char *a)
 void set_error_detail(const char *msg) { g_detail = msg; }
 
 // pinned host scratch for scalar readbacks (one per thread)
+// 64 KiB of pinned host memory per thread, freed when the thread ends
+struct PinnedScratch {
+    int *p = nullptr;
+    ~PinnedScratch()
+    {
+        if (p) cudaFreeHost(p);
+    }
+};
+
 static int *pinned_scratch()
 {
-    static thread_local int *p = nullptr;
-    if (!p) {
-        if (cudaMallocHost((void **)&p, 1 << 16) != cudaSuccess) p = nullptr;
+    static thread_local PinnedScratch s;
+    if (!s.p) {
+        if (cudaMallocHost((void **)&s.p, 1 << 16) != cudaSuccess) s.p = nullptr;
     }
-    return p;
+    return s.p;
 }
 
 // ------------------------------------------------------------------ library-managed cache
@@ -64,6 +73,34 @@ struct DevCache {
     size_t cap = 0;
 };
 static DevCache g_cache[64];
+
+// Stream-ordered pool of the workspaces of concurrent batch groups, one per device; it keeps what
+// it has allocated between calls (wm_release_cache returns it to the system).
+struct BatchPool {
+    std::mutex mu;
+    cudaMemPool_t pool = nullptr;
+};
+static BatchPool g_batch_pool[64];
+
+static cudaMemPool_t batch_pool(int dev)
+{
+    BatchPool &bp = g_batch_pool[dev & 63];
+    std::lock_guard<std::mutex> lk(bp.mu);
+    if (!bp.pool) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        if (cudaMemPoolCreate(&bp.pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            bp.pool = nullptr;
+            return nullptr;
+        }
+        unsigned long long keep = ~0ull;
+        cudaMemPoolSetAttribute(bp.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    return bp.pool;
+}
 
 struct Caps {
     long long chunk;        // pairs popped per traversal step (= capacity of each pair list)
@@ -1024,56 +1061,133 @@ int wm_batch(const wm_instance *inst, int32_t count, int32_t dtype, int32_t layo
     }
     std::stable_sort(keyed.begin(), keyed.end(),
                      [](const std::pair<long long, int> &a, const std::pair<long long, int> &b) { return a.first < b.first; });
-    wm_stats sum{};
-    int rc = WM_OK;
-    for (size_t a = 0; a < keyed.size() && rc == WM_OK;) {
+    // the groups (a run of one key, cut where it would exceed 2^30 points)
+    std::vector<std::vector<int>> groups;
+    for (size_t a = 0; a < keyed.size();) {
         size_t b = a;
-        std::vector<int> idx;
-        long long total = 0;
+        long long ptotal = 0;
+        std::vector<int> part;
         while (b < keyed.size() && keyed[b].first == keyed[a].first) {
-            idx.push_back(keyed[b].second);
-            total += inst[keyed[b].second].n;
+            const int i = keyed[b].second;
+            if (!part.empty() && ptotal + inst[i].n > 0x3fffffff) {
+                groups.push_back(part);
+                part.clear();
+                ptotal = 0;
+            }
+            part.push_back(i);
+            ptotal += inst[i].n;
             ++b;
         }
-        // one group: at most 2^30 points (split longer runs)
-        std::vector<int> part;
-        long long ptotal = 0;
-        for (size_t t = 0; t <= idx.size() && rc == WM_OK; ++t) {
-            if (t < idx.size() && ptotal + inst[idx[t]].n <= 0x3fffffff) {
-                part.push_back(idx[t]);
-                ptotal += inst[idx[t]].n;
-                continue;
-            }
-            if (!part.empty()) {
-                int d = 0;
-                for (int i : part) d = std::max(d, (int)inst[i].d);
-                const int mp = inst[part[0]].min_pts <= 1 ? 1 : inst[part[0]].min_pts;
-                BatchCtx c{inst, &part, d, mp, dtype, layout};
-                wm_stats gs{};
-                wm_opts o = opts ? *opts : wm_opts{};
-                o.stats = &gs;
-                const long long extra = ptotal * (8LL * (d + 1) + 200) + (long long)part.size() * 64;
-                rc = run_call(&o, ptotal, d + 1, mp > 1 ? mp : 0, batch_body, &c, extra);
-                sum.ms_total += gs.ms_total; sum.ms_ingest += gs.ms_ingest; sum.ms_build_tree += gs.ms_build_tree;
-                sum.ms_core_dist += gs.ms_core_dist; sum.ms_wspd += gs.ms_wspd; sum.ms_bccp += gs.ms_bccp;
-                sum.ms_kruskal += gs.ms_kruskal; sum.ms_dendrogram += gs.ms_dendrogram; sum.rounds += gs.rounds;
-                sum.pairs_retrieved += gs.pairs_retrieved; sum.bccp_evals += gs.bccp_evals;
-                sum.bccp_tile_evals += gs.bccp_tile_evals; sum.knn_evals += gs.knn_evals;
-                sum.fp64_rechecks += gs.fp64_rechecks; sum.candidate_edges += gs.candidate_edges;
-                sum.tree_nodes += gs.tree_nodes; sum.tree_depth = std::max(sum.tree_depth, gs.tree_depth);
-                sum.workspace_bytes_used = std::max(sum.workspace_bytes_used, gs.workspace_bytes_used);
-                sum.getpairs_visits += gs.getpairs_visits; sum.getrho_visits += gs.getrho_visits;
-                sum.getpairs_launches += gs.getpairs_launches; sum.bccp_dual_evals += gs.bccp_dual_evals;
-                sum.rho_shrinks += gs.rho_shrinks; sum.tile_launches += gs.tile_launches;
-                sum.ms_knn_kernel += gs.ms_knn_kernel; sum.ms_tile_kernel += gs.ms_tile_kernel;
-                sum.ms_getpairs += gs.ms_getpairs;
-                sum.max_pending_pairs = std::max(sum.max_pending_pairs, gs.max_pending_pairs);
-            }
-            part.clear();
-            ptotal = 0;
-            if (t < idx.size()) { part.push_back(idx[t]); ptotal = inst[idx[t]].n; }
-        }
+        if (!part.empty()) groups.push_back(part);
         a = b;
+    }
+    struct GroupRun {
+        int rc = WM_OK;
+        wm_stats st{};
+        std::string detail;
+    };
+    std::vector<GroupRun> res(groups.size());
+    auto group_args = [&](size_t g, long long &ptotal, int &d, int &mp) {
+        ptotal = 0;
+        d = 0;
+        for (int i : groups[g]) { ptotal += inst[i].n; d = std::max(d, (int)inst[i].d); }
+        mp = inst[groups[g][0]].min_pts <= 1 ? 1 : inst[groups[g][0]].min_pts;
+    };
+    const bool caller_ws = opts && opts->workspace;
+    const int kBatchThreads = 4;
+    if (groups.size() == 1 || caller_ws) {
+        for (size_t g = 0; g < groups.size(); ++g) {
+            long long ptotal;
+            int d, mp;
+            group_args(g, ptotal, d, mp);
+            BatchCtx c{inst, &groups[g], d, mp, dtype, layout};
+            wm_opts o = opts ? *opts : wm_opts{};
+            o.stats = &res[g].st;
+            const long long extra = ptotal * (8LL * (d + 1) + 200) + (long long)groups[g].size() * 64;
+            res[g].rc = run_call(&o, ptotal, d + 1, mp > 1 ? mp : 0, batch_body, &c, extra);
+            res[g].detail = g_detail;
+            if (res[g].rc) break;
+        }
+    } else {
+        // groups run concurrently, each on a stream of its own with a workspace from the device's
+        // stream-ordered pool; the streams wait for the caller's stream first
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return WM_ECUDA;
+        cudaStream_t caller = opts ? (cudaStream_t)opts->stream : nullptr;
+        cudaEvent_t ready;
+        if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess) return WM_ECUDA;
+        cudaEventRecord(ready, caller);
+        cudaMemPool_t pool = batch_pool(dev);
+        std::atomic<size_t> next{0};
+        std::atomic<bool> failed{false};
+        auto worker = [&]() {
+            cudaSetDevice(dev);
+            cudaStream_t st = nullptr;
+            if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) { failed = true; return; }
+            cudaStreamWaitEvent(st, ready, 0);
+            for (size_t g; !failed && (g = next.fetch_add(1)) < groups.size();) {
+                long long ptotal;
+                int d, mp;
+                group_args(g, ptotal, d, mp);
+                BatchCtx c{inst, &groups[g], d, mp, dtype, layout};
+                const long long extra = ptotal * (8LL * (d + 1) + 200) + (long long)groups[g].size() * 64;
+                Caps cp = default_caps(ptotal, mp > 1 ? mp : 0);
+                cp.extra_bytes = extra;
+                size_t bytes = estimate_bytes(ptotal, d + 1, mp > 1 ? mp : 0, cp);
+                int rc = WM_ENOMEM;
+                for (int attempt = 0; attempt < 4; ++attempt) {
+                    void *ws = nullptr;
+                    if (!pool || cudaMallocFromPoolAsync(&ws, bytes, pool, st) != cudaSuccess) {
+                        cudaGetLastError();
+                        set_detail("workspace of %s%lld bytes could not be allocated", "", (long long)bytes);
+                        rc = WM_ENOMEM;
+                        break;
+                    }
+                    wm_opts o = opts ? *opts : wm_opts{};
+                    o.stream = st;
+                    o.workspace = ws;
+                    o.workspace_bytes = bytes;
+                    o.stats = &res[g].st;
+                    rc = run_call(&o, ptotal, d + 1, mp > 1 ? mp : 0, batch_body, &c, extra);
+                    cudaFreeAsync(ws, st);
+                    cudaStreamSynchronize(st);
+                    if (rc != WM_ENOMEM) break;
+                    bytes *= 2;   // the data needed more than the estimate
+                }
+                res[g].rc = rc;
+                res[g].detail = g_detail;
+                if (rc) failed = true;
+            }
+            cudaStreamDestroy(st);
+        };
+        std::vector<std::thread> threads;
+        const int nt = (int)std::min<size_t>(kBatchThreads, groups.size());
+        for (int t = 0; t < nt; ++t) threads.emplace_back(worker);
+        for (auto &t : threads) t.join();
+        cudaEventDestroy(ready);
+    }
+    wm_stats sum{};
+    int rc = WM_OK;
+    for (size_t g = 0; g < groups.size(); ++g) {
+        const wm_stats &gs = res[g].st;
+        if (rc == WM_OK && res[g].rc != WM_OK) {
+            rc = res[g].rc;
+            g_detail = res[g].detail;
+        }
+        sum.ms_total += gs.ms_total; sum.ms_ingest += gs.ms_ingest; sum.ms_build_tree += gs.ms_build_tree;
+        sum.ms_core_dist += gs.ms_core_dist; sum.ms_wspd += gs.ms_wspd; sum.ms_bccp += gs.ms_bccp;
+        sum.ms_kruskal += gs.ms_kruskal; sum.ms_dendrogram += gs.ms_dendrogram; sum.rounds += gs.rounds;
+        sum.pairs_retrieved += gs.pairs_retrieved; sum.bccp_evals += gs.bccp_evals;
+        sum.bccp_tile_evals += gs.bccp_tile_evals; sum.knn_evals += gs.knn_evals;
+        sum.fp64_rechecks += gs.fp64_rechecks; sum.candidate_edges += gs.candidate_edges;
+        sum.tree_nodes += gs.tree_nodes; sum.tree_depth = std::max(sum.tree_depth, gs.tree_depth);
+        sum.workspace_bytes_used = std::max(sum.workspace_bytes_used, gs.workspace_bytes_used);
+        sum.getpairs_visits += gs.getpairs_visits; sum.getrho_visits += gs.getrho_visits;
+        sum.getpairs_launches += gs.getpairs_launches; sum.bccp_dual_evals += gs.bccp_dual_evals;
+        sum.rho_shrinks += gs.rho_shrinks; sum.tile_launches += gs.tile_launches;
+        sum.ms_knn_kernel += gs.ms_knn_kernel; sum.ms_tile_kernel += gs.ms_tile_kernel;
+        sum.ms_getpairs += gs.ms_getpairs;
+        sum.max_pending_pairs = std::max(sum.max_pending_pairs, gs.max_pending_pairs);
     }
     if (opts && opts->stats) *opts->stats = sum;
     return rc;
@@ -1098,6 +1212,12 @@ int wm_release_cache(void)
     }
     dc.ptr = nullptr;
     dc.cap = 0;
+    BatchPool &bp = g_batch_pool[dev & 63];
+    std::lock_guard<std::mutex> lk2(bp.mu);
+    if (bp.pool) {
+        cudaDeviceSynchronize();
+        cudaMemPoolTrimTo(bp.pool, 0);
+    }
     return WM_OK;
 }
 
