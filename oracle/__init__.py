@@ -69,6 +69,10 @@ def _load():
             lib.wmo_inorder_leaves.argtypes = [i64, P, P, P]
             lib.wmo_reachability.restype = ctypes.c_int
             lib.wmo_reachability.argtypes = [i64, P, P, P, i32, P, P]
+            lib.wmo_core_dist2_kdtree.restype = ctypes.c_int
+            lib.wmo_core_dist2_kdtree.argtypes = [P, i64, i32, i32, P]
+            lib.wmo_boruvka.restype = ctypes.c_int
+            lib.wmo_boruvka.argtypes = [P, i64, i32, P, P, P, P]
             _lib = lib
     return _lib
 
@@ -202,6 +206,54 @@ def reachability(n: int, u, v, w2, s: int = 0):
     _check(_load().wmo_reachability(n, _p(u), _p(v), _p(w2), int(s), _p(order), _p(reach)),
            "reachability")
     return order, reach
+
+
+def core_dist2_kdtree(x, min_pts: int) -> np.ndarray:
+    """core_dist2 computed by an exact k-d tree search (for sizes brute force cannot reach)."""
+    x = _pts(x)
+    n, d = x.shape
+    out = np.empty(n, dtype=np.float64)
+    _check(_load().wmo_core_dist2_kdtree(_p(x), n, d, int(min_pts), _p(out)), "core_dist2_kdtree")
+    return out
+
+
+def boruvka(x, cd2=None):
+    """The K-minimum spanning tree (EMST, or G_MR when cd2 is given) by Boruvka's algorithm over an
+    exact k-d tree: the tree prim_complete + sort_edges gives, for sizes brute force cannot reach.
+    Returns (u, v, w2) in K order, u < v."""
+    x = _pts(x)
+    n, d = x.shape
+    m = max(n - 1, 0)
+    u = np.empty(max(m, 1), dtype=np.int32)
+    v = np.empty(max(m, 1), dtype=np.int32)
+    w2 = np.empty(max(m, 1), dtype=np.float64)
+    cdp = None
+    if cd2 is not None:
+        cd2 = np.ascontiguousarray(cd2, dtype=np.float64)
+        cdp = _p(cd2)
+    _check(_load().wmo_boruvka(_p(x), n, d, cdp, _p(u), _p(v), _p(w2)), "boruvka")
+    return u[:m], v[:m], w2[:m]
+
+
+def emst_at_scale(x):
+    """emst() by the k-d tree Boruvka solver (same result, any size the host can hold)."""
+    x = _pts(x)
+    u, v, w2 = boruvka(x)
+    return {"u": u, "v": v, "w2": w2, "w": np.sqrt(w2), "total": total_weight(w2)}
+
+
+def hdbscan_at_scale(x, min_pts: int, s: int = 0):
+    """hdbscan() with the k-d tree core distances and Boruvka MST (same results, any size)."""
+    x = _pts(x)
+    n = x.shape[0]
+    cd2 = core_dist2_kdtree(x, min_pts)
+    u, v, w2 = boruvka(x, cd2)
+    out = {"cd2": cd2, "cd": np.sqrt(cd2), "u": u, "v": v, "w2": w2, "w": np.sqrt(w2), "total": total_weight(w2)}
+    if n >= 2:
+        left, right, height, size = dendrogram(n, u, v, w2, s)
+        order, reach = reachability(n, u, v, w2, s)
+        out.update(left=left, right=right, height=height, size=size, order=order, reach=reach)
+    return out
 
 
 # ------------------------------------------------------------------ composed problem calls

@@ -29,6 +29,10 @@
  *   - Reported weights are sqrt(w2) (IEEE correctly rounded).
  *
  * Points are row-major: x[i*d + k] is coordinate k of point i.
+ *
+ * The definitions are evaluated by brute force (wmo_core_dist2, wmo_prim).  For sizes brute
+ * force cannot reach, wmo_core_dist2_kdtree and wmo_boruvka compute the same values by exact
+ * searches over a k-d tree (end of this file); tests/test_oracle.py pins them to the brute force.
  */
 #include <math.h>
 #include <stdint.h>
@@ -478,4 +482,313 @@ int wmo_reachability(int64_t n, const int32_t *eu, const int32_t *ev, const doub
     }
     free(vis); free(h); free_adj(&g);
     return k == n ? 0 : -3;
+}
+
+/* ==================================================================================
+ * Exact solvers for sizes where the O(n^2) definitions above are too slow.  They compute the
+ * same things (the K-minimum spanning tree of the complete graph, the core distances) by other
+ * algorithms over a k-d tree in FP64, pruning only with bounds that can never exceed the value
+ * they bound, and are pinned against the brute-force functions above in tests/test_oracle.py.
+ * ================================================================================== */
+
+typedef struct {
+    int32_t lo, hi;       /* points perm[lo..hi) */
+    int32_t left, right;  /* children, -1 for a leaf (leaves hold at most 8 points) */
+} kdnode_t;
+
+typedef struct {
+    int64_t n;
+    int32_t d, nn;
+    const double *x;
+    int32_t *perm;
+    kdnode_t *node;
+    double *blo, *bhi;    /* bounding box of node t: blo[t*d + k], bhi[t*d + k] */
+} kdtree_t;
+
+/* the points of perm[lo..hi) with coordinate k of rank < mid first (quickselect) */
+static void kd_select(const double *x, int32_t d, int32_t *perm, int32_t lo, int32_t hi, int32_t mid, int32_t k)
+{
+    while (hi - lo > 1) {
+        double piv = x[(int64_t)perm[lo + (hi - lo) / 2] * d + k];
+        int32_t i = lo, j = hi - 1;
+        while (i <= j) {
+            while (x[(int64_t)perm[i] * d + k] < piv) ++i;
+            while (x[(int64_t)perm[j] * d + k] > piv) --j;
+            if (i <= j) {
+                int32_t t = perm[i]; perm[i] = perm[j]; perm[j] = t;
+                ++i; --j;
+            }
+        }
+        if (mid <= j) hi = j + 1;
+        else if (mid >= i) lo = i;
+        else return;
+    }
+}
+
+static int32_t kd_build_rec(kdtree_t *t, int32_t lo, int32_t hi)
+{
+    const int32_t d = t->d, me = t->nn++;
+    double *blo = t->blo + (int64_t)me * d, *bhi = t->bhi + (int64_t)me * d;
+    for (int32_t k = 0; k < d; ++k) { blo[k] = INFINITY; bhi[k] = -INFINITY; }
+    for (int32_t i = lo; i < hi; ++i) {
+        const double *p = t->x + (int64_t)t->perm[i] * d;
+        for (int32_t k = 0; k < d; ++k) {
+            if (p[k] < blo[k]) blo[k] = p[k];
+            if (p[k] > bhi[k]) bhi[k] = p[k];
+        }
+    }
+    t->node[me].lo = lo; t->node[me].hi = hi; t->node[me].left = -1; t->node[me].right = -1;
+    if (hi - lo <= 8) return me;
+    int32_t kw = 0;
+    for (int32_t k = 1; k < d; ++k)
+        if (bhi[k] - blo[k] > bhi[kw] - blo[kw]) kw = k;
+    const int32_t mid = lo + (hi - lo) / 2;
+    kd_select(t->x, d, t->perm, lo, hi, mid, kw);
+    const int32_t l = kd_build_rec(t, lo, mid);
+    const int32_t r = kd_build_rec(t, mid, hi);
+    t->node[me].left = l; t->node[me].right = r;
+    return me;
+}
+
+static int kd_build(kdtree_t *t, const double *x, int64_t n, int32_t d)
+{
+    t->n = n; t->d = d; t->x = x; t->nn = 0;
+    const int64_t cap = 2 * (n / 4 + 2) + 8;   /* leaves hold >= 4 points except small inputs */
+    t->perm = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    t->node = (kdnode_t *)malloc(sizeof(kdnode_t) * (size_t)(cap + 2 * n / 4 + 8));
+    t->blo = (double *)malloc(sizeof(double) * (size_t)d * (size_t)(cap + 2 * n / 4 + 8));
+    t->bhi = (double *)malloc(sizeof(double) * (size_t)d * (size_t)(cap + 2 * n / 4 + 8));
+    if (!t->perm || !t->node || !t->blo || !t->bhi) return -2;
+    for (int64_t i = 0; i < n; ++i) t->perm[i] = (int32_t)i;
+    if (n > 0) kd_build_rec(t, 0, (int32_t)n);
+    return 0;
+}
+
+static void kd_free(kdtree_t *t) { free(t->perm); free(t->node); free(t->blo); free(t->bhi); }
+
+/* Lower bound of D(p, q) over every q in the box of node t.  Each gap is rounded from an exact
+ * difference at least as large as the box's (rounding is monotone), squared and summed in the
+ * order of wmo_sqdist, so the bound never exceeds the FP64 distance of any point inside. */
+static double kd_box_lb(const kdtree_t *t, int32_t nd, const double *p)
+{
+    const double *lo = t->blo + (int64_t)nd * t->d, *hi = t->bhi + (int64_t)nd * t->d;
+    double s = 0.0;
+    for (int32_t k = 0; k < t->d; ++k) {
+        double g = 0.0;
+        if (p[k] < lo[k]) g = lo[k] - p[k];
+        else if (p[k] > hi[k]) g = p[k] - hi[k];
+        double g2 = g * g;
+        s = s + g2;
+    }
+    return s;
+}
+
+/*
+ * cd2[p] = the minpts-th smallest D(p,q), q = p included: the value wmo_core_dist2 computes, found
+ * by a nearest-first search that skips a box only when its lower bound is not below the current
+ * minpts-th smallest value.  Returns 0, -1 on bad arguments, -2 on allocation failure.
+ */
+int wmo_core_dist2_kdtree(const double *x, int64_t n, int32_t d, int32_t minpts, double *cd2)
+{
+    if (minpts < 1 || (int64_t)minpts > n || n > 0x7fffffff) return -1;
+    kdtree_t t;
+    if (kd_build(&t, x, n, d)) { kd_free(&t); return -2; }
+    int err = 0;
+#pragma omp parallel
+    {
+        double *heap = (double *)malloc(sizeof(double) * (size_t)minpts);   /* max-heap of the best */
+        int32_t *stk = (int32_t *)malloc(sizeof(int32_t) * 256);
+        if (!heap || !stk) {
+#pragma omp atomic write
+            err = -2;
+        }
+#pragma omp for schedule(dynamic, 256)
+        for (int64_t p = 0; p < n; ++p) {
+            if (!heap || !stk) continue;
+            const double *xp = x + p * d;
+            int32_t hn = 0, sp = 0;
+            stk[sp++] = 0;
+            while (sp > 0) {
+                const int32_t nd = stk[--sp];
+                if (hn == minpts && kd_box_lb(&t, nd, xp) >= heap[0]) continue;
+                const kdnode_t *N = &t.node[nd];
+                if (N->left < 0) {
+                    for (int32_t i = N->lo; i < N->hi; ++i) {
+                        const double w = wmo_sqdist(x, d, p, t.perm[i]);
+                        if (hn < minpts) {              /* sift up */
+                            int32_t c = hn++;
+                            while (c > 0 && heap[(c - 1) / 2] < w) { heap[c] = heap[(c - 1) / 2]; c = (c - 1) / 2; }
+                            heap[c] = w;
+                        } else if (w < heap[0]) {       /* replace the maximum, sift down */
+                            int32_t c = 0;
+                            for (;;) {
+                                int32_t l = 2 * c + 1, r = l + 1, m = c;
+                                double vm = w;
+                                if (l < hn && heap[l] > vm) { m = l; vm = heap[l]; }
+                                if (r < hn && heap[r] > vm) { m = r; vm = heap[r]; }
+                                if (m == c) break;
+                                heap[c] = heap[m];
+                                c = m;
+                            }
+                            heap[c] = w;
+                        }
+                    }
+                } else if (sp + 2 <= 256) {
+                    const double l0 = kd_box_lb(&t, N->left, xp), l1 = kd_box_lb(&t, N->right, xp);
+                    stk[sp++] = l0 <= l1 ? N->right : N->left;   /* nearer child on top */
+                    stk[sp++] = l0 <= l1 ? N->left : N->right;
+                }
+            }
+            cd2[p] = heap[0];
+        }
+        free(heap);
+        free(stk);
+    }
+    kd_free(&t);
+    return err;
+}
+
+/*
+ * The K-minimum spanning tree of the complete graph (EMST, or G_MR when cd2 != NULL) by Boruvka's
+ * algorithm: every round, each point finds its K-minimum edge to a point of another component
+ * (a search over the tree that skips boxes whose points all lie in its component and boxes whose
+ * lower bound exceeds the best w2 so far), each component keeps the K-minimum of its points', and
+ * those edges are added (K is a strict total order, so they form a forest; each is the K-minimum
+ * edge across its component's cut, so it is in the tree).  Output in K order, eu < ev.
+ * Returns 0, -1 on bad arguments, -2 on allocation failure.
+ */
+static int32_t bv_find(int32_t *par, int32_t x)
+{
+    while (par[x] != x) { par[x] = par[par[x]]; x = par[x]; }
+    return x;
+}
+
+int wmo_boruvka(const double *x, int64_t n, int32_t d, const double *cd2, int32_t *eu, int32_t *ev, double *ew2)
+{
+    if (n < 1 || n > 0x7fffffff) return -1;
+    if (n == 1) return 0;
+    kdtree_t t;
+    if (kd_build(&t, x, n, d)) { kd_free(&t); return -2; }
+    int32_t *par = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *comp = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *ncomp = (int32_t *)malloc(sizeof(int32_t) * (size_t)t.nn);
+    double *ncd = (double *)malloc(sizeof(double) * (size_t)t.nn);
+    double *bw = (double *)malloc(sizeof(double) * (size_t)n);     /* per point: best edge */
+    int32_t *bq = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    double *cw = (double *)malloc(sizeof(double) * (size_t)n);     /* per component root */
+    int32_t *ca = (int32_t *)malloc(sizeof(int32_t) * (size_t)n), *cb = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    if (!par || !comp || !ncomp || !ncd || !bw || !bq || !cw || !ca || !cb) {
+        free(par); free(comp); free(ncomp); free(ncd); free(bw); free(bq); free(cw); free(ca); free(cb);
+        kd_free(&t);
+        return -2;
+    }
+    for (int64_t i = 0; i < n; ++i) par[i] = (int32_t)i;
+    /* node minimum core distance (children have larger ids than their parent) */
+    for (int32_t nd = t.nn - 1; nd >= 0; --nd) {
+        const kdnode_t *N = &t.node[nd];
+        if (!cd2) { ncd[nd] = 0.0; continue; }
+        if (N->left < 0) {
+            double m = INFINITY;
+            for (int32_t i = N->lo; i < N->hi; ++i) if (cd2[t.perm[i]] < m) m = cd2[t.perm[i]];
+            ncd[nd] = m;
+        } else {
+            ncd[nd] = ncd[N->left] < ncd[N->right] ? ncd[N->left] : ncd[N->right];
+        }
+    }
+    int64_t m = 0;
+    int err = 0;
+    while (m < n - 1 && !err) {
+        for (int64_t i = 0; i < n; ++i) comp[i] = bv_find(par, (int32_t)i);
+        for (int32_t nd = t.nn - 1; nd >= 0; --nd) {
+            const kdnode_t *N = &t.node[nd];
+            if (N->left < 0) {
+                int32_t c = comp[t.perm[N->lo]];
+                for (int32_t i = N->lo + 1; i < N->hi && c >= 0; ++i) if (comp[t.perm[i]] != c) c = -1;
+                ncomp[nd] = c;
+            } else {
+                ncomp[nd] = (ncomp[N->left] >= 0 && ncomp[N->left] == ncomp[N->right]) ? ncomp[N->left] : -1;
+            }
+        }
+#pragma omp parallel
+        {
+            int32_t *stk = (int32_t *)malloc(sizeof(int32_t) * 256);
+            if (!stk) {
+#pragma omp atomic write
+                err = -2;
+            }
+#pragma omp for schedule(dynamic, 256)
+            for (int64_t p = 0; p < n; ++p) {
+                double best = INFINITY;
+                int32_t bestq = -1;
+                if (!stk) { bw[p] = best; bq[p] = bestq; continue; }
+                const double *xp = x + p * d;
+                const int32_t cp = comp[p];
+                const double cdp = cd2 ? cd2[p] : 0.0;
+                int32_t sp = 0;
+                stk[sp++] = 0;
+                while (sp > 0) {
+                    const int32_t nd = stk[--sp];
+                    if (ncomp[nd] == cp) continue;
+                    double lb = kd_box_lb(&t, nd, xp);
+                    if (cd2) {
+                        if (cdp > lb) lb = cdp;
+                        if (ncd[nd] > lb) lb = ncd[nd];
+                    }
+                    if (lb > best) continue;
+                    const kdnode_t *N = &t.node[nd];
+                    if (N->left < 0) {
+                        for (int32_t i = N->lo; i < N->hi; ++i) {
+                            const int32_t q = t.perm[i];
+                            if (comp[q] == cp) continue;
+                            double w = wmo_sqdist(x, d, p, q);
+                            if (cd2) {
+                                if (cdp > w) w = cdp;
+                                if (cd2[q] > w) w = cd2[q];
+                            }
+                            const int32_t a = (int32_t)p < q ? (int32_t)p : q, b = (int32_t)p < q ? q : (int32_t)p;
+                            if (bestq < 0 ||
+                                key_less(w, a, b, best, (int32_t)p < bestq ? (int32_t)p : bestq,
+                                         (int32_t)p < bestq ? bestq : (int32_t)p)) {
+                                best = w;
+                                bestq = q;
+                            }
+                        }
+                    } else if (sp + 2 <= 256) {
+                        const double l0 = kd_box_lb(&t, N->left, xp), l1 = kd_box_lb(&t, N->right, xp);
+                        stk[sp++] = l0 <= l1 ? N->right : N->left;
+                        stk[sp++] = l0 <= l1 ? N->left : N->right;
+                    } else {
+#pragma omp atomic write
+                        err = -3;   /* deeper than a balanced tree can be */
+                    }
+                }
+                bw[p] = best;
+                bq[p] = bestq;
+            }
+            free(stk);
+        }
+        if (err) break;
+        for (int64_t i = 0; i < n; ++i) { cw[i] = INFINITY; ca[i] = -1; cb[i] = -1; }
+        for (int64_t p = 0; p < n; ++p) {
+            if (bq[p] < 0) continue;
+            const int32_t c = comp[p];
+            const int32_t a = (int32_t)p < bq[p] ? (int32_t)p : bq[p], b = (int32_t)p < bq[p] ? bq[p] : (int32_t)p;
+            if (ca[c] < 0 || key_less(bw[p], a, b, cw[c], ca[c], cb[c])) { cw[c] = bw[p]; ca[c] = a; cb[c] = b; }
+        }
+        int64_t added = 0;
+        for (int64_t c = 0; c < n; ++c) {
+            if (ca[c] < 0) continue;
+            const int32_t ra = bv_find(par, ca[c]), rb = bv_find(par, cb[c]);
+            if (ra == rb) continue;   /* the other component chose the same edge */
+            par[ra] = rb;
+            eu[m] = ca[c]; ev[m] = cb[c]; ew2[m] = cw[c];
+            ++m;
+            ++added;
+        }
+        if (added == 0) { err = -4; break; }
+    }
+    free(par); free(comp); free(ncomp); free(ncd); free(bw); free(bq); free(cw); free(ca); free(cb);
+    kd_free(&t);
+    if (err) return err;
+    return wmo_sort_edges(m, eu, ev, ew2);
 }

@@ -431,3 +431,54 @@ def test_core_dist_subset_and_nearest_edge_agree_with_full_oracle():
         assert (min(p, q), max(p, q)) in es            # cut property of the singleton {p}
         first = np.flatnonzero((iu == p) | (iv == p))[0]
         assert (iu[first], iv[first]) == (min(p, q), max(p, q)) and w2[first] == w
+
+
+# ---------------------------------------------------------------- the solvers used at scale
+# k-d tree Boruvka and k-d tree k-NN compute the same trees and core distances as the brute-force
+# definitions above by other algorithms; every case must agree exactly (edge list in K order and
+# bit-identical w2), including fully tied inputs (grids, duplicates) where only K decides.
+
+@pytest.mark.parametrize("kind,n,d,seed", [("uniform", 1200, 2, 0), ("gmm", 1500, 3, 1), ("varden", 1500, 5, 2),
+                                           ("uniform", 700, 7, 3), ("varden", 900, 3, 4)])
+def test_boruvka_equals_prim_emst(kind, n, d, seed):
+    x = synthdata.generate(kind, n, d, seed=seed)
+    e = oracle.emst(x)
+    u, v, w2 = oracle.boruvka(x)
+    assert np.array_equal(u, e["u"]) and np.array_equal(v, e["v"]) and np.array_equal(w2, e["w2"])
+
+
+@pytest.mark.parametrize("k,d", [(12, 2), (6, 3)])
+def test_boruvka_equals_prim_on_tied_grid(k, d):
+    x = synthdata.unit_grid(k, d, seed=k)
+    e = oracle.emst(x)
+    u, v, w2 = oracle.boruvka(x)
+    assert np.array_equal(u, e["u"]) and np.array_equal(v, e["v"]) and np.array_equal(w2, e["w2"])
+    assert math.isclose(oracle.total_weight(w2), k ** d - 1, rel_tol=1e-12)
+
+
+def test_boruvka_with_duplicate_points():
+    x = np.repeat(synthdata.uniform(200, 3, seed=5), 3, axis=0)
+    e = oracle.emst(x)
+    u, v, w2 = oracle.boruvka(x)
+    assert np.array_equal(u, e["u"]) and np.array_equal(v, e["v"]) and np.array_equal(w2, e["w2"])
+    assert np.count_nonzero(w2 == 0.0) == 400
+
+
+@pytest.mark.parametrize("kind,n,d,min_pts,seed", [("gmm", 1500, 3, 10, 0), ("uniform", 1000, 2, 5, 1),
+                                                   ("varden", 1200, 5, 4, 2), ("uniform", 600, 7, 20, 3)])
+def test_kdtree_core_distances_and_boruvka_gmr_equal_brute_force(kind, n, d, min_pts, seed):
+    x = synthdata.generate(kind, n, d, seed=seed)
+    cd2 = oracle.core_dist2(x, min_pts)
+    assert np.array_equal(oracle.core_dist2_kdtree(x, min_pts), cd2)
+    pu, pv, pw, _ = oracle.prim_complete(x, cd2)
+    pu, pv, pw = oracle.sort_edges(pu, pv, pw)
+    u, v, w2 = oracle.boruvka(x, cd2)
+    assert np.array_equal(u, pu) and np.array_equal(v, pv) and np.array_equal(w2, pw)
+
+
+def test_hdbscan_at_scale_equals_hdbscan():
+    x = synthdata.gaussian_mixture(1200, 3, seed=7)
+    a = oracle.hdbscan(x, 10, 5)
+    b = oracle.hdbscan_at_scale(x, 10, 5)
+    for key in ("cd2", "u", "v", "w2", "left", "right", "height", "size", "order", "reach"):
+        assert np.array_equal(a[key], b[key]), key
