@@ -260,21 +260,28 @@ def dist_setup():
     return ws, rank, local
 
 
+def oracle_step(w, xs):
+    """One run of the FP64 oracle's exact k-d tree solvers (the same results as its brute force,
+    pinned to it in tests/test_oracle.py) on the points xs."""
+    import oracle
+    if w["problem"] == "hdbscan":
+        oracle.hdbscan_at_scale(xs, w["min_pts"], s=0)
+    else:
+        oracle.emst_at_scale(xs)
+
+
 def run_reference(args, w, ws, rank):
-    """The FP64 CPU oracle timed on a bounded sample of the workload (rank 0 only)."""
+    """The FP64 CPU oracle timed on the workload (its first 10^6 points at most; rank 0 only)."""
     if rank != 0:
         return
     import oracle
     x = make_points(w)
-    ns = args.ref_sample
+    ns = min(w["n"], args.ref_sample) if args.ref_sample > 0 else min(w["n"], 1_000_000)
     xs = np.ascontiguousarray(x[:ns])
     oracle.build()
 
     def step():
-        if w["problem"] == "hdbscan":
-            oracle.hdbscan(xs, w["min_pts"], s=0)
-        else:
-            oracle.emst(xs)
+        oracle_step(w, xs)
     for _ in range(args.warmup if args.ref_warmup is None else args.ref_warmup):
         step()
     times = []
@@ -292,7 +299,8 @@ def run_reference(args, w, ws, rank):
                        "sample_points": ns},
             "cpu_baseline": {"value": v, "unit": "Mpoints/s", "cores": cores, "kind": "oracle",
                              "sample": f"first {ns} of the {w['n']} points (the generator shuffles rows), "
-                                       f"brute-force FP64 oracle, OpenMP on {cores} host threads"},
+                                       f"FP64 oracle (exact k-d tree k-NN and Boruvka, plus the dendrogram "
+                                       f"and plot for HDBSCAN*), OpenMP on {cores} host threads"},
             "e2e": {"value": v, "unit": "Mpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -301,17 +309,15 @@ def cpu_baseline(w, sample):
     import oracle
     oracle.build()
     x = make_points(w)
+    sample = min(w["n"], sample) if sample > 0 else min(w["n"], 1_000_000)
     xs = np.ascontiguousarray(x[:sample])
     t0 = time.perf_counter()
-    if w["problem"] == "hdbscan":
-        oracle.hdbscan(xs, w["min_pts"], s=0)
-    else:
-        oracle.emst(xs)
+    oracle_step(w, xs)
     t = time.perf_counter() - t0
     cores = os.cpu_count()
     return {"value": sample / t / 1e6, "unit": "Mpoints/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {sample} of the {w['n']} points, one brute-force FP64 oracle run "
-                      f"({t:.1f} s, OpenMP on {cores} host threads)"}
+            "sample": f"first {sample} of the {w['n']} points, one run of the FP64 oracle's exact k-d tree "
+                      f"solvers ({t:.1f} s, OpenMP on {cores} host threads)"}
 
 
 def main():
@@ -322,9 +328,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="hdbscan-gmm-1m-3d", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--cpu-sample", type=int, default=120_000)
-    ap.add_argument("--ref-sample", type=int, default=40_000)
-    ap.add_argument("--ref-warmup", type=int, default=1)
+    ap.add_argument("--cpu-sample", type=int, default=0, help="points for the CPU baseline (0: min(n, 1e6))")
+    ap.add_argument("--ref-sample", type=int, default=0, help="points for --impl reference (0: min(n, 1e6))")
+    ap.add_argument("--ref-warmup", type=int, default=None, help="warm-up runs of --impl reference (default: --warmup)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=64)
