@@ -257,8 +257,25 @@ template <int MODE, int DP>
 __global__ void __launch_bounds__(256) findpair_dfs_kernel(TravArgs a, DfsArgs s)
 {
     __shared__ int2 wst[kDfsWarpsPerBlock][kDfsWarpCap];
+    // GetPairs: retrieved pairs gathered per warp and size class, reserved in the global lists 32
+    // at a time
+    __shared__ int2 rbuf[MODE == 1 ? kDfsWarpsPerBlock : 1][5][32];
     const int lane = threadIdx.x & 31;
     int2 *ws = wst[threadIdx.x >> 5];
+    int2 (*rb)[32] = rbuf[MODE == 1 ? threadIdx.x >> 5 : 0];
+    int rcnt[5] = {0, 0, 0, 0, 0};   // warp-uniform fill of each class buffer
+    // moves class c's buffer to its global list
+    auto flush_class = [&](int c) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(a.list_count + c, rcnt[c]);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        for (int i = lane; i < rcnt[c]; i += 32) {
+            if (base + i < a.list_cap[c]) a.list[c][base + i] = rb[c][i];
+            else atomicOr(a.overflow, 4u);
+        }
+        rcnt[c] = 0;
+        __syncwarp();
+    };
     // counts are clamped to the capacities, so that no access leaves the buffers even after an
     // overflow (the host then discards the traversal)
     const int tp = min(*s.top, a.frontier_cap), xc = min(*s.xin_count, s.xcap);
@@ -340,27 +357,26 @@ __global__ void __launch_bounds__(256) findpair_dfs_kernel(TravArgs a, DfsArgs s
             }
         } else {
             if (__any_sync(0xffffffffu, cls >= 0)) {
-                // one ballot per class; lanes 0..4 reserve the five lists' slots concurrently
-                unsigned bal[5];
-#pragma unroll
-                for (int c = 0; c < 5; ++c) bal[c] = __ballot_sync(0xffffffffu, cls == c);
-                unsigned lb = 0, mine = 0;
 #pragma unroll
                 for (int c = 0; c < 5; ++c) {
-                    if (lane == c) lb = bal[c];
-                    if (cls == c) mine = bal[c];
+                    const unsigned bal = __ballot_sync(0xffffffffu, cls == c);
+                    const int nc = __popc(bal);
+                    if (nc == 0) continue;
+                    if (rcnt[c] + nc > 32) flush_class(c);
+                    if (cls == c) {
+                        ++n_ret;
+                        rb[c][rcnt[c] + __popc(bal & lanemask_lt())] = me;
+                    }
+                    rcnt[c] += nc;
                 }
-                int base = 0;
-                if (lane < 5 && lb) base = atomicAdd(a.list_count + lane, __popc(lb));
-                base = __shfl_sync(0xffffffffu, base, cls >= 0 ? cls : 0);
-                if (cls >= 0) {
-                    ++n_ret;
-                    const int bs = base + __popc(mine & lanemask_lt());
-                    if (bs < a.list_cap[cls]) a.list[cls][bs] = me;
-                    else atomicOr(a.overflow, 4u);
-                }
+                __syncwarp();
             }
         }
+    }
+    if (MODE == 1) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+            if (rcnt[c] > 0) flush_class(c);
     }
     // what is left on the warp stack goes to the step output (every popped pair was visited)
     if (!stop && sp > 0) {
