@@ -293,6 +293,12 @@ __global__ void __launch_bounds__(256) findpair_dfs_kernel(TravArgs a, DfsArgs s
     float rho_w = INFINITY;    // GetRho: smallest candidate this warp has written
     int sp = 0, it = 0;        // warp stack size (warp-uniform), rounds on the warp's own stack
     bool fed = stop;           // no more input for this warp
+    // every popped pair costs one visit in the breadth-first phase: a contiguous share per warp
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long share = (m + nw - 1) / nw;
+    long long in_next = gw * share;
+    const long long in_end = min((long long)m, in_next + share);
     while (!stop) {
         // one round: the next 32 popped pairs while there are any (every popped pair is visited
         // in this step, breadth first), then up to `budget` rounds of the warp's own stack
@@ -300,14 +306,13 @@ __global__ void __launch_bounds__(256) findpair_dfs_kernel(TravArgs a, DfsArgs s
         int k = 0;
         bool from_input = false;
         if (!fed) {
-            int base = 0;
-            if (lane == 0) base = atomicAdd(s.next, 32);
-            base = __shfl_sync(0xffffffffu, base, 0);
-            k = base < m ? min(32, m - base) : 0;
+            const long long base = in_next;
+            k = base < in_end ? (int)min(32LL, in_end - base) : 0;
             if (k == 0) fed = true;
             else {
                 from_input = true;
-                if (lane < k) me = input(base + lane);
+                in_next += 32;
+                if (lane < k) me = input((int)base + lane);
             }
         }
         if (!from_input) {
