@@ -101,8 +101,9 @@ __global__ void reserve_hi_kernel(const EdgeK *__restrict__ e, const int *__rest
             roots[j] = make_int2(-1, -1);
         } else {
             roots[j] = make_int2(ru, rv);
-            atomicMin(&Rhi[ru], x.hi);
-            atomicMin(&Rhi[rv], x.hi);
+            // a WriteMin that cannot lower the value is skipped (many edges share a big root)
+            if (x.hi < *(volatile unsigned long long *)&Rhi[ru]) atomicMin(&Rhi[ru], x.hi);
+            if (x.hi < *(volatile unsigned long long *)&Rhi[rv]) atomicMin(&Rhi[rv], x.hi);
         }
     }
 }
@@ -117,8 +118,8 @@ __global__ void reserve_lo_kernel(const EdgeK *__restrict__ e, const int *__rest
         const int2 r = roots[j];
         if (r.x < 0) continue;
         const EdgeK x = e[list[j]];
-        if (Rhi[r.x] == x.hi) atomicMin(&Rlo[r.x], x.lo);
-        if (Rhi[r.y] == x.hi) atomicMin(&Rlo[r.y], x.lo);
+        if (Rhi[r.x] == x.hi && x.lo < *(volatile unsigned long long *)&Rlo[r.x]) atomicMin(&Rlo[r.x], x.lo);
+        if (Rhi[r.y] == x.hi && x.lo < *(volatile unsigned long long *)&Rlo[r.y]) atomicMin(&Rlo[r.y], x.lo);
     }
 }
 

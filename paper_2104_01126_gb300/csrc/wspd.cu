@@ -815,14 +815,15 @@ __global__ void huge_emit_kernel(TravArgs a, int m)
     }
 }
 
-// BCCP of one medium or big pair per warp (pairs handed out through *next): the larger side A
+// BCCP of one medium or big pair per warp (pairs handed out in small chunks): the larger side A
 // on the lanes (kItems points each), the smaller side B staged in shared memory in chunks of
 // kTileQ.  FP32 screen against a running warp minimum, FP64 re-evaluation of every candidate
 // inside the band of the running minimum (the threshold only decreases, so every candidate of
 // the final band is re-evaluated), warp K-minimum, emitted when its FP64 w2 lies in
 // [rho_lo, rho_hi).
 template <int D, bool HDB, bool FP64>
-__global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const int2 *__restrict__ pairs, int m, int *next)
+__global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const int2 *__restrict__ pairs, int m, int *next,
+                                                             int chunk)
 {
     constexpr int DD = D > 0 ? D : kMaxDim;
     constexpr int kTileQ = tile_q(DD);
@@ -832,12 +833,19 @@ __global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const i
     const int d = D > 0 ? D : a.d;
     const int n = a.n;
     unsigned long long n_ev = 0, n_re = 0;
+    // pairs handed out `chunk` at a time (sizes vary too much for a static deal; on long lists
+    // one counter increment per pair would serialise the warps on it)
+    int j = 0, jend = 0;
     while (true) {
-        int j = 0;
-        if (lane == 0) j = atomicAdd(next, 1);
-        j = __shfl_sync(0xffffffffu, j, 0);
-        if (j >= m) break;
-        const int2 pr = pairs[j];
+        if (j == jend) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(next, chunk);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base >= m) break;
+            j = base;
+            jend = min(base + chunk, m);
+        }
+        const int2 pr = pairs[j++];
         const int4 lp = a.links[pr.x], lq = a.links[pr.y];
         const bool pa = lp.y - lp.x >= lq.y - lq.x;   // A: the larger side, on the lanes
         const int abeg = pa ? lp.x : lq.x, aend = pa ? lp.y : lq.y;
@@ -1140,15 +1148,16 @@ void run_bccp_tiles(TravArgs &a, const int *counts_host, int *next, cudaStream_t
         const int grid = (int)std::min<long long>(152 * 4, ((long long)m + 7) / 8);
         const int2 *pl = a.list[c];
         int *nx = next + (c - 2);
-#define WM_TILE(DV)                                                                                                \
-    do {                                                                                                           \
-        if (fp64) {                                                                                                \
-            if (hdb) launch(bccp_pair_tile_kernel<DV, true, true>, grid, 256, 0, st, a, pl, m, nx);               \
-            else launch(bccp_pair_tile_kernel<DV, false, true>, grid, 256, 0, st, a, pl, m, nx);                  \
-        } else {                                                                                                   \
-            if (hdb) launch(bccp_pair_tile_kernel<DV, true, false>, grid, 256, 0, st, a, pl, m, nx);              \
-            else launch(bccp_pair_tile_kernel<DV, false, false>, grid, 256, 0, st, a, pl, m, nx);                 \
-        }                                                                                                          \
+        const int chunk = (long long)m > 128LL * grid * 8 ? 4 : 1;   // long lists: fewer counter increments
+#define WM_TILE(DV)                                                                                    \
+    do {                                                                                               \
+        if (fp64) {                                                                                    \
+            if (hdb) launch(bccp_pair_tile_kernel<DV, true, true>, grid, 256, 0, st, a, pl, m, nx, chunk);       \
+            else launch(bccp_pair_tile_kernel<DV, false, true>, grid, 256, 0, st, a, pl, m, nx, chunk);          \
+        } else {                                                                                       \
+            if (hdb) launch(bccp_pair_tile_kernel<DV, true, false>, grid, 256, 0, st, a, pl, m, nx, chunk);      \
+            else launch(bccp_pair_tile_kernel<DV, false, false>, grid, 256, 0, st, a, pl, m, nx, chunk);         \
+        }                                                                                              \
     } while (0)
         switch (a.d) {
         case 2: WM_TILE(2); break;
