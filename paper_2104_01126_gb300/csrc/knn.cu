@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
     const int n = a.n, d = a.d;
     const bool exact32 = a.eta == 0.0;   // FP32 copy is exact: threshold in FP32
     unsigned long long n_ev = 0, n_re = 0;
+    // 32-query groups handed out dynamically: their costs differ too much for a static deal
     while (true) {
         int q0 = 0;
         if (lane == 0) q0 = atomicAdd(a.next_group, 32);
@@ -491,8 +492,7 @@ int core_distances(Points &P, Tree &T, int min_pts, bool fp64, HdbState &H, Aren
     if (ar.failed) return WM_ENOMEM;
     cudaMemsetAsync(cnts, 0, 8 * sizeof(int), st);
     cudaMemsetAsync(a.stat, 0, 4 * sizeof(unsigned long long), st);
-    // launch shape: warps per block limited by shared memory; 32-query groups are handed out
-    // dynamically, so the grid only has to fill the SMs
+    // launch shape: warps per block limited by shared memory; the grid fills the SMs
     const int dmp = d <= 3 ? 4 : d <= 7 ? 8 : 16;
     size_t per_warp = (size_t)32 * dmp * 4 + (size_t)KL * 32 * ((fp64 ? 8 : 4) + 4);
     int wpb = (int)std::min<size_t>(8, std::max<size_t>(1, (48u << 10) / per_warp));

@@ -53,20 +53,17 @@ __device__ inline int uf_find_ro(const int *uf, int x)
 __global__ void filter_connected_kernel(const EdgeK *__restrict__ in, int m, const int *__restrict__ uf,
                                         EdgeK *__restrict__ out, int *count)
 {
-    const int lane = threadIdx.x & 31;
-    const int limit = (m + 31) & ~31;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t - lane < limit; t += gridDim.x * blockDim.x) {
+    __shared__ int sh[32];
+    for (int b0 = blockIdx.x * blockDim.x; b0 < m; b0 += gridDim.x * blockDim.x) {
+        const int t = b0 + threadIdx.x;
         bool keep = false;
         EdgeK e;
         if (t < m) {
             e = in[t];
             keep = uf_find_ro(uf, edge_u(e)) != uf_find_ro(uf, edge_v(e));
         }
-        unsigned b = __ballot_sync(0xffffffffu, keep);
-        int base = 0;
-        if (lane == 0 && b) base = atomicAdd(count, __popc(b));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (keep) out[base + __popc(b & lanemask_lt())] = e;
+        const int slot = block_append(count, keep ? 1 : 0, sh);
+        if (keep) out[slot] = e;
     }
 }
 
@@ -170,10 +167,10 @@ __global__ void reset_compact_kernel(const int *__restrict__ list, const int *__
                                      unsigned long long *Rlo, const int2 *__restrict__ roots,
                                      const int *__restrict__ status, int *__restrict__ next, int *next_cnt)
 {
+    __shared__ int sh[32];
     const int m = *cnt;
-    const int lane = threadIdx.x & 31;
-    const int limit = (m + 31) & ~31;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j - lane < limit; j += gridDim.x * blockDim.x) {
+    for (int b0 = blockIdx.x * blockDim.x; b0 < m; b0 += gridDim.x * blockDim.x) {
+        const int j = b0 + threadIdx.x;
         bool keep = false;
         int i = 0;
         if (j < m) {
@@ -185,11 +182,8 @@ __global__ void reset_compact_kernel(const int *__restrict__ list, const int *__
             i = list[j];
             keep = status[i] == kPending;
         }
-        const unsigned b = __ballot_sync(0xffffffffu, keep);
-        int base = 0;
-        if (lane == 0 && b) base = atomicAdd(next_cnt, __popc(b));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (keep) next[base + __popc(b & lanemask_lt())] = i;
+        const int slot = block_append(next_cnt, keep ? 1 : 0, sh);
+        if (keep) next[slot] = i;
     }
 }
 

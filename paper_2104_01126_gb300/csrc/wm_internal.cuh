@@ -155,6 +155,39 @@ __device__ inline void box_bounds(const float *__restrict__ lo, const float *__r
 
 __device__ inline unsigned lanemask_lt() { unsigned m; asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m)); return m; }
 
+// Block-wide append of cnt >= 0 items per thread: one atomic on the counter per block (a counter
+// bumped once per warp by thousands of warps serialises them).  Every thread of the block must
+// call it (block-uniform control flow; blockDim.x a multiple of 32); sh: 32 ints of shared
+// memory.  Returns the thread's first slot.
+__device__ inline int block_append(int *counter, int cnt, int *sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        const int t = lane < nw ? sh[lane] : 0;
+        int s = t;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, s, 31);
+        int base = 0;
+        if (lane == 0 && total) base = atomicAdd(counter, total);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (lane < nw) sh[lane] = base + s - t;
+    }
+    __syncthreads();
+    const int r = sh[wid] + x - cnt;
+    __syncthreads();
+    return r;
+}
+
 // ------------------------------------------------------------------------- host-side API
 // util.cu
 int scan_exclusive_i32(const int *in, int *out, int n, int *total_dev, cudaStream_t st, Arena &ar);

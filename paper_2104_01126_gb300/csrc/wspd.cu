@@ -515,11 +515,12 @@ __global__ void pack_nodes_kernel(int N, int d, int DP, const float *__restrict_
 // connected (and, for GetRho, |A| > beta).
 __global__ void frontier_init_kernel(TravArgs a, int mode, int2 *__restrict__ out, int *out_count)
 {
-    const int limit = (a.N + 31) & ~31;
-    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x - (threadIdx.x & 31) < limit; x += gridDim.x * blockDim.x) {
+    __shared__ int sh[32];
+    for (int b0 = blockIdx.x * blockDim.x; b0 < a.N; b0 += gridDim.x * blockDim.x) {
+        const int x = b0 + threadIdx.x;
         int push = 0;
         if (x < a.N && a.left[x] >= 0 && a.comp[x] < 0 && (mode == 1 || nsize(a, x) > a.beta)) push = 1;
-        int slot = warp_append(out_count, push);
+        const int slot = block_append(out_count, push, sh);
         if (push) {
             if (slot < a.frontier_cap) out[slot] = make_int2(a.left[x], a.right[x]);
             else atomicOr(a.overflow, 1u);
