@@ -161,6 +161,7 @@ __device__ inline void warp_emit(const TravArgs &a, bool has, const KMin &m)
     }
 }
 
+
 // ------------------------------------------------------------------ packed node records
 // links = {begin, end, left, right}; meta = {diam2 bound, cdmin, cdmax, 0};
 // box[node][2*DP] = lo[0..DP), hi[0..DP) with padded dimensions set to 0.
@@ -829,8 +830,22 @@ __global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const i
     constexpr int DD = D > 0 ? D : kMaxDim;
     constexpr int kTileQ = tile_q(DD);
     __shared__ float qs[8][kTileQ * (DD + 1)];
+    __shared__ EdgeK ebuf[8][32];   // per warp: emitted edges, appended to the batch 32 at a time
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     float *q = qs[wib];
+    EdgeK *eb = ebuf[wib];
+    int ecnt = 0;   // warp-uniform
+    auto flush_edges = [&]() {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(a.edge_count, ecnt);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (lane < ecnt) {
+            if (base + lane < a.edge_cap) a.edges[base + lane] = eb[lane];
+            else atomicOr(a.overflow, 2u);
+        }
+        ecnt = 0;
+        __syncwarp();
+    };
     const int d = D > 0 ? D : a.d;
     const int n = a.n;
     unsigned long long n_ev = 0, n_re = 0;
@@ -955,8 +970,18 @@ __global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const i
             unsigned long long ol = __shfl_xor_sync(0xffffffffu, best.lo, o);
             if (oh < best.hi || (oh == best.hi && ol < best.lo)) { best.hi = oh; best.lo = ol; }
         }
-        warp_emit(a, lane == 0 && in_range(a, best), best);
+        if (in_range(a, best)) {   // best is the same on every lane
+            if (lane == 0) {
+                EdgeK e;
+                e.hi = best.hi;
+                e.lo = best.lo;
+                eb[ecnt] = e;
+            }
+            __syncwarp();
+            if (++ecnt == 32) flush_edges();
+        }
     }
+    if (ecnt > 0) flush_edges();
     n_re = warp_sum_u64(n_re);
     if (lane == 0 && n_ev) {
         atomicAdd(a.stat + 1, n_ev);
