@@ -201,21 +201,28 @@ __global__ void sum_partials_kernel(const double *partial, int m, double *out)
     if (threadIdx.x == 0) *out = sm[0];
 }
 
-// first index in the K-sorted edge array whose w2 >= bound (binary search, one thread)
-__global__ void lower_bound_w2_kernel(const EdgeK *__restrict__ e, int m, double bound, int *out)
+// appends the edges of src whose w2 lies in [lo, hi) to dst (non-negative doubles and +inf order
+// like their bit patterns)
+__global__ void take_range_kernel(const EdgeK *__restrict__ src, int m, double lo, double hi, EdgeK *__restrict__ dst,
+                                  int *count, int cap, unsigned *overflow)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int lo = 0, hi = m;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (edge_w2(e[mid]) < bound) lo = mid + 1; else hi = mid;
+    __shared__ int sh[32];
+    const unsigned long long blo = (unsigned long long)__double_as_longlong(lo);
+    const unsigned long long bhi = (unsigned long long)__double_as_longlong(hi);
+    for (int b0 = blockIdx.x * blockDim.x; b0 < m; b0 += gridDim.x * blockDim.x) {
+        const int t = b0 + threadIdx.x;
+        EdgeK e;
+        bool take = false;
+        if (t < m) {
+            e = src[t];
+            take = e.hi >= blo && e.hi < bhi;
+        }
+        const int slot = block_append(count, take ? 1 : 0, sh);
+        if (take) {
+            if (slot < cap) dst[slot] = e;
+            else atomicOr(overflow, 2u);
+        }
     }
-    *out = lo;
-}
-
-__global__ void copy_edges_kernel(const EdgeK *__restrict__ src, int m, EdgeK *__restrict__ dst)
-{
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) dst[i] = src[i];
 }
 
 }  // namespace
@@ -364,7 +371,6 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     int nE = 0;
     double rho_lo = 0.0;
     long long beta = 2;
-    int rpos = 0;   // HDBSCAN*: next unconsumed repair edge
     const double inf = INFINITY;
     int rounds = 0;
     while (nE < target) {
@@ -470,23 +476,14 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         C.stats.getpairs_launches += steps;
         C.stats.ms_wspd += tw.ms();
         // ---- HDBSCAN*: repair edges of this weight range join the batch
-        if (hdb && hdb->nrep > rpos) {
-            int hi_idx;
-            if (rho_hi == inf) {
-                hi_idx = hdb->nrep;
-            } else {
-                launch(lower_bound_w2_kernel, 1, 32, 0, st, hdb->rep, hdb->nrep, rho_hi, cnts + 9);
-                WM_CK(cudaMemcpyAsync(C.pin, cnts + 9, sizeof(int), cudaMemcpyDeviceToHost, st));
-                WM_CK(cudaStreamSynchronize(st));
-                hi_idx = C.pin[0];
-            }
-            int take = hi_idx - rpos;
-            if (take > 0) {
-                if ((long long)m + take > caps.edges) { *overflow_bits = 2; return 0; }
-                launch(copy_edges_kernel, grid_for(take, 256), 256, 0, st, hdb->rep + rpos, take, a.edges + m);
-                m += take;
-                rpos = hi_idx;
-            }
+        if (hdb && hdb->nrep > 0 && rho_hi > rho_lo) {
+            launch(take_range_kernel, grid_for(hdb->nrep, 256), 256, 0, st, hdb->rep, hdb->nrep, rho_lo, rho_hi,
+                   a.edges, ecount, (int)caps.edges, ovf);
+            WM_CK(cudaMemcpyAsync(C.pin, ecount, sizeof(int), cudaMemcpyDeviceToHost, st));
+            WM_CK(cudaMemcpyAsync(C.pin + 1, ovf, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+            WM_CK(cudaStreamSynchronize(st));
+            if (C.pin[1]) { *overflow_bits = (unsigned)C.pin[1]; return 0; }
+            m = C.pin[0];
         }
         // ---- sort + Kruskal
         Timer tk;

@@ -13,7 +13,7 @@ struct HdbState {
     float *cdmin = nullptr;   // per node: min cd2 rounded down
     float *cdmax = nullptr;   // per node: max cd2 rounded up
     EdgeK *rep = nullptr;     // repair edges {(p,q): w2(p,q) <= cd2(p)} with mutual-reachability
-    int nrep = 0;             //   weights, sorted by K
+    int nrep = 0;             //   weights, each pair once, in no particular order
 };
 
 int core_distances(Points &P, Tree &T, int min_pts, bool fp64, HdbState &H, Arena &ar, cudaStream_t st, int *pin,

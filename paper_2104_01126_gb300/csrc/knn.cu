@@ -399,10 +399,23 @@ __global__ void cd_bounds_kernel(int N, const int *__restrict__ left, const int 
     }
 }
 
-__global__ void rep_flags_kernel(const int *__restrict__ rep_cnt, int n, int *__restrict__ out)
+// A pair (p, q) whose distance is within both core distances is in both points' lists: only the
+// endpoint with the smaller input id emits it, so every repair edge appears once.
+__device__ inline bool rep_keep(int i, int j, double D, const double *__restrict__ cd64, const int *__restrict__ pid)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = rep_cnt[i];
+    return !(__double_as_longlong(D) <= __double_as_longlong(cd64[j]) && pid[j] < pid[i]);
+}
+
+__global__ void rep_flags_kernel(const int *__restrict__ rep_q, const double *__restrict__ rep_d,
+                                 const int *__restrict__ rep_cnt, int n, int KL, const double *__restrict__ cd64,
+                                 const int *__restrict__ pid, int *__restrict__ out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int k = 0;
+        for (int r = 0; r < rep_cnt[i]; ++r)
+            k += rep_keep(i, rep_q[(size_t)i * (KL - 1) + r], rep_d[(size_t)i * (KL - 1) + r], cd64, pid);
+        out[i] = k;
+    }
 }
 
 // repair edge of positions (i, j) with FP64 squared distance D: weight max(cd2 i, cd2 j, D)
@@ -411,40 +424,42 @@ __global__ void rep_emit_kernel(const int *__restrict__ rep_q, const double *__r
                                 const double *__restrict__ cd64, const int *__restrict__ pid, EdgeK *__restrict__ out)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int c = rep_cnt[i], o = off[i];
-        for (int r = 0; r < c; ++r) {
-            int j = rep_q[(size_t)i * (KL - 1) + r];
-            double w = fmax(fmax(cd64[i], cd64[j]), rep_d[(size_t)i * (KL - 1) + r]);
-            out[o + r] = make_edge(w, pid[i], pid[j]);
+        int o = off[i];
+        for (int r = 0; r < rep_cnt[i]; ++r) {
+            const int j = rep_q[(size_t)i * (KL - 1) + r];
+            const double D = rep_d[(size_t)i * (KL - 1) + r];
+            if (!rep_keep(i, j, D, cd64, pid)) continue;
+            const double c = __double_as_longlong(cd64[i]) >= __double_as_longlong(cd64[j]) ? cd64[i] : cd64[j];
+            out[o++] = make_edge(__double_as_longlong(c) >= __double_as_longlong(D) ? c : D, pid[i], pid[j]);
         }
     }
 }
 
+// the exact lists of the slow queries, appended after the others (count: running total)
 __global__ void rep_emit_extra_kernel(const int *__restrict__ ep, const int *__restrict__ eq,
                                       const double *__restrict__ ed, const int *__restrict__ cnt, int cap,
                                       const double *__restrict__ cd64, const int *__restrict__ pid, EdgeK *__restrict__ out,
-                                      const int *__restrict__ base)
+                                      int *count)
 {
-    int m = min(*cnt, cap);
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x) {
-        int i = ep[t], j = eq[t];
-        double w = fmax(fmax(cd64[i], cd64[j]), ed[t]);
-        out[*base + t] = make_edge(w, pid[i], pid[j]);
+    __shared__ int sh[32];
+    const int m = min(*cnt, cap);
+    for (int b0 = blockIdx.x * blockDim.x; b0 < m; b0 += gridDim.x * blockDim.x) {
+        const int t = b0 + threadIdx.x;
+        bool keep = false;
+        int i = 0, j = 0;
+        double D = 0.0;
+        if (t < m) {
+            i = ep[t];
+            j = eq[t];
+            D = ed[t];
+            keep = rep_keep(i, j, D, cd64, pid);
+        }
+        const int slot = block_append(count, keep ? 1 : 0, sh);
+        if (keep) {
+            const double c = __double_as_longlong(cd64[i]) >= __double_as_longlong(cd64[j]) ? cd64[i] : cd64[j];
+            out[slot] = make_edge(__double_as_longlong(c) >= __double_as_longlong(D) ? c : D, pid[i], pid[j]);
+        }
     }
-}
-
-// order-preserving removal of repeated keys from a K-sorted array: flag, scan, scatter
-__global__ void first_of_run_kernel(const EdgeK *__restrict__ in, int m, int *__restrict__ flag)
-{
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x)
-        flag[t] = t == 0 || in[t - 1].hi != in[t].hi || in[t - 1].lo != in[t].lo;
-}
-
-__global__ void scatter_first_kernel(const EdgeK *__restrict__ in, int m, const int *__restrict__ pos,
-                                     EdgeK *__restrict__ out)
-{
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x)
-        if (t == 0 || in[t - 1].hi != in[t].hi || in[t - 1].lo != in[t].lo) out[pos[t]] = in[t];
 }
 
 __global__ void core_out_kernel(const double *__restrict__ cd64, const int *__restrict__ pid, int n, double *out)
@@ -544,43 +559,24 @@ int core_distances(Points &P, Tree &T, int min_pts, bool fp64, HdbState &H, Aren
     cudaMemsetAsync(T.arrive, 0, sizeof(int) * N, st);
     launch(cd_bounds_kernel, grid_for(N, 256), 256, 0, st, N, T.left, T.right, T.parent, T.begin, H.cd64, nmin, nmax,
                                                        H.cdmin, H.cdmax, T.arrive);
-    // repair edges: compact, weight, sort
-    launch(rep_flags_kernel, grid_for(n, 256, 1 << 20), 256, 0, st, a.rep_cnt, n, off);
+    // repair edges: one copy of each, weighted, in no particular order (each MemoGFK round takes
+    // those of its weight range)
+    launch(rep_flags_kernel, grid_for(n, 256), 256, 0, st, a.rep_q, a.rep_d, a.rep_cnt, n, KL, H.cd64, P.pid, off);
     int rc = scan_exclusive_i32(off, off, n, cnts + 3, st, ar);
     if (rc) return rc;
     launch(rep_emit_kernel, grid_for(n, 256), 256, 0, st, a.rep_q, a.rep_d, a.rep_cnt, off, n, KL, H.cd64, P.pid, rep);
     launch(rep_emit_extra_kernel, grid_for(extra_cap, 256), 256, 0, st, ex_p, ex_q, ex_d, cnts + 1, extra_cap, H.cd64,
-                                                                    P.pid, rep, cnts + 3);
+           P.pid, rep, cnts + 3);
     cudaMemcpyAsync(pin, cnts, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
     unsigned long long hs[2];
     cudaMemcpyAsync(pin + 8, a.stat, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;
     memcpy(hs, pin + 8, sizeof hs);
-    int nextra = std::min(pin[1], extra_cap);
-    int nrep = pin[3] + nextra;
+    const int nrep = pin[3];
     if (stats) {
         stats->knn_evals = (int64_t)hs[0];
         stats->fp64_rechecks += (int64_t)hs[1];
         stats->tie_overflow = pin[2] ? 1 : 0;
-    }
-    EdgeK *tmp = ar.get<EdgeK>((size_t)nrep + 1);
-    if (!tmp) return WM_ENOMEM;
-    EdgeK *sorted = rep;
-    rc = radix_sort_edges(rep, tmp, nrep, st, ar, &sorted, pin + 4096);
-    if (rc) return rc;
-    // (p,q) appears twice when p and q are in each other's core ball: keep one copy, in K order
-    if (nrep > 0) {
-        int *flag = ar.get<int>(nrep);
-        if (!flag) return WM_ENOMEM;
-        EdgeK *other = sorted == rep ? tmp : rep;
-        launch(first_of_run_kernel, grid_for(nrep, 256), 256, 0, st, sorted, nrep, flag);
-        rc = scan_exclusive_i32(flag, flag, nrep, cnts + 5, st, ar);
-        if (rc) return rc;
-        launch(scatter_first_kernel, grid_for(nrep, 256), 256, 0, st, sorted, nrep, flag, other);
-        cudaMemcpyAsync(pin, cnts + 5, sizeof(int), cudaMemcpyDeviceToHost, st);
-        if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;
-        nrep = pin[0];
-        if (other != rep) cudaMemcpyAsync(rep, other, sizeof(EdgeK) * nrep, cudaMemcpyDeviceToDevice, st);
     }
     H.rep = rep;
     H.nrep = nrep;
