@@ -28,7 +28,7 @@ namespace wm {
 namespace {
 
 // ---------------------------------------------------------------------------- list ranking
-// S[a] = sum of w over the list from a to its end (inclusive).  Pointer jumping (Wyllie).
+// Pointer jumping (Wyllie): S[a] = sum of w from a to the end of its list.
 __global__ void lr_init_kernel(const int *__restrict__ succ, const int *__restrict__ w, int m, int *__restrict__ nxt,
                                int *__restrict__ S)
 {
@@ -51,6 +51,52 @@ __global__ void lr_step_kernel(const int *__restrict__ nxt, const int *__restric
             nxt2[a] = -1;
         }
     }
+}
+
+// Ruling-set list ranking: every head and about one element in 16 (picked by a multiplicative
+// hash of its index, so that no index pattern of the list lengthens the sublists) is a splitter.
+// A splitter walks its sublist up to the next splitter (prefix sums on the way), the splitters'
+// list is ranked by pointer jumping, and every element adds its splitter's rank: O(m) work, walks
+// of about 16 dependent steps, pointer jumping over about m/16 elements.
+__global__ void lr_mark_kernel(const int *__restrict__ succ, int m, int *__restrict__ haspred)
+{
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < m; a += gridDim.x * blockDim.x)
+        if (succ[a] >= 0) haspred[succ[a]] = 1;
+}
+
+__global__ void lr_flag_kernel(const int *__restrict__ haspred, int m, int *__restrict__ flag)
+{
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < m; a += gridDim.x * blockDim.x)
+        flag[a] = !haspred[a] || ((unsigned)a * 0x9E3779B1u) >> 28 == 0;
+}
+
+__global__ void lr_walk_kernel(const int *__restrict__ succ, const int *__restrict__ w, const int *__restrict__ flag,
+                               const int *__restrict__ sid, int m, int *__restrict__ owner, int *__restrict__ pre,
+                               int *__restrict__ snext, int *__restrict__ ssum)
+{
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < m; a += gridDim.x * blockDim.x) {
+        if (!flag[a]) continue;
+        const int s = sid[a];
+        int x = a, p = 0, nx = -1;
+        for (int it = 0; it < m; ++it) {
+            owner[x] = s;
+            p += w[x];
+            pre[x] = p;
+            const int y = succ[x];
+            if (y < 0) break;
+            if (flag[y]) { nx = sid[y]; break; }
+            x = y;
+        }
+        snext[s] = nx;
+        ssum[s] = p;
+    }
+}
+
+__global__ void lr_finish_kernel(const int *__restrict__ owner, const int *__restrict__ pre, const int *__restrict__ w,
+                                 const int *__restrict__ SS, int m, int *__restrict__ S)
+{
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < m; a += gridDim.x * blockDim.x)
+        S[a] = SS[owner[a]] - pre[a] + w[a];
 }
 
 // --------------------------------------------------------------------------- Euler tour (tree)
@@ -307,7 +353,8 @@ static bool dev_ptr(const void *p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-static int list_rank(const int *succ, const int *w, int m, int *S, Arena &ar, cudaStream_t st)
+// pointer jumping over m elements (the splitter list)
+static int wyllie(const int *succ, const int *w, int m, int *S, Arena &ar, cudaStream_t st)
 {
     size_t mark = ar.off;
     int *n0 = ar.get<int>(m), *n1 = ar.get<int>(m), *S1 = ar.get<int>(m);
@@ -323,6 +370,33 @@ static int list_rank(const int *succ, const int *w, int m, int *S, Arena &ar, cu
         x = Sa; Sa = Sb; Sb = x;
     }
     if (Sa != S) cudaMemcpyAsync(S, Sa, sizeof(int) * m, cudaMemcpyDeviceToDevice, st);
+    ar.off = mark;
+    return 0;
+}
+
+// S[a] = sum of w over the list from a to its end (inclusive), for every element of the lists
+// given by succ (-1 ends a list).
+static int list_rank(const int *succ, const int *w, int m, int *S, Arena &ar, cudaStream_t st, int *pin)
+{
+    if (m <= 0) return 0;
+    size_t mark = ar.off;
+    int *haspred = ar.get<int>(m), *flag = ar.get<int>(m + 1), *sid = ar.get<int>(m + 1);
+    int *owner = ar.get<int>(m), *pre = ar.get<int>(m);
+    int *snext = ar.get<int>(m), *ssum = ar.get<int>(m), *SS = ar.get<int>(m), *ns_d = ar.get<int>(1);
+    if (ar.failed) return WM_ENOMEM;
+    const int g = grid_for(m, 256);
+    cudaMemsetAsync(haspred, 0, sizeof(int) * m, st);
+    launch(lr_mark_kernel, g, 256, 0, st, succ, m, haspred);
+    launch(lr_flag_kernel, g, 256, 0, st, haspred, m, flag);
+    int rc = scan_exclusive_i32(flag, sid, m, ns_d, st, ar);
+    if (rc) return rc;
+    launch(lr_walk_kernel, g, 256, 0, st, succ, w, flag, sid, m, owner, pre, snext, ssum);
+    cudaMemcpyAsync(pin, ns_d, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;
+    const int ns = pin[0];
+    rc = wyllie(snext, ssum, ns, SS, ar, st);
+    if (rc) return rc;
+    launch(lr_finish_kernel, g, 256, 0, st, owner, pre, w, SS, m, S);
     ar.off = mark;
     return 0;
 }
@@ -366,7 +440,7 @@ int dendrogram_impl(const EdgeK *E, int n, int start, int key_squared, wm_dnode 
     if (rc0) return rc0;
     launch(adjacency_kernel, g, 256, 0, st, E, m, deg, cur, adj, slot);
     launch(tour_succ_kernel, g, 256, 0, st, E, m, deg, adj, slot, start, succ, w);
-    rc0 = list_rank(succ, w, L, S, ar, st);
+    rc0 = list_rank(succ, w, L, S, ar, st, pin);
     if (rc0) return rc0;
     fill_i32(tin, -1, n, st);
     {
@@ -398,7 +472,7 @@ int dendrogram_impl(const EdgeK *E, int n, int start, int key_squared, wm_dnode 
     launch(children_kernel, g, 256, 0, st, par, total, n, nch, ch, bad);
     launch(order_children_kernel, g, 256, 0, st, E, m, n, ch, nch, child, tin, tout, lc, rc, bad);
     launch(dtour_kernel, g, 256, 0, st, total, n, par, lc, rc, succ, w);
-    rc0 = list_rank(succ, w, 2 * total, S, ar, st);
+    rc0 = list_rank(succ, w, 2 * total, S, ar, st, pin);
     if (rc0) return rc0;
     wm_dnode *od = out_dendro;
     int *oo = out_order;
