@@ -213,16 +213,28 @@ __global__ void level_union_kernel(const int *__restrict__ ex, const int *__rest
     }
 }
 
+// rootrank / minheavy updates aggregated per warp: edges of one warp often share a component
+// (a large one at the top levels), so each group of equal roots issues one atomic
 __global__ void level_mark_kernel(const int *__restrict__ ex, const int *__restrict__ ey, int m, int bit, int *uf,
                                   int *rootrank, int *minheavy)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-        if (((i >> bit) & 1) == 0) {
-            atomicMax(&rootrank[uf_find(uf, ex[i])], i);
-        } else {
-            atomicMin(&minheavy[uf_find(uf, ex[i])], i);
-            atomicMin(&minheavy[uf_find(uf, ey[i])], i);
-        }
+    const int lane = threadIdx.x & 31;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i - lane < m; i += gridDim.x * blockDim.x) {
+        const bool ok = i < m;
+        const bool light = ok && ((i >> bit) & 1) == 0, heavy = ok && !light;
+        const int kx = ok ? uf_find(uf, ex[i]) : -1;
+        const int ky = heavy ? uf_find(uf, ey[i]) : -1;
+        int key = light ? kx : -1;
+        unsigned grp = __match_any_sync(0xffffffffu, key);
+        int v = __reduce_max_sync(grp, light ? i : -1);
+        if (key >= 0 && lane == __ffs(grp) - 1) atomicMax(&rootrank[key], v);
+        key = heavy ? kx : -1;
+        grp = __match_any_sync(0xffffffffu, key);
+        v = __reduce_min_sync(grp, heavy ? i : 0x7fffffff);
+        if (key >= 0 && lane == __ffs(grp) - 1) atomicMin(&minheavy[key], v);
+        grp = __match_any_sync(0xffffffffu, ky);
+        v = __reduce_min_sync(grp, heavy ? i : 0x7fffffff);
+        if (ky >= 0 && lane == __ffs(grp) - 1) atomicMin(&minheavy[ky], v);
     }
 }
 
@@ -238,6 +250,83 @@ __global__ void level_link_kernel(int *ex, int *ey, int m, int bit, int n, int *
             ex[i] = rootrank[cx] >= 0 ? n + rootrank[cx] : cx;
             ey[i] = rootrank[cy] >= 0 ? n + rootrank[cy] : cy;
         }
+    }
+}
+
+// The lowest kLeafLevels levels: the subproblems are aligned blocks of at most kLeafChunk edges
+// that share no vertex (after the relabelling of the levels above, every vertex and merge node
+// occurs in one subproblem of a level), so one CTA runs all of them for its block in shared
+// memory.  Vertices get local ids on entry (the first occurrence claims map[v]); the merge node
+// of local edge r is 2 * kLeafChunk + r.  The steps of a level are those of the global kernels.
+constexpr int kLeafLevels = 10;
+constexpr int kLeafChunk = 1 << kLeafLevels;
+constexpr int kLeafThreads = 512;
+
+__device__ inline int sm_find(int *uf, int x)
+{
+    for (int it = 0; it < 3 * kLeafChunk; ++it) {
+        int p = uf[x];
+        if (p == x) return x;
+        int g = uf[p];
+        if (g != p) uf[x] = g;
+        x = p;
+    }
+    return x;
+}
+
+__global__ void __launch_bounds__(kLeafThreads) level_leaf_kernel(const int *__restrict__ ex, const int *__restrict__ ey,
+                                                                  int m, int n, int top, int *map,
+                                                                  int *__restrict__ par)
+{
+    __shared__ int uf[3 * kLeafChunk], rr[3 * kLeafChunk], mh[3 * kLeafChunk];
+    __shared__ int lx[kLeafChunk], ly[kLeafChunk];
+    const int b = blockIdx.x * kLeafChunk;
+    const int cnt = min(kLeafChunk, m - b);
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const int me = 2 * t;
+        int prev = atomicCAS(&map[ex[b + t]], -1, me);
+        lx[t] = prev < 0 ? me : prev;
+        prev = atomicCAS(&map[ey[b + t]], -1, me + 1);
+        ly[t] = prev < 0 ? me + 1 : prev;
+    }
+    for (int bit = top - 1; bit >= 0; --bit) {
+        for (int v = threadIdx.x; v < 3 * kLeafChunk; v += blockDim.x) {
+            uf[v] = v;
+            rr[v] = -1;
+            mh[v] = 0x7fffffff;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+            if ((t >> bit) & 1) continue;
+            const int x = lx[t], y = ly[t];
+            for (int it = 0; it < 3 * kLeafChunk; ++it) {
+                int a = sm_find(uf, x), c = sm_find(uf, y);
+                if (a == c) break;
+                if (a > c) { int q = a; a = c; c = q; }
+                if (atomicCAS(&uf[c], c, a) == c) break;
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+            if (((t >> bit) & 1) == 0) {
+                atomicMax(&rr[sm_find(uf, lx[t])], t);
+            } else {
+                atomicMin(&mh[sm_find(uf, lx[t])], t);
+                atomicMin(&mh[sm_find(uf, ly[t])], t);
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+            if (((t >> bit) & 1) == 0) {
+                const int c = sm_find(uf, lx[t]);
+                if (rr[c] == t && mh[c] != 0x7fffffff) par[n + b + t] = n + b + mh[c];
+            } else {
+                const int cx = sm_find(uf, lx[t]), cy = sm_find(uf, ly[t]);
+                lx[t] = rr[cx] >= 0 ? 2 * kLeafChunk + rr[cx] : cx;
+                ly[t] = rr[cy] >= 0 ? 2 * kLeafChunk + rr[cy] : cy;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -460,13 +549,16 @@ int dendrogram_impl(const EdgeK *E, int n, int start, int key_squared, wm_dnode 
     launch(endpoints_init_kernel, g, 256, 0, st, E, m, ex, ey);
     int levels = 0;
     while ((1LL << levels) < (long long)m) ++levels;
-    for (int k = levels; k >= 1; --k) {
+    for (int k = levels; k > kLeafLevels; --k) {
         const int bit = k - 1;
         launch(level_init_kernel, g, 256, 0, st, ex, ey, m, uf, rootrank, minheavy);
         launch(level_union_kernel, g, 256, 0, st, ex, ey, m, bit, uf);
         launch(level_mark_kernel, g, 256, 0, st, ex, ey, m, bit, uf, rootrank, minheavy);
         launch(level_link_kernel, g, 256, 0, st, ex, ey, m, bit, n, uf, rootrank, minheavy, par);
     }
+    fill_i32(uf, -1, total, st);
+    launch(level_leaf_kernel, (m + kLeafChunk - 1) / kLeafChunk, kLeafThreads, 0, st, ex, ey, m, n,
+           std::min(levels, kLeafLevels), uf, par);
     // ---- children, left/right, in-order
     cudaMemsetAsync(nch, 0, sizeof(int) * m, st);
     launch(children_kernel, g, 256, 0, st, par, total, n, nch, ch, bad);
