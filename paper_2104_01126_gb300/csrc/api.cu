@@ -119,7 +119,7 @@ static size_t estimate_bytes(long long n, int d, int min_pts, const Caps &c)
     size_t b = 0;
     b += (size_t)n * d * 8;                 // device copy of the input
     b += (size_t)n * d * 12 * 2;            // points + build scratch
-    b += (size_t)n * 36;                    // pid, pos, uf, R (2 x 8 B), component-label scratch
+    b += (size_t)n * 52;                    // pid, pos, uf, R (4 x 8 B), component-label scratch
     b += (size_t)N * (8 * d + 48);          // tree arrays (+ build scratch counters)
     b += (size_t)n * 8;                     // small lists
     b += (size_t)N * (32 + 8 * dp);         // packed node records
@@ -154,8 +154,10 @@ __global__ void init_uf_kernel(int *uf, unsigned long long *R, int n)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         uf[i] = i;
-        R[i] = ~0ull;
+        R[i] = ~0ull;   // four reservation words per vertex (two sets of two)
         R[n + i] = ~0ull;
+        R[2LL * n + i] = ~0ull;
+        R[3LL * n + i] = ~0ull;
     }
 }
 
@@ -700,7 +702,7 @@ static int emst_body(Call &C, void *vctx, const Caps &caps, unsigned *ovf)
     WM_TRY(prepare(C, x.pts, x.n, x.d, x.dtype, x.layout, S));
     const int n = (int)x.n;
     int *uf = C.ar.get<int>(n);
-    unsigned long long *R = C.ar.get<unsigned long long>(2LL * n);
+    unsigned long long *R = C.ar.get<unsigned long long>(4LL * n);
     EdgeK *E = C.ar.get<EdgeK>(n);
     if (C.ar.failed) return WM_ENOMEM;
     launch(init_uf_kernel, grid_for(n, 256), 256, 0, C.st, uf, R, n);
@@ -731,7 +733,7 @@ static int hdbscan_body(Call &C, void *vctx, const Caps &caps, unsigned *ovf)
     WM_TRY(core_distances(S.P, S.T, x.min_pts, C.precision == WM_PREC_FP64, H, C.ar, C.st, C.pin, &C.stats));
     C.stats.ms_core_dist = tc.ms();
     int *uf = C.ar.get<int>(n);
-    unsigned long long *R = C.ar.get<unsigned long long>(2LL * n);
+    unsigned long long *R = C.ar.get<unsigned long long>(4LL * n);
     EdgeK *E = C.ar.get<EdgeK>(n);
     if (C.ar.failed) return WM_ENOMEM;
     launch(init_uf_kernel, grid_for(n, 256), 256, 0, C.st, uf, R, n);
@@ -905,7 +907,7 @@ static int batch_body(Call &C, void *vctx, const Caps &caps, unsigned *ovf)
         C.stats.ms_core_dist = tc.ms();
     }
     int *uf = ar.get<int>(n);
-    unsigned long long *R = ar.get<unsigned long long>(2LL * n);
+    unsigned long long *R = ar.get<unsigned long long>(4LL * n);
     EdgeK *E = ar.get<EdgeK>(n);
     if (ar.failed) return WM_ENOMEM;
     launch(init_uf_kernel, grid_for(n, 256), 256, 0, st, uf, R, n);

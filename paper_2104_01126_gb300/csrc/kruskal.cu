@@ -12,6 +12,7 @@
 // the sequential condition.  Exact copies of an edge (the same key twice in a batch) all win the
 // same root; the link is a compare-and-swap, so one copy links and the others are rejected in
 // the next step.
+#include <algorithm>
 #include <cstdio>
 
 #include "wm_internal.cuh"
@@ -19,8 +20,6 @@
 namespace wm {
 
 namespace {
-
-constexpr int kPending = 0, kAccept = 1, kReject = 2;
 
 // Every loop that follows union-find pointers is bounded: a valid forest over n < 2^30 vertices
 // has no path longer than n, so the bound is never reached unless the structure is corrupt.
@@ -67,60 +66,83 @@ __global__ void filter_connected_kernel(const EdgeK *__restrict__ in, int m, con
     }
 }
 
-__global__ void init_list_kernel(int *list, int m, int *status)
+__global__ void init_list_kernel(int *list, int m)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-        list[i] = i;
-        status[i] = kPending;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) list[i] = i;
+}
+
+// The reservations of step s live in set s & 1; set (s - 1) & 1, written by the previous step, is
+// cleared here (its roots list and count are intact until the next step), so a step needs no
+// separate reset pass.
+__device__ inline void clear_reservations(const int2 *__restrict__ roots, int m, unsigned long long *Rhi,
+                                          unsigned long long *Rlo)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+        const int2 r = roots[j];
+        if (r.x >= 0) {
+            Rhi[r.x] = ~0ull; Rhi[r.y] = ~0ull;
+            Rlo[r.x] = ~0ull; Rlo[r.y] = ~0ull;
+        }
     }
 }
 
+struct StepArgs {
+    const EdgeK *e;
+    const int *list;          // pending edges of this step
+    const int *cnt;           // their number
+    int2 *roots;              // roots of each pending edge (-1: rejected)
+    unsigned long long *Rhi, *Rlo;   // reservation set of this step
+    const int2 *prev_roots;   // previous step: roots, count, reservation set (cleared here)
+    const int *prev_cnt;
+    unsigned long long *prev_hi, *prev_lo;
+    int *zero_cnt;            // the counter the next step appends into: zeroed here
+    int *next;                // pending edges after this step, and their counter
+    int *next_cnt;
+};
+
 // Finds the roots; rejects edges inside one component (and invalid edges, flagged in *bad: every
 // edge must have 0 <= u < v < n); WriteMin of the w2 bits on both roots.
-__global__ void reserve_hi_kernel(const EdgeK *__restrict__ e, const int *__restrict__ list, const int *__restrict__ cnt,
-                                  int n, int *uf, unsigned long long *Rhi, int2 *__restrict__ roots,
-                                  int *__restrict__ status, int *bad)
+__global__ void reserve_hi_kernel(StepArgs a, int n, int *uf, int *bad)
 {
-    const int m = *cnt;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.zero_cnt = 0;
+    clear_reservations(a.prev_roots, *a.prev_cnt, a.prev_hi, a.prev_lo);
+    const int m = *a.cnt;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
-        const int i = list[j];
-        const EdgeK x = e[i];
+        const EdgeK x = a.e[a.list[j]];
         const int u = edge_u(x), v = edge_v(x);
         if (u < 0 || u >= v || v >= n) {
             atomicOr(bad, 1);
-            status[i] = kReject;
-            roots[j] = make_int2(-1, -1);
+            a.roots[j] = make_int2(-1, -1);
             continue;
         }
         const int ru = uf_find_halving(uf, u), rv = uf_find_halving(uf, v);
         if (ru == rv) {
-            status[i] = kReject;
-            roots[j] = make_int2(-1, -1);
+            a.roots[j] = make_int2(-1, -1);
         } else {
-            roots[j] = make_int2(ru, rv);
+            a.roots[j] = make_int2(ru, rv);
             // a WriteMin that cannot lower the value is skipped (many edges share a big root)
-            if (x.hi < *(volatile unsigned long long *)&Rhi[ru]) atomicMin(&Rhi[ru], x.hi);
-            if (x.hi < *(volatile unsigned long long *)&Rhi[rv]) atomicMin(&Rhi[rv], x.hi);
+            if (x.hi < *(volatile unsigned long long *)&a.Rhi[ru]) atomicMin(&a.Rhi[ru], x.hi);
+            if (x.hi < *(volatile unsigned long long *)&a.Rhi[rv]) atomicMin(&a.Rhi[rv], x.hi);
         }
     }
 }
 
 // Among the edges that won the w2 WriteMin of a root: WriteMin of the id pair.
-__global__ void reserve_lo_kernel(const EdgeK *__restrict__ e, const int *__restrict__ list, const int *__restrict__ cnt,
-                                  const unsigned long long *__restrict__ Rhi, unsigned long long *Rlo,
-                                  const int2 *__restrict__ roots)
+__global__ void reserve_lo_kernel(StepArgs a)
 {
-    const int m = *cnt;
+    const int m = *a.cnt;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
-        const int2 r = roots[j];
+        const int2 r = a.roots[j];
         if (r.x < 0) continue;
-        const EdgeK x = e[list[j]];
-        if (Rhi[r.x] == x.hi && x.lo < *(volatile unsigned long long *)&Rlo[r.x]) atomicMin(&Rlo[r.x], x.lo);
-        if (Rhi[r.y] == x.hi && x.lo < *(volatile unsigned long long *)&Rlo[r.y]) atomicMin(&Rlo[r.y], x.lo);
+        const EdgeK x = a.e[a.list[j]];
+        if (a.Rhi[r.x] == x.hi && x.lo < *(volatile unsigned long long *)&a.Rlo[r.x]) atomicMin(&a.Rlo[r.x], x.lo);
+        if (a.Rhi[r.y] == x.hi && x.lo < *(volatile unsigned long long *)&a.Rlo[r.y]) atomicMin(&a.Rlo[r.y], x.lo);
     }
 }
 
-__device__ inline void append_edge(const EdgeK &x, bool has, EdgeK *out, int *out_count, int out_cap, int *bad)
+// warp-aggregated append of the lanes with has set
+template <typename T>
+__device__ inline void warp_append(const T &x, bool has, T *out, int *out_count, int out_cap, int *bad)
 {
     const int lane = threadIdx.x & 31;
     const unsigned b = __ballot_sync(0xffffffffu, has);
@@ -134,57 +156,122 @@ __device__ inline void append_edge(const EdgeK &x, bool has, EdgeK *out, int *ou
     }
 }
 
-// The holder of a root's reservation links that root under the other root and is accepted.
-// Accepted edges are appended to the output (in no particular order).
-__global__ void commit_kernel(const EdgeK *__restrict__ e, const int *__restrict__ list, const int *__restrict__ cnt,
-                              int *uf, const unsigned long long *__restrict__ Rhi,
-                              const unsigned long long *__restrict__ Rlo, const int2 *__restrict__ roots,
-                              int *__restrict__ status, EdgeK *__restrict__ out, int *out_count, int out_cap, int *bad)
+// The holder of a root's reservation links that root under the other root and is accepted
+// (appended to the output, in no particular order); edges that hold neither stay pending and
+// are appended to the next list.
+__global__ void commit_kernel(StepArgs a, int *uf, EdgeK *__restrict__ out, int *out_count, int out_cap, int *bad)
 {
-    const int m = *cnt;
+    const int m = *a.cnt;
     const int lane = threadIdx.x & 31;
     const int limit = (m + 31) & ~31;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j - lane < limit; j += gridDim.x * blockDim.x) {
-        bool acc = false;
+        bool acc = false, keep = false;
+        int i = 0;
         EdgeK x;
         x.hi = 0; x.lo = 0;
         if (j < m) {
-            const int2 r = roots[j];
+            const int2 r = a.roots[j];
             if (r.x >= 0) {
-                const int i = list[j];
-                x = e[i];
-                if (Rhi[r.y] == x.hi && Rlo[r.y] == x.lo) acc = atomicCAS(&uf[r.y], r.y, r.x) == r.y;
-                else if (Rhi[r.x] == x.hi && Rlo[r.x] == x.lo) acc = atomicCAS(&uf[r.x], r.x, r.y) == r.x;
-                if (acc) status[i] = kAccept;
+                i = a.list[j];
+                x = a.e[i];
+                if (a.Rhi[r.y] == x.hi && a.Rlo[r.y] == x.lo) acc = atomicCAS(&uf[r.y], r.y, r.x) == r.y;
+                else if (a.Rhi[r.x] == x.hi && a.Rlo[r.x] == x.lo) acc = atomicCAS(&uf[r.x], r.x, r.y) == r.x;
+                keep = !acc;
             }
         }
-        append_edge(x, acc, out, out_count, out_cap, bad);
+        warp_append(x, acc, out, out_count, out_cap, bad);
+        warp_append(i, keep, a.next, a.next_cnt, 0x7fffffff, bad);
     }
 }
 
-// Clears the reservations that were made and compacts the pending edges.
-__global__ void reset_compact_kernel(const int *__restrict__ list, const int *__restrict__ cnt, unsigned long long *Rhi,
-                                     unsigned long long *Rlo, const int2 *__restrict__ roots,
-                                     const int *__restrict__ status, int *__restrict__ next, int *next_cnt)
+// The last steps of a batch, when few edges are pending: one CTA runs the steps to the end with
+// block barriers between the phases instead of kernel boundaries (the phases are those of the
+// kernels above; reservations use the step's set and are cleared after each step).  It does
+// nothing when more than kTailMax edges are pending; the host then runs more grid-wide steps.
+constexpr int kTailThreads = 1024, kTailMax = 16384;
+
+__global__ void __launch_bounds__(kTailThreads) tail_kernel(StepArgs a, int *cnt_in, int *prev_cnt, int n, int *uf,
+                                                            EdgeK *__restrict__ out, int *out_count, int out_cap,
+                                                            int *bad)
 {
-    __shared__ int sh[32];
-    const int m = *cnt;
-    for (int b0 = blockIdx.x * blockDim.x; b0 < m; b0 += gridDim.x * blockDim.x) {
-        const int j = b0 + threadIdx.x;
-        bool keep = false;
-        int i = 0;
-        if (j < m) {
-            const int2 r = roots[j];
-            if (r.x >= 0) {
-                Rhi[r.x] = ~0ull; Rhi[r.y] = ~0ull;
-                Rlo[r.x] = ~0ull; Rlo[r.y] = ~0ull;
+    __shared__ int s_next;
+    const int m0 = *cnt_in;
+    if (m0 == 0 || m0 > kTailMax) return;
+    const int lane = threadIdx.x & 31;
+    clear_reservations(a.prev_roots, *prev_cnt, a.prev_hi, a.prev_lo);
+    __syncthreads();
+    if (threadIdx.x == 0) *prev_cnt = 0;
+    int *lin = const_cast<int *>(a.list), *lout = a.next;
+    int m = m0;
+    for (int it = 0; it < m0 + 8 && m > 0; ++it) {
+        if (threadIdx.x == 0) s_next = 0;
+        for (int j = threadIdx.x; j < m; j += blockDim.x) {
+            const EdgeK x = a.e[lin[j]];
+            const int u = edge_u(x), v = edge_v(x);
+            if (u < 0 || u >= v || v >= n) {
+                atomicOr(bad, 1);
+                a.roots[j] = make_int2(-1, -1);
+                continue;
             }
-            i = list[j];
-            keep = status[i] == kPending;
+            const int ru = uf_find_halving(uf, u), rv = uf_find_halving(uf, v);
+            if (ru == rv) {
+                a.roots[j] = make_int2(-1, -1);
+            } else {
+                a.roots[j] = make_int2(ru, rv);
+                if (x.hi < *(volatile unsigned long long *)&a.Rhi[ru]) atomicMin(&a.Rhi[ru], x.hi);
+                if (x.hi < *(volatile unsigned long long *)&a.Rhi[rv]) atomicMin(&a.Rhi[rv], x.hi);
+            }
         }
-        const int slot = block_append(next_cnt, keep ? 1 : 0, sh);
-        if (keep) next[slot] = i;
+        __syncthreads();
+        for (int j = threadIdx.x; j < m; j += blockDim.x) {
+            const int2 r = a.roots[j];
+            if (r.x < 0) continue;
+            const EdgeK x = a.e[lin[j]];
+            if (a.Rhi[r.x] == x.hi && x.lo < *(volatile unsigned long long *)&a.Rlo[r.x]) atomicMin(&a.Rlo[r.x], x.lo);
+            if (a.Rhi[r.y] == x.hi && x.lo < *(volatile unsigned long long *)&a.Rlo[r.y]) atomicMin(&a.Rlo[r.y], x.lo);
+        }
+        __syncthreads();
+        const int limit = (m + 31) & ~31;
+        for (int j = threadIdx.x; j - lane < limit; j += blockDim.x) {
+            bool acc = false, keep = false;
+            int i = 0;
+            EdgeK x;
+            x.hi = 0; x.lo = 0;
+            if (j < m) {
+                const int2 r = a.roots[j];
+                if (r.x >= 0) {
+                    i = lin[j];
+                    x = a.e[i];
+                    if (a.Rhi[r.y] == x.hi && a.Rlo[r.y] == x.lo) acc = atomicCAS(&uf[r.y], r.y, r.x) == r.y;
+                    else if (a.Rhi[r.x] == x.hi && a.Rlo[r.x] == x.lo) acc = atomicCAS(&uf[r.x], r.x, r.y) == r.x;
+                    keep = !acc;
+                }
+            }
+            warp_append(x, acc, out, out_count, out_cap, bad);
+            warp_append(i, keep, lout, &s_next, 0x7fffffff, bad);
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < m; j += blockDim.x) {
+            const int2 r = a.roots[j];
+            if (r.x >= 0) {
+                a.Rhi[r.x] = ~0ull; a.Rhi[r.y] = ~0ull;
+                a.Rlo[r.x] = ~0ull; a.Rlo[r.y] = ~0ull;
+            }
+        }
+        m = s_next;
+        int *t = lin; lin = lout; lout = t;
+        __syncthreads();
     }
+    if (threadIdx.x == 0) {
+        *cnt_in = m;
+        if (m > 0) atomicOr(bad, 4);
+    }
+}
+
+__global__ void clear_kernel(const int2 *__restrict__ roots, const int *__restrict__ cnt, unsigned long long *Rhi,
+                             unsigned long long *Rlo)
+{
+    clear_reservations(roots, *cnt, Rhi, Rlo);
 }
 
 }  // namespace
@@ -196,58 +283,84 @@ int filter_connected(const EdgeK *in, int m, const int *uf, EdgeK *out, int *cou
     return 0;
 }
 
-// Kruskal over the batch e[0..m) (any order).  R holds 2 n 64-bit reservation words, all ~0 on
-// entry (kept so).  Accepted edges are appended to out at out_base (in no particular order);
-// *accepted receives their number.
+// Kruskal over the batch e[0..m) (any order).  R holds 4 n 64-bit reservation words (two sets
+// of two), all ~0 on entry (kept so).  Accepted edges are appended to out at out_base (in no
+// particular order); *accepted receives their number.
 int batch_kruskal(const EdgeK *e, int m, int n, int *uf, unsigned long long *R, EdgeK *out, int out_base, int *accepted,
                   Arena &ar, cudaStream_t st, int *pinned)
 {
     *accepted = 0;
     if (m <= 0) return 0;
     size_t mark = ar.off;
-    int *listA = ar.get<int>(m), *listB = ar.get<int>(m), *status = ar.get<int>(m);
-    int2 *roots = ar.get<int2>(m);
-    int *cnt = ar.get<int>(4);   // [0] / [1] pending counts, [2] accepted, [3] bad
+    int *list[2] = {ar.get<int>(m), ar.get<int>(m)};
+    int2 *roots[2] = {ar.get<int2>(m), ar.get<int2>(m)};
+    // [0..3] pending counts (step s reads s % 4, appends into (s + 1) % 4, zeroes (s + 2) % 4),
+    // [4] accepted, [5] bad
+    int *cnt = ar.get<int>(8);
     if (ar.failed) return WM_ENOMEM;
-    unsigned long long *Rhi = R, *Rlo = R + n;
-    launch(init_list_kernel, grid_for(m, 256), 256, 0, st, listA, m, status);
-    const int init[4] = {m, 0, 0, 0};   // pageable source: copied out before the call returns
+    unsigned long long *Rhi[2] = {R, R + 2LL * n}, *Rlo[2] = {R + n, R + 3LL * n};
+    launch(init_list_kernel, grid_for(m, 256), 256, 0, st, list[0], m);
+    const int init[8] = {m, 0, 0, 0, 0, 0, 0, 0};   // pageable source: copied out before the call returns
     cudaMemcpyAsync(cnt, init, sizeof init, cudaMemcpyHostToDevice, st);
     int step = 0;
     const int grid = grid_for(m, 256);
+    auto args = [&](int s) {
+        const int c = s & 1, p = c ^ 1;
+        StepArgs a;
+        a.e = e;
+        a.list = list[c];
+        a.cnt = cnt + (s & 3);
+        a.roots = roots[c];
+        a.Rhi = Rhi[c];
+        a.Rlo = Rlo[c];
+        a.prev_roots = roots[p];
+        a.prev_cnt = cnt + ((s + 3) & 3);   // 0 before the first step
+        a.prev_hi = Rhi[p];
+        a.prev_lo = Rlo[p];
+        a.zero_cnt = cnt + ((s + 2) & 3);
+        a.next = list[p];
+        a.next_cnt = cnt + ((s + 1) & 3);
+        return a;
+    };
     while (true) {
         for (int b = 0; b < 4; ++b, ++step) {
-            int *lin = (step & 1) ? listB : listA, *lout = (step & 1) ? listA : listB;
-            int *cin = cnt + (step & 1), *cout = cnt + ((step + 1) & 1);
-            launch(reserve_hi_kernel, grid, 256, 0, st, e, lin, cin, n, uf, Rhi, roots, status, cnt + 3);
-            launch(reserve_lo_kernel, grid, 256, 0, st, e, lin, cin, Rhi, Rlo, roots);
-            launch(commit_kernel, grid, 256, 0, st, e, lin, cin, uf, Rhi, Rlo, roots, status, out + out_base,
-                   cnt + 2, n - 1 - out_base, cnt + 3);
-            // cout must be zero before this kernel appends into it: it was consumed two steps ago
-            launch(reset_compact_kernel, grid, 256, 0, st, lin, cin, Rhi, Rlo, roots, status, lout, cout);
-            // the consumed input counter becomes the next output counter: zero it now
-            cudaMemsetAsync(cin, 0, sizeof(int), st);
+            // the pending list shrinks by a factor of about 2 to 4 per step: a smaller grid (the
+            // loops are grid-strided, so any size is correct) keeps the nearly empty steps short
+            const int g = std::max(152, grid_for(std::max(1, m >> std::min(step, 30)), 256));
+            const StepArgs a = args(step);
+            launch(reserve_hi_kernel, g, 256, 0, st, a, n, uf, cnt + 5);
+            launch(reserve_lo_kernel, g, 256, 0, st, a);
+            launch(commit_kernel, g, 256, 0, st, a, uf, out + out_base, cnt + 4, n - 1 - out_base, cnt + 5);
         }
-        cudaMemcpyAsync(pinned, cnt, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
+        launch(tail_kernel, 1, kTailThreads, 0, st, args(step), cnt + (step & 3), cnt + ((step + 3) & 3), n, uf,
+               out + out_base, cnt + 4, n - 1 - out_base, cnt + 5);
+        cudaMemcpyAsync(pinned, cnt, 6 * sizeof(int), cudaMemcpyDeviceToHost, st);
         if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;
-        if (pinned[3] & 1) {
+        if (pinned[5] & 1) {
             set_error_detail("a candidate edge handed to Kruskal has an endpoint outside [0, n) or u >= v");
             return WM_EINTERNAL;
         }
-        if (pinned[3] & 2) {
+        if (pinned[5] & 2) {
             set_error_detail("Kruskal accepted more than n-1 edges in total");
             return WM_EINTERNAL;
         }
-        if (pinned[step & 1] == 0) break;
+        if (pinned[5] & 4) {
+            set_error_detail("batched Kruskal made no progress in its single-block steps");
+            return WM_EINTERNAL;
+        }
+        if (pinned[step & 3] == 0) break;
         if (step > 4 * (m + 8)) {
             char msg[160];
             snprintf(msg, sizeof msg, "batched Kruskal made no progress (reservations): %d of %d edges pending",
-                     pinned[step & 1], m);
+                     pinned[step & 3], m);
             set_error_detail(msg);
             return WM_EINTERNAL;
         }
     }
-    *accepted = pinned[2];
+    // the last step's reservations are still set
+    const int last = (step - 1) & 1;
+    launch(clear_kernel, grid, 256, 0, st, roots[last], cnt + ((step - 1) & 3), Rhi[last], Rlo[last]);
+    *accepted = pinned[4];
     ar.off = mark;
     return 0;
 }
