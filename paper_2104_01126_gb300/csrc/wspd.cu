@@ -105,6 +105,14 @@ __device__ inline double exact_w2(const TravArgs &a, int i, int j, float d32, fl
     return dist64(a.x64, a.n, a.d, i, j);
 }
 
+// a recheck candidate held back so that the FP64 work of several lanes runs in one instruction
+struct Deferred {
+    int i = -1, j = 0;
+    float sd = 0.f, c32 = 0.f;
+};
+
+__device__ inline float screen_value(const Deferred &c, bool hdb) { return hdb ? fmaxf(c.sd, c.c32) : c.sd; }
+
 struct KMin {
     unsigned long long hi, lo;   // w2 bits, (min id << 32) | max id
 };
@@ -464,19 +472,25 @@ __global__ void __launch_bounds__(256) bccp_group_kernel(TravArgs a, const int2 
 #pragma unroll
             for (int o = G / 2; o; o >>= 1) smin = fminf(smin, __shfl_xor_sync(0xffffffffu, smin, o));
             const float T = screen_threshold(smin, a);
+            // a lane's first candidate is rechecked after the loop, where the lanes run together
+            // (an FP64 instruction costs the same however few lanes are active); later ones inline
+            Deferred df;
             {
                 int i = pb + (nb > 0 ? g / nb : 0), j = qb + (nb > 0 ? g % nb : 0);
                 for (int e = g; e < tot; e += G) {
                     const float sd = dist32(a.x32, n, d, i, j);
                     const float c32 = a.cd32 ? fmaxf(a.cd32[i], a.cd32[j]) : 0.f;
                     if (fmaxf(sd, c32) <= T) {
-                        kmin_update(best, exact_w2(a, i, j, sd, c32), a.pid[i], a.pid[j]);
+                        if (df.i < 0) df = Deferred{i, j, sd, c32};
+                        else kmin_update(best, exact_w2(a, i, j, sd, c32), a.pid[i], a.pid[j]);
                         ++n_re;
                     }
                     j += G;
                     while (j >= qb + nb) { j -= nb; ++i; }
                 }
             }
+            __syncwarp();
+            if (df.i >= 0) kmin_update(best, exact_w2(a, df.i, df.j, df.sd, df.c32), a.pid[df.i], a.pid[df.j]);
         }
 #pragma unroll
         for (int o = G / 2; o; o >>= 1) {
@@ -867,6 +881,7 @@ __global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const i
         const int abeg = pa ? lp.x : lq.x, aend = pa ? lp.y : lq.y;
         const int bbeg = pa ? lq.x : lp.x, bend = pa ? lq.y : lp.y;
         KMin best{~0ull, ~0ull};
+        Deferred df;                // this lane's first candidate, rechecked at the end of the pair
         float run_min = INFINITY;   // screened minimum over the chunks done so far
         for (int a0 = abeg; a0 < aend; a0 += kTileA) {
             const int a1 = min(a0 + kTileA, aend);
@@ -943,7 +958,8 @@ __global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const i
                             const float sd = s;
                             if (HDB) s = fmaxf(s, c32);
                             if (s <= T) {
-                                kmin_update(best, exact_w2(a, i, b0 + jj, sd, c32), a.pid[i], a.pid[b0 + jj]);
+                                if (df.i < 0) df = Deferred{i, b0 + jj, sd, c32};
+                                else kmin_update(best, exact_w2(a, i, b0 + jj, sd, c32), a.pid[i], a.pid[b0 + jj]);
                                 ++nre;
                             }
                         }
@@ -964,6 +980,9 @@ __global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const i
                 n_ev += (unsigned long long)((a1 - a0) * nb);
             }
         }
+        __syncwarp();
+        if (!FP64 && df.i >= 0 && screen_value(df, HDB) <= screen_threshold(run_min, a))
+            kmin_update(best, exact_w2(a, df.i, df.j, df.sd, df.c32), a.pid[df.i], a.pid[df.j]);
         // warp K-minimum of the pair
         for (int o = 16; o; o >>= 1) {
             unsigned long long oh = __shfl_xor_sync(0xffffffffu, best.hi, o);
