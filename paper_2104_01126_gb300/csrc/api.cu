@@ -118,8 +118,8 @@ static size_t estimate_bytes(long long n, int d, int min_pts, const Caps &c)
     const int dp = d <= 4 ? 4 : d <= 8 ? 8 : 16;
     size_t b = 0;
     b += (size_t)n * d * 8;                 // device copy of the input
-    b += (size_t)n * d * 12 * 2;            // points + build scratch
-    b += (size_t)n * 52;                    // pid, pos, uf, R (4 x 8 B), component-label scratch
+    b += (size_t)n * d * 28;                // points in input order, in tree order, build scratch
+    b += (size_t)n * 60;                    // ids (3), pos, uf, R (4 x 8 B), component-label scratch
     b += (size_t)N * (8 * d + 48);          // tree arrays (+ build scratch counters)
     b += (size_t)n * 8;                     // small lists
     b += (size_t)N * (32 + 8 * dp);         // packed node records

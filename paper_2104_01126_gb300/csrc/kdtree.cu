@@ -7,9 +7,11 @@
 //
 // Build: nodes with more than 32 points are split level by level over the whole GPU; each level
 // computes boxes with warp work-units of 256 points, counts the left side, and partitions the
-// points in place through a scratch copy.  A node of 2..32 points is finished by one warp, which
+// FP32 coordinates and ids between two ping-pong buffers (a child that leaves the top levels is
+// written to the final arrays directly); the FP64 coordinates are gathered once at the end.  A node of 2..32 points is finished by one warp, which
 // holds its points in registers and splits recursively with ballots and shuffles.
 #include <cstring>
+#include <utility>
 
 #include "wm_internal.cuh"
 
@@ -184,32 +186,37 @@ __global__ void children_kernel(const int *__restrict__ act, int A, int next_id,
     }
 }
 
+// Partition of each active node's points by its split.  The points of a child that stays active
+// (more than 32 points) go to the other ping-pong buffer (w32, wpid); those of a child that leaves
+// the top levels go straight to their final place (f32, fpid), which no active node reads.
 __global__ void scatter_units_kernel(Level L, const int *__restrict__ total_units, const int *__restrict__ nbegin,
                                      const int *__restrict__ nend, const float *__restrict__ x32,
-                                     const double *__restrict__ x64, const int *__restrict__ pid, int n, int d,
-                                     const int *__restrict__ sdim, const float *__restrict__ sval,
-                                     const int *__restrict__ count_split, const int *__restrict__ cnt,
-                                     int *__restrict__ curl, int *__restrict__ curr, float *__restrict__ t32,
-                                     double *__restrict__ t64, int *__restrict__ tpid)
+                                     const int *__restrict__ pid, int n, int d, const int *__restrict__ sdim,
+                                     const float *__restrict__ sval, const int *__restrict__ count_split,
+                                     const int *__restrict__ cnt, int *__restrict__ curl, int *__restrict__ curr,
+                                     float *__restrict__ w32, int *__restrict__ wpid, float *__restrict__ f32,
+                                     int *__restrict__ fpid)
 {
     const int lane = threadIdx.x & 31;
     const int TU = *total_units;
     for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < TU; u += (gridDim.x * blockDim.x) >> 5) {
         int j = find_unit_node(L.unit_off, L.A, u);
         int nd = L.act[j];
-        int nb = nbegin[nd];
+        int nb = nbegin[nd], ne = nend[nd];
         int b = nb + (u - L.unit_off[j]) * kUnit;
-        int e = min(b + kUnit, nend[nd]);
+        int e = min(b + kUnit, ne);
         int k = sdim[j];
         float s = sval[j];
         int cs = count_split[j];
         int Lc = cnt[nd];
+        const bool lbig = Lc > 32, rbig = ne - nb - Lc > 32;
         for (int i0 = b; i0 < e; i0 += 32) {
             int i = i0 + lane;
             bool valid = i < e;
             int dst = i;
+            bool fl;
             if (!cs) {
-                bool fl = valid && x32[(size_t)k * n + i] < s;
+                fl = valid && x32[(size_t)k * n + i] < s;
                 unsigned bl = __ballot_sync(0xffffffffu, fl);
                 unsigned br = __ballot_sync(0xffffffffu, valid && !fl);
                 int bsl = 0, bsr = 0;
@@ -221,37 +228,27 @@ __global__ void scatter_units_kernel(Level L, const int *__restrict__ total_unit
                 bsr = __shfl_sync(0xffffffffu, bsr, 0);
                 if (fl) dst = nb + bsl + __popc(bl & lanemask_lt());
                 else dst = nb + Lc + bsr + __popc(br & lanemask_lt());
+            } else {
+                fl = i < nb + Lc;
             }
             if (valid) {
-                for (int kk = 0; kk < d; ++kk) {
-                    t32[(size_t)kk * n + dst] = x32[(size_t)kk * n + i];
-                    t64[(size_t)kk * n + dst] = x64[(size_t)kk * n + i];
-                }
-                tpid[dst] = pid[i];
+                const bool big = fl ? lbig : rbig;
+                float *o32 = big ? w32 : f32;
+                for (int kk = 0; kk < d; ++kk) o32[(size_t)kk * n + dst] = x32[(size_t)kk * n + i];
+                (big ? wpid : fpid)[dst] = pid[i];
             }
         }
     }
 }
 
-__global__ void copyback_units_kernel(Level L, const int *__restrict__ total_units, const int *__restrict__ nbegin,
-                                      const int *__restrict__ nend, float *__restrict__ x32, double *__restrict__ x64,
-                                      int *__restrict__ pid, int n, int d, const float *__restrict__ t32,
-                                      const double *__restrict__ t64, const int *__restrict__ tpid)
+// FP64 coordinates in tree order: x64[k][p] = src[k][pid[p]]
+__global__ void gather64_kernel(const double *__restrict__ src, const int *__restrict__ pid, int n, int d,
+                                double *__restrict__ x64)
 {
-    const int lane = threadIdx.x & 31;
-    const int TU = *total_units;
-    for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < TU; u += (gridDim.x * blockDim.x) >> 5) {
-        int j = find_unit_node(L.unit_off, L.A, u);
-        int nd = L.act[j];
-        int b = nbegin[nd] + (u - L.unit_off[j]) * kUnit;
-        int e = min(b + kUnit, nend[nd]);
-        for (int i = b + lane; i < e; i += 32) {
-            for (int kk = 0; kk < d; ++kk) {
-                x32[(size_t)kk * n + i] = t32[(size_t)kk * n + i];
-                x64[(size_t)kk * n + i] = t64[(size_t)kk * n + i];
-            }
-            pid[i] = tpid[i];
-        }
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)n * d;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(t / n), p = (int)(t % n);
+        x64[t] = src[(size_t)k * n + pid[p]];
     }
 }
 
@@ -268,8 +265,7 @@ __global__ void compact_children_kernel(const int *__restrict__ flag, const int 
 template <int DM>
 __global__ void small_subtree_kernel(const int *__restrict__ small, const int *__restrict__ small_base, int S,
                                      int *nbegin, int *nend, int *nleft, int *nright, int *nparent, int *ndepth,
-                                     float *lo, float *hi, float *x32, double *x64, int *pid, int n, int N, int d,
-                                     int *max_depth)
+                                     float *lo, float *hi, float *x32, int *pid, int n, int N, int d, int *max_depth)
 {
     const int lane = threadIdx.x & 31;
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -279,12 +275,10 @@ __global__ void small_subtree_kernel(const int *__restrict__ small, const int *_
     const int b0 = nbegin[root];
     const int m = nend[root] - b0;
     float c32[DM];
-    double c64[DM];
     int myid = -1;
     if (lane < m) {
-        for (int k = 0; k < DM; ++k) {
-            if (k < d) { c32[k] = x32[(size_t)k * n + b0 + lane]; c64[k] = x64[(size_t)k * n + b0 + lane]; }
-        }
+        for (int k = 0; k < DM; ++k)
+            if (k < d) c32[k] = x32[(size_t)k * n + b0 + lane];
         myid = pid[b0 + lane];
     }
     // explicit stack of (lo_lane, hi_lane, node)
@@ -333,7 +327,6 @@ __global__ void small_subtree_kernel(const int *__restrict__ small, const int *_
         for (int k = 0; k < DM; ++k) {
             if (k >= d) break;
             c32[k] = __shfl_sync(0xffffffffu, c32[k], src);
-            c64[k] = __shfl_sync(0xffffffffu, c64[k], src);
         }
         myid = __shfl_sync(0xffffffffu, myid, src);
         int l = next, r = next + 1;
@@ -352,9 +345,8 @@ __global__ void small_subtree_kernel(const int *__restrict__ small, const int *_
         st_lo[sp] = rl; st_hi[sp] = rl + Lc; st_nd[sp] = l; ++sp;
     }
     if (lane < m) {
-        for (int k = 0; k < DM; ++k) {
-            if (k < d) { x32[(size_t)k * n + b0 + lane] = c32[k]; x64[(size_t)k * n + b0 + lane] = c64[k]; }
-        }
+        for (int k = 0; k < DM; ++k)
+            if (k < d) x32[(size_t)k * n + b0 + lane] = c32[k];
         pid[b0 + lane] = myid;
     }
     if (lane == 0) atomicMax(max_depth, mdepth);
@@ -449,6 +441,11 @@ int build_tree(Points &P, Tree &T, Arena &ar, cudaStream_t st, int *pinned)
     T.arrive = ar.get<int>(N);
     int *depth = ar.get<int>(N);
     int *maxdep = ar.get<int>(1);
+    // final (tree-order) point arrays; the ingest arrays (input order) become the first
+    // ping-pong buffer of the top levels
+    float *f32 = ar.get<float>((size_t)n * d);
+    int *fpid = ar.get<int>(n);
+    double *f64 = ar.get<double>((size_t)n * d);
     if (ar.failed) return WM_ENOMEM;
     // root
     int h0[6] = {0, n, -1, -1, -1, 0};
@@ -473,9 +470,10 @@ int build_tree(Points &P, Tree &T, Arena &ar, cudaStream_t st, int *pinned)
     int *cnt = ar.get<int>(N), *curl = ar.get<int>(N), *curr = ar.get<int>(N);
     int *small = ar.get<int>(n / 2 + 2), *small_sz = ar.get<int>(n / 2 + 2), *small_base = ar.get<int>(n / 2 + 2);
     float *t32 = ar.get<float>((size_t)n * d);
-    double *t64 = ar.get<double>((size_t)n * d);
     int *tpid = ar.get<int>(n);
     if (ar.failed) return WM_ENOMEM;
+    float *r32 = P.x32, *w32 = t32;   // level buffers: read, write
+    int *rpid = P.pid, *wpid = tpid;
 
     int A = 0, S = 0, next_id = 1;
     if (n > 32) {
@@ -484,6 +482,10 @@ int build_tree(Points &P, Tree &T, Arena &ar, cudaStream_t st, int *pinned)
     } else if (n > 1) {
         cudaMemsetAsync(small, 0, sizeof(int), st);
         S = 1;
+    }
+    if (A == 0) {   // no top level: the points go to their final arrays as they are
+        cudaMemcpyAsync(f32, P.x32, sizeof(float) * n * d, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(fpid, P.pid, sizeof(int) * n, cudaMemcpyDeviceToDevice, st);
     }
     cudaMemsetAsync(curl, 0, sizeof(int) * N, st);
     cudaMemsetAsync(curr, 0, sizeof(int) * N, st);
@@ -496,14 +498,15 @@ int build_tree(Points &P, Tree &T, Arena &ar, cudaStream_t st, int *pinned)
         if (rc) return rc;
         const int gw = 152 * 8;   // blocks of 256 threads, 8 warps each
         launch(box_init_kernel, grid_for(A, 256, 1 << 20), 256, 0, st, act, A, N, d, T.lo, T.hi, cnt);
-        launch(box_units_kernel, gw, 256, 0, st, L, tot, T.begin, T.end, P.x32, n, N, d, T.lo, T.hi);
+        launch(box_units_kernel, gw, 256, 0, st, L, tot, T.begin, T.end, r32, n, N, d, T.lo, T.hi);
         launch(split_kernel, grid_for(A, 256, 1 << 20), 256, 0, st, act, A, N, d, T.lo, T.hi, sdim, sval);
-        launch(count_units_kernel, gw, 256, 0, st, L, tot, T.begin, T.end, P.x32, n, sdim, sval, cnt);
+        launch(count_units_kernel, gw, 256, 0, st, L, tot, T.begin, T.end, r32, n, sdim, sval, cnt);
         launch(children_kernel, grid_for(A, 256, 1 << 20), 256, 0, st, act, A, next_id, T.begin, T.end, T.left, T.right,
                                                                    T.parent, cnt, depth, csplit, isbig, issmall);
-        launch(scatter_units_kernel, gw, 256, 0, st, L, tot, T.begin, T.end, P.x32, P.x64, P.pid, n, d, sdim, sval, csplit,
-                                                 cnt, curl, curr, t32, t64, tpid);
-        launch(copyback_units_kernel, gw, 256, 0, st, L, tot, T.begin, T.end, P.x32, P.x64, P.pid, n, d, t32, t64, tpid);
+        launch(scatter_units_kernel, gw, 256, 0, st, L, tot, T.begin, T.end, r32, rpid, n, d, sdim, sval, csplit,
+                                                 cnt, curl, curr, w32, wpid, f32, fpid);
+        std::swap(r32, w32);
+        std::swap(rpid, wpid);
         // next lists
         rc = scan_exclusive_i32(isbig, prebig, 2 * A, tot + 1, st, ar);
         if (rc) return rc;
@@ -527,7 +530,7 @@ int build_tree(Points &P, Tree &T, Arena &ar, cudaStream_t st, int *pinned)
         launch(add_const_kernel, grid_for(S, 256, 1 << 20), 256, 0, st, small_base, S, next_id);
         int blocks = (S + 7) / 8;
 #define WM_SMALL(DM) launch(small_subtree_kernel<DM>, blocks, 256, 0, st, small, small_base, S, T.begin, T.end, T.left, \
-        T.right, T.parent, depth, T.lo, T.hi, P.x32, P.x64, P.pid, n, N, d, maxdep)
+        T.right, T.parent, depth, T.lo, T.hi, f32, fpid, n, N, d, maxdep)
         if (d <= 2) WM_SMALL(2);
         else if (d <= 3) WM_SMALL(3);
         else if (d <= 4) WM_SMALL(4);
@@ -540,6 +543,10 @@ int build_tree(Points &P, Tree &T, Arena &ar, cudaStream_t st, int *pinned)
         int m1 = -1;
         cudaMemcpyAsync(T.left, &m1, sizeof(int), cudaMemcpyHostToDevice, st);
     }
+    launch(gather64_kernel, grid_for((long long)n * d, 256), 256, 0, st, P.x64, fpid, n, d, f64);
+    P.x32 = f32;
+    P.pid = fpid;
+    P.x64 = f64;
     launch(finish_boxes_kernel, grid_for(N, 256), 256, 0, st, N, n, d, T.begin, T.left, P.x32, T.lo, T.hi, P.delta, T.diam2,
                                                          depth, maxdep);
     launch(inverse_perm_kernel, grid_for(n, 256, 1 << 20), 256, 0, st, P.pid, P.pos, n);
