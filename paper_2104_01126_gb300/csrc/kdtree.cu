@@ -58,7 +58,8 @@ constexpr int kUnit = 256;   // points per warp work-unit
 struct Level {
     const int *act;      // active node ids (size > 32)
     int A;
-    const int *unit_off; // [A+1] prefix of units per node
+    const int *unit_off; // [A] prefix of work-units per node
+    const long long *tot;   // (A << 32) | total work-units, on the device
 };
 
 __device__ inline int find_unit_node(const int *__restrict__ unit_off, int A, int u)
@@ -71,38 +72,52 @@ __device__ inline int find_unit_node(const int *__restrict__ unit_off, int A, in
     return lo;
 }
 
-__global__ void units_count_kernel(const int *__restrict__ act, int A, const int *__restrict__ nbegin,
-                                   const int *__restrict__ nend, int *__restrict__ units)
+__device__ inline void init_node_box(int nd, int N, int d, float *lo, float *hi, int *cnt)
 {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < A) {
-        int nd = act[j];
-        int sz = nend[nd] - nbegin[nd];
-        units[j] = (sz + kUnit - 1) / kUnit;
-    }
+    for (int k = 0; k < d; ++k) { lo[(size_t)k * N + nd] = INFINITY; hi[(size_t)k * N + nd] = -INFINITY; }
+    cnt[nd] = 0;
 }
 
-__global__ void box_init_kernel(const int *__restrict__ act, int A, int N, int d, float *lo, float *hi, int *cnt)
+// the root as the first level's only active node
+__global__ void level0_kernel(int n, int N, int d, float *lo, float *hi, int *cnt, int *act, int *unit_off,
+                              long long *tot)
 {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < A) {
-        int nd = act[j];
-        for (int k = 0; k < d; ++k) { lo[(size_t)k * N + nd] = INFINITY; hi[(size_t)k * N + nd] = -INFINITY; }
-        cnt[nd] = 0;
-    }
+    init_node_box(0, N, d, lo, hi, cnt);
+    act[0] = 0;
+    unit_off[0] = 0;
+    *tot = (1LL << 32) | (long long)((n + kUnit - 1) / kUnit);
 }
 
-__global__ void box_units_kernel(Level L, const int *__restrict__ total_units, const int *__restrict__ nbegin,
-                                 const int *__restrict__ nend, const float *__restrict__ x32, int n, int N, int d,
-                                 float *lo, float *hi)
+// True for the warp whose unit of node nd completed the node's units (one per node and phase);
+// the counter is left at 0 for the next phase.  The caller's global writes of the phase precede.
+__device__ inline bool last_unit(int *ucnt, int nd, int nunits)
 {
     const int lane = threadIdx.x & 31;
-    const int TU = *total_units;
+    __threadfence();
+    int done = 0;
+    if (lane == 0) {
+        done = atomicAdd(&ucnt[nd], 1) == nunits - 1;
+        if (done) ucnt[nd] = 0;
+    }
+    done = __shfl_sync(0xffffffffu, done, 0);
+    if (done) __threadfence();
+    return done;
+}
+
+// Box of every active node from its units; the unit that completes a node picks the split: the
+// midpoint of the widest dimension.
+__global__ void box_units_kernel(Level L, const int *__restrict__ nbegin, const int *__restrict__ nend,
+                                 const float *__restrict__ x32, int n, int N, int d, float *lo, float *hi, int *ucnt,
+                                 int *__restrict__ sdim, float *__restrict__ sval)
+{
+    const int lane = threadIdx.x & 31;
+    const int TU = (int)(*L.tot & 0xffffffffLL);
     for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < TU; u += (gridDim.x * blockDim.x) >> 5) {
         int j = find_unit_node(L.unit_off, L.A, u);
         int nd = L.act[j];
-        int b = nbegin[nd] + (u - L.unit_off[j]) * kUnit;
-        int e = min(b + kUnit, nend[nd]);
+        const int nb = nbegin[nd], ne = nend[nd];
+        int b = nb + (u - L.unit_off[j]) * kUnit;
+        int e = min(b + kUnit, ne);
         for (int k = 0; k < d; ++k) {
             float mn = INFINITY, mx = -INFINITY;
             for (int i = b + lane; i < e; i += 32) {
@@ -119,77 +134,89 @@ __global__ void box_units_kernel(Level L, const int *__restrict__ total_units, c
                 atomicMaxF(&hi[(size_t)k * N + nd], mx);
             }
         }
-    }
-}
-
-__global__ void split_kernel(const int *__restrict__ act, int A, int N, int d, const float *__restrict__ lo,
-                             const float *__restrict__ hi, int *__restrict__ sdim, float *__restrict__ sval)
-{
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < A) {
-        int nd = act[j];
-        int best = 0;
-        float ext = -1.f;
-        for (int k = 0; k < d; ++k) {
-            float e = hi[(size_t)k * N + nd] - lo[(size_t)k * N + nd];
-            if (e > ext) { ext = e; best = k; }
+        if (last_unit(ucnt, nd, (ne - nb + kUnit - 1) / kUnit) && lane == 0) {
+            int best = 0;
+            float ext = -1.f;
+            for (int k = 0; k < d; ++k) {
+                float ee = *(volatile float *)&hi[(size_t)k * N + nd] - *(volatile float *)&lo[(size_t)k * N + nd];
+                if (ee > ext) { ext = ee; best = k; }
+            }
+            float l = *(volatile float *)&lo[(size_t)best * N + nd], h = *(volatile float *)&hi[(size_t)best * N + nd];
+            sdim[j] = best;
+            sval[j] = l + (h - l) * 0.5f;
         }
-        float l = lo[(size_t)best * N + nd], h = hi[(size_t)best * N + nd];
-        sdim[j] = best;
-        sval[j] = l + (h - l) * 0.5f;
     }
 }
 
-__global__ void count_units_kernel(Level L, const int *__restrict__ total_units, const int *__restrict__ nbegin,
-                                   const int *__restrict__ nend, const float *__restrict__ x32, int n,
-                                   const int *__restrict__ sdim, const float *__restrict__ sval, int *cnt)
+// Left-side counts from the units; the unit that completes a node creates its two children and
+// the flags of the next level's lists: bigu[2j + s] = (child is active) << 32 | its work-units,
+// is_small[2j + s] = child has 2..32 points.
+__global__ void count_units_kernel(Level L, int next_id, int *nbegin, int *nend, int *nleft, int *nright, int *nparent,
+                                   int *__restrict__ ndepth, const float *__restrict__ x32, int n,
+                                   const int *__restrict__ sdim, const float *__restrict__ sval, int *cnt, int *ucnt,
+                                   int *__restrict__ count_split, long long *__restrict__ bigu,
+                                   int *__restrict__ is_small)
 {
     const int lane = threadIdx.x & 31;
-    const int TU = *total_units;
+    const int TU = (int)(*L.tot & 0xffffffffLL);
     for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < TU; u += (gridDim.x * blockDim.x) >> 5) {
         int j = find_unit_node(L.unit_off, L.A, u);
         int nd = L.act[j];
-        int b = nbegin[nd] + (u - L.unit_off[j]) * kUnit;
-        int e = min(b + kUnit, nend[nd]);
+        const int nb = nbegin[nd], ne = nend[nd];
+        int b = nb + (u - L.unit_off[j]) * kUnit;
+        int e = min(b + kUnit, ne);
         int k = sdim[j];
         float s = sval[j];
         int c = 0;
         for (int i = b + lane; i < e; i += 32) c += x32[(size_t)k * n + i] < s ? 1 : 0;
         for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
         if (lane == 0 && c) atomicAdd(&cnt[nd], c);
+        if (last_unit(ucnt, nd, (ne - nb + kUnit - 1) / kUnit) && lane == 0) {
+            const int sz = ne - nb;
+            int Lc = *(volatile int *)&cnt[nd];
+            int cs = 0;
+            if (Lc == 0 || Lc == sz) { Lc = sz / 2; cs = 1; }   // all points on one side: split by count
+            count_split[j] = cs;
+            cnt[nd] = Lc;
+            const int l = next_id + 2 * j, r = l + 1;
+            nleft[nd] = l; nright[nd] = r;
+            nbegin[l] = nb; nend[l] = nb + Lc; nbegin[r] = nb + Lc; nend[r] = ne;
+            nparent[l] = nd; nparent[r] = nd;
+            nleft[l] = nright[l] = nleft[r] = nright[r] = -1;
+            ndepth[l] = ndepth[r] = ndepth[nd] + 1;
+            const int sl = Lc, sr = sz - Lc;
+            bigu[2 * j] = sl > 32 ? (1LL << 32) | (long long)((sl + kUnit - 1) / kUnit) : 0;
+            bigu[2 * j + 1] = sr > 32 ? (1LL << 32) | (long long)((sr + kUnit - 1) / kUnit) : 0;
+            is_small[2 * j] = sl > 1 && sl <= 32;
+            is_small[2 * j + 1] = sr > 1 && sr <= 32;
+        }
     }
 }
 
-// Children of each active node; classification flags for the next level lists.
-__global__ void children_kernel(const int *__restrict__ act, int A, int next_id, int *nbegin, int *nend,
-                                int *nleft, int *nright, int *nparent, int *__restrict__ cnt, int *__restrict__ ndepth,
-                                int *__restrict__ count_split, int *__restrict__ is_big, int *__restrict__ is_small)
+// The next level's lists from the flags and their prefixes; a new active node gets its work-unit
+// offset and an empty box.
+__global__ void next_level_kernel(const long long *__restrict__ bigu, const long long *__restrict__ prebigu,
+                                  const int *__restrict__ is_small, const int *__restrict__ presmall, int m, int next_id,
+                                  int N, int d, int *__restrict__ act, int *__restrict__ unit_off,
+                                  int *__restrict__ small, float *lo, float *hi, int *cnt)
 {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < A) {
-        int nd = act[j];
-        int b = nbegin[nd], e = nend[nd], sz = e - b;
-        int Lc = cnt[nd];
-        int cs = 0;
-        if (Lc == 0 || Lc == sz) { Lc = sz / 2; cs = 1; }
-        count_split[j] = cs;
-        cnt[nd] = Lc;
-        int l = next_id + 2 * j, r = l + 1;
-        nleft[nd] = l; nright[nd] = r;
-        nbegin[l] = b; nend[l] = b + Lc; nbegin[r] = b + Lc; nend[r] = e;
-        nparent[l] = nd; nparent[r] = nd;
-        nleft[l] = nright[l] = nleft[r] = nright[r] = -1;
-        ndepth[l] = ndepth[r] = ndepth[nd] + 1;
-        int sl = Lc, sr = sz - Lc;
-        is_big[2 * j] = sl > 32; is_big[2 * j + 1] = sr > 32;
-        is_small[2 * j] = sl > 1 && sl <= 32; is_small[2 * j + 1] = sr > 1 && sr <= 32;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const int id = next_id + i;
+        if (bigu[i]) {
+            const long long pre = prebigu[i];
+            const int k = (int)(pre >> 32);
+            act[k] = id;
+            unit_off[k] = (int)(pre & 0xffffffffLL);
+            init_node_box(id, N, d, lo, hi, cnt);
+        }
+        if (is_small[i]) small[presmall[i]] = id;
     }
 }
 
 // Partition of each active node's points by its split.  The points of a child that stays active
 // (more than 32 points) go to the other ping-pong buffer (w32, wpid); those of a child that leaves
 // the top levels go straight to their final place (f32, fpid), which no active node reads.
-__global__ void scatter_units_kernel(Level L, const int *__restrict__ total_units, const int *__restrict__ nbegin,
+__global__ void scatter_units_kernel(Level L, const int *__restrict__ nbegin,
                                      const int *__restrict__ nend, const float *__restrict__ x32,
                                      const int *__restrict__ pid, int n, int d, const int *__restrict__ sdim,
                                      const float *__restrict__ sval, const int *__restrict__ count_split,
@@ -198,7 +225,7 @@ __global__ void scatter_units_kernel(Level L, const int *__restrict__ total_unit
                                      int *__restrict__ fpid)
 {
     const int lane = threadIdx.x & 31;
-    const int TU = *total_units;
+    const int TU = (int)(*L.tot & 0xffffffffLL);
     for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < TU; u += (gridDim.x * blockDim.x) >> 5) {
         int j = find_unit_node(L.unit_off, L.A, u);
         int nd = L.act[j];
@@ -252,31 +279,42 @@ __global__ void gather64_kernel(const double *__restrict__ src, const int *__res
     }
 }
 
-// compaction of the next level's lists: out[prefix[i]] = value(i) where flag[i]
-__global__ void compact_children_kernel(const int *__restrict__ flag, const int *__restrict__ pre, int m,
-                                        int next_id, int *__restrict__ out)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m && flag[i]) out[pre[i]] = next_id + i;
-}
-
 // ------------------------------------------------------------------ warp-local small subtrees
-// One warp per node of 2..32 points.  Node ids of the subtree: base + 0 .. base + 2m - 3.
-template <int DM>
-__global__ void small_subtree_kernel(const int *__restrict__ small, const int *__restrict__ small_base, int S,
-                                     int *nbegin, int *nend, int *nleft, int *nright, int *nparent, int *ndepth,
-                                     float *lo, float *hi, float *x32, int *pid, int n, int N, int d, int *max_depth)
+// float <-> unsigned key of the same order, for the warp min/max reductions on integers
+__device__ inline unsigned f2key(float f)
 {
-    const int lane = threadIdx.x & 31;
+    const unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : u | 0x80000000u;
+}
+__device__ inline float key2f(unsigned k) { return __uint_as_float((k & 0x80000000u) ? k & 0x7fffffffu : ~k); }
+
+// One warp per node of 2..32 points.  Node ids of the subtree: base + 0 .. base + 2m - 3.  The
+// points stay in registers (lane = position in the node's range); a split permutes them through
+// the warp's shared-memory slots.
+template <int DM>
+__global__ void __launch_bounds__(256) small_subtree_kernel(const int *__restrict__ small,
+                                                            const int *__restrict__ small_base, int S, int *nbegin,
+                                                            int *nend, int *nleft, int *nright, int *nparent,
+                                                            int *ndepth, float *lo, float *hi, float *x32, int *pid,
+                                                            int n, int N, int d, int *max_depth)
+{
+    __shared__ float shx[8][DM * 32];
+    __shared__ int shid[8][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (wid >= S) return;
+    float *sx = shx[wib];
+    int *sid = shid[wib];
     const int root = small[wid];
     int next = small_base[wid];
     const int b0 = nbegin[root];
     const int m = nend[root] - b0;
     float c32[DM];
     int myid = -1;
+#pragma unroll
+    for (int k = 0; k < DM; ++k) c32[k] = 0.f;
     if (lane < m) {
+#pragma unroll
         for (int k = 0; k < DM; ++k)
             if (k < d) c32[k] = x32[(size_t)k * n + b0 + lane];
         myid = pid[b0 + lane];
@@ -295,40 +333,42 @@ __global__ void small_subtree_kernel(const int *__restrict__ small, const int *_
         mdepth = max(mdepth, dep);
         // box over the lanes in range
         int best = 0;
-        float ext = -1.f, bl = 0.f, bh = 0.f;
+        float ext = -1.f, bl = 0.f, bh = 0.f, cv = 0.f;
+#pragma unroll
         for (int k = 0; k < DM; ++k) {
             if (k >= d) break;
-            float mn = in ? c32[k] : INFINITY, mx = in ? c32[k] : -INFINITY;
-            for (int o = 16; o; o >>= 1) {
-                mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            }
+            const unsigned key = f2key(c32[k]);
+            const float mn = key2f(__reduce_min_sync(0xffffffffu, in ? key : 0xffffffffu));
+            const float mx = key2f(__reduce_max_sync(0xffffffffu, in ? key : 0u));
             if (lane == 0) { lo[(size_t)k * N + nd] = mn; hi[(size_t)k * N + nd] = mx; }
-            if (mx - mn > ext) { ext = mx - mn; best = k; bl = mn; bh = mx; }
+            if (mx - mn > ext) { ext = mx - mn; best = k; bl = mn; bh = mx; cv = c32[k]; }
         }
         if (sz == 1) continue;   // leaf: box = the point
         float sv = bl + (bh - bl) * 0.5f;
-        float cv = 0.f;
-        for (int k = 0; k < DM; ++k) if (k == best) cv = c32[k];
         bool fl = in && cv < sv;
         unsigned bal = __ballot_sync(0xffffffffu, fl);
         int Lc = __popc(bal);
         bool cs = (Lc == 0 || Lc == sz);
         if (cs) { Lc = sz / 2; fl = in && (lane - rl) < Lc; bal = __ballot_sync(0xffffffffu, fl); }
         unsigned bar = __ballot_sync(0xffffffffu, in && !fl);
-        int dst = lane;
-        if (in) dst = fl ? rl + __popc(bal & lanemask_lt()) : rl + Lc + __popc(bar & lanemask_lt());
-        // permute: lane dst receives from this lane; build the inverse with a shuffle search
-        int src = lane;
-        for (int q = 0; q < 32; ++q) {
-            int dq = __shfl_sync(0xffffffffu, dst, q);
-            if (dq == lane) src = q;
+        if (!cs) {
+            // permute the lanes in range: this lane's point moves to position dst
+            const int dst = fl ? rl + __popc(bal & lanemask_lt()) : rl + Lc + __popc(bar & lanemask_lt());
+            if (in) {
+#pragma unroll
+                for (int k = 0; k < DM; ++k)
+                    if (k < d) sx[k * 32 + dst] = c32[k];
+                sid[dst] = myid;
+            }
+            __syncwarp();
+            if (in) {
+#pragma unroll
+                for (int k = 0; k < DM; ++k)
+                    if (k < d) c32[k] = sx[k * 32 + lane];
+                myid = sid[lane];
+            }
+            __syncwarp();
         }
-        for (int k = 0; k < DM; ++k) {
-            if (k >= d) break;
-            c32[k] = __shfl_sync(0xffffffffu, c32[k], src);
-        }
-        myid = __shfl_sync(0xffffffffu, myid, src);
         int l = next, r = next + 1;
         next += 2;
         if (lane == 0) {
@@ -345,6 +385,7 @@ __global__ void small_subtree_kernel(const int *__restrict__ small, const int *_
         st_lo[sp] = rl; st_hi[sp] = rl + Lc; st_nd[sp] = l; ++sp;
     }
     if (lane < m) {
+#pragma unroll
         for (int k = 0; k < DM; ++k)
             if (k < d) x32[(size_t)k * n + b0 + lane] = c32[k];
         pid[b0 + lane] = myid;
@@ -460,14 +501,15 @@ int build_tree(Points &P, Tree &T, Arena &ar, cudaStream_t st, int *pinned)
     size_t mark = ar.off;
     // scratch
     int *act = ar.get<int>(n / 16 + 2), *act2 = ar.get<int>(n / 16 + 2);
-    int *units = ar.get<int>(n / 16 + 3);
-    int *tot = ar.get<int>(4);
+    int *uoff = ar.get<int>(n / 16 + 2), *uoff2 = ar.get<int>(n / 16 + 2);
+    long long *tot = ar.get<long long>(2);
+    int *tsmall = ar.get<int>(2);
     int *sdim = ar.get<int>(n / 16 + 2);
     float *sval = ar.get<float>(n / 16 + 2);
     int *csplit = ar.get<int>(n / 16 + 2);
-    int *isbig = ar.get<int>(n / 8 + 4), *issmall = ar.get<int>(n / 8 + 4);
-    int *prebig = ar.get<int>(n / 8 + 4), *presmall = ar.get<int>(n / 8 + 4);
-    int *cnt = ar.get<int>(N), *curl = ar.get<int>(N), *curr = ar.get<int>(N);
+    long long *bigu = ar.get<long long>(n / 8 + 4), *prebigu = ar.get<long long>(n / 8 + 4);
+    int *issmall = ar.get<int>(n / 8 + 4), *presmall = ar.get<int>(n / 8 + 4);
+    int *cnt = ar.get<int>(N), *curl = ar.get<int>(N), *curr = ar.get<int>(N), *ucnt = ar.get<int>(N);
     int *small = ar.get<int>(n / 2 + 2), *small_sz = ar.get<int>(n / 2 + 2), *small_base = ar.get<int>(n / 2 + 2);
     float *t32 = ar.get<float>((size_t)n * d);
     int *tpid = ar.get<int>(n);
@@ -477,7 +519,7 @@ int build_tree(Points &P, Tree &T, Arena &ar, cudaStream_t st, int *pinned)
 
     int A = 0, S = 0, next_id = 1;
     if (n > 32) {
-        cudaMemsetAsync(act, 0, sizeof(int), st);   // act[0] = root (0)
+        launch(level0_kernel, 1, 1, 0, st, n, N, d, T.lo, T.hi, cnt, act, uoff, tot);
         A = 1;
     } else if (n > 1) {
         cudaMemsetAsync(small, 0, sizeof(int), st);
@@ -489,43 +531,44 @@ int build_tree(Points &P, Tree &T, Arena &ar, cudaStream_t st, int *pinned)
     }
     cudaMemsetAsync(curl, 0, sizeof(int) * N, st);
     cudaMemsetAsync(curr, 0, sizeof(int) * N, st);
+    cudaMemsetAsync(ucnt, 0, sizeof(int) * N, st);
     int levels = 0;
+    long long *tcur = tot, *tnext = tot + 1;
     while (A > 0) {
         ++levels;
-        Level L{act, A, units};
-        launch(units_count_kernel, grid_for(A, 256, 1 << 20), 256, 0, st, act, A, T.begin, T.end, units);
-        int rc = scan_exclusive_i32(units, units, A, tot, st, ar);
-        if (rc) return rc;
+        const Level L{act, A, uoff, tcur};
         const int gw = 152 * 8;   // blocks of 256 threads, 8 warps each
-        launch(box_init_kernel, grid_for(A, 256, 1 << 20), 256, 0, st, act, A, N, d, T.lo, T.hi, cnt);
-        launch(box_units_kernel, gw, 256, 0, st, L, tot, T.begin, T.end, r32, n, N, d, T.lo, T.hi);
-        launch(split_kernel, grid_for(A, 256, 1 << 20), 256, 0, st, act, A, N, d, T.lo, T.hi, sdim, sval);
-        launch(count_units_kernel, gw, 256, 0, st, L, tot, T.begin, T.end, r32, n, sdim, sval, cnt);
-        launch(children_kernel, grid_for(A, 256, 1 << 20), 256, 0, st, act, A, next_id, T.begin, T.end, T.left, T.right,
-                                                                   T.parent, cnt, depth, csplit, isbig, issmall);
-        launch(scatter_units_kernel, gw, 256, 0, st, L, tot, T.begin, T.end, r32, rpid, n, d, sdim, sval, csplit,
-                                                 cnt, curl, curr, w32, wpid, f32, fpid);
+        launch(box_units_kernel, gw, 256, 0, st, L, T.begin, T.end, r32, n, N, d, T.lo, T.hi, ucnt, sdim, sval);
+        launch(count_units_kernel, gw, 256, 0, st, L, next_id, T.begin, T.end, T.left, T.right, T.parent, depth, r32, n,
+                                                sdim, sval, cnt, ucnt, csplit, bigu, issmall);
+        launch(scatter_units_kernel, gw, 256, 0, st, L, T.begin, T.end, r32, rpid, n, d, sdim, sval, csplit, cnt, curl,
+                                                  curr, w32, wpid, f32, fpid);
         std::swap(r32, w32);
         std::swap(rpid, wpid);
         // next lists
-        rc = scan_exclusive_i32(isbig, prebig, 2 * A, tot + 1, st, ar);
+        int rc = scan_exclusive_i64(bigu, prebigu, 2 * A, tnext, st, ar);
         if (rc) return rc;
-        rc = scan_exclusive_i32(issmall, presmall, 2 * A, tot + 2, st, ar);
+        rc = scan_exclusive_i32(issmall, presmall, 2 * A, tsmall, st, ar);
         if (rc) return rc;
-        launch(compact_children_kernel, grid_for(2 * A, 256, 1 << 20), 256, 0, st, isbig, prebig, 2 * A, next_id, act2);
-        launch(compact_children_kernel, grid_for(2 * A, 256, 1 << 20), 256, 0, st, issmall, presmall, 2 * A, next_id,
-                                                                               small + S);
-        cudaMemcpyAsync(pinned, tot + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
+        launch(next_level_kernel, grid_for(2 * A, 256, 1 << 20), 256, 0, st, bigu, prebigu, issmall, presmall, 2 * A,
+                                                                        next_id, N, d, act2, uoff2, small + S, T.lo, T.hi,
+                                                                        cnt);
+        cudaMemcpyAsync(pinned, tnext, sizeof(long long), cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(pinned + 2, tsmall, sizeof(int), cudaMemcpyDeviceToHost, st);
         if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;
         next_id += 2 * A;
-        A = pinned[0];
-        S += pinned[1];
-        int *t = act; act = act2; act2 = t;
+        long long tn;
+        memcpy(&tn, pinned, sizeof tn);
+        A = (int)(tn >> 32);
+        S += pinned[2];
+        std::swap(act, act2);
+        std::swap(uoff, uoff2);
+        std::swap(tcur, tnext);
     }
     // sizes of the small roots and their node-id bases
     if (S > 0) {
         launch(small_sizes_kernel, grid_for(S, 256, 1 << 20), 256, 0, st, small, S, T.begin, T.end, small_sz);
-        int rc = scan_exclusive_i32(small_sz, small_base, S, tot + 3, st, ar);
+        int rc = scan_exclusive_i32(small_sz, small_base, S, tsmall + 1, st, ar);
         if (rc) return rc;
         launch(add_const_kernel, grid_for(S, 256, 1 << 20), 256, 0, st, small_base, S, next_id);
         int blocks = (S + 7) / 8;
