@@ -57,10 +57,21 @@ constexpr int kUnit = 256;   // points per warp work-unit
 
 struct Level {
     const int *act;      // active node ids (size > 32)
-    int A;
     const int *unit_off; // [A] prefix of work-units per node
     const long long *tot;   // (A << 32) | total work-units, on the device
 };
+
+// Per-level scalars kept on the device, so that several levels run between host syncs:
+// [0] first node id of the level's children, [1] offset of its small roots in the small list,
+// [2] 2 A (length of the child flag arrays), [3] A.
+__global__ void level_begin_kernel(const long long *__restrict__ tot, const int *__restrict__ tsmall, int *state)
+{
+    state[0] += state[2];
+    state[1] += *tsmall;
+    const int A = (int)(*tot >> 32);
+    state[3] = A;
+    state[2] = 2 * A;
+}
 
 __device__ inline int find_unit_node(const int *__restrict__ unit_off, int A, int u)
 {
@@ -111,9 +122,9 @@ __global__ void box_units_kernel(Level L, const int *__restrict__ nbegin, const 
                                  int *__restrict__ sdim, float *__restrict__ sval)
 {
     const int lane = threadIdx.x & 31;
-    const int TU = (int)(*L.tot & 0xffffffffLL);
+    const int TU = (int)(*L.tot & 0xffffffffLL), A = (int)(*L.tot >> 32);
     for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < TU; u += (gridDim.x * blockDim.x) >> 5) {
-        int j = find_unit_node(L.unit_off, L.A, u);
+        int j = find_unit_node(L.unit_off, A, u);
         int nd = L.act[j];
         const int nb = nbegin[nd], ne = nend[nd];
         int b = nb + (u - L.unit_off[j]) * kUnit;
@@ -151,16 +162,16 @@ __global__ void box_units_kernel(Level L, const int *__restrict__ nbegin, const 
 // Left-side counts from the units; the unit that completes a node creates its two children and
 // the flags of the next level's lists: bigu[2j + s] = (child is active) << 32 | its work-units,
 // is_small[2j + s] = child has 2..32 points.
-__global__ void count_units_kernel(Level L, int next_id, int *nbegin, int *nend, int *nleft, int *nright, int *nparent,
+__global__ void count_units_kernel(Level L, const int *__restrict__ state, int *nbegin, int *nend, int *nleft, int *nright, int *nparent,
                                    int *__restrict__ ndepth, const float *__restrict__ x32, int n,
                                    const int *__restrict__ sdim, const float *__restrict__ sval, int *cnt, int *ucnt,
                                    int *__restrict__ count_split, long long *__restrict__ bigu,
                                    int *__restrict__ is_small)
 {
     const int lane = threadIdx.x & 31;
-    const int TU = (int)(*L.tot & 0xffffffffLL);
+    const int TU = (int)(*L.tot & 0xffffffffLL), A = (int)(*L.tot >> 32);
     for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < TU; u += (gridDim.x * blockDim.x) >> 5) {
-        int j = find_unit_node(L.unit_off, L.A, u);
+        int j = find_unit_node(L.unit_off, A, u);
         int nd = L.act[j];
         const int nb = nbegin[nd], ne = nend[nd];
         int b = nb + (u - L.unit_off[j]) * kUnit;
@@ -178,7 +189,7 @@ __global__ void count_units_kernel(Level L, int next_id, int *nbegin, int *nend,
             if (Lc == 0 || Lc == sz) { Lc = sz / 2; cs = 1; }   // all points on one side: split by count
             count_split[j] = cs;
             cnt[nd] = Lc;
-            const int l = next_id + 2 * j, r = l + 1;
+            const int l = state[0] + 2 * j, r = l + 1;
             nleft[nd] = l; nright[nd] = r;
             nbegin[l] = nb; nend[l] = nb + Lc; nbegin[r] = nb + Lc; nend[r] = ne;
             nparent[l] = nd; nparent[r] = nd;
@@ -196,10 +207,12 @@ __global__ void count_units_kernel(Level L, int next_id, int *nbegin, int *nend,
 // The next level's lists from the flags and their prefixes; a new active node gets its work-unit
 // offset and an empty box.
 __global__ void next_level_kernel(const long long *__restrict__ bigu, const long long *__restrict__ prebigu,
-                                  const int *__restrict__ is_small, const int *__restrict__ presmall, int m, int next_id,
-                                  int N, int d, int *__restrict__ act, int *__restrict__ unit_off,
-                                  int *__restrict__ small, float *lo, float *hi, int *cnt)
+                                  const int *__restrict__ is_small, const int *__restrict__ presmall,
+                                  const int *__restrict__ state, int N, int d, int *__restrict__ act,
+                                  int *__restrict__ unit_off, int *__restrict__ small, float *lo, float *hi, int *cnt)
 {
+    const int m = state[2], next_id = state[0];
+    small += state[1];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
         const int id = next_id + i;
         if (bigu[i]) {
@@ -225,9 +238,9 @@ __global__ void scatter_units_kernel(Level L, const int *__restrict__ nbegin,
                                      int *__restrict__ fpid)
 {
     const int lane = threadIdx.x & 31;
-    const int TU = (int)(*L.tot & 0xffffffffLL);
+    const int TU = (int)(*L.tot & 0xffffffffLL), A = (int)(*L.tot >> 32);
     for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < TU; u += (gridDim.x * blockDim.x) >> 5) {
-        int j = find_unit_node(L.unit_off, L.A, u);
+        int j = find_unit_node(L.unit_off, A, u);
         int nd = L.act[j];
         int nb = nbegin[nd], ne = nend[nd];
         int b = nb + (u - L.unit_off[j]) * kUnit;
@@ -503,7 +516,7 @@ int build_tree(Points &P, Tree &T, Arena &ar, cudaStream_t st, int *pinned)
     int *act = ar.get<int>(n / 16 + 2), *act2 = ar.get<int>(n / 16 + 2);
     int *uoff = ar.get<int>(n / 16 + 2), *uoff2 = ar.get<int>(n / 16 + 2);
     long long *tot = ar.get<long long>(2);
-    int *tsmall = ar.get<int>(2);
+    int *tsmall = ar.get<int>(2), *lstate = ar.get<int>(4);
     int *sdim = ar.get<int>(n / 16 + 2);
     float *sval = ar.get<float>(n / 16 + 2);
     int *csplit = ar.get<int>(n / 16 + 2);
@@ -532,38 +545,57 @@ int build_tree(Points &P, Tree &T, Arena &ar, cudaStream_t st, int *pinned)
     cudaMemsetAsync(curl, 0, sizeof(int) * N, st);
     cudaMemsetAsync(curr, 0, sizeof(int) * N, st);
     cudaMemsetAsync(ucnt, 0, sizeof(int) * N, st);
-    int levels = 0;
+    {
+        const int init[4] = {1, 0, 0, 0};   // pageable source: copied before the call returns
+        cudaMemcpyAsync(lstate, init, sizeof init, cudaMemcpyHostToDevice, st);
+        cudaMemsetAsync(tsmall, 0, sizeof(int), st);
+    }
+    // Levels run kLevelsPerSync at a time with their counts on the device; the host sizes the
+    // launches from a bound on A (at most doubling per level, at most n / 33) and learns the
+    // real A at each sync.  Levels after the last active one find A = 0 and do nothing.
+    constexpr int kLevelsPerSync = 4;
+    const int amax = n / 33 + 1;
     long long *tcur = tot, *tnext = tot + 1;
+    int abound = A;
     while (A > 0) {
-        ++levels;
-        const Level L{act, A, uoff, tcur};
-        const int gw = 152 * 8;   // blocks of 256 threads, 8 warps each
-        launch(box_units_kernel, gw, 256, 0, st, L, T.begin, T.end, r32, n, N, d, T.lo, T.hi, ucnt, sdim, sval);
-        launch(count_units_kernel, gw, 256, 0, st, L, next_id, T.begin, T.end, T.left, T.right, T.parent, depth, r32, n,
-                                                sdim, sval, cnt, ucnt, csplit, bigu, issmall);
-        launch(scatter_units_kernel, gw, 256, 0, st, L, T.begin, T.end, r32, rpid, n, d, sdim, sval, csplit, cnt, curl,
-                                                  curr, w32, wpid, f32, fpid);
-        std::swap(r32, w32);
-        std::swap(rpid, wpid);
-        // next lists
-        int rc = scan_exclusive_i64(bigu, prebigu, 2 * A, tnext, st, ar);
-        if (rc) return rc;
-        rc = scan_exclusive_i32(issmall, presmall, 2 * A, tsmall, st, ar);
-        if (rc) return rc;
-        launch(next_level_kernel, grid_for(2 * A, 256, 1 << 20), 256, 0, st, bigu, prebigu, issmall, presmall, 2 * A,
-                                                                        next_id, N, d, act2, uoff2, small + S, T.lo, T.hi,
-                                                                        cnt);
-        cudaMemcpyAsync(pinned, tnext, sizeof(long long), cudaMemcpyDeviceToHost, st);
-        cudaMemcpyAsync(pinned + 2, tsmall, sizeof(int), cudaMemcpyDeviceToHost, st);
+        for (int g = 0; g < kLevelsPerSync; ++g) {
+            launch(level_begin_kernel, 1, 1, 0, st, tcur, tsmall, lstate);
+            const Level L{act, uoff, tcur};
+            const int gw = 152 * 8;   // blocks of 256 threads, 8 warps each
+            launch(box_units_kernel, gw, 256, 0, st, L, T.begin, T.end, r32, n, N, d, T.lo, T.hi, ucnt, sdim, sval);
+            launch(count_units_kernel, gw, 256, 0, st, L, lstate, T.begin, T.end, T.left, T.right, T.parent, depth, r32,
+                                                    n, sdim, sval, cnt, ucnt, csplit, bigu, issmall);
+            launch(scatter_units_kernel, gw, 256, 0, st, L, T.begin, T.end, r32, rpid, n, d, sdim, sval, csplit, cnt,
+                                                      curl, curr, w32, wpid, f32, fpid);
+            std::swap(r32, w32);
+            std::swap(rpid, wpid);
+            // next lists
+            int rc = scan_exclusive_i64_dev(bigu, prebigu, lstate + 2, 2 * abound, tnext, st, ar);
+            if (rc) return rc;
+            rc = scan_exclusive_i32_dev(issmall, presmall, lstate + 2, 2 * abound, tsmall, st, ar);
+            if (rc) return rc;
+            launch(next_level_kernel, grid_for(2 * abound, 256, 1 << 20), 256, 0, st, bigu, prebigu, issmall, presmall,
+                                                                                 lstate, N, d, act2, uoff2, small, T.lo,
+                                                                                 T.hi, cnt);
+            std::swap(act, act2);
+            std::swap(uoff, uoff2);
+            std::swap(tcur, tnext);
+            abound = std::min(2 * abound, amax);
+        }
+        cudaMemcpyAsync(pinned, tcur, sizeof(long long), cudaMemcpyDeviceToHost, st);
         if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;
-        next_id += 2 * A;
         long long tn;
         memcpy(&tn, pinned, sizeof tn);
         A = (int)(tn >> 32);
-        S += pinned[2];
-        std::swap(act, act2);
-        std::swap(uoff, uoff2);
-        std::swap(tcur, tnext);
+        abound = A;
+    }
+    if (n > 32) {
+        // fold the last level's children and small roots into the totals
+        launch(level_begin_kernel, 1, 1, 0, st, tcur, tsmall, lstate);
+        cudaMemcpyAsync(pinned, lstate, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;
+        next_id = pinned[0];
+        S = pinned[1];
     }
     // sizes of the small roots and their node-id bases
     if (S > 0) {

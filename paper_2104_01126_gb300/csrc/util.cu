@@ -39,8 +39,10 @@ __device__ inline T block_exclusive_scan(T v, T *smem_warp, T &total)
 }
 
 template <typename T>
-__global__ void scan_reduce_kernel(const T *__restrict__ in, int n, T *__restrict__ block_sums)
+__global__ void scan_reduce_kernel(const T *__restrict__ in, int n, T *__restrict__ block_sums,
+                                   const int *__restrict__ n_dev)
 {
+    if (n_dev) n = min(n, *n_dev);
     __shared__ T sw[32];
     long long base = (long long)blockIdx.x * kScanTile;
     T s = 0;
@@ -56,8 +58,10 @@ __global__ void scan_reduce_kernel(const T *__restrict__ in, int n, T *__restric
 
 template <typename T>
 __global__ void scan_down_kernel(const T *__restrict__ in, T *__restrict__ out, int n,
-                                 const T *__restrict__ block_offs, T *total_dev, int nblocks)
+                                 const T *__restrict__ block_offs, T *total_dev, int nblocks,
+                                 const int *__restrict__ n_dev)
 {
+    if (n_dev) n = min(n, *n_dev);
     __shared__ T sw[32];
     long long base = (long long)blockIdx.x * kScanTile;
     T v[kScanItems];
@@ -93,8 +97,10 @@ void fill_i32(int *p, int v, size_t n, cudaStream_t st)
 }
 
 // out[i] = sum_{j<i} in[j]; *total_dev (optional, device) = sum of all.  in may equal out.
+// With n_dev, the length is min(n, *n_dev), read on the device (n is then a bound).
 template <typename T>
-static int scan_exclusive_t(const T *in, T *out, int n, T *total_dev, cudaStream_t st, Arena &ar)
+static int scan_exclusive_t(const T *in, T *out, int n, T *total_dev, cudaStream_t st, Arena &ar,
+                            const int *n_dev = nullptr)
 {
     if (n <= 0) {
         if (total_dev) cudaMemsetAsync(total_dev, 0, sizeof(T), st);
@@ -102,16 +108,17 @@ static int scan_exclusive_t(const T *in, T *out, int n, T *total_dev, cudaStream
     }
     int nb = (n + kScanTile - 1) / kScanTile;
     if (nb == 1) {
-        launch(scan_down_kernel<T>, 1, kScanBlock, 0, st, in, out, n, (const T *)nullptr, total_dev, 1);
+        launch(scan_down_kernel<T>, 1, kScanBlock, 0, st, in, out, n, (const T *)nullptr, total_dev, 1, n_dev);
         return 0;
     }
     size_t mark = ar.off;
     T *sums = ar.get<T>(nb);
     if (!sums) return WM_ENOMEM;
-    launch(scan_reduce_kernel<T>, nb, kScanBlock, 0, st, in, n, sums);
+    // blocks past the device length contribute 0, so the last block still writes the total
+    launch(scan_reduce_kernel<T>, nb, kScanBlock, 0, st, in, n, sums, n_dev);
     int rc = scan_exclusive_t<T>(sums, sums, nb, (T *)nullptr, st, ar);
     if (rc) return rc;
-    launch(scan_down_kernel<T>, nb, kScanBlock, 0, st, in, out, n, (const T *)sums, total_dev, nb);
+    launch(scan_down_kernel<T>, nb, kScanBlock, 0, st, in, out, n, (const T *)sums, total_dev, nb, n_dev);
     ar.off = mark;
     return 0;
 }
@@ -124,6 +131,18 @@ int scan_exclusive_i32(const int *in, int *out, int n, int *total_dev, cudaStrea
 int scan_exclusive_i64(const long long *in, long long *out, int n, long long *total_dev, cudaStream_t st, Arena &ar)
 {
     return scan_exclusive_t<long long>(in, out, n, total_dev, st, ar);
+}
+
+int scan_exclusive_i32_dev(const int *in, int *out, const int *n_dev, int n_max, int *total_dev, cudaStream_t st,
+                           Arena &ar)
+{
+    return scan_exclusive_t<int>(in, out, n_max, total_dev, st, ar, n_dev);
+}
+
+int scan_exclusive_i64_dev(const long long *in, long long *out, const int *n_dev, int n_max, long long *total_dev,
+                           cudaStream_t st, Arena &ar)
+{
+    return scan_exclusive_t<long long>(in, out, n_max, total_dev, st, ar, n_dev);
 }
 
 // ------------------------------------------------------------------------------ radix sort

@@ -192,6 +192,11 @@ __device__ inline int block_append(int *counter, int cnt, int *sh)
 // util.cu
 int scan_exclusive_i32(const int *in, int *out, int n, int *total_dev, cudaStream_t st, Arena &ar);
 int scan_exclusive_i64(const long long *in, long long *out, int n, long long *total_dev, cudaStream_t st, Arena &ar);
+// the same with the length read on the device: min(n_max, *n_dev)
+int scan_exclusive_i32_dev(const int *in, int *out, const int *n_dev, int n_max, int *total_dev, cudaStream_t st,
+                           Arena &ar);
+int scan_exclusive_i64_dev(const long long *in, long long *out, const int *n_dev, int n_max, long long *total_dev,
+                           cudaStream_t st, Arena &ar);
 // message for the last failure on this thread (read by wm_last_error_detail)
 void set_error_detail(const char *msg);
 // host_scratch: at least 16 KiB of host memory (pinned preferred) for the digit histogram readback
