@@ -132,7 +132,7 @@ static size_t estimate_bytes(long long n, int d, int min_pts, const Caps &c)
         long long kk = min_pts + 16;
         b += (size_t)n * 12 + (size_t)n * 8;            // cd64, cd32, node bounds
         b += (size_t)n * kk * 16 * 2;                   // repair edges + sort tmp
-        b += (size_t)n * 160;                           // dendrogram / Euler tour scratch
+        b += (size_t)n * 192;                           // dendrogram / Euler tour scratch
     }
     return b + (8u << 20) + (size_t)n * 64 + (size_t)c.extra_bytes;
 }
@@ -203,10 +203,13 @@ __global__ void sum_partials_kernel(const double *partial, int m, double *out)
     if (threadIdx.x == 0) *out = sm[0];
 }
 
-// appends the edges of src whose w2 lies in [lo, hi) to dst (non-negative doubles and +inf order
-// like their bit patterns)
-__global__ void take_range_kernel(const EdgeK *__restrict__ src, int m, double lo, double hi, EdgeK *__restrict__ dst,
-                                  int *count, int cap, unsigned *overflow)
+// Splits the repair edges src[0..m) at the start of a round's Kruskal: those whose w2 lies in
+// [lo, hi) join the batch dst, those at or above hi are kept for later rounds (rest), and those
+// whose endpoints are already connected are dropped (no later round can accept them).
+// Non-negative doubles and +inf order like their bit patterns.
+__global__ void take_range_kernel(const EdgeK *__restrict__ src, int m, double lo, double hi, const int *__restrict__ uf,
+                                  EdgeK *__restrict__ dst, int *count, int cap, EdgeK *__restrict__ rest,
+                                  int *rest_count, unsigned *overflow)
 {
     __shared__ int sh[32];
     const unsigned long long blo = (unsigned long long)__double_as_longlong(lo);
@@ -214,16 +217,24 @@ __global__ void take_range_kernel(const EdgeK *__restrict__ src, int m, double l
     for (int b0 = blockIdx.x * blockDim.x; b0 < m; b0 += gridDim.x * blockDim.x) {
         const int t = b0 + threadIdx.x;
         EdgeK e;
-        bool take = false;
+        bool take = false, keep = false;
         if (t < m) {
             e = src[t];
-            take = e.hi >= blo && e.hi < bhi;
+            int ru = edge_u(e), rv = edge_v(e);
+            for (int it = 0; it < 64 && uf[ru] != ru; ++it) ru = uf[ru];
+            for (int it = 0; it < 64 && uf[rv] != rv; ++it) rv = uf[rv];
+            if (uf[ru] != ru || uf[rv] != rv || ru != rv) {   // a chain longer than 64 is kept
+                take = e.hi >= blo && e.hi < bhi;
+                keep = e.hi >= bhi;
+            }
         }
-        const int slot = block_append(count, take ? 1 : 0, sh);
+        int slot = block_append(count, take ? 1 : 0, sh);
         if (take) {
             if (slot < cap) dst[slot] = e;
             else atomicOr(overflow, 2u);
         }
+        slot = block_append(rest_count, keep ? 1 : 0, sh);
+        if (keep) rest[slot] = e;
     }
 }
 
@@ -294,8 +305,8 @@ static void set_rho(TravArgs &a, double lo, double hi)
 // MemoGFK rounds (Algorithm 3).  On return E_out holds the tree edges in K order: n-1 of them, or
 // `target` when the points form several instances that must not be joined (a batch): then every
 // edge weight is below rho_cap, rho_hi never exceeds it, and no pair at or above it is retrieved.
-// hdb: optional HDBSCAN* state (node cd bounds, per-position cd2, sorted repair edges).
-static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps &caps, EdgeK *E_out, int *uf,
+// hdb: optional HDBSCAN* state (node cd bounds, per-position cd2, repair edges: consumed).
+static int memogfk(Call &C, Points &P, Tree &T, HdbState *hdb, const Caps &caps, EdgeK *E_out, int *uf,
                    unsigned long long *R, unsigned *overflow_bits, long long target = -1, double rho_cap = INFINITY)
 {
     const int n = P.n;
@@ -328,6 +339,12 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     EdgeK *batch = ar.get<EdgeK>(caps.edges), *filt = ar.get<EdgeK>(caps.edges), *tmp = ar.get<EdgeK>(caps.edges);
     int *cnts = ar.get<int>(64);
     unsigned *rho = ar.get<unsigned>(2);
+    // HDBSCAN* repair edges still to be taken by a round, ping-pong between the state's list and a
+    // second buffer: each round keeps only those above its range whose endpoints are not yet
+    // connected (the state's list is consumed)
+    EdgeK *rep_cur = hdb ? hdb->rep : nullptr;
+    int rep_n = hdb ? hdb->nrep : 0;
+    EdgeK *rep_alt = rep_n > 0 ? ar.get<EdgeK>(rep_n) : nullptr;
     double *samples = ar.get<double>(4096);
     unsigned *ovf = ar.get<unsigned>(2);
     unsigned long long *stat = ar.get<unsigned long long>(8);
@@ -369,6 +386,12 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     a.stat = stat;
     a.rho_bits = rho;
     EdgeK *spare = filt;   // second edge buffer for compaction when rho_hi shrinks
+    int *nodes[2] = {ar.get<int>(T.N / 2 + 1), ar.get<int>(T.N / 2 + 1)};
+    if (ar.failed) return WM_ENOMEM;
+    a.node_in = nullptr;
+    a.node_in_n = nullptr;
+    a.node_out = nodes[0];
+    a.node_out_n = cnts + 10;
 
     int nE = 0;
     double rho_lo = 0.0;
@@ -478,14 +501,18 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         C.stats.getpairs_launches += steps;
         C.stats.ms_wspd += tw.ms();
         // ---- HDBSCAN*: repair edges of this weight range join the batch
-        if (hdb && hdb->nrep > 0 && rho_hi > rho_lo) {
-            launch(take_range_kernel, grid_for(hdb->nrep, 256), 256, 0, st, hdb->rep, hdb->nrep, rho_lo, rho_hi,
-                   a.edges, ecount, (int)caps.edges, ovf);
+        if (rep_n > 0 && rho_hi > rho_lo) {
+            WM_CK(cudaMemsetAsync(cnts + 9, 0, sizeof(int), st));
+            launch(take_range_kernel, grid_for(rep_n, 256), 256, 0, st, rep_cur, rep_n, rho_lo, rho_hi, uf, a.edges,
+                   ecount, (int)caps.edges, rep_alt, cnts + 9, ovf);
             WM_CK(cudaMemcpyAsync(C.pin, ecount, sizeof(int), cudaMemcpyDeviceToHost, st));
             WM_CK(cudaMemcpyAsync(C.pin + 1, ovf, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+            WM_CK(cudaMemcpyAsync(C.pin + 2, cnts + 9, sizeof(int), cudaMemcpyDeviceToHost, st));
             WM_CK(cudaStreamSynchronize(st));
             if (C.pin[1]) { *overflow_bits = (unsigned)C.pin[1]; return 0; }
             m = C.pin[0];
+            rep_n = C.pin[2];
+            std::swap(rep_cur, rep_alt);
         }
         // ---- sort + Kruskal
         Timer tk;
@@ -507,6 +534,11 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         }
         rho_lo = rho_hi;
         beta *= 2;
+        // this round's surviving nodes are the next round's input
+        a.node_in = a.node_out;
+        a.node_in_n = a.node_out_n;
+        a.node_out = a.node_out == nodes[0] ? nodes[1] : nodes[0];
+        a.node_out_n = a.node_out_n == cnts + 10 ? cnts + 11 : cnts + 10;
     }
     {
         // every round appended its tree edges unordered: put the tree in K order

@@ -213,10 +213,12 @@ __global__ void level_union_kernel(const int *__restrict__ ex, const int *__rest
     }
 }
 
-// rootrank / minheavy updates aggregated per warp: edges of one warp often share a component
-// (a large one at the top levels), so each group of equal roots issues one atomic
+// Component roots of every edge's endpoints (rx, ry; ry for heavy edges only), rootrank (largest
+// light edge of a component) and minheavy (smallest heavy edge touching it).  The updates are
+// aggregated per warp: edges of one warp often share a component (a large one at the top levels),
+// so each group of equal roots issues one atomic.
 __global__ void level_mark_kernel(const int *__restrict__ ex, const int *__restrict__ ey, int m, int bit, int *uf,
-                                  int *rootrank, int *minheavy)
+                                  int *rootrank, int *minheavy, int *__restrict__ rx, int *__restrict__ ry)
 {
     const int lane = threadIdx.x & 31;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i - lane < m; i += gridDim.x * blockDim.x) {
@@ -224,6 +226,7 @@ __global__ void level_mark_kernel(const int *__restrict__ ex, const int *__restr
         const bool light = ok && ((i >> bit) & 1) == 0, heavy = ok && !light;
         const int kx = ok ? uf_find(uf, ex[i]) : -1;
         const int ky = heavy ? uf_find(uf, ey[i]) : -1;
+        if (ok) { rx[i] = kx; ry[i] = ky; }
         int key = light ? kx : -1;
         unsigned grp = __match_any_sync(0xffffffffu, key);
         int v = __reduce_max_sync(grp, light ? i : -1);
@@ -238,18 +241,29 @@ __global__ void level_mark_kernel(const int *__restrict__ ex, const int *__restr
     }
 }
 
-__global__ void level_link_kernel(int *ex, int *ey, int m, int bit, int n, int *uf, const int *__restrict__ rootrank,
-                                  const int *__restrict__ minheavy, int *__restrict__ par)
+// Parents of the light components' top merges; heavy endpoints relabelled to their component's
+// top merge.  The next level's union-find entries and its (other) rootrank / minheavy set are
+// initialised here for the endpoints each edge has from now on: this level reads neither.
+__global__ void level_link_kernel(int *ex, int *ey, int m, int bit, int n, const int *__restrict__ rx,
+                                  const int *__restrict__ ry, const int *__restrict__ rootrank,
+                                  const int *__restrict__ minheavy, int *__restrict__ par, int *uf, int *rr_next,
+                                  int *mh_next)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        int x = ex[i], y = ey[i];
         if (((i >> bit) & 1) == 0) {
-            int c = uf_find(uf, ex[i]);
+            const int c = rx[i];
             if (rootrank[c] == i && minheavy[c] != 0x7fffffff) par[n + i] = n + minheavy[c];
         } else {
-            int cx = uf_find(uf, ex[i]), cy = uf_find(uf, ey[i]);
-            ex[i] = rootrank[cx] >= 0 ? n + rootrank[cx] : cx;
-            ey[i] = rootrank[cy] >= 0 ? n + rootrank[cy] : cy;
+            const int cx = rx[i], cy = ry[i];
+            x = rootrank[cx] >= 0 ? n + rootrank[cx] : cx;
+            y = rootrank[cy] >= 0 ? n + rootrank[cy] : cy;
+            ex[i] = x;
+            ey[i] = y;
         }
+        uf[x] = x; uf[y] = y;
+        rr_next[x] = -1; rr_next[y] = -1;
+        mh_next[x] = 0x7fffffff; mh_next[y] = 0x7fffffff;
     }
 }
 
@@ -258,9 +272,10 @@ __global__ void level_link_kernel(int *ex, int *ey, int m, int bit, int n, int *
 // occurs in one subproblem of a level), so one CTA runs all of them for its block in shared
 // memory.  Vertices get local ids on entry (the first occurrence claims map[v]); the merge node
 // of local edge r is 2 * kLeafChunk + r.  The steps of a level are those of the global kernels.
-constexpr int kLeafLevels = 10;
+constexpr int kLeafLevels = 11;
 constexpr int kLeafChunk = 1 << kLeafLevels;
-constexpr int kLeafThreads = 512;
+constexpr int kLeafThreads = 1024;
+constexpr int kLeafSmem = (3 * 3 * kLeafChunk + 2 * kLeafChunk) * (int)sizeof(int);   // uf, rr, mh; lx, ly
 
 __device__ inline int sm_find(int *uf, int x)
 {
@@ -278,8 +293,9 @@ __global__ void __launch_bounds__(kLeafThreads) level_leaf_kernel(const int *__r
                                                                   int m, int n, int top, int *map,
                                                                   int *__restrict__ par)
 {
-    __shared__ int uf[3 * kLeafChunk], rr[3 * kLeafChunk], mh[3 * kLeafChunk];
-    __shared__ int lx[kLeafChunk], ly[kLeafChunk];
+    extern __shared__ int leaf_smem[];
+    int *uf = leaf_smem, *rr = uf + 3 * kLeafChunk, *mh = rr + 3 * kLeafChunk;
+    int *lx = mh + 3 * kLeafChunk, *ly = lx + kLeafChunk;
     const int b = blockIdx.x * kLeafChunk;
     const int cnt = min(kLeafChunk, m - b);
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
@@ -516,6 +532,7 @@ int dendrogram_impl(const EdgeK *E, int n, int start, int key_squared, wm_dnode 
     int *child = ar.get<int>(m), *tin = ar.get<int>(n), *tout = ar.get<int>(n);
     int *par = ar.get<int>(total), *pmin = ar.get<int>(n), *ex = ar.get<int>(m), *ey = ar.get<int>(m);
     int *uf = ar.get<int>(total), *rootrank = ar.get<int>(total), *minheavy = ar.get<int>(total);
+    int *rootrank2 = ar.get<int>(total), *minheavy2 = ar.get<int>(total), *rxa = ar.get<int>(m), *rya = ar.get<int>(m);
     int *nch = ar.get<int>(m), *ch = ar.get<int>(2 * m), *lc = ar.get<int>(m), *rc = ar.get<int>(m);
     int *bad = ar.get<int>(1);
     if (ar.failed) return WM_ENOMEM;
@@ -549,15 +566,18 @@ int dendrogram_impl(const EdgeK *E, int n, int start, int key_squared, wm_dnode 
     launch(endpoints_init_kernel, g, 256, 0, st, E, m, ex, ey);
     int levels = 0;
     while ((1LL << levels) < (long long)m) ++levels;
-    for (int k = levels; k > kLeafLevels; --k) {
+    if (levels > kLeafLevels) launch(level_init_kernel, g, 256, 0, st, ex, ey, m, uf, rootrank, minheavy);
+    for (int k = levels, set = 0; k > kLeafLevels; --k, set ^= 1) {
         const int bit = k - 1;
-        launch(level_init_kernel, g, 256, 0, st, ex, ey, m, uf, rootrank, minheavy);
+        int *rr = set ? rootrank2 : rootrank, *mh = set ? minheavy2 : minheavy;
+        int *rrn = set ? rootrank : rootrank2, *mhn = set ? minheavy : minheavy2;
         launch(level_union_kernel, g, 256, 0, st, ex, ey, m, bit, uf);
-        launch(level_mark_kernel, g, 256, 0, st, ex, ey, m, bit, uf, rootrank, minheavy);
-        launch(level_link_kernel, g, 256, 0, st, ex, ey, m, bit, n, uf, rootrank, minheavy, par);
+        launch(level_mark_kernel, g, 256, 0, st, ex, ey, m, bit, uf, rr, mh, rxa, rya);
+        launch(level_link_kernel, g, 256, 0, st, ex, ey, m, bit, n, rxa, rya, rr, mh, par, uf, rrn, mhn);
     }
     fill_i32(uf, -1, total, st);
-    launch(level_leaf_kernel, (m + kLeafChunk - 1) / kLeafChunk, kLeafThreads, 0, st, ex, ey, m, n,
+    cudaFuncSetAttribute(level_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kLeafSmem);
+    launch(level_leaf_kernel, (m + kLeafChunk - 1) / kLeafChunk, kLeafThreads, kLeafSmem, st, ex, ey, m, n,
            std::min(levels, kLeafLevels), uf, par);
     // ---- children, left/right, in-order
     cudaMemsetAsync(nch, 0, sizeof(int) * m, st);

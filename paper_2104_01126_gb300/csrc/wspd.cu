@@ -531,10 +531,19 @@ __global__ void pack_nodes_kernel(int N, int d, int DP, const float *__restrict_
 __global__ void frontier_init_kernel(TravArgs a, int mode, int2 *__restrict__ out, int *out_count)
 {
     __shared__ int sh[32];
-    for (int b0 = blockIdx.x * blockDim.x; b0 < a.N; b0 += gridDim.x * blockDim.x) {
-        const int x = b0 + threadIdx.x;
-        int push = 0;
-        if (x < a.N && a.left[x] >= 0 && a.comp[x] < 0 && (mode == 1 || nsize(a, x) > a.beta)) push = 1;
+    // GetRho reads the previous round's node list (every node in the first round) and writes
+    // the survivors; GetPairs reads the survivors
+    const int *in = mode == 0 ? a.node_in : a.node_out;
+    const int m = in ? *(mode == 0 ? a.node_in_n : a.node_out_n) : a.N;
+    for (int b0 = blockIdx.x * blockDim.x; b0 < m; b0 += gridDim.x * blockDim.x) {
+        const int t = b0 + threadIdx.x;
+        const int x = t < m ? (in ? in[t] : t) : -1;
+        const bool cand = x >= 0 && a.left[x] >= 0 && a.comp[x] < 0;
+        if (mode == 0 && a.node_out) {
+            const int s = block_append(a.node_out_n, cand ? 1 : 0, sh);
+            if (cand) a.node_out[s] = x;
+        }
+        const int push = cand && (mode == 1 || nsize(a, x) > a.beta) ? 1 : 0;
         const int slot = block_append(out_count, push, sh);
         if (push) {
             if (slot < a.frontier_cap) out[slot] = make_int2(a.left[x], a.right[x]);
@@ -1033,6 +1042,7 @@ int launch_comp_labels(const Tree &T, const Points &P, int *uf, const int4 *link
 void traversal_init(int mode, TravArgs &a, int2 *stack, int *cnt, cudaStream_t st)
 {
     cudaMemsetAsync(cnt, 0, sizeof(int) * kTravCounters, st);
+    if (mode == 0 && a.node_out_n) cudaMemsetAsync(a.node_out_n, 0, sizeof(int), st);
     launch(frontier_init_kernel, grid_for(a.N, 256), 256, 0, st, a, mode, stack, cnt + 0);
 }
 

@@ -44,6 +44,11 @@ struct TravArgs {
     int *edge_count = nullptr;
     int edge_cap = 0;
     unsigned *overflow = nullptr;      // bit 0 frontier, bit 1 edges, bit 2 big pairs
+    // internal nodes not known to be connected, kept from round to round (connectivity only
+    // grows): the GetRho frontier reads node_in (all nodes when null) and writes the survivors
+    // to node_out, which the GetPairs frontier of the same round reads
+    const int *node_in = nullptr, *node_in_n = nullptr;
+    int *node_out = nullptr, *node_out_n = nullptr;
     unsigned long long *stat = nullptr; // [0] pairs retrieved, [1] evals, [2] fp64 rechecks,
                                         // [3] tile evals, [4] GetPairs visits, [5] GetRho visits,
                                         // [6] dual-tree evals, [7] peak pending pairs
