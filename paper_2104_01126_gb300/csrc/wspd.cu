@@ -75,6 +75,20 @@ __device__ inline float dist32(const float *__restrict__ x32, int n, int d, int 
     return s;
 }
 
+// dist32 with the dimension fixed at compile time (D > 0), the same operations in the same order
+template <int D>
+__device__ inline float dist32t(const float *__restrict__ x32, int n, int d, int i, int j)
+{
+    if (D <= 0) return dist32(x32, n, d, i, j);
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < (D > 0 ? D : 1); ++k) {
+        float t = x32[(size_t)k * n + i] - x32[(size_t)k * n + j];
+        s = fmaf(t, t, s);
+    }
+    return s;
+}
+
 __device__ inline double dist64(const double *__restrict__ x64, int n, int d, int i, int j)
 {
     double s = 0.0;
@@ -429,7 +443,7 @@ __global__ void __launch_bounds__(256) findpair_dfs_kernel(TravArgs a, DfsArgs s
 // |A| x |B| product (a = e / |B|, b = e % |B|).  FP32 screen, group minimum, band threshold,
 // FP64 recheck of every candidate inside the band, group K-minimum; the group leader emits the
 // edge when its FP64 w2 lies in [rho_lo, rho_hi).
-template <int G>
+template <int G, int D>
 __global__ void __launch_bounds__(256) bccp_group_kernel(TravArgs a, const int2 *__restrict__ pairs,
                                                          const int *__restrict__ count)
 {
@@ -458,35 +472,44 @@ __global__ void __launch_bounds__(256) bccp_group_kernel(TravArgs a, const int2 
                 kmin_update(best, w, a.pid[i], a.pid[j]);
             }
         } else {
-            // lane g visits e = g, g + G, ... of the na x nb grid; (i, j) advance without division
+            // lane g visits e = g, g + G, ... of the na x nb grid; (i, j) advance without division.
+            // The classes using this kernel have |A||B| <= kPer G, so a lane's screened values
+            // stay in registers for the band test (no second evaluation).
+            constexpr int kPer = 8;
+            static_assert(kTinyMax <= kPer && kSmallMax <= 8 * kPer, "group kernel: a class exceeds kPer per lane");
+            float sv[kPer];
             float smin = INFINITY;
             {
                 int i = pb + (nb > 0 ? g / nb : 0), j = qb + (nb > 0 ? g % nb : 0);
-                for (int e = g; e < tot; e += G) {
-                    const float sd = dist32(a.x32, n, d, i, j);
-                    smin = fminf(smin, a.cd32 ? fmaxf(sd, fmaxf(a.cd32[i], a.cd32[j])) : sd);
-                    j += G;
-                    while (j >= qb + nb) { j -= nb; ++i; }
+#pragma unroll
+                for (int t = 0; t < kPer; ++t) {
+                    sv[t] = INFINITY;
+                    if (g + t * G < tot) {
+                        const float sd = dist32t<D>(a.x32, n, d, i, j);
+                        sv[t] = a.cd32 ? fmaxf(sd, fmaxf(a.cd32[i], a.cd32[j])) : sd;
+                        smin = fminf(smin, sv[t]);
+                        j += G;
+                        while (j >= qb + nb) { j -= nb; ++i; }
+                    }
                 }
             }
 #pragma unroll
             for (int o = G / 2; o; o >>= 1) smin = fminf(smin, __shfl_xor_sync(0xffffffffu, smin, o));
             const float T = screen_threshold(smin, a);
-            // a lane's first candidate is rechecked after the loop, where the lanes run together
-            // (an FP64 instruction costs the same however few lanes are active); later ones inline
+            // the candidates (few) are evaluated again for the recheck.  A lane's first candidate is
+            // rechecked after the loop, where the lanes run together (an FP64 instruction costs the
+            // same however few lanes are active); later ones inline
             Deferred df;
-            {
-                int i = pb + (nb > 0 ? g / nb : 0), j = qb + (nb > 0 ? g % nb : 0);
-                for (int e = g; e < tot; e += G) {
-                    const float sd = dist32(a.x32, n, d, i, j);
+#pragma unroll
+            for (int t = 0; t < kPer; ++t) {
+                if (g + t * G < tot && sv[t] <= T) {
+                    const int e = g + t * G;
+                    const int i = pb + e / nb, j = qb + e % nb;
+                    const float sd = dist32t<D>(a.x32, n, d, i, j);
                     const float c32 = a.cd32 ? fmaxf(a.cd32[i], a.cd32[j]) : 0.f;
-                    if (fmaxf(sd, c32) <= T) {
-                        if (df.i < 0) df = Deferred{i, j, sd, c32};
-                        else kmin_update(best, exact_w2(a, i, j, sd, c32), a.pid[i], a.pid[j]);
-                        ++n_re;
-                    }
-                    j += G;
-                    while (j >= qb + nb) { j -= nb; ++i; }
+                    if (df.i < 0) df = Deferred{i, j, sd, c32};
+                    else kmin_update(best, exact_w2(a, i, j, sd, c32), a.pid[i], a.pid[j]);
+                    ++n_re;
                 }
             }
             __syncwarp();
@@ -1150,12 +1173,26 @@ void keep_below(const EdgeK *in, int m, double bound, EdgeK *out, int *count, cu
 }
 
 // BCCP of the tiny, small and medium pair lists (counts read back by the host).
-void run_bccp_groups(TravArgs &a, const int *counts_host, cudaStream_t st)
+template <int D>
+static void run_bccp_groups_d(TravArgs &a, const int *counts_host, cudaStream_t st)
 {
     if (counts_host[0] > 0)
-        launch(bccp_group_kernel<1>, grid_for((long long)counts_host[0], 256), 256, 0, st, a, a.list[0], a.list_count + 0);
+        launch(bccp_group_kernel<1, D>, grid_for((long long)counts_host[0], 256), 256, 0, st, a, a.list[0],
+               a.list_count + 0);
     if (counts_host[1] > 0)
-        launch(bccp_group_kernel<8>, grid_for((long long)counts_host[1] * 8, 256), 256, 0, st, a, a.list[1], a.list_count + 1);
+        launch(bccp_group_kernel<8, D>, grid_for((long long)counts_host[1] * 8, 256), 256, 0, st, a, a.list[1],
+               a.list_count + 1);
+}
+
+void run_bccp_groups(TravArgs &a, const int *counts_host, cudaStream_t st)
+{
+    switch (a.d) {
+    case 2: run_bccp_groups_d<2>(a, counts_host, st); break;
+    case 3: run_bccp_groups_d<3>(a, counts_host, st); break;
+    case 5: run_bccp_groups_d<5>(a, counts_host, st); break;
+    case 7: run_bccp_groups_d<7>(a, counts_host, st); break;
+    default: run_bccp_groups_d<0>(a, counts_host, st); break;
+    }
 }
 
 void pack_nodes(const Tree &T, int d, int dp, int4 *links, float4 *meta, float *box, cudaStream_t st)
