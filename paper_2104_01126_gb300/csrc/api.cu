@@ -26,7 +26,6 @@ std::atomic<long long> g_launch_count{0};
 int ingest_points(const void *dev_src, int n, int d, int dtype, int layout, Points &P, Arena &ar, cudaStream_t st,
                   unsigned *pinned);
 int build_tree(Points &P, Tree &T, Arena &ar, cudaStream_t st, int *pinned);
-int filter_connected(const EdgeK *in, int m, const int *uf, EdgeK *out, int *count_dev, cudaStream_t st);
 int batch_kruskal(const EdgeK *e, int m, int n, int *uf, unsigned long long *R, EdgeK *out, int out_base, int *accepted,
                   Arena &ar, cudaStream_t st, int *pinned);
 
@@ -514,17 +513,12 @@ static int memogfk(Call &C, Points &P, Tree &T, HdbState *hdb, const Caps &caps,
             rep_n = C.pin[2];
             std::swap(rep_cur, rep_alt);
         }
-        // ---- sort + Kruskal
+        // ---- Kruskal (its first step rejects the edges whose endpoints are already connected)
         Timer tk;
         int accepted = 0;
         if (m > 0) {
-            EdgeK *fout = a.edges == batch ? filt : batch;
-            WM_TRY(filter_connected(a.edges, m, uf, fout, cnts + 8, st));
-            WM_CK(cudaMemcpyAsync(C.pin, cnts + 8, sizeof(int), cudaMemcpyDeviceToHost, st));
-            WM_CK(cudaStreamSynchronize(st));
-            int mf = C.pin[0];
-            C.stats.candidate_edges += mf;
-            WM_TRY(batch_kruskal(fout, mf, n, uf, R, E_out, nE, &accepted, ar, st, C.pin));
+            C.stats.candidate_edges += m;
+            WM_TRY(batch_kruskal(a.edges, m, n, uf, R, E_out, nE, &accepted, ar, st, C.pin));
         }
         C.stats.ms_kruskal += tk.ms();
         nE += accepted;

@@ -38,34 +38,6 @@ __device__ inline int uf_find_halving(int *uf, int x)
     return x;
 }
 
-__device__ inline int uf_find_ro(const int *uf, int x)
-{
-    for (int it = 0; it < kChaseLimit; ++it) {
-        int p = uf[x];
-        if (p == x) return x;
-        x = p;
-    }
-    return x;
-}
-
-// Drops edges whose endpoints are already connected (the union-find is flat here).
-__global__ void filter_connected_kernel(const EdgeK *__restrict__ in, int m, const int *__restrict__ uf,
-                                        EdgeK *__restrict__ out, int *count)
-{
-    __shared__ int sh[32];
-    for (int b0 = blockIdx.x * blockDim.x; b0 < m; b0 += gridDim.x * blockDim.x) {
-        const int t = b0 + threadIdx.x;
-        bool keep = false;
-        EdgeK e;
-        if (t < m) {
-            e = in[t];
-            keep = uf_find_ro(uf, edge_u(e)) != uf_find_ro(uf, edge_v(e));
-        }
-        const int slot = block_append(count, keep ? 1 : 0, sh);
-        if (keep) out[slot] = e;
-    }
-}
-
 __global__ void init_list_kernel(int *list, int m)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) list[i] = i;
@@ -275,13 +247,6 @@ __global__ void clear_kernel(const int2 *__restrict__ roots, const int *__restri
 }
 
 }  // namespace
-
-int filter_connected(const EdgeK *in, int m, const int *uf, EdgeK *out, int *count_dev, cudaStream_t st)
-{
-    cudaMemsetAsync(count_dev, 0, sizeof(int), st);
-    if (m > 0) launch(filter_connected_kernel, grid_for(m, 256), 256, 0, st, in, m, uf, out, count_dev);
-    return 0;
-}
 
 // Kruskal over the batch e[0..m) (any order).  R holds 4 n 64-bit reservation words (two sets
 // of two), all ~0 on entry (kept so).  Accepted edges are appended to out at out_base (in no
