@@ -430,6 +430,8 @@ static int memogfk(Call &C, Points &P, Tree &T, HdbState *hdb, const Caps &caps,
         };
         std::vector<int> ev_kind;        // 0 = traversal interval, 1 = BCCP interval
         int steps = 0;
+        int last_e = 0;                  // edge count and overflow bits read after the last flush
+        unsigned last_ovf = 0;
         mark_event();
         while (true) {
             for (int b = 0; b < kPoll; ++b, ++steps) traversal_step(1, a, stack, xbuf, tcnt, steps, chunk, st);
@@ -459,6 +461,8 @@ static int memogfk(Call &C, Points &P, Tree &T, HdbState *hdb, const Caps &caps,
                 WM_CK(cudaMemcpyAsync(C.pin, ecount, sizeof(int), cudaMemcpyDeviceToHost, st));
                 WM_CK(cudaMemcpyAsync(C.pin + 1, ovf, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
                 WM_CK(cudaStreamSynchronize(st));
+                last_e = C.pin[0];
+                last_ovf = (unsigned)C.pin[1];
                 if (!(C.pin[1] & 2u)) break;
                 if (attempt >= 8) { *overflow_bits = 2; return 0; }
                 const int valid = std::min<long long>(C.pin[0], caps.edges) > 0 ? (int)std::min<long long>(C.pin[0], caps.edges) : 0;
@@ -486,17 +490,10 @@ static int memogfk(Call &C, Points &P, Tree &T, HdbState *hdb, const Caps &caps,
             if (empty) break;
             if (steps > 10000000) { set_detail("WSPD GetPairs traversal did not terminate%s", ""); return WM_EINTERNAL; }
         }
-        WM_CK(cudaMemcpyAsync(C.pin, ecount, sizeof(int), cudaMemcpyDeviceToHost, st));
-        WM_CK(cudaMemcpyAsync(C.pin + 1, ovf, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-        WM_CK(cudaStreamSynchronize(st));
-        if (C.pin[1]) { *overflow_bits = (unsigned)C.pin[1]; return 0; }
-        int m = C.pin[0];
-        for (size_t k = 0; k + 1 < evs.size(); ++k) {
-            double ms = C.event_ms(evs[k], evs[k + 1]);
-            if (ev_kind[k] == 0) C.stats.ms_getpairs += ms;
-            else { C.stats.ms_bccp += ms; C.stats.ms_tile_kernel += ms; }
-        }
-        for (cudaEvent_t e : evs) cudaEventDestroy(e);
+        // the traversal ends with a flush whose sync read the edge count and the overflow bits;
+        // nothing has run since
+        if (last_ovf) { *overflow_bits = last_ovf; return 0; }
+        int m = last_e;
         C.stats.getpairs_launches += steps;
         C.stats.ms_wspd += tw.ms();
         // ---- HDBSCAN*: repair edges of this weight range join the batch
@@ -521,6 +518,16 @@ static int memogfk(Call &C, Points &P, Tree &T, HdbState *hdb, const Caps &caps,
             WM_TRY(batch_kruskal(a.edges, m, n, uf, R, E_out, nE, &accepted, ar, st, C.pin));
         }
         C.stats.ms_kruskal += tk.ms();
+        // the interval events of this round are complete once the stream has synced (Kruskal)
+        if (!evs.empty()) {
+            WM_CK(cudaEventSynchronize(evs.back()));
+            for (size_t k = 0; k + 1 < evs.size(); ++k) {
+                double ms = C.event_ms(evs[k], evs[k + 1]);
+                if (ev_kind[k] == 0) C.stats.ms_getpairs += ms;
+                else { C.stats.ms_bccp += ms; C.stats.ms_tile_kernel += ms; }
+            }
+            for (cudaEvent_t e : evs) cudaEventDestroy(e);
+        }
         nE += accepted;
         if (rho_hi >= rho_cap && nE < target) {
             set_detail("MemoGFK round with rho_hi = its cap left the forest incomplete%s (%lld edges)", "", nE);

@@ -1115,14 +1115,14 @@ void traversal_step(int mode, TravArgs &a, int2 *stack, int2 *const xbuf[2], int
 #undef WM_FP
 }
 
-// GetRho: the whole traversal, polling emptiness every 2 steps.
+// GetRho: the whole traversal, polling emptiness every 3 steps.
 int run_traversal(TravArgs &a, int2 *stack, int2 *const xbuf[2], int *cnt, int chunk, cudaStream_t st, int *pinned,
                   unsigned *overflow_out, int *steps_out)
 {
     traversal_init(0, a, stack, cnt, st);
     int steps = 0;
     while (true) {
-        for (int b = 0; b < 2; ++b, ++steps) traversal_step(0, a, stack, xbuf, cnt, steps, chunk, st);
+        for (int b = 0; b < 3; ++b, ++steps) traversal_step(0, a, stack, xbuf, cnt, steps, chunk, st);
         cudaMemcpyAsync(pinned, cnt, sizeof(int) * kTravCounters, cudaMemcpyDeviceToHost, st);
         cudaMemcpyAsync(pinned + kTravCounters, a.overflow, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
         if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;
