@@ -133,10 +133,12 @@ __device__ inline void warp_append(const T &x, bool has, T *out, int *out_count,
 // are appended to the next list.
 __global__ void commit_kernel(StepArgs a, int *uf, EdgeK *__restrict__ out, int *out_count, int out_cap, int *bad)
 {
+    __shared__ int sh[32];
     const int m = *a.cnt;
-    const int lane = threadIdx.x & 31;
-    const int limit = (m + 31) & ~31;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j - lane < limit; j += gridDim.x * blockDim.x) {
+    // block-uniform loop: the appends take one counter atomic per block (a batch of millions of
+    // edges would otherwise serialise tens of thousands of warps on two counters)
+    for (int b0 = blockIdx.x * blockDim.x; b0 < m; b0 += gridDim.x * blockDim.x) {
+        const int j = b0 + threadIdx.x;
         bool acc = false, keep = false;
         int i = 0;
         EdgeK x;
@@ -151,8 +153,13 @@ __global__ void commit_kernel(StepArgs a, int *uf, EdgeK *__restrict__ out, int 
                 keep = !acc;
             }
         }
-        warp_append(x, acc, out, out_count, out_cap, bad);
-        warp_append(i, keep, a.next, a.next_cnt, 0x7fffffff, bad);
+        int slot = block_append(out_count, acc ? 1 : 0, sh);
+        if (acc) {
+            if (slot < out_cap) out[slot] = x;
+            else atomicOr(bad, 2);
+        }
+        slot = block_append(a.next_cnt, keep ? 1 : 0, sh);
+        if (keep) a.next[slot] = i;
     }
 }
 
@@ -287,11 +294,12 @@ int batch_kruskal(const EdgeK *e, int m, int n, int *uf, unsigned long long *R, 
         a.next_cnt = cnt + ((s + 1) & 3);
         return a;
     };
+    int base_m = m, base_step = 0;   // pending edges at the last host sync, and that step
     while (true) {
         for (int b = 0; b < 4; ++b, ++step) {
             // the pending list shrinks by a factor of about 2 to 4 per step: a smaller grid (the
             // loops are grid-strided, so any size is correct) keeps the nearly empty steps short
-            const int g = std::max(152, grid_for(std::max(1, m >> std::min(step, 30)), 256));
+            const int g = std::max(152, grid_for(std::max(1, base_m >> std::min(step - base_step, 30)), 256));
             const StepArgs a = args(step);
             launch(reserve_hi_kernel, g, 256, 0, st, a, n, uf, cnt + 5);
             launch(reserve_lo_kernel, g, 256, 0, st, a);
@@ -314,6 +322,8 @@ int batch_kruskal(const EdgeK *e, int m, int n, int *uf, unsigned long long *R, 
             return WM_EINTERNAL;
         }
         if (pinned[step & 3] == 0) break;
+        base_m = pinned[step & 3];
+        base_step = step;
         if (step > 4 * (m + 8)) {
             char msg[160];
             snprintf(msg, sizeof msg, "batched Kruskal made no progress (reservations): %d of %d edges pending",
