@@ -202,13 +202,10 @@ __global__ void sum_partials_kernel(const double *partial, int m, double *out)
     if (threadIdx.x == 0) *out = sm[0];
 }
 
-// Splits the repair edges src[0..m) at the start of a round's Kruskal: those whose w2 lies in
-// [lo, hi) join the batch dst, those at or above hi are kept for later rounds (rest), and those
-// whose endpoints are already connected are dropped (no later round can accept them).
-// Non-negative doubles and +inf order like their bit patterns.
-__global__ void take_range_kernel(const EdgeK *__restrict__ src, int m, double lo, double hi, const int *__restrict__ uf,
-                                  EdgeK *__restrict__ dst, int *count, int cap, EdgeK *__restrict__ rest,
-                                  int *rest_count, unsigned *overflow)
+// appends the edges of src whose w2 lies in [lo, hi) to dst (non-negative doubles and +inf order
+// like their bit patterns)
+__global__ void take_range_kernel(const EdgeK *__restrict__ src, int m, double lo, double hi, EdgeK *__restrict__ dst,
+                                  int *count, int cap, unsigned *overflow)
 {
     __shared__ int sh[32];
     const unsigned long long blo = (unsigned long long)__double_as_longlong(lo);
@@ -216,24 +213,16 @@ __global__ void take_range_kernel(const EdgeK *__restrict__ src, int m, double l
     for (int b0 = blockIdx.x * blockDim.x; b0 < m; b0 += gridDim.x * blockDim.x) {
         const int t = b0 + threadIdx.x;
         EdgeK e;
-        bool take = false, keep = false;
+        bool take = false;
         if (t < m) {
             e = src[t];
-            int ru = edge_u(e), rv = edge_v(e);
-            for (int it = 0; it < 64 && uf[ru] != ru; ++it) ru = uf[ru];
-            for (int it = 0; it < 64 && uf[rv] != rv; ++it) rv = uf[rv];
-            if (uf[ru] != ru || uf[rv] != rv || ru != rv) {   // a chain longer than 64 is kept
-                take = e.hi >= blo && e.hi < bhi;
-                keep = e.hi >= bhi;
-            }
+            take = e.hi >= blo && e.hi < bhi;
         }
-        int slot = block_append(count, take ? 1 : 0, sh);
+        const int slot = block_append(count, take ? 1 : 0, sh);
         if (take) {
             if (slot < cap) dst[slot] = e;
             else atomicOr(overflow, 2u);
         }
-        slot = block_append(rest_count, keep ? 1 : 0, sh);
-        if (keep) rest[slot] = e;
     }
 }
 
@@ -304,8 +293,8 @@ static void set_rho(TravArgs &a, double lo, double hi)
 // MemoGFK rounds (Algorithm 3).  On return E_out holds the tree edges in K order: n-1 of them, or
 // `target` when the points form several instances that must not be joined (a batch): then every
 // edge weight is below rho_cap, rho_hi never exceeds it, and no pair at or above it is retrieved.
-// hdb: optional HDBSCAN* state (node cd bounds, per-position cd2, repair edges: consumed).
-static int memogfk(Call &C, Points &P, Tree &T, HdbState *hdb, const Caps &caps, EdgeK *E_out, int *uf,
+// hdb: optional HDBSCAN* state (node cd bounds, per-position cd2, repair edges).
+static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps &caps, EdgeK *E_out, int *uf,
                    unsigned long long *R, unsigned *overflow_bits, long long target = -1, double rho_cap = INFINITY)
 {
     const int n = P.n;
@@ -338,19 +327,13 @@ static int memogfk(Call &C, Points &P, Tree &T, HdbState *hdb, const Caps &caps,
     EdgeK *batch = ar.get<EdgeK>(caps.edges), *filt = ar.get<EdgeK>(caps.edges), *tmp = ar.get<EdgeK>(caps.edges);
     int *cnts = ar.get<int>(64);
     unsigned *rho = ar.get<unsigned>(2);
-    // HDBSCAN* repair edges still to be taken by a round, ping-pong between the state's list and a
-    // second buffer: each round keeps only those above its range whose endpoints are not yet
-    // connected (the state's list is consumed)
-    EdgeK *rep_cur = hdb ? hdb->rep : nullptr;
-    int rep_n = hdb ? hdb->nrep : 0;
-    EdgeK *rep_alt = rep_n > 0 ? ar.get<EdgeK>(rep_n) : nullptr;
     double *samples = ar.get<double>(4096);
     unsigned *ovf = ar.get<unsigned>(2);
     unsigned long long *stat = ar.get<unsigned long long>(8);
     int *comp_scratch = ar.get<int>(2LL * n + 1);
     if (ar.failed) return WM_ENOMEM;
-    // counters: [2..6] pair-list counts, [7] edge count, [8] filtered count, [9] repair lower
-    // bound, [12..13] 64-bit huge-pair item total, [16..17] tile-kernel pair dispensers,
+    // counters: [2..6] pair-list counts, [7] edge count, [10..11] counts of the two node lists,
+    // [12..13] 64-bit huge-pair item total, [16..17] tile-kernel pair dispensers,
     // [32..32+kTravCounters) traversal state
     int *lcount = cnts + 2, *ecount = cnts + 7, *tcnt = cnts + 32;
     {
@@ -497,18 +480,14 @@ static int memogfk(Call &C, Points &P, Tree &T, HdbState *hdb, const Caps &caps,
         C.stats.getpairs_launches += steps;
         C.stats.ms_wspd += tw.ms();
         // ---- HDBSCAN*: repair edges of this weight range join the batch
-        if (rep_n > 0 && rho_hi > rho_lo) {
-            WM_CK(cudaMemsetAsync(cnts + 9, 0, sizeof(int), st));
-            launch(take_range_kernel, grid_for(rep_n, 256), 256, 0, st, rep_cur, rep_n, rho_lo, rho_hi, uf, a.edges,
-                   ecount, (int)caps.edges, rep_alt, cnts + 9, ovf);
+        if (hdb && hdb->nrep > 0 && rho_hi > rho_lo) {
+            launch(take_range_kernel, grid_for(hdb->nrep, 256), 256, 0, st, hdb->rep, hdb->nrep, rho_lo, rho_hi,
+                   a.edges, ecount, (int)caps.edges, ovf);
             WM_CK(cudaMemcpyAsync(C.pin, ecount, sizeof(int), cudaMemcpyDeviceToHost, st));
             WM_CK(cudaMemcpyAsync(C.pin + 1, ovf, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-            WM_CK(cudaMemcpyAsync(C.pin + 2, cnts + 9, sizeof(int), cudaMemcpyDeviceToHost, st));
             WM_CK(cudaStreamSynchronize(st));
             if (C.pin[1]) { *overflow_bits = (unsigned)C.pin[1]; return 0; }
             m = C.pin[0];
-            rep_n = C.pin[2];
-            std::swap(rep_cur, rep_alt);
         }
         // ---- Kruskal (its first step rejects the edges whose endpoints are already connected)
         Timer tk;
