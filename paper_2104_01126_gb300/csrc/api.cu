@@ -294,6 +294,7 @@ static void set_rho(TravArgs &a, double lo, double hi)
 // `target` when the points form several instances that must not be joined (a batch): then every
 // edge weight is below rho_cap, rho_hi never exceeds it, and no pair at or above it is retrieved.
 // hdb: optional HDBSCAN* state (node cd bounds, per-position cd2, repair edges).
+constexpr int kRouteBig = 1024;   // big-pair lists up to this length go to the dual-tree kernel
 static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps &caps, EdgeK *E_out, int *uf,
                    unsigned long long *R, unsigned *overflow_bits, long long target = -1, double rho_cap = INFINITY)
 {
@@ -438,8 +439,15 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
             const int e_before = e;
             for (int attempt = 0;; ++attempt) {
                 run_bccp_groups(a, lc, st);
-                run_bccp_tiles(a, lc, cnts + 16, st, hdb != nullptr, a.fp64 != 0);
-                WM_TRY(run_bccp_huge(a, lc[4], huge_items, (long long *)(cnts + 12), st, ar, hdb != nullptr,
+                // a short list of big pairs would occupy a few warps for long: the pruned
+                // dual-tree kernel spreads each pair over warps of 32 query points instead
+                const bool route_big = lc[3] > 0 && lc[3] <= kRouteBig;
+                int lt[5] = {lc[0], lc[1], lc[2], route_big ? 0 : lc[3], lc[4]};
+                run_bccp_tiles(a, lt, cnts + 16, st, hdb != nullptr, a.fp64 != 0);
+                if (route_big)
+                    WM_TRY(run_bccp_huge(a, a.list[3], lc[3], huge_items, (long long *)(cnts + 12), st, ar,
+                                         hdb != nullptr, a.fp64 != 0, stack_warps));
+                WM_TRY(run_bccp_huge(a, a.list[4], lc[4], huge_items, (long long *)(cnts + 12), st, ar, hdb != nullptr,
                                      a.fp64 != 0, stack_warps));
                 WM_CK(cudaMemcpyAsync(C.pin, ecount, sizeof(int), cudaMemcpyDeviceToHost, st));
                 WM_CK(cudaMemcpyAsync(C.pin + 1, ovf, sizeof(unsigned), cudaMemcpyDeviceToHost, st));

@@ -616,11 +616,11 @@ constexpr int kTileA = 32 * kItems;
 // points of the smaller side staged per warp (8 warps per block, static shared memory < 48 KB)
 __host__ __device__ constexpr int tile_q(int dd) { return dd <= 8 ? 128 : 64; }
 
-__global__ void huge_items_kernel(const TravArgs a, int m, long long *__restrict__ items)
+__global__ void huge_items_kernel(const TravArgs a, const int2 *__restrict__ pairs, int m, long long *__restrict__ items)
 {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j < m) {
-        int P = a.list[4][j].x, Q = a.list[4][j].y;
+        int P = pairs[j].x, Q = pairs[j].y;
         int4 lp = a.links[P], lq = a.links[Q];
         int small = min(lp.y - lp.x, lq.y - lq.x);   // the query side
         items[j] = (small + 31) / 32;
@@ -633,7 +633,8 @@ __global__ void huge_items_kernel(const TravArgs a, int m, long long *__restrict
 }
 
 template <int DP, int DM, bool HDB, bool FP64>
-__global__ void __launch_bounds__(256) bccp_dual_kernel(TravArgs a, int m, const long long *__restrict__ item_off,
+__global__ void __launch_bounds__(256) bccp_dual_kernel(TravArgs a, const int2 *__restrict__ pairs, int m,
+                                                        const long long *__restrict__ item_off,
                                                         const long long *__restrict__ total_items)
 {
     const int lane = threadIdx.x & 31;
@@ -650,7 +651,7 @@ __global__ void __launch_bounds__(256) bccp_dual_kernel(TravArgs a, int m, const
             if (item_off[mid] <= item) lo = mid; else hi = mid - 1;
         }
         const int j = lo;
-        const int P = a.list[4][j].x, Q = a.list[4][j].y;
+        const int P = pairs[j].x, Q = pairs[j].y;
         const int4 lp = a.links[P], lq = a.links[Q];
         // queries: the smaller side; its points far from the other side are pruned at the other
         // tree's root, the rest run a nearest-first descent into it
@@ -1201,23 +1202,24 @@ void pack_nodes(const Tree &T, int d, int dp, int4 *links, float4 *meta, float *
            T.diam2, T.cdmin, T.cdmax, links, meta, box);
 }
 
-// Pruned BCCP of the huge pairs (m of them): one warp per 32 points of a pair's smaller side.
-int run_bccp_huge(TravArgs &a, int m, long long *items, long long *total, cudaStream_t st, Arena &ar, bool hdb,
+// Pruned BCCP of the pairs of a list (the huge pairs, or a short list of big pairs that the
+// tile kernel would give to a few warps only): one warp per 32 points of a pair's smaller side.
+int run_bccp_huge(TravArgs &a, const int2 *pairs, int m, long long *items, long long *total, cudaStream_t st, Arena &ar, bool hdb,
                   bool fp64, int stack_warps)
 {
     if (m <= 0) return 0;
-    launch(huge_items_kernel, grid_for(m, 256, 1 << 20), 256, 0, st, a, m, items);
+    launch(huge_items_kernel, grid_for(m, 256, 1 << 20), 256, 0, st, a, pairs, m, items);
     int rc = scan_exclusive_i64(items, items, m, total, st, ar);
     if (rc) return rc;
     const int blocks = stack_warps / 8;
 #define WM_DUAL(DPV, DMV)                                                                                     \
     do {                                                                                                      \
         if (fp64) {                                                                                           \
-            if (hdb) launch(bccp_dual_kernel<DPV, DMV, true, true>, blocks, 256, 0, st, a, m, items, total);   \
-            else launch(bccp_dual_kernel<DPV, DMV, false, true>, blocks, 256, 0, st, a, m, items, total);      \
+            if (hdb) launch(bccp_dual_kernel<DPV, DMV, true, true>, blocks, 256, 0, st, a, pairs, m, items, total);   \
+            else launch(bccp_dual_kernel<DPV, DMV, false, true>, blocks, 256, 0, st, a, pairs, m, items, total);      \
         } else {                                                                                              \
-            if (hdb) launch(bccp_dual_kernel<DPV, DMV, true, false>, blocks, 256, 0, st, a, m, items, total);  \
-            else launch(bccp_dual_kernel<DPV, DMV, false, false>, blocks, 256, 0, st, a, m, items, total);     \
+            if (hdb) launch(bccp_dual_kernel<DPV, DMV, true, false>, blocks, 256, 0, st, a, pairs, m, items, total);  \
+            else launch(bccp_dual_kernel<DPV, DMV, false, false>, blocks, 256, 0, st, a, pairs, m, items, total);     \
         }                                                                                                     \
     } while (0)
     if (a.d <= 2) WM_DUAL(4, 2);

@@ -92,7 +92,7 @@ void sample_w2(const EdgeK *e, int m, int k, double *out, cudaStream_t st);
 void keep_below(const EdgeK *in, int m, double bound, EdgeK *out, int *count, cudaStream_t st);
 void run_bccp_tiles(TravArgs &a, const int *counts_host, int *next, cudaStream_t st, bool hdb, bool fp64);
 void run_bccp_groups(TravArgs &a, const int *counts_host, cudaStream_t st);
-int run_bccp_huge(TravArgs &a, int m, long long *items, long long *total, cudaStream_t st, Arena &ar, bool hdb,
+int run_bccp_huge(TravArgs &a, const int2 *pairs, int m, long long *items, long long *total, cudaStream_t st, Arena &ar, bool hdb,
                   bool fp64, int stack_warps);
 void pack_nodes(const Tree &T, int d, int dp, int4 *links, float4 *meta, float *box, cudaStream_t st);
 
