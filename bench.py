@@ -233,9 +233,9 @@ def run_serving(wm, jobs, workers, budget, rate_hz=None, seed=1):
 # was measured (sha256), and only for that workload; otherwise the traffic is null.
 MEASURED_TRAFFIC = {
     "bccp": {"bytes": 649192704, "source": "paper_2104_01126_gb300/csrc/wspd.cu",
-             "sha256": "db0cf9ee5f13248b6a7f9e7392dc3104c568efb951b9dead7093911f6f01abb0"},
+             "sha256": "37e646b38af4809f57ea97ef9ace2e0e1cdb91f8766807db17c6dbccce8f9518"},
     "getpairs": {"bytes": 2799996416, "source": "paper_2104_01126_gb300/csrc/wspd.cu",
-                 "sha256": "db0cf9ee5f13248b6a7f9e7392dc3104c568efb951b9dead7093911f6f01abb0"},
+                 "sha256": "37e646b38af4809f57ea97ef9ace2e0e1cdb91f8766807db17c6dbccce8f9518"},
     "knn": {"bytes": 299425792, "source": "paper_2104_01126_gb300/csrc/knn.cu",
             "sha256": "6ae5b2e070e73329be4943549c702cde3167fd62a2199c79ce797dcc00fb3410"},
 }

@@ -136,23 +136,6 @@ __device__ inline double sqdist64(const double *__restrict__ x64, int n, int d, 
 __device__ inline float lower_w2(float q) { float r = __fsub_rd(__fmul_rd(q, 1.0f - kBoxRel), kAbsTiny); return r > 0.f ? r : 0.f; }
 __device__ inline float upper_w2(float q) { return __fadd_ru(__fmul_ru(q, 1.0f + kBoxRel), kAbsTiny); }
 
-// Squared distance between two boxes (lower bound, FP32) and squared max distance (upper).
-__device__ inline void box_bounds(const float *__restrict__ lo, const float *__restrict__ hi, int N, int d,
-                                  int a, int b, float &lb, float &ub)
-{
-    float s = 0.f, t = 0.f;
-    for (int k = 0; k < d; ++k) {
-        float alo = lo[(size_t)k * N + a], ahi = hi[(size_t)k * N + a];
-        float blo = lo[(size_t)k * N + b], bhi = hi[(size_t)k * N + b];
-        float g = fmaxf(fmaxf(blo - ahi, alo - bhi), 0.f);
-        float m = fmaxf(bhi - alo, ahi - blo);
-        s = fmaf(g, g, s);
-        t = fmaf(m, m, t);
-    }
-    lb = lower_w2(s);
-    ub = upper_w2(t);
-}
-
 __device__ inline unsigned lanemask_lt() { unsigned m; asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m)); return m; }
 
 // Block-wide append of cnt >= 0 items per thread: one atomic on the counter per block (a counter

@@ -27,29 +27,7 @@ namespace wm {
 
 namespace {
 
-__device__ inline bool is_leaf(const TravArgs &a, int x) { return a.left[x] < 0; }
 __device__ inline int nsize(const TravArgs &a, int x) { return a.end[x] - a.begin[x]; }
-
-// lower / upper bound of BCCP (or BCCP*) of (P,Q) on the w2 scale, and the well-separation test
-__device__ inline void pair_bounds(const TravArgs &a, int P, int Q, float &lbB, float &ubB, bool &ws)
-{
-    float lb, ub;
-    box_bounds(a.lo, a.hi, a.N, a.d, P, Q, lb, ub);
-    float dP = a.diam2[P], dQ = a.diam2[Q];
-    float dm = fmaxf(dP, dQ);
-    ws = lb > dm;
-    lbB = lb;
-    ubB = ub;
-    if (a.cdmin) {
-        float cminP = a.cdmin[P], cminQ = a.cdmin[Q], cmaxP = a.cdmax[P], cmaxQ = a.cdmax[Q];
-        float lhs = fmaxf(lb, fmaxf(cminP, cminQ));
-        float rhs = fmaxf(dm, fmaxf(cmaxP, cmaxQ));
-        ws = ws || lhs >= rhs;
-        lbB = lhs;
-        ubB = fmaxf(ub, fmaxf(cmaxP, cmaxQ));
-    }
-    if (is_leaf(a, P) && is_leaf(a, Q)) ws = true;
-}
 
 // threshold of the FP32 screen: any candidate whose screened value exceeds T cannot beat the
 // screened minimum s once both are evaluated exactly in FP64.  With an exact FP32 copy (eta = 0)
