@@ -91,8 +91,8 @@ typedef struct {
     double ms_build_tree;
     double ms_core_dist;
     double ms_wspd;       /* GetRho + GetPairs traversals (including inline BCCP)   */
-    double ms_bccp;       /* BCCP / BCCP* tile kernel                               */
-    double ms_kruskal;    /* edge sort + batched Kruskal                             */
+    double ms_bccp;       /* BCCP / BCCP* kernels (all size classes), CUDA events   */
+    double ms_kruskal;    /* batched Kruskal of every round + final sort of the tree */
     double ms_dendrogram;
     int64_t rounds;       /* MemoGFK rounds                                         */
     int64_t pairs_retrieved;   /* well-separated pairs whose BCCP was evaluated     */
@@ -109,13 +109,13 @@ typedef struct {
                                       neighbours at its core distance than kept      */
     int32_t reserved;
     double ms_knn_kernel;          /* CUDA-event time of the k-NN kernel (one launch)   */
-    double ms_tile_kernel;         /* CUDA-event time summed over BCCP tile launches    */
-    int64_t tile_launches;         /* number of BCCP tile kernel launches               */
+    double ms_tile_kernel;         /* CUDA-event time summed over the BCCP flushes      */
+    int64_t tile_launches;         /* BCCP flushes that launched the big-pair kernels   */
     double ms_getpairs;            /* CUDA-event time summed over GetPairs step launches  */
     int64_t getpairs_launches;     /* number of GetPairs step launches                  */
     int64_t getpairs_visits;       /* node pairs examined by the GetPairs traversals     */
     int64_t getrho_visits;         /* node pairs examined by the GetRho traversals       */
-    int64_t bccp_dual_evals;       /* distance evaluations in the pruned BCCP of huge pairs */
+    int64_t bccp_dual_evals;       /* distance evaluations in the pruned dual-tree BCCP */
     int64_t rho_shrinks;           /* times a round lowered rho_hi to fit its edge batch  */
     int64_t max_pending_pairs;     /* peak node pairs pending in a WSPD traversal         */
 } wm_stats;
