@@ -421,7 +421,7 @@ def main():
     ms_max = max_over_ranks(ms, dist, device="cuda")
     value = whole_job_value(n, ws, ms_max)
 
-    # ---- roofline: the dominant kernel (by live CUDA-event time) among those with counted work
+    # ---- roofline: the dominant single kernel (by live CUDA-event time) among those with counted work
     s0 = stats[-1]
     clocks = clk.summary()
     peaks = load_peaks()
@@ -452,13 +452,17 @@ def main():
         kernels.append({"kernel": "bccp_group/pair_tile/dual kernels (all BCCP classes)", "bound": "alu", "achieved": tf,
                         "peak": fp32_peak, "unit": "TFLOP/s", "frac": tf / fp32_peak,
                         "traffic": measured_traffic("bccp", args.workload), "ms": s0.ms_bccp, "launches": None,
+                        "aggregate": True,
                         "note": "summed over every BCCP launch of the step (group, tile and dual-tree kernels); "
                                 "traffic: DRAM bytes of those launches in one step",
                         "work": f"{s0.bccp_evals} distance evaluations x {per} flop",
                         "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock), derived"})
+    # the primary entry is the single kernel with the most live time per step; the BCCP entry
+    # sums several kernels (size classes), so it is listed in "all" but not chosen
     roof = None
-    if kernels:
-        roof = dict(max(kernels, key=lambda k: k["ms"]))
+    singles = [k for k in kernels if not k.get("aggregate")]
+    if singles:
+        roof = dict(max(singles, key=lambda k: k["ms"]))
         roof["all"] = kernels
 
     # ---- end to end through the C ABI with host buffers
