@@ -73,6 +73,8 @@ def _load():
             lib.wmo_core_dist2_kdtree.argtypes = [P, i64, i32, i32, P]
             lib.wmo_boruvka.restype = ctypes.c_int
             lib.wmo_boruvka.argtypes = [P, i64, i32, P, P, P, P]
+            lib.wmo_set_kd_stack_cap.restype = ctypes.c_int
+            lib.wmo_set_kd_stack_cap.argtypes = [i32]
             _lib = lib
     return _lib
 
@@ -92,6 +94,12 @@ def _pts(x) -> np.ndarray:
 def _check(rc: int, what: str):
     if rc != 0:
         raise RuntimeError(f"oracle {what} failed with code {rc}")
+
+
+def set_kd_stack_cap(cap: int = 256):
+    """Capacity of the k-d tree solvers' search stacks (default 256, never reached by a median
+    split tree).  Tests lower it to check that a search that would overflow fails loudly."""
+    _check(_load().wmo_set_kd_stack_cap(int(cap)), "set_kd_stack_cap")
 
 
 def sqdist(x, i: int, j: int) -> float:

@@ -566,6 +566,19 @@ static int kd_build(kdtree_t *t, const double *x, int64_t n, int32_t d)
 
 static void kd_free(kdtree_t *t) { free(t->perm); free(t->node); free(t->blo); free(t->bhi); }
 
+/* Capacity (node ids) of the per-thread search stacks of the two k-d tree solvers below.  A
+ * median-split tree of n < 2^31 points is at most 32 levels deep and a search holds at most two
+ * entries per level, so 256 is never reached; a search that would exceed it fails with -3 instead
+ * of dropping nodes.  wmo_set_kd_stack_cap lowers it so that tests can reach that path. */
+static int32_t g_kd_stack_cap = 256;
+
+int wmo_set_kd_stack_cap(int32_t cap)
+{
+    if (cap < 2 || cap > 256) return -1;
+    g_kd_stack_cap = cap;
+    return 0;
+}
+
 /* Lower bound of D(p, q) over every q in the box of node t.  Each gap is rounded from an exact
  * difference at least as large as the box's (rounding is monotone), squared and summed in the
  * order of wmo_sqdist, so the bound never exceeds the FP64 distance of any point inside. */
@@ -586,7 +599,8 @@ static double kd_box_lb(const kdtree_t *t, int32_t nd, const double *p)
 /*
  * cd2[p] = the minpts-th smallest D(p,q), q = p included: the value wmo_core_dist2 computes, found
  * by a nearest-first search that skips a box only when its lower bound is not below the current
- * minpts-th smallest value.  Returns 0, -1 on bad arguments, -2 on allocation failure.
+ * minpts-th smallest value.  Returns 0, -1 on bad arguments, -2 on allocation failure, -3 when a
+ * search stack would overflow (the values are then not valid).
  */
 int wmo_core_dist2_kdtree(const double *x, int64_t n, int32_t d, int32_t minpts, double *cd2)
 {
@@ -633,10 +647,14 @@ int wmo_core_dist2_kdtree(const double *x, int64_t n, int32_t d, int32_t minpts,
                             heap[c] = w;
                         }
                     }
-                } else if (sp + 2 <= 256) {
+                } else if (sp + 2 <= g_kd_stack_cap) {
                     const double l0 = kd_box_lb(&t, N->left, xp), l1 = kd_box_lb(&t, N->right, xp);
                     stk[sp++] = l0 <= l1 ? N->right : N->left;   /* nearer child on top */
                     stk[sp++] = l0 <= l1 ? N->left : N->right;
+                } else {
+#pragma omp atomic write
+                    err = -3;   /* the search would drop a subtree: fail instead */
+                    break;
                 }
             }
             cd2[p] = heap[0];
@@ -655,7 +673,8 @@ int wmo_core_dist2_kdtree(const double *x, int64_t n, int32_t d, int32_t minpts,
  * lower bound exceeds the best w2 so far), each component keeps the K-minimum of its points', and
  * those edges are added (K is a strict total order, so they form a forest; each is the K-minimum
  * edge across its component's cut, so it is in the tree).  Output in K order, eu < ev.
- * Returns 0, -1 on bad arguments, -2 on allocation failure.
+ * Returns 0, -1 on bad arguments, -2 on allocation failure, -3 when a search stack would overflow,
+ * -4 when a round adds no edge.
  */
 static int32_t bv_find(int32_t *par, int32_t x)
 {
@@ -753,13 +772,14 @@ int wmo_boruvka(const double *x, int64_t n, int32_t d, const double *cd2, int32_
                                 bestq = q;
                             }
                         }
-                    } else if (sp + 2 <= 256) {
+                    } else if (sp + 2 <= g_kd_stack_cap) {
                         const double l0 = kd_box_lb(&t, N->left, xp), l1 = kd_box_lb(&t, N->right, xp);
                         stk[sp++] = l0 <= l1 ? N->right : N->left;
                         stk[sp++] = l0 <= l1 ? N->left : N->right;
                     } else {
 #pragma omp atomic write
                         err = -3;   /* deeper than a balanced tree can be */
+                        break;
                     }
                 }
                 bw[p] = best;

@@ -482,3 +482,18 @@ def test_hdbscan_at_scale_equals_hdbscan():
     b = oracle.hdbscan_at_scale(x, 10, 5)
     for key in ("cd2", "u", "v", "w2", "left", "right", "height", "size", "order", "reach"):
         assert np.array_equal(a[key], b[key]), key
+
+
+def test_kdtree_solvers_fail_loudly_when_a_search_stack_overflows():
+    # A median-split tree never fills the 256-entry search stacks; with the capacity lowered, a
+    # search that would have to drop a subtree must fail instead of returning a wrong value.
+    x = synthdata.uniform(5000, 3, seed=11)
+    oracle.set_kd_stack_cap(6)
+    try:
+        with pytest.raises(RuntimeError, match="code -3"):
+            oracle.core_dist2_kdtree(x, 10)
+        with pytest.raises(RuntimeError, match="code -3"):
+            oracle.boruvka(x)
+    finally:
+        oracle.set_kd_stack_cap(256)
+    assert np.array_equal(oracle.core_dist2_kdtree(x, 10), oracle.core_dist2(x, 10))
