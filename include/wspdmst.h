@@ -53,7 +53,8 @@ extern "C" {
 #define WM_EINVAL (-1)    /* bad argument: n < 1, d not in [1,16], minPts < 1 or > n,
                               non-finite coordinate or |coordinate| > 2^60, bad enum value */
 #define WM_ENOMEM (-2)    /* device memory (or the caller's workspace) exhausted */
-#define WM_ETIMEOUT (-3)  /* a bounded device-side wait gave up */
+#define WM_ETIMEOUT (-3)  /* reserved for a bounded device-side wait that gives up; no call
+                              returns it in this version (the kernels never wait on one another) */
 #define WM_ECUDA (-4)     /* a CUDA runtime call failed */
 #define WM_EINTERNAL (-5) /* an internal consistency check failed (a bug) */
 
@@ -105,8 +106,12 @@ typedef struct {
     int64_t tree_depth;
     size_t workspace_bytes_used;   /* peak workspace use of this call               */
     double max_rel_screen_err;     /* max |fp32 - fp64| / fp64 over rechecked winners */
-    int32_t tie_overflow;          /* HDBSCAN*: some point had more equal-distance
-                                      neighbours at its core distance than kept      */
+    int32_t tie_overflow;          /* HDBSCAN*: 1 when the pairs within some point's core
+                                      distance (the tie-repair edges) exceeded their
+                                      buffer, which takes inputs far from general position
+                                      (many exact duplicates).  The call still returns
+                                      WM_OK with an MST of G_MR, but that tree may differ
+                                      from the K-minimum one; 0 otherwise             */
     int32_t reserved;
     double ms_knn_kernel;          /* CUDA-event time of the k-NN kernel (one launch)   */
     double ms_tile_kernel;         /* CUDA-event time summed over the BCCP flushes      */
@@ -134,19 +139,19 @@ typedef struct {
 /* ---------------------------------------------------------------------- entry points */
 
 /*
- * wm_emst -- Euclidean minimum spanning tree (Sec. 2.1 "EMST"; method: Sec. 3.1, Algorithm 3).
+ * wm_emst -- Euclidean minimum spanning tree (Sec. 2.1 "EMST"; method: Sec. 3.2, Algorithm 3).
  *   pts        n points, dtype WM_F32/WM_F64, layout WM_AOS/WM_SOA (host or device)
  *   n >= 1, 1 <= d <= 16
  *   out_edges  n-1 wm_edge, K order (host or device; may be NULL when n == 1)
  *   out_total_weight  sum of the n-1 weights (host pointer; may be NULL)
  *   opts       may be NULL
- * Returns WM_OK or WM_EINVAL / WM_ENOMEM / WM_ETIMEOUT / WM_ECUDA / WM_EINTERNAL.
+ * Returns WM_OK or WM_EINVAL / WM_ENOMEM / WM_ECUDA / WM_EINTERNAL.
  */
 int wm_emst(const void *pts, int64_t n, int32_t d, int32_t dtype, int32_t layout,
             wm_edge *out_edges, double *out_total_weight, const wm_opts *opts);
 
 /*
- * wm_hdbscan -- HDBSCAN* (Sec. 2.1 "HDBSCAN*"; method: Sec. 3.2.2 with the disjunctive
+ * wm_hdbscan -- HDBSCAN* (Sec. 2.1 "HDBSCAN*"; method: Sec. 3.1.2 with the disjunctive
  * well-separation, Algorithm 3 with BCCP*, and Sec. 4 for the ordered dendrogram).
  *   min_pts          1 <= min_pts <= n
  *   out_mst          n-1 wm_edge of the MST of G_MR, K order           (may be NULL)
@@ -224,16 +229,24 @@ int wm_single_linkage(const wm_edge *tree, int64_t n, int32_t start, wm_dnode *o
  * cudaFree, cudaMallocHost or other allocating routine and creates no CUDA events.  The caller
  * still owns the input and the outputs, which may be host or device memory as for wm_emst.
  *
- *   Limits   1 <= n <= WM_NOALLOC_MAX_POINTS, 1 <= d <= 16; a larger n returns WM_EINVAL.  An
- *            input whose pair traversal needs more scratch than the array holds returns
+ *   Limits   1 <= n <= WM_NOALLOC_MAX_POINTS, 1 <= d <= 16; a larger n returns WM_EINVAL.  When
+ *            a traversal or edge-batch capacity overflows, the call doubles it and restarts, as
+ *            wm_emst does; an input whose buffers then no longer fit in the array returns
  *            WM_ENOMEM with a message (wm_emst, which allocates, still handles it).
- *   Memory   every GPU on which the library is loaded holds the array until the process exits.
- *   Set-up   the first call on a device, with that device current, looks up the array's device
- *            address once (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   Memory   the array is part of the library's device code: it is reserved on a GPU when that
+ *            code is loaded there, which under CUDA's lazy module loading is the first call into
+ *            the library on that GPU that launches a kernel or looks the array up (any entry
+ *            point), and at library load otherwise.  It stays reserved until the process exits.
+ *            A caller that reserves the rest of the device for a pool of its own should make one
+ *            call first (a one-point input will do), so that the array is already in place.
+ *   Set-up   the first call of this entry point on a device, with that device current, looks up
+ *            the array's device address once (cudaGetSymbolAddress); make that first call before
+ *            any stream capture.
  *   Sharing  all calls on a device use the same array, which keeps the last call's contents (the
  *            call initialises everything it reads).  Calls whose GPU work overlapped would race
  *            on it; within one process this entry point prevents that by holding a per-device
- *            lock for the whole call and returning only after its GPU work has completed.
+ *            lock for the whole call and returning only after its GPU work has completed, on
+ *            every path including the error returns.
  */
 #define WM_NOALLOC_MAX_POINTS 32768
 #define WM_NOALLOC_SCRATCH_BYTES (64u << 20)

@@ -209,12 +209,24 @@ def _is_cuda_tensor(x) -> bool:
     return t is not None and isinstance(x, t.Tensor) and x.is_cuda
 
 
-def _points(x):
-    """Returns (keepalive, pointer, n, d, dtype code, on_device, torch device or None)."""
+def _points(x, layout: str = "aos"):
+    """Returns (keepalive, pointer, n, d, dtype code, on_device, torch device or None).
+
+    layout "aos": x has shape (n, d), a row per point; "soa": x has shape (d, n), a row per
+    coordinate (the C ABI's WM_SOA)."""
+    if layout not in ("aos", "soa"):
+        raise ValueError("layout must be 'aos' or 'soa'")
+    r = _points_aos(x)
+    if layout == "soa":
+        return r[0], r[1], r[3], r[2], r[4], r[5], r[6]
+    return r
+
+
+def _points_aos(x):
     t = _torch()
     if t is not None and isinstance(x, t.Tensor):
         if x.dim() != 2:
-            raise ValueError("points must have shape (n, d)")
+            raise ValueError("points must be a 2-D array")
         if x.dtype not in (t.float32, t.float64):
             x = x.to(t.float64)
         x = x.contiguous()
@@ -222,7 +234,7 @@ def _points(x):
         return x, x.data_ptr(), x.shape[0], x.shape[1], code, x.is_cuda, (x.device if x.is_cuda else None)
     a = np.asarray(x)
     if a.ndim != 2:
-        raise ValueError("points must have shape (n, d)")
+        raise ValueError("points must be a 2-D array")
     if a.dtype not in (np.float32, np.float64):
         a = a.astype(np.float64)
     a = np.ascontiguousarray(a)
@@ -284,10 +296,13 @@ def _dnode_result(buf, m: int, device):
 
 
 # ---------------------------------------------------------------------------------- API
-def emst(points, precision: str = "fp32", stream=None, return_stats: bool = False, workspace=None):
-    """Euclidean MST (wm_emst).  Returns dict(u, v, w, total[, stats]); edges in K order."""
+def emst(points, precision: str = "fp32", stream=None, return_stats: bool = False, workspace=None,
+         layout: str = "aos"):
+    """Euclidean MST (wm_emst).  Returns dict(u, v, w, total[, stats]); edges in K order.
+    workspace: optional (device pointer, bytes) of a caller-owned arena; layout: "aos" for an
+    (n, d) array, "soa" for a (d, n) array."""
     lib = load()
-    keep, ptr, n, d, code, on_dev, dev = _points(points)
+    keep, ptr, n, d, code, on_dev, dev = _points(points, layout)
     m = max(n - 1, 0)
     buf, bptr = _out_buffer(16 * m, dev)
     total = ctypes.c_double(0.0)
@@ -295,7 +310,8 @@ def emst(points, precision: str = "fp32", stream=None, return_stats: bool = Fals
     if stream is None and on_dev:
         stream = _current_stream(dev)
     o = _opts(precision, stream, st, workspace)
-    rc = lib.wm_emst(ptr, n, d, code, WM_AOS, bptr if m > 0 else None, ctypes.byref(total), ctypes.byref(o))
+    rc = lib.wm_emst(ptr, n, d, code, WM_SOA if layout == "soa" else WM_AOS, bptr if m > 0 else None,
+                     ctypes.byref(total), ctypes.byref(o))
     _check(rc, "wm_emst")
     u, v, w = _edges_result(buf, m, dev)
     out = {"u": u, "v": v, "w": w, "total": total.value}
@@ -326,10 +342,11 @@ def emst_noalloc(points, precision: str = "fp32", stream=None):
 
 
 def hdbscan(points, min_pts: int = 10, start: int = 0, precision: str = "fp32", stream=None,
-            return_stats: bool = False, workspace=None):
-    """HDBSCAN* (wm_hdbscan): MST of G_MR, core distances, ordered dendrogram, reachability plot."""
+            return_stats: bool = False, workspace=None, layout: str = "aos"):
+    """HDBSCAN* (wm_hdbscan): MST of G_MR, core distances, ordered dendrogram, reachability plot.
+    workspace and layout as for emst()."""
     lib = load()
-    keep, ptr, n, d, code, on_dev, dev = _points(points)
+    keep, ptr, n, d, code, on_dev, dev = _points(points, layout)
     m = max(n - 1, 0)
     ebuf, eptr = _out_buffer(16 * m, dev)
     cbuf, cptr = _out_buffer(8 * n, dev)
@@ -340,7 +357,8 @@ def hdbscan(points, min_pts: int = 10, start: int = 0, precision: str = "fp32", 
     if stream is None and on_dev:
         stream = _current_stream(dev)
     o = _opts(precision, stream, st, workspace)
-    rc = lib.wm_hdbscan(ptr, n, d, code, WM_AOS, int(min_pts), eptr if m else None, cptr, dptr if m else None,
+    rc = lib.wm_hdbscan(ptr, n, d, code, WM_SOA if layout == "soa" else WM_AOS, int(min_pts), eptr if m else None,
+                        cptr, dptr if m else None,
                         optr, rptr, int(start), ctypes.byref(o))
     _check(rc, "wm_hdbscan")
     u, v, w = _edges_result(ebuf, m, dev)

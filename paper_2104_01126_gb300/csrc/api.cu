@@ -677,6 +677,11 @@ static int run_call(const wm_opts *opts, long long n, int d, int min_pts, Body b
             caps.extra_bytes += std::max<long long>(256LL << 20, (long long)(need / 2));
             continue;
         }
+        if (rc == 0 && (ovf & 8u)) {
+            set_detail("a BCCP traversal stack overflowed (internal error)%s", "");
+            rc = WM_EINTERNAL;
+            break;
+        }
         if (rc == 0 && ovf == 0) break;
         if (rc == WM_ENOMEM && user_ws) {
             set_detail("caller workspace too small%s (%lld bytes given)", "", (long long)C.ar.cap);
@@ -1323,24 +1328,59 @@ extern "C" int wm_emst_noalloc(const void *pts, int64_t n, int32_t d, int32_t dt
     C.ar.base = (char *)nd.scratch;
     C.ar.cap = WM_NOALLOC_SCRATCH_BYTES;
     // Capacities sized for WM_NOALLOC_MAX_POINTS: traversal chunks of 4096 pairs and edge batches of
-    // 4n + 65536; WSPD stack and pair lists follow from the chunk (see memogfk).
+    // 4n + 65536; WSPD stack and pair lists follow from the chunk (see memogfk).  A capacity that
+    // overflows is doubled and the call restarts, as wm_emst does, for as long as the array holds
+    // the larger buffers.
     Caps caps;
     caps.chunk = 4096;
     caps.edges = 4 * n + 65536;
     caps.frontier_scale = 1;
     caps.extra_bytes = 0;
     EmstCtx c{pts, n, d, dtype, layout, out_edges, out_total_weight};
+    int rc = 0;
     unsigned ovf = 0;
-    int rc = emst_body(C, &c, caps, &ovf);
-    if (rc == 0 && (ovf || C.ar.failed)) rc = WM_ENOMEM;
-    if (rc == WM_ENOMEM)
-        set_detail("wm_emst_noalloc: this input needs more than the %s%lld-byte static scratch; use wm_emst", "",
-                   (long long)WM_NOALLOC_SCRATCH_BYTES);
+    size_t peak = 0;
+    for (int attempt = 0; attempt < 6; ++attempt) {
+        C.ar.off = 0;
+        C.ar.peak = 0;
+        C.ar.failed = false;
+        C.stats = wm_stats{};
+        ovf = 0;
+        rc = emst_body(C, &c, caps, &ovf);
+        // On every path (success, overflow, out of scratch, CUDA error) the GPU work of this attempt
+        // must have finished before the array is reused by the next attempt or, once the lock is
+        // released, by another call.
+        const cudaError_t se = cudaStreamSynchronize(C.st);
+        peak = std::max(peak, C.ar.peak);
+        if (rc == 0 && se != cudaSuccess) {
+            set_detail("CUDA error %s%lld", cudaGetErrorString(se), 0);
+            rc = WM_ECUDA;
+        }
+        if (rc == 0 && C.ar.failed) rc = WM_ENOMEM;
+        if (rc == WM_ENOMEM) {
+            set_detail("wm_emst_noalloc: this input needs more than the %s%lld-byte static scratch; use wm_emst", "",
+                       (long long)WM_NOALLOC_SCRATCH_BYTES);
+            break;
+        }
+        if (rc == 0 && (ovf & 8u)) {
+            set_detail("a BCCP traversal stack overflowed (internal error)%s", "");
+            rc = WM_EINTERNAL;
+        }
+        if (rc != 0 || ovf == 0) break;
+        if (ovf & 1u) caps.frontier_scale *= 2;
+        if (ovf & 2u) caps.edges *= 2;
+    }
+    if (rc == 0 && ovf) {
+        rc = WM_ENOMEM;
+        set_detail("wm_emst_noalloc: the pair traversal or the edge batch still overflowed after %s%lld restarts "
+                   "with doubled capacities; use wm_emst", "", 5LL);
+    }
     cudaError_t le = cudaGetLastError();
     if (rc == 0 && le != cudaSuccess) {
         set_detail("CUDA error %s%lld", cudaGetErrorString(le), 0);
         rc = WM_ECUDA;
     }
+    C.ar.peak = peak;
     C.stats.workspace_bytes_used = C.ar.peak;
     C.stats.ms_total = total.ms();
     if (opts && opts->stats) *opts->stats = C.stats;

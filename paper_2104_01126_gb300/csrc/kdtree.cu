@@ -1,5 +1,5 @@
 // kdtree.cu -- ingest of the input points and the spatial-median k-d tree (Sec. 2.3 "k-d tree";
-// Sec. 3.1.1: spatial-median splits down to one point per leaf).
+// Sec. 3.2.1: spatial-median splits down to one point per leaf).
 //
 // A node splits its tight bounding box at the midpoint of the widest dimension.  If every point
 // falls on one side (all points equal, or an extent of one float ulp) the node splits its points

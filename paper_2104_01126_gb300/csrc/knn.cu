@@ -1,5 +1,5 @@
 // knn.cu -- core distances for HDBSCAN* (Sec. 2.1: cd(p) = distance to the minPts-th nearest
-// neighbour, p itself counted; Sec. 2.3 / 3.2.2: computed with k-NN queries, k = minPts), the
+// neighbour, p itself counted; Sec. 2.3 / 3.1.3: computed with k-NN queries, k = minPts), the
 // per-node cd_min / cd_max bounds (Table 1) and the repair edges that make the returned MST the
 // canonical one under the key K.
 //
@@ -46,6 +46,7 @@ struct KnnArgs {
     int *slow;           // slow query list
     int *slow_cnt;
     int *next_group;     // dispenser of 32-query groups
+    int *err;            // set when a traversal stack would overflow (an internal error)
     unsigned long long *stat;   // [0] evals, [1] fp64 rechecks
 };
 
@@ -242,7 +243,11 @@ __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
                     l1 += __shfl_xor_sync(0xffffffffu, l1, o);
                 }
                 int first = l0 <= l1 ? c1 : c0, second = l0 <= l1 ? c0 : c1;
-                if (sp + 2 > a.stack_cap) { sp = 0; break; }   // cannot happen: cap = depth + 4
+                if (sp + 2 > a.stack_cap) {   // cannot happen: cap = depth + 4; reported, not ignored
+                    if (lane == 0) atomicOr(a.err, 1);
+                    sp = 0;
+                    break;
+                }
                 if (lane == 0) { stk[sp] = first; stk[sp + 1] = second; }
                 __syncwarp();
                 sp += 2;
@@ -515,6 +520,7 @@ int core_distances(Points &P, Tree &T, int min_pts, bool fp64, HdbState &H, Aren
     int blocks = 152 * std::max(1, 32 / wpb);
     int total_warps = blocks * wpb;
     a.next_group = cnts + 6;
+    a.err = cnts + 5;
     a.stack = ar.get<int>((size_t)total_warps * a.stack_cap);
     a.wscratch = ar.get<double>((size_t)total_warps * KL * 32);
     if (!a.stack || !a.wscratch) return WM_ENOMEM;
@@ -567,11 +573,15 @@ int core_distances(Points &P, Tree &T, int min_pts, bool fp64, HdbState &H, Aren
     launch(rep_emit_kernel, grid_for(n, 256), 256, 0, st, a.rep_q, a.rep_d, a.rep_cnt, off, n, KL, H.cd64, P.pid, rep);
     launch(rep_emit_extra_kernel, grid_for(extra_cap, 256), 256, 0, st, ex_p, ex_q, ex_d, cnts + 1, extra_cap, H.cd64,
            P.pid, rep, cnts + 3);
-    cudaMemcpyAsync(pin, cnts, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(pin, cnts, 8 * sizeof(int), cudaMemcpyDeviceToHost, st);
     unsigned long long hs[2];
     cudaMemcpyAsync(pin + 8, a.stat, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;
     memcpy(hs, pin + 8, sizeof hs);
+    if (pin[5]) {
+        set_error_detail("k-NN: a traversal stack overflowed (internal error)");
+        return WM_EINTERNAL;
+    }
     const int nrep = pin[3];
     if (stats) {
         stats->knn_evals = (int64_t)hs[0];

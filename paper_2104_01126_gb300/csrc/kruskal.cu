@@ -1,4 +1,4 @@
-// kruskal.cu -- batched Kruskal over a union-find shared across rounds (Sec. 3.1.2
+// kruskal.cu -- batched Kruskal over a union-find shared across rounds (Sec. 3.2.2
 // "ParallelKruskal", Algorithms 2 and 3), made deterministic with reservations.
 //
 // A batch of edges is accepted exactly as sequential Kruskal would accept it in the order of the

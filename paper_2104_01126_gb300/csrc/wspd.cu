@@ -1,5 +1,5 @@
-// wspd.cu -- the lazily traversed well-separated pair decomposition of MemoGFK (Sec. 3.1.1,
-// Algorithm 1; Sec. 3.1.3, Algorithm 3) and the BCCP / BCCP* computations (Sec. 2.3, 3.1.2, 3.2.2).
+// wspd.cu -- the lazily traversed well-separated pair decomposition of MemoGFK (Sec. 3.2.1,
+// Algorithm 1; Sec. 3.2.3, Algorithm 3) and the BCCP / BCCP* computations (Sec. 2.3, 3.2.2, 3.1.2).
 //
 // Per round the host runs, with the union-find state of the previous rounds:
 //   comp labels  : every node gets the component id shared by all its points, or -1 (mixed);
@@ -19,7 +19,7 @@
 // Well-separation tests use boxes (the nodes' bounding volumes).  Geometric separation is
 // d(A,B) > max(diam A, diam B) with d and diam the box distance and box diagonal, made strict and
 // rigorous so that every cross pair is strictly heavier than every pair inside A or inside B; for
-// HDBSCAN* the disjunction with mutual unreachability (Sec. 3.2.2) is used.  Two single points
+// HDBSCAN* the disjunction with mutual unreachability (Sec. 3.1.2) is used.  Two single points
 // always form a pair.
 #include "wspd.cuh"
 
@@ -793,7 +793,10 @@ __global__ void __launch_bounds__(256) bccp_dual_kernel(TravArgs a, const int2 *
                     l0 += __shfl_xor_sync(0xffffffffu, l0, o);
                     l1 += __shfl_xor_sync(0xffffffffu, l1, o);
                 }
-                if (sp + 2 > a.stack_cap) break;   // cannot happen: cap = tree depth + 4
+                if (sp + 2 > a.stack_cap) {   // cannot happen: cap = tree depth + 4; reported, not ignored
+                    if (lane == 0) atomicOr(a.overflow, 8u);
+                    break;
+                }
                 if (lane == 0) {
                     stk[sp] = l0 <= l1 ? c1 : c0;
                     stk[sp + 1] = l0 <= l1 ? c0 : c1;

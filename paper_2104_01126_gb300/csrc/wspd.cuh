@@ -43,7 +43,8 @@ struct TravArgs {
     EdgeK *edges = nullptr;
     int *edge_count = nullptr;
     int edge_cap = 0;
-    unsigned *overflow = nullptr;      // bit 0 frontier, bit 1 edges, bit 2 big pairs
+    unsigned *overflow = nullptr;      // bit 0 frontier, bit 1 edges, bit 2 big pairs,
+                                       // bit 3 a traversal stack overflowed (internal error)
     // internal nodes not known to be connected, kept from round to round (connectivity only
     // grows): the GetRho frontier reads node_in (all nodes when null) and writes the survivors
     // to node_out, which the GetPairs frontier of the same round reads

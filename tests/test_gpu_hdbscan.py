@@ -1,5 +1,5 @@
 """HDBSCAN* parity: core distances, MST of G_MR, ordered dendrogram and reachability plot from
-the CUDA path against the FP64 oracle, element by element (Sec. 2.1, Sec. 3.2, Sec. 4)."""
+the CUDA path against the FP64 oracle, element by element (Sec. 2.1, Sec. 3.1, Sec. 4)."""
 import numpy as np
 import pytest
 

@@ -6,7 +6,7 @@ force in tests/test_oracle.py) and compare every output of the CUDA path with th
   - HDBSCAN* on the bench workload (10^6 Gaussian-mixture points in 3-D, minPts 10, FP32 screen,
     the call bench.py times): MST edges and weights, core distances, dendrogram, order and bars;
   - EMST on the scale generators: 10^7 points (uniform 2-D and 3-D, varden 2-D), and 10^6 points
-    (3 x 10^5 in 7-D) for the other generator / dimension pairs.
+    for the other generator / dimension pairs (3 x 10^5 for varden 7-D).
 """
 import math
 
@@ -41,7 +41,7 @@ def test_hdbscan_bench_workload_full_parity():
                                       ("varden", 2, 10_000_000), ("uniform", 3, 1_000_000),
                                       ("varden", 2, 1_000_000), ("varden", 3, 1_000_000),
                                       ("uniform", 5, 1_000_000), ("varden", 5, 1_000_000),
-                                      ("varden", 7, 300_000)])
+                                      ("uniform", 7, 1_000_000), ("varden", 7, 300_000)])
 def test_emst_full_parity(kind, d, n):
     import torch
     x = synthdata.generate(kind, n, d, seed=0)

@@ -51,7 +51,8 @@ def _find_edge(keys, ws, a, b):
     return ws[i] if i < len(keys) and keys[i] == k else None
 
 
-@pytest.mark.parametrize("kind,d", [("uniform", 2), ("uniform", 3), ("varden", 3), ("uniform", 5)])
+@pytest.mark.parametrize("kind,d", [("uniform", 2), ("uniform", 3), ("varden", 3), ("uniform", 5), ("varden", 5),
+                                    ("uniform", 7), ("varden", 7)])
 def test_emst_ten_million_points(kind, d):
     n = 10_000_000
     x = synthdata.generate(kind, n, d, seed=0)

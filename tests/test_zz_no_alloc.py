@@ -28,7 +28,7 @@ def lib():
     return wm.load()
 
 
-def _call_noalloc(lib, x, precision=0):
+def _call_noalloc(lib, x, precision=0, stream=None):
     """wm_emst_noalloc through ctypes with host input and host outputs."""
     x = np.ascontiguousarray(x)
     n, d = x.shape
@@ -36,6 +36,7 @@ def _call_noalloc(lib, x, precision=0):
     total = ctypes.c_double(-1.0)
     opts = wm._Opts()
     opts.precision = precision
+    opts.stream = stream
     dtype = wm.WM_F32 if x.dtype == np.float32 else wm.WM_F64
     rc = lib.wm_emst_noalloc(x.ctypes.data, n, d, dtype, wm.WM_AOS, out.ctypes.data, ctypes.byref(total),
                              ctypes.byref(opts))
@@ -49,7 +50,8 @@ def _same(noalloc_out, noalloc_total, ref):
     assert abs(noalloc_total - ref["total"]) <= 1e-12 * max(ref["total"], 1e-300)
 
 
-@pytest.mark.parametrize("kind,n,d,prec", [("uniform", 20000, 2, 0), ("gmm", 32768, 3, 0), ("uniform", 5000, 5, 1)])
+@pytest.mark.parametrize("kind,n,d,prec", [("uniform", 20000, 2, 0), ("gmm", 32768, 3, 0), ("uniform", 5000, 5, 1),
+                                           ("uniform", 32768, 7, 0), ("uniform", 32768, 16, 0)])
 def test_noalloc_matches_wm_emst_on_two_calls_in_a_row(lib, kind, n, d, prec):
     xs = [synthdata.generate(kind, n, d, seed) for seed in (1, 2)]
     for x in xs:   # two calls in a row; the second reuses the static scratch left by the first
@@ -86,3 +88,31 @@ def test_noalloc_tiny_inputs(lib):
         assert rc == 0
         ref = wm.emst(x)
         _same(out, total, ref)
+
+
+def test_noalloc_two_threads_on_two_streams(lib):
+    # Calls from two host threads, each on a stream of its own, share the one static array: the
+    # entry point serialises them per device and returns only after its GPU work has finished,
+    # so every result must still equal wm_emst's.
+    import threading
+    inputs = [[synthdata.generate(kind, 6000 + 997 * i, d, seed=40 + 10 * t + i) for i in range(3)]
+              for t, (kind, d) in enumerate((("uniform", 3), ("gmm", 2)))]
+    refs = [[wm.emst(x) for x in xs] for xs in inputs]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    results = [[None] * 3, [None] * 3]
+
+    def worker(t):
+        torch.cuda.set_device(0)
+        for i, x in enumerate(inputs[t]):
+            results[t][i] = _call_noalloc(lib, x, stream=streams[t].cuda_stream)
+
+    threads = [threading.Thread(target=worker, args=(t,)) for t in range(2)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    for t in range(2):
+        for i in range(3):
+            rc, out, total = results[t][i]
+            assert rc == 0
+            _same(out, total, refs[t][i])
