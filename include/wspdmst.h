@@ -123,6 +123,14 @@ typedef struct {
     int64_t bccp_dual_evals;       /* distance evaluations in the pruned dual-tree BCCP */
     int64_t rho_shrinks;           /* times a round lowered rho_hi to fit its edge batch  */
     int64_t max_pending_pairs;     /* peak node pairs pending in a WSPD traversal         */
+    int64_t bccp_pairs_below;      /* retrieved pairs whose BCCP lay below the round's
+                                      range (found in an earlier round)                   */
+    int64_t bccp_pairs_above;      /* retrieved pairs whose BCCP lay at or above the
+                                      round's range (found again in a later round)        */
+    int64_t bccp_evals_outside;    /* distance evaluations spent on those pairs (group
+                                      and tile kernels)                                   */
+    int64_t bccp_tile_evals_skipped; /* point pairs of the tile kernel whose evaluation a
+                                        chunk's bounding box ruled out                   */
 } wm_stats;
 
 /* Options.  A zero-initialised struct (or NULL) gives the defaults. */
@@ -304,6 +312,34 @@ int wm_poll(wm_server *s, int64_t ticket, int32_t *status, double *latency_ms);
 int wm_wait(wm_server *s, int64_t ticket, double *latency_ms);
 /* Counters: jobs finished, peak admitted bytes, peak number of jobs running together. */
 int wm_server_counters(wm_server *s, int64_t *finished, size_t *peak_bytes, int32_t *peak_running);
+
+/*
+ * Tuning.  Parameters that change how fast a call runs, never what it returns (every setting
+ * yields the same K-minimum tree, dendrogram and plot).  A call takes them from a built-in table
+ * chosen by (problem, d, n) and written by the project's autotuner (paper_2104_01126_gb300/
+ * autotune.py), unless wm_set_tuning has set an override for the whole process.
+ */
+typedef struct {
+    int32_t tight_diameters; /* 1: a node's diameter bound is the smallest of its box diagonal,
+                                its largest pairwise distance (<= 32 points) and twice its
+                                bounding-sphere radius; 0: the box diagonal alone           */
+    int32_t chunk_log2;      /* WSPD traversal: node pairs popped per step = 2^chunk_log2;
+                                0 = from n (min(2^21, max(2^12, 4n)))                        */
+    int32_t dfs_budget;      /* WSPD traversal: depth-first rounds a warp runs on its own
+                                stack per step (1..64)                                       */
+    int32_t route_big;       /* BCCP: a flush's big pairs go to the pruned dual-tree kernel
+                                when there are at most this many                              */
+    int32_t medium_max;      /* BCCP: pairs with |A||B| up to this (65..4096) take one warp   */
+    int32_t big_max;         /* BCCP: pairs up to this (>= medium_max) take the tile kernel;
+                                larger ones the dual-tree kernel                              */
+    int32_t reserved[10];
+} wm_tuning;
+
+/* The parameters a call with these sizes uses (min_pts = 0 for EMST). */
+int wm_get_tuning(int64_t n, int32_t d, int32_t min_pts, wm_tuning *out);
+/* Overrides the table for every later call of the process (NULL restores it).  WM_EINVAL for
+ * out-of-range values.  Not for use while other threads are inside library calls. */
+int wm_set_tuning(const wm_tuning *t);
 
 /*
  * wm_query_footprint -- an upper estimate of the device workspace, in bytes, that a call with

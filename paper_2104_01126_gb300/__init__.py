@@ -21,7 +21,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["emst", "hdbscan", "single_linkage", "query_footprint", "library_path", "load",
-           "WMError", "Stats", "version", "batch"]
+           "WMError", "Stats", "version", "batch", "get_tuning", "set_tuning", "tuning"]
 
 WM_F32, WM_F64 = 0, 1
 WM_AOS, WM_SOA = 0, 1
@@ -59,13 +59,24 @@ class _Stats(ctypes.Structure):
                 ("ms_getpairs", ctypes.c_double), ("getpairs_launches", ctypes.c_int64),
                 ("getpairs_visits", ctypes.c_int64), ("getrho_visits", ctypes.c_int64),
                 ("bccp_dual_evals", ctypes.c_int64), ("rho_shrinks", ctypes.c_int64),
-                ("max_pending_pairs", ctypes.c_int64)]
+                ("max_pending_pairs", ctypes.c_int64), ("bccp_pairs_below", ctypes.c_int64),
+                ("bccp_pairs_above", ctypes.c_int64), ("bccp_evals_outside", ctypes.c_int64),
+                ("bccp_tile_evals_skipped", ctypes.c_int64)]
 
 
 class _Opts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("precision", ctypes.c_int32),
                 ("reserved0", ctypes.c_int32), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t), ("stats", ctypes.POINTER(_Stats))]
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("tight_diameters", ctypes.c_int32), ("chunk_log2", ctypes.c_int32), ("dfs_budget", ctypes.c_int32),
+                ("route_big", ctypes.c_int32), ("medium_max", ctypes.c_int32), ("big_max", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 10)]
+
+
+TUNING_FIELDS = ("tight_diameters", "chunk_log2", "dfs_budget", "route_big", "medium_max", "big_max")
 
 
 class _Instance(ctypes.Structure):
@@ -123,6 +134,10 @@ class Stats:
     bccp_dual_evals: int = 0
     rho_shrinks: int = 0
     max_pending_pairs: int = 0
+    bccp_pairs_below: int = 0
+    bccp_pairs_above: int = 0
+    bccp_evals_outside: int = 0
+    bccp_tile_evals_skipped: int = 0
 
     @classmethod
     def _from(cls, s: _Stats) -> "Stats":
@@ -181,6 +196,10 @@ def load(build_if_missing: bool = True):
         lib.wm_batch.argtypes = [ctypes.POINTER(_Instance), i32, i32, i32, ctypes.POINTER(_Opts)]
         lib.wm_emst_noalloc.restype = ctypes.c_int
         lib.wm_emst_noalloc.argtypes = [P, i64, i32, i32, i32, P, P, ctypes.POINTER(_Opts)]
+        lib.wm_get_tuning.restype = ctypes.c_int
+        lib.wm_get_tuning.argtypes = [i64, i32, i32, ctypes.POINTER(_Tuning)]
+        lib.wm_set_tuning.restype = ctypes.c_int
+        lib.wm_set_tuning.argtypes = [ctypes.POINTER(_Tuning)]
         _lib = lib
         return lib
 
@@ -482,6 +501,42 @@ def query_footprint(n: int, d: int, min_pts: int = 0) -> int:
     b = ctypes.c_size_t(0)
     _check(lib.wm_query_footprint(n, d, min_pts, ctypes.byref(b)), "wm_query_footprint")
     return b.value
+
+
+def get_tuning(n: int, d: int, min_pts: int = 0) -> dict:
+    """The speed parameters a call with these sizes uses (wm_get_tuning)."""
+    t = _Tuning()
+    _check(load().wm_get_tuning(int(n), int(d), int(min_pts), ctypes.byref(t)), "wm_get_tuning")
+    return {f: getattr(t, f) for f in TUNING_FIELDS}
+
+
+def set_tuning(params=None):
+    """Overrides the built-in tuning table for every later call (wm_set_tuning); None restores it.
+    params: a dict of TUNING_FIELDS (missing fields keep the table's value for n = 10^6, d = 3)."""
+    lib = load()
+    if params is None:
+        _check(lib.wm_set_tuning(None), "wm_set_tuning")
+        return
+    base = get_tuning(1_000_000, 3, 0)
+    base.update(params)
+    t = _Tuning()
+    for f in TUNING_FIELDS:
+        setattr(t, f, int(base[f]))
+    _check(lib.wm_set_tuning(ctypes.byref(t)), "wm_set_tuning")
+
+
+class tuning:
+    """Context manager: `with tuning(dfs_budget=4): ...` runs calls with an override."""
+
+    def __init__(self, **params):
+        self.params = params
+
+    def __enter__(self):
+        set_tuning(self.params)
+        return self
+
+    def __exit__(self, *exc):
+        set_tuning(None)
 
 
 def kernel_launch_count() -> int:

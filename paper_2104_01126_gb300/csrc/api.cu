@@ -25,7 +25,7 @@ std::atomic<long long> g_launch_count{0};
 
 int ingest_points(const void *dev_src, int n, int d, int dtype, int layout, Points &P, Arena &ar, cudaStream_t st,
                   unsigned *pinned);
-int build_tree(Points &P, Tree &T, Arena &ar, cudaStream_t st, int *pinned);
+int build_tree(Points &P, Tree &T, Arena &ar, cudaStream_t st, int *pinned, bool tight_diameters);
 int batch_kruskal(const EdgeK *e, int m, int n, int *uf, unsigned long long *R, EdgeK *out, int out_base, int *accepted,
                   Arena &ar, cudaStream_t st, int *pinned);
 
@@ -124,7 +124,7 @@ static size_t estimate_bytes(long long n, int d, int min_pts, const Caps &c)
     b += (size_t)N * (32 + 8 * dp);         // packed node records
     b += (size_t)((N / 2 + 2 + (2 * depth + 4) * 2 * c.chunk) * c.frontier_scale + 8 * c.chunk) * 8;   // stack, step outputs
     b += (size_t)8 * (c.chunk + 1) * (5 * 8 + 16 + 4 + 8);   // pair lists (8 chunks each), huge-pair slots
-    b += (size_t)152 * 64 * (depth + 4) * 4;                                                           // dual stacks
+    b += (size_t)num_sms() * 64 * (depth + 4) * 4;                                                           // dual stacks
     b += (size_t)c.edges * 16 * 3 + (size_t)c.edges * 24;   // batch, filtered, sort tmp, kruskal
     b += (size_t)n * 16 * 2;                // output tree + conversion
     if (min_pts > 0) {
@@ -144,6 +144,33 @@ static Caps default_caps(long long n, int min_pts)
     c.frontier_scale = 1;
     c.extra_bytes = 0;
     return c;
+}
+
+// ------------------------------------------------------------------------------- tuning
+// The built-in table (written by the autotuner): builtin_tuning(n, d, min_pts, &t).
+#include "tuning_table.inc"
+
+static std::mutex g_tune_mu;
+static bool g_tune_set = false;
+static wm_tuning g_tune_override{};
+
+static bool tuning_valid(const wm_tuning &t)
+{
+    return (t.tight_diameters == 0 || t.tight_diameters == 1) &&
+           (t.chunk_log2 == 0 || (t.chunk_log2 >= 12 && t.chunk_log2 <= 24)) && t.dfs_budget >= 1 &&
+           t.dfs_budget <= 64 && t.route_big >= 0 && t.medium_max >= 65 && t.medium_max <= 4096 &&
+           t.big_max >= t.medium_max;
+}
+
+static wm_tuning tuning_for(long long n, int d, int min_pts)
+{
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        if (g_tune_set) return g_tune_override;
+    }
+    wm_tuning t{};
+    builtin_tuning(n, d, min_pts, &t);
+    return t;
 }
 
 // ------------------------------------------------------------------------------- kernels
@@ -234,6 +261,7 @@ struct Call {
     Arena ar;
     int *pin = nullptr;
     wm_stats stats{};
+    wm_tuning tune{};
     int precision = WM_PREC_FP32_SCREEN;
     bool timing = true;   // per-kernel CUDA-event timing into stats
     double event_ms(cudaEvent_t a, cudaEvent_t b)
@@ -294,7 +322,6 @@ static void set_rho(TravArgs &a, double lo, double hi)
 // `target` when the points form several instances that must not be joined (a batch): then every
 // edge weight is below rho_cap, rho_hi never exceeds it, and no pair at or above it is retrieved.
 // hdb: optional HDBSCAN* state (node cd bounds, per-position cd2, repair edges).
-constexpr int kRouteBig = 1024;   // big-pair lists up to this length go to the dual-tree kernel
 static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps &caps, EdgeK *E_out, int *uf,
                    unsigned long long *R, unsigned *overflow_bits, long long target = -1, double rho_cap = INFINITY)
 {
@@ -319,7 +346,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     EdgeK *huge_best = ar.get<EdgeK>(lcap + 1);
     unsigned *huge_sbest = ar.get<unsigned>(lcap + 1);
     long long *huge_items = ar.get<long long>(lcap + 1);
-    const int stack_warps = 152 * 8 * 8;   // warps of the dual-tree kernel (grid-stride)
+    const int stack_warps = num_sms() * 8 * 8;   // warps of the dual-tree kernel (grid-stride)
     int *dual_stack = ar.get<int>((size_t)stack_warps * (T.depth + 4));
     const int dp = P.d <= 4 ? 4 : P.d <= 8 ? 8 : 16;
     int4 *links = ar.get<int4>(T.N);
@@ -330,7 +357,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     unsigned *rho = ar.get<unsigned>(2);
     double *samples = ar.get<double>(4096);
     unsigned *ovf = ar.get<unsigned>(2);
-    unsigned long long *stat = ar.get<unsigned long long>(8);
+    unsigned long long *stat = ar.get<unsigned long long>(16);
     int *comp_scratch = ar.get<int>(2LL * n + 1);
     if (ar.failed) return WM_ENOMEM;
     // counters: [2..6] pair-list counts, [7] edge count, [10..11] counts of the two node lists,
@@ -342,7 +369,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         if (hdb) { T2.cdmin = hdb->cdmin; T2.cdmax = hdb->cdmax; }
         pack_nodes(T2, P.d, dp, links, meta, box, st);
     }
-    WM_CK(cudaMemsetAsync(stat, 0, 8 * sizeof(unsigned long long), st));
+    WM_CK(cudaMemsetAsync(stat, 0, 16 * sizeof(unsigned long long), st));
     WM_CK(cudaMemsetAsync(ovf, 0, 2 * sizeof(unsigned), st));
     WM_CK(cudaMemsetAsync(cnts, 0, 64 * sizeof(int), st));
 
@@ -354,6 +381,10 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     a.fp64 = C.precision == WM_PREC_FP64;
     a.eta = a.fp64 ? 0.0 : 2.0 * (double)P.delta * std::sqrt((double)P.d) * (1.0 + 1e-6);
     a.exact32 = a.eta == 0.0;
+    a.delta32 = P.delta;
+    a.dfs_budget = C.tune.dfs_budget;
+    a.medium_max = C.tune.medium_max;
+    a.big_max = C.tune.big_max;
     if (hdb) {
         a.cdmin = hdb->cdmin; a.cdmax = hdb->cdmax; a.cd32 = hdb->cd32; a.cd64 = hdb->cd64;
     }
@@ -428,7 +459,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
             int lc[5] = {C.pin[2], C.pin[3], C.pin[4], C.pin[5], C.pin[6]};
             int e = C.pin[7];
             bool flush = empty;
-            for (int c = 0; c < 5; ++c) flush = flush || lc[c] > lcap - (long long)kPoll * dfs_step_visits(chunk);
+            for (int c = 0; c < 5; ++c) flush = flush || lc[c] > lcap - (long long)kPoll * dfs_step_visits(chunk, a.dfs_budget);
             if (!flush) continue;
             mark_event();
             ev_kind.push_back(0);
@@ -441,7 +472,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
                 run_bccp_groups(a, lc, st);
                 // a short list of big pairs would occupy a few warps for long: the pruned
                 // dual-tree kernel spreads each pair over warps of 32 query points instead
-                const bool route_big = lc[3] > 0 && lc[3] <= kRouteBig;
+                const bool route_big = lc[3] > 0 && lc[3] <= C.tune.route_big;
                 int lt[5] = {lc[0], lc[1], lc[2], route_big ? 0 : lc[3], lc[4]};
                 run_bccp_tiles(a, lt, cnts + 16, st, hdb != nullptr, a.fp64 != 0);
                 if (route_big)
@@ -537,9 +568,9 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         WM_CK(cudaStreamSynchronize(st));
         C.stats.ms_kruskal += ts.ms();
     }
-    WM_CK(cudaMemcpyAsync(C.pin, stat, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    WM_CK(cudaMemcpyAsync(C.pin, stat, 16 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     WM_CK(cudaStreamSynchronize(st));
-    unsigned long long hs[8];
+    unsigned long long hs[16];
     memcpy(hs, C.pin, sizeof hs);
     C.stats.getpairs_visits = (int64_t)hs[4];
     C.stats.getrho_visits = (int64_t)hs[5];
@@ -550,6 +581,10 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     C.stats.bccp_evals = (int64_t)hs[1];
     C.stats.fp64_rechecks += (int64_t)hs[2];
     C.stats.bccp_tile_evals = (int64_t)hs[3];
+    C.stats.bccp_pairs_below = (int64_t)hs[8];
+    C.stats.bccp_pairs_above = (int64_t)hs[9];
+    C.stats.bccp_evals_outside = (int64_t)hs[10];
+    C.stats.bccp_tile_evals_skipped = (int64_t)hs[11];
     ar.off = mark;
     return 0;
 }
@@ -577,7 +612,7 @@ static int prepare(Call &C, const void *pts, int64_t n, int32_t d, int32_t dtype
     if (rc) return rc;
     C.stats.ms_ingest = ti.ms();
     Timer tt;
-    WM_TRY(build_tree(S.P, S.T, C.ar, st, C.pin));
+    WM_TRY(build_tree(S.P, S.T, C.ar, st, C.pin, C.tune.tight_diameters != 0));
     C.stats.ms_build_tree = tt.ms();
     C.stats.tree_nodes = S.T.N;
     C.stats.tree_depth = S.T.depth;
@@ -636,6 +671,8 @@ static int run_call(const wm_opts *opts, long long n, int d, int min_pts, Body b
     if (!C.pin) { set_detail("cudaMallocHost failed%s", ""); return WM_ENOMEM; }
     Caps caps = default_caps(n, min_pts);
     caps.extra_bytes = extra_bytes;
+    C.tune = tuning_for(n, d, min_pts);
+    if (C.tune.chunk_log2) caps.chunk = 1LL << C.tune.chunk_log2;
     const bool user_ws = opts && opts->workspace;
     int rc = 0;
     unsigned ovf_seen = 0;   // capacities that overflowed in earlier attempts
@@ -1212,9 +1249,32 @@ int wm_batch(const wm_instance *inst, int32_t count, int32_t dtype, int32_t layo
         sum.ms_knn_kernel += gs.ms_knn_kernel; sum.ms_tile_kernel += gs.ms_tile_kernel;
         sum.ms_getpairs += gs.ms_getpairs;
         sum.max_pending_pairs = std::max(sum.max_pending_pairs, gs.max_pending_pairs);
+        sum.bccp_pairs_below += gs.bccp_pairs_below; sum.bccp_pairs_above += gs.bccp_pairs_above;
+        sum.bccp_evals_outside += gs.bccp_evals_outside;
+        sum.bccp_tile_evals_skipped += gs.bccp_tile_evals_skipped;
     }
     if (opts && opts->stats) *opts->stats = sum;
     return rc;
+}
+
+int wm_get_tuning(int64_t n, int32_t d, int32_t min_pts, wm_tuning *out)
+{
+    if (!out || n < 1 || d < 1 || d > kMaxDim || min_pts < 0) return WM_EINVAL;
+    *out = tuning_for(n, d, min_pts);
+    return WM_OK;
+}
+
+int wm_set_tuning(const wm_tuning *t)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (!t) {
+        g_tune_set = false;
+        return WM_OK;
+    }
+    if (!tuning_valid(*t)) return WM_EINVAL;
+    g_tune_override = *t;
+    g_tune_set = true;
+    return WM_OK;
 }
 
 int wm_query_footprint(int64_t n, int32_t d, int32_t min_pts, size_t *bytes)
@@ -1325,6 +1385,7 @@ extern "C" int wm_emst_noalloc(const void *pts, int64_t n, int32_t d, int32_t dt
     C.precision = precision;
     C.timing = false;
     C.pin = g_noalloc_host;
+    C.tune = tuning_for(n, d, 0);
     C.ar.base = (char *)nd.scratch;
     C.ar.cap = WM_NOALLOC_SCRATCH_BYTES;
     // Capacities sized for WM_NOALLOC_MAX_POINTS: traversal chunks of 4096 pairs and edge batches of

@@ -207,7 +207,7 @@ void batch_edge_place(const EdgeK *keys, const EdgeK *E, int m, const long long 
 
 void batch_totals(const wm_edge *stage, const long long *base, int k, double *tot, cudaStream_t st)
 {
-    launch(inst_total_kernel, std::min(k, 152 * 16), 256, 0, st, stage, base, k, tot);
+    launch(inst_total_kernel, std::min(k, num_sms() * 16), 256, 0, st, stage, base, k, tot);
 }
 
 void batch_cd(const double *cd64, const int *pid, int total, double *stage, cudaStream_t st)

@@ -433,6 +433,135 @@ __global__ void finish_boxes_kernel(int N, int n, int d, const int *__restrict__
     if ((threadIdx.x & 31) == 0) atomicMax(max_depth, dmax);
 }
 
+// Tighter diameter bounds.  The box diagonal can be far above the largest distance between the
+// points of a node, most of all in high dimension, where a few points set the box's extent in each
+// coordinate, and a smaller bound lets node pairs pass the geometric separation test of the WSPD
+// higher up the tree (fewer, larger pairs).  Any rigorous upper bound of the diameter keeps the
+// MST argument valid, so every internal node takes the smallest of
+//   - its box diagonal (finish_boxes_kernel),
+//   - m <= 32 points: the largest pairwise distance of its points,
+//   - m > 32: 2 r, r an upper bound of the distance from the box centre c to any of its points;
+//     for m <= kDiamDirect r is found from the points, above it from the children's radii
+//     (every point of child i is within r_i + |c - c_i| of c), bottom-up.
+// Point distances are evaluated in FP32 (relative error <= 2^-19 for exactly representable
+// operands, covered by the 2^-18 margin) and widened by the FP32 copy's absolute error delta per
+// coordinate into bounds on the FP64 points; the centre distances in FP64 with a margin.
+constexpr int kDiamDirect = 4096;
+
+template <int DM>
+__global__ void __launch_bounds__(256) tight_diam_kernel(int N, int n, int d, const int *__restrict__ nbegin,
+                                                         const int *__restrict__ nend, const int *__restrict__ nleft,
+                                                         const float *__restrict__ x32, const float *__restrict__ lo,
+                                                         const float *__restrict__ hi, float delta,
+                                                         float *__restrict__ diam2, float *__restrict__ rad)
+{
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const double dsq = (double)delta * sqrt((double)d) * (1.0 + 1e-6);
+    // a warp reads the records of 32 consecutive nodes and then works through those with
+    // 3..kDiamDirect points together (a leaf's radius is only needed for composition above
+    // kDiamDirect points, and two points' box diagonal is already their distance)
+    for (int base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < N; base += nw * 32) {
+        const int mine = base + lane;
+        int mb = 0, mm = 0;
+        if (mine < N && nleft[mine] >= 0) {
+            mb = nbegin[mine];
+            mm = nend[mine] - mb;
+        }
+        unsigned todo = __ballot_sync(0xffffffffu, mm >= 3 && mm <= kDiamDirect);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int nd = base + src;
+            const int b = __shfl_sync(0xffffffffu, mb, src), m = __shfl_sync(0xffffffffu, mm, src);
+            float c[DM];
+#pragma unroll
+            for (int k = 0; k < DM; ++k) c[k] = k < d ? 0.5f * (lo[(size_t)k * N + nd] + hi[(size_t)k * N + nd]) : 0.f;
+            float mr = 0.f;
+            for (int i = b + lane; i < b + m; i += 32) {
+                float s = 0.f;
+#pragma unroll
+                for (int k = 0; k < DM; ++k) {
+                    if (k < d) {
+                        const float t = x32[(size_t)k * n + i] - c[k];
+                        s = fmaf(t, t, s);
+                    }
+                }
+                mr = fmaxf(mr, s);
+            }
+            for (int o = 16; o; o >>= 1) mr = fmaxf(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+            const double r = sqrt((double)mr * (1.0 + 1.0 / 262144.0)) * (1.0 + 1e-12) + dsq;
+            double bound = 4.0 * r * r;
+            if (m <= 32) {
+                float p[DM];
+#pragma unroll
+                for (int k = 0; k < DM; ++k) p[k] = (k < d && lane < m) ? x32[(size_t)k * n + b + lane] : 0.f;
+                float mx = 0.f;
+                for (int j = 1; j < m; ++j) {
+                    float s = 0.f;
+#pragma unroll
+                    for (int k = 0; k < DM; ++k) {
+                        if (k < d) {
+                            const float t = p[k] - __shfl_sync(0xffffffffu, p[k], j);
+                            s = fmaf(t, t, s);
+                        }
+                    }
+                    if (lane < j) mx = fmaxf(mx, s);
+                }
+                for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                const double q = sqrt((double)mx * (1.0 + 1.0 / 262144.0)) * (1.0 + 1e-12) + 2.0 * dsq;
+                bound = fmin(bound, q * q);
+            }
+            if (lane == 0) {
+                rad[nd] = __double2float_ru(r);
+                const float f = __double2float_ru(bound * (1.0 + 1.0 / 1099511627776.0) + 1e-300);
+                if (f < diam2[nd]) diam2[nd] = f;
+            }
+        }
+    }
+}
+
+// Radii of the nodes above kDiamDirect points, bottom-up with arrival counters: each node whose
+// parent is above the limit starts a climb; the second child to arrive at a parent composes it.
+__global__ void diam_up_kernel(int N, int d, const int *__restrict__ nbegin, const int *__restrict__ nend,
+                               const int *__restrict__ nleft, const int *__restrict__ nright,
+                               const int *__restrict__ nparent, const float *__restrict__ lo,
+                               const float *__restrict__ hi, float *diam2, float *rad, int *arrive)
+{
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x) {
+        const int px = nparent[x];
+        if (nend[x] - nbegin[x] > kDiamDirect || px < 0 || nend[px] - nbegin[px] <= kDiamDirect) continue;
+        int cur = x;
+        for (int it = 0; it < 128; ++it) {   // at most the tree depth
+            const int p = nparent[cur];
+            if (p < 0) break;
+            __threadfence();
+            if (atomicAdd(&arrive[p], 1) == 0) break;   // the sibling composes the parent
+            __threadfence();
+            double r = 0.0;
+            for (int side = 0; side < 2; ++side) {
+                const int ch = side ? nright[p] : nleft[p];
+                double cc = 0.0;
+                for (int k = 0; k < d; ++k) {
+                    const double cp = 0.5 * ((double)lo[(size_t)k * N + p] + (double)hi[(size_t)k * N + p]);
+                    const double ci = 0.5 * ((double)lo[(size_t)k * N + ch] + (double)hi[(size_t)k * N + ch]);
+                    const double t = cp - ci;
+                    cc += t * t;
+                }
+                // nodes of one or two points have no radius of their own: every point lies in the
+                // box, within half its (rounded-up) diagonal of the centre
+                const double rc = nend[ch] - nbegin[ch] < 3 ? 0.5 * sqrt((double)diam2[ch]) * (1.0 + 1e-12)
+                                                             : (double)((volatile float *)rad)[ch];
+                r = fmax(r, (sqrt(cc) * (1.0 + 1e-12) + rc) * (1.0 + 1e-12));
+            }
+            rad[p] = __double2float_ru(r);
+            const float f = __double2float_ru(4.0 * r * r * (1.0 + 1.0 / 1099511627776.0) + 1e-300);
+            if (f < diam2[p]) diam2[p] = f;
+            cur = p;
+        }
+    }
+}
+
 __global__ void inverse_perm_kernel(const int *__restrict__ pid, int *__restrict__ pos, int n)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -478,7 +607,7 @@ int ingest_points(const void *dev_src, int n, int d, int dtype, int layout, Poin
     return 0;
 }
 
-int build_tree(Points &P, Tree &T, Arena &ar, cudaStream_t st, int *pinned)
+int build_tree(Points &P, Tree &T, Arena &ar, cudaStream_t st, int *pinned, bool tight_diameters)
 {
     const int n = P.n, d = P.d;
     const int N = 2 * n - 1;
@@ -561,7 +690,7 @@ int build_tree(Points &P, Tree &T, Arena &ar, cudaStream_t st, int *pinned)
         for (int g = 0; g < kLevelsPerSync; ++g) {
             launch(level_begin_kernel, 1, 1, 0, st, tcur, tsmall, lstate);
             const Level L{act, uoff, tcur};
-            const int gw = 152 * 8;   // blocks of 256 threads, 8 warps each
+            const int gw = num_sms() * 8;   // blocks of 256 threads, 8 warps each
             launch(box_units_kernel, gw, 256, 0, st, L, T.begin, T.end, r32, n, N, d, T.lo, T.hi, ucnt, sdim, sval);
             launch(count_units_kernel, gw, 256, 0, st, L, lstate, T.begin, T.end, T.left, T.right, T.parent, depth, r32,
                                                     n, sdim, sval, cnt, ucnt, csplit, bigu, issmall);
@@ -624,6 +753,26 @@ int build_tree(Points &P, Tree &T, Arena &ar, cudaStream_t st, int *pinned)
     P.x64 = f64;
     launch(finish_boxes_kernel, grid_for(N, 256), 256, 0, st, N, n, d, T.begin, T.left, P.x32, T.lo, T.hi, P.delta, T.diam2,
                                                          depth, maxdep);
+    if (tight_diameters) {
+        // a warp handles 32 consecutive nodes per iteration
+        const int blocks = (int)std::min<long long>(((long long)N + 255) / 256, (long long)num_sms() * 16);
+        float *rad = ar.get<float>(N);
+        if (!rad) return WM_ENOMEM;
+#define WM_TD(DM) launch(tight_diam_kernel<DM>, blocks, 256, 0, st, N, n, d, T.begin, T.end, T.left, P.x32, T.lo, T.hi, \
+                         P.delta, T.diam2, rad)
+        if (d <= 2) WM_TD(2);
+        else if (d <= 3) WM_TD(3);
+        else if (d <= 4) WM_TD(4);
+        else if (d <= 5) WM_TD(5);
+        else if (d <= 8) WM_TD(8);
+        else WM_TD(16);
+#undef WM_TD
+        if (n > kDiamDirect) {
+            cudaMemsetAsync(T.arrive, 0, sizeof(int) * N, st);
+            launch(diam_up_kernel, grid_for(N, 256), 256, 0, st, N, d, T.begin, T.end, T.left, T.right, T.parent, T.lo,
+                   T.hi, T.diam2, rad, T.arrive);
+        }
+    }
     launch(inverse_perm_kernel, grid_for(n, 256, 1 << 20), 256, 0, st, P.pid, P.pos, n);
     cudaMemcpyAsync(pinned, maxdep, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;

@@ -517,7 +517,7 @@ int core_distances(Points &P, Tree &T, int min_pts, bool fp64, HdbState &H, Aren
     size_t per_warp = (size_t)32 * dmp * 4 + (size_t)KL * 32 * ((fp64 ? 8 : 4) + 4);
     int wpb = (int)std::min<size_t>(8, std::max<size_t>(1, (48u << 10) / per_warp));
     size_t smem = per_warp * wpb;
-    int blocks = 152 * std::max(1, 32 / wpb);
+    int blocks = num_sms() * std::max(1, 32 / wpb);
     int total_warps = blocks * wpb;
     a.next_group = cnts + 6;
     a.err = cnts + 5;
@@ -558,7 +558,7 @@ int core_distances(Points &P, Tree &T, int min_pts, bool fp64, HdbState &H, Aren
     if (nslow > 0) {
         size_t sm2 = (size_t)min_pts * 32 * 8 + 32 * 4;
         cudaFuncSetAttribute(knn_slow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
-        launch(knn_slow_kernel, std::min(nslow, 152 * 8), 32, sm2, st, a, a.slow, nslow, ex_q, ex_p, ex_d, cnts + 1,
+        launch(knn_slow_kernel, std::min(nslow, num_sms() * 8), 32, sm2, st, a, a.slow, nslow, ex_q, ex_p, ex_d, cnts + 1,
                                                                      extra_cap, cnts + 2);
     }
     // node bounds

@@ -299,7 +299,7 @@ int batch_kruskal(const EdgeK *e, int m, int n, int *uf, unsigned long long *R, 
         for (int b = 0; b < 4; ++b, ++step) {
             // the pending list shrinks by a factor of about 2 to 4 per step: a smaller grid (the
             // loops are grid-strided, so any size is correct) keeps the nearly empty steps short
-            const int g = std::max(152, grid_for(std::max(1, base_m >> std::min(step - base_step, 30)), 256));
+            const int g = std::max(num_sms(), grid_for(std::max(1, base_m >> std::min(step - base_step, 30)), 256));
             const StepArgs a = args(step);
             launch(reserve_hi_kernel, g, 256, 0, st, a, n, uf, cnt + 5);
             launch(reserve_lo_kernel, g, 256, 0, st, a);

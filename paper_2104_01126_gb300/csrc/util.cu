@@ -241,7 +241,7 @@ int radix_sort_edges(EdgeK *keys, EdgeK *tmp, int m, cudaStream_t st, Arena &ar,
     unsigned *hhist = (unsigned *)host_scratch;
     if (!ghist) return WM_ENOMEM;
     cudaMemsetAsync(ghist, 0, sizeof(unsigned) * 16 * 256, st);
-    launch(rs_hist_all, grid_for(m, 256, 152 * 4), 256, 0, st, keys, m, ghist);
+    launch(rs_hist_all, grid_for(m, 256, num_sms() * 4), 256, 0, st, keys, m, ghist);
     cudaMemcpyAsync(hhist, ghist, sizeof(unsigned) * 16 * 256, cudaMemcpyDeviceToHost, st);
     cudaError_t ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) { ar.off = mark; return WM_ECUDA; }

@@ -196,9 +196,29 @@ inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
     kernel<<<grid, block, smem, st>>>(std::forward<Args>(args)...);
 }
 
-// kernel launch helpers
-inline int grid_for(long long work, int block, int max_blocks = 152 * 16)
+// Streaming multiprocessors of the current device (read once per device and cached); grids are
+// sized in multiples of it.
+inline int num_sms()
 {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); dev = 0; }
+    std::atomic<int> &c = cache[dev & 63];
+    int v = c.load(std::memory_order_relaxed);
+    if (v <= 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            v = 1;
+        }
+        c.store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
+// kernel launch helpers
+inline int grid_for(long long work, int block, int max_blocks = -1)
+{
+    if (max_blocks < 0) max_blocks = num_sms() * 16;
     long long g = (work + block - 1) / block;
     if (g < 1) g = 1;
     if (g > max_blocks) g = max_blocks;

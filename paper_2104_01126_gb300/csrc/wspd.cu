@@ -43,6 +43,23 @@ __device__ inline float screen_threshold(float s, const TravArgs &a)
     return __double2float_ru(q * q * (1.0 + 2.0 * kEps32) + 1.5e-42);
 }
 
+// True when a screened value s proves that the exact FP64 weight of its point pair is at or above
+// rho_hi, so that the pair's edge cannot belong to this round and needs no FP64 recheck.  The
+// bound used is a rigorous lower bound of that weight: with an exact FP32 copy, w2 >= s (1 - 2^-18)
+// - 2e-42 (the screen errs by at most 2^-19 relative plus subnormal rounding, the FP64 evaluation
+// by 2^-48); otherwise (sqrt of that - eta)^2 (1 - 2^-40).  For HDBSCAN* s may be a core distance
+// cd32, which bounds cd64 from below within 2^-22, so the smaller of the two bounds is taken.
+__device__ inline bool screened_above(float s, const TravArgs &a)
+{
+    double lo = (double)s * (1.0 - 1.0 / 262144.0) - 2e-42;
+    if (!a.exact32) {
+        const double r = lo > 0.0 ? sqrt(lo) - a.eta : 0.0;
+        lo = r > 0.0 ? r * r * (1.0 - 1.0 / 1099511627776.0) : 0.0;
+    }
+    if (a.cd64) lo = fmin(lo, (double)s * (1.0 - 1.0 / 4194304.0));
+    return lo >= a.rho_hi;
+}
+
 __device__ inline float dist32(const float *__restrict__ x32, int n, int d, int i, int j)
 {
     float s = 0.f;
@@ -139,10 +156,40 @@ __device__ inline bool in_range(const TravArgs &a, const KMin &m)
            m.hi < (unsigned long long)__double_as_longlong(a.rho_hi);
 }
 
+// outcome of a BCCP against the round's range: -1 below rho_lo, 0 inside, 1 at or above rho_hi
+__device__ inline int range_side(const TravArgs &a, const KMin &m)
+{
+    if (m.hi == ~0ull || m.hi >= (unsigned long long)__double_as_longlong(a.rho_hi)) return 1;
+    return m.hi < (unsigned long long)__double_as_longlong(a.rho_lo) ? -1 : 0;
+}
+
+// per-thread tallies of BCCP outcomes outside the round's range (stat[8..10])
+struct Waste {
+    unsigned long long below = 0, above = 0, ev = 0;
+    __device__ void add(int side, unsigned long long evals)
+    {
+        if (side < 0) ++below;
+        if (side > 0) ++above;
+        if (side != 0) ev += evals;
+    }
+};
+
 __device__ inline unsigned long long warp_sum_u64(unsigned long long v)
 {
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+__device__ inline void waste_flush(const TravArgs &a, Waste w)
+{
+    w.below = warp_sum_u64(w.below);
+    w.above = warp_sum_u64(w.above);
+    w.ev = warp_sum_u64(w.ev);
+    if ((threadIdx.x & 31) == 0 && (w.below | w.above)) {
+        atomicAdd(a.stat + 8, w.below);
+        atomicAdd(a.stat + 9, w.above);
+        atomicAdd(a.stat + 10, w.ev);
+    }
 }
 
 // warp-aggregated append of one edge per lane that has one
@@ -163,7 +210,7 @@ __device__ inline void warp_emit(const TravArgs &a, bool has, const KMin &m)
 
 
 // ------------------------------------------------------------------ packed node records
-// links = {begin, end, left, right}; meta = {diam2 bound, cdmin, cdmax, 0};
+// links = {begin, end, left, right}; meta = {diam2 bound, cdmin, cdmax, comp label};
 // box[node][2*DP] = lo[0..DP), hi[0..DP) with padded dimensions set to 0.
 template <int DP>
 __device__ inline void pair_bounds_packed(const TravArgs &a, int P, int Q, const int4 &lp, const int4 &lq,
@@ -206,8 +253,8 @@ __device__ inline void pair_bounds_packed(const TravArgs &a, int P, int Q, const
 // pair-size classes of a retrieved well-separated pair (by |A||B|)
 constexpr int kTinyMax = 8;      // one thread per pair
 constexpr int kSmallMax = 64;    // 8 lanes per pair
-constexpr int kMediumMax = 1024; // one warp per pair
-constexpr long long kBigMax = 65536; // warp tiles (brute force); larger pairs: pruned dual-tree BCCP
+// (larger pairs: one warp per pair up to TravArgs::medium_max, warp tiles (brute force) up to
+// big_max, the pruned dual-tree BCCP above)
 
 // One FindPair visit of the node pair me (Algorithm 1's recursion body).  MODE 0 = GetRho
 // (WriteMin candidates into rho_cand, pruned by rho_now), MODE 1 = GetPairs (classifies a
@@ -235,7 +282,7 @@ __device__ inline void visit_pair(const TravArgs &a, int2 me, float rho_now, int
         if (lbB >= a.rho_hi_f || ubB < a.rho_lo_f) return;
         if (ws) {
             long long prod = (long long)sp * sq;
-            cls = prod <= kTinyMax ? 0 : prod <= kSmallMax ? 1 : prod <= kMediumMax ? 2 : prod <= kBigMax ? 3 : 4;
+            cls = prod <= kTinyMax ? 0 : prod <= kSmallMax ? 1 : prod <= a.medium_max ? 2 : prod <= a.big_max ? 3 : 4;
             return;
         }
     }
@@ -431,12 +478,14 @@ __global__ void __launch_bounds__(256) bccp_group_kernel(TravArgs a, const int2 
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
     const int n = a.n, d = a.d;
     unsigned long long n_ev = 0, n_re = 0;
+    Waste waste;
     for (int base = warp * PPW; base < m; base += nwarps * PPW) {
         const int pi = base + lane / G;
         const bool valid = pi < m;
         int pb = 0, qb = 0, na = 0, nb = 0;
+        int2 pr = make_int2(0, 0);
         if (valid) {
-            int2 pr = pairs[pi];
+            pr = pairs[pi];
             int4 lp = a.links[pr.x], lq = a.links[pr.y];
             pb = lp.x; na = lp.y - lp.x; qb = lq.x; nb = lq.y - lq.x;
         }
@@ -473,7 +522,9 @@ __global__ void __launch_bounds__(256) bccp_group_kernel(TravArgs a, const int2 
             }
 #pragma unroll
             for (int o = G / 2; o; o >>= 1) smin = fminf(smin, __shfl_xor_sync(0xffffffffu, smin, o));
-            const float T = screen_threshold(smin, a);
+            // a pair whose screened minimum already proves its BCCP above the round's range
+            // gets no recheck (its edge belongs to a later round, if any)
+            const float T = screened_above(smin, a) ? -1.f : screen_threshold(smin, a);
             // the candidates (few) are evaluated again for the recheck.  A lane's first candidate is
             // rechecked after the loop, where the lanes run together (an FP64 instruction costs the
             // same however few lanes are active); later ones inline
@@ -500,8 +551,10 @@ __global__ void __launch_bounds__(256) bccp_group_kernel(TravArgs a, const int2 
             if (oh < best.hi || (oh == best.hi && ol < best.lo)) { best.hi = oh; best.lo = ol; }
         }
         if (g == 0) n_ev += (unsigned long long)tot;
+        if (valid && g == 0) waste.add(range_side(a, best), (unsigned long long)tot);
         warp_emit(a, valid && g == 0 && in_range(a, best), best);
     }
+    waste_flush(a, waste);
     n_ev = warp_sum_u64(n_ev);
     n_re = warp_sum_u64(n_re);
     if (lane == 0 && n_ev) {
@@ -837,12 +890,16 @@ __global__ void __launch_bounds__(256) bccp_dual_kernel(TravArgs a, const int2 *
 __global__ void huge_emit_kernel(TravArgs a, int m)
 {
     const int lane = threadIdx.x & 31;
+    Waste waste;
     const int limit = (m + 31) & ~31;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j - lane < limit; j += gridDim.x * blockDim.x) {
         KMin b{~0ull, ~0ull};
         if (j < m) { b.hi = a.huge_best[j].hi; b.lo = a.huge_best[j].lo; }
+        // (a BCCP above the range may be a partial minimum here: the dual-tree search prunes at rho_hi)
+        if (j < m) waste.add(range_side(a, b), 0);
         warp_emit(a, j < m && in_range(a, b), b);
     }
+    waste_flush(a, waste);
 }
 
 // BCCP of one medium or big pair per warp (pairs handed out in small chunks): the larger side A
@@ -876,7 +933,8 @@ __global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const i
     };
     const int d = D > 0 ? D : a.d;
     const int n = a.n;
-    unsigned long long n_ev = 0, n_re = 0;
+    unsigned long long n_ev = 0, n_re = 0, n_skip = 0;
+    Waste waste;
     // pairs handed out `chunk` at a time (sizes vary too much for a static deal; on long lists
     // one counter increment per pair would serialise the warps on it)
     int j = 0, jend = 0;
@@ -915,14 +973,78 @@ __global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const i
             for (int b0 = bbeg; b0 < bend; b0 += kTileQ) {
                 const int nb = min(kTileQ, bend - b0);
                 __syncwarp();
-                // stage the B chunk: q[jj*(DD+1) + k], last slot = cd (HDB)
+                // stage the B chunk: q[jj*(DD+1) + k], last slot = cd (HDB); gather its bounding box
+                // and smallest core distance on the way
+                float blo[DD], bhi[DD];
+#pragma unroll
+                for (int k = 0; k < DD; ++k) { blo[k] = INFINITY; bhi[k] = -INFINITY; }
+                float bcd = INFINITY;
                 for (int jj = lane; jj < nb; jj += 32) {
 #pragma unroll
                     for (int k = 0; k < DD; ++k)
-                        if (D > 0 || k < d) q[jj * (DD + 1) + k] = a.x32[(size_t)k * n + b0 + jj];
-                    q[jj * (DD + 1) + DD] = HDB ? a.cd32[b0 + jj] : 0.f;
+                        if (D > 0 || k < d) {
+                            const float v = a.x32[(size_t)k * n + b0 + jj];
+                            q[jj * (DD + 1) + k] = v;
+                            blo[k] = fminf(blo[k], v);
+                            bhi[k] = fmaxf(bhi[k], v);
+                        }
+                    const float c = HDB ? a.cd32[b0 + jj] : 0.f;
+                    q[jj * (DD + 1) + DD] = c;
+                    bcd = fminf(bcd, c);
                 }
-                __syncwarp();
+                // Chunk pruning: an A point skips the chunk when a rigorous lower bound of its
+                // FP64 w2 to every point of the chunk exceeds both the band threshold of the
+                // running screened minimum (then none of them can be a candidate) and rho_hi
+                // (then none of them can give this round's edge), with the margins the dual-tree
+                // kernel uses.  The box is widened by delta so that it holds the FP64 points.
+                float thr_now;
+                if (FP64) {
+                    thr_now = best.hi == ~0ull ? INFINITY : __double2float_ru(__longlong_as_double((long long)best.hi));
+                    for (int o = 16; o; o >>= 1) thr_now = fminf(thr_now, __shfl_xor_sync(0xffffffffu, thr_now, o));
+                } else {
+                    thr_now = run_min == INFINITY ? INFINITY : screen_threshold(run_min, a);
+                }
+                thr_now = fminf(thr_now, a.rho_hi_f) * (1.0f + 1.0f / 131072.0f);
+                bool live[kItems];
+                bool any_live = false;
+                if (thr_now < INFINITY) {
+#pragma unroll
+                    for (int k = 0; k < DD; ++k) {
+                        if (D > 0 || k < d) {
+                            for (int o = 16; o; o >>= 1) {
+                                blo[k] = fminf(blo[k], __shfl_xor_sync(0xffffffffu, blo[k], o));
+                                bhi[k] = fmaxf(bhi[k], __shfl_xor_sync(0xffffffffu, bhi[k], o));
+                            }
+                            if (!a.exact32) {
+                                blo[k] = __fsub_rd(blo[k], a.delta32);
+                                bhi[k] = __fadd_ru(bhi[k], a.delta32);
+                            }
+                        }
+                    }
+                    if (HDB) for (int o = 16; o; o >>= 1) bcd = fminf(bcd, __shfl_xor_sync(0xffffffffu, bcd, o));
+#pragma unroll
+                    for (int it = 0; it < kItems; ++it) {
+                        float g2 = 0.f;
+#pragma unroll
+                        for (int k = 0; k < DD; ++k) {
+                            if (D > 0 || k < d) {
+                                const float g = fmaxf(fmaxf(blo[k] - ax[it][k], ax[it][k] - bhi[k]), 0.f);
+                                g2 = fmaf(g, g, g2);
+                            }
+                        }
+                        float lbw = lower_w2(g2);
+                        if (HDB) lbw = fmaxf(lbw, fmaxf(acd[it], bcd) * (1.0f - 1.0f / 4194304.0f));
+                        live[it] = av[it] && lbw <= thr_now;
+                        any_live = any_live || live[it];
+                    }
+                } else {
+#pragma unroll
+                    for (int it = 0; it < kItems; ++it) { live[it] = av[it]; any_live = any_live || live[it]; }
+                }
+                if (!__any_sync(0xffffffffu, any_live)) {
+                    n_skip += (unsigned long long)((a1 - a0) * nb);
+                    continue;
+                }
                 if (!FP64) {
                     float mn[kItems];
 #pragma unroll
@@ -949,14 +1071,18 @@ __global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const i
                     }
                     float wmn = INFINITY;
 #pragma unroll
-                    for (int it = 0; it < kItems; ++it) if (av[it]) wmn = fminf(wmn, mn[it]);
+                    for (int it = 0; it < kItems; ++it) {
+                        if (!live[it]) mn[it] = INFINITY;   // pruned: no candidate in this chunk
+                        wmn = fminf(wmn, mn[it]);
+                    }
                     for (int o = 16; o; o >>= 1) wmn = fminf(wmn, __shfl_xor_sync(0xffffffffu, wmn, o));
                     run_min = fminf(run_min, wmn);
-                    const float T = screen_threshold(run_min, a);
+                    // nothing to recheck while the running minimum proves the pair above the range
+                    const float T = screened_above(run_min, a) ? -1.f : screen_threshold(run_min, a);
                     int nre = 0;
 #pragma unroll
                     for (int it = 0; it < kItems; ++it) {
-                        if (!av[it] || mn[it] > T) continue;
+                        if (!live[it] || mn[it] > T) continue;
                         const int i = a0 + lane + 32 * it;
                         for (int jj = 0; jj < nb; ++jj) {
                             const float *qq = q + jj * (DD + 1);
@@ -982,7 +1108,7 @@ __global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const i
                 } else {
 #pragma unroll
                     for (int it = 0; it < kItems; ++it) {
-                        if (!av[it]) continue;
+                        if (!live[it]) continue;
                         const int i = a0 + lane + 32 * it;
                         for (int jj = 0; jj < nb; ++jj) {
                             double w = dist64(a.x64, n, d, i, b0 + jj);
@@ -995,7 +1121,7 @@ __global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const i
             }
         }
         __syncwarp();
-        if (!FP64 && df.i >= 0 && screen_value(df, HDB) <= screen_threshold(run_min, a))
+        if (!FP64 && df.i >= 0 && !screened_above(run_min, a) && screen_value(df, HDB) <= screen_threshold(run_min, a))
             kmin_update(best, exact_w2(a, df.i, df.j, df.sd, df.c32), a.pid[df.i], a.pid[df.j]);
         // warp K-minimum of the pair
         for (int o = 16; o; o >>= 1) {
@@ -1003,6 +1129,7 @@ __global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const i
             unsigned long long ol = __shfl_xor_sync(0xffffffffu, best.lo, o);
             if (oh < best.hi || (oh == best.hi && ol < best.lo)) { best.hi = oh; best.lo = ol; }
         }
+        if (lane == 0) waste.add(range_side(a, best), (unsigned long long)(aend - abeg) * (unsigned long long)(bend - bbeg));
         if (in_range(a, best)) {   // best is the same on every lane
             if (lane == 0) {
                 EdgeK e;
@@ -1015,12 +1142,14 @@ __global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const i
         }
     }
     if (ecnt > 0) flush_edges();
+    waste_flush(a, waste);
     n_re = warp_sum_u64(n_re);
     if (lane == 0 && n_ev) {
         atomicAdd(a.stat + 1, n_ev);
         atomicAdd(a.stat + 3, n_ev);
         atomicAdd(a.stat + 2, n_re);
     }
+    if (lane == 0 && n_skip) atomicAdd(a.stat + 11, n_skip);
 }
 
 }  // namespace
@@ -1051,23 +1180,27 @@ void traversal_init(int mode, TravArgs &a, int2 *stack, int *cnt, cudaStream_t s
     launch(frontier_init_kernel, grid_for(a.N, 256), 256, 0, st, a, mode, stack, cnt + 0);
 }
 
-// Warps of a step: at most 2 chunk / (64 kDfsBudget + kDfsWarpCap), so that a step's output
-// (children of at most chunk + warps * 32 * kDfsBudget visits, plus every warp's full stack) fits
+// Warps of a step: at most 2 chunk / (64 budget + kDfsWarpCap), so that a step's output
+// (children of at most chunk + warps * 32 * budget visits, plus every warp's full stack) fits
 // in 4 * chunk pairs.
-int dfs_warps(int chunk)
+int dfs_warps(int chunk, int budget)
 {
-    long long w = 2LL * chunk / (64 * kDfsBudget + kDfsWarpCap);
-    w = w > 152 * 4 * kDfsWarpsPerBlock ? 152 * 4 * kDfsWarpsPerBlock : w;
+    long long w = 2LL * chunk / (64 * budget + kDfsWarpCap);
+    const long long wmax = (long long)num_sms() * 4 * kDfsWarpsPerBlock;
+    w = w > wmax ? wmax : w;
     w = w / kDfsWarpsPerBlock * kDfsWarpsPerBlock;
     return (int)(w < kDfsWarpsPerBlock ? kDfsWarpsPerBlock : w);
 }
 
-long long dfs_out_cap(int chunk)
+long long dfs_out_cap(int chunk, int budget)
 {
-    return 2LL * chunk + (long long)dfs_warps(chunk) * (64 * kDfsBudget + kDfsWarpCap);
+    return 2LL * chunk + (long long)dfs_warps(chunk, budget) * (64 * budget + kDfsWarpCap);
 }
 
-long long dfs_step_visits(int chunk) { return (long long)chunk + (long long)dfs_warps(chunk) * 32 * kDfsBudget; }
+long long dfs_step_visits(int chunk, int budget)
+{
+    return (long long)chunk + (long long)dfs_warps(chunk, budget) * 32 * budget;
+}
 
 void traversal_step(int mode, TravArgs &a, int2 *stack, int2 *const xbuf[2], int *cnt, int step, int chunk,
                     cudaStream_t st)
@@ -1083,9 +1216,9 @@ void traversal_step(int mode, TravArgs &a, int2 *stack, int2 *const xbuf[2], int
     s.next = cnt + 3;
     s.done = (unsigned *)(cnt + 4);
     s.chunk = chunk;
-    s.xcap = (int)std::min<long long>(dfs_out_cap(chunk), 4LL * chunk);   // the output buffers hold 4 * chunk pairs
-    s.budget = kDfsBudget;
-    const int grid = dfs_warps(chunk) / kDfsWarpsPerBlock;
+    s.xcap = (int)std::min<long long>(dfs_out_cap(chunk, a.dfs_budget), 4LL * chunk);   // the output buffers hold 4 * chunk pairs
+    s.budget = a.dfs_budget;
+    const int grid = dfs_warps(chunk, a.dfs_budget) / kDfsWarpsPerBlock;
 #define WM_FP(DPV)                                                                                \
     do {                                                                                          \
         if (mode == 0) launch(findpair_dfs_kernel<0, DPV>, grid, 32 * kDfsWarpsPerBlock, 0, st, a, s); \
@@ -1220,7 +1353,7 @@ void run_bccp_tiles(TravArgs &a, const int *counts_host, int *next, cudaStream_t
     for (int c = 2; c <= 3; ++c) {
         const int m = counts_host[c];
         if (m <= 0) continue;
-        const int grid = (int)std::min<long long>(152 * 4, ((long long)m + 7) / 8);
+        const int grid = (int)std::min<long long>((long long)num_sms() * 4, ((long long)m + 7) / 8);
         const int2 *pl = a.list[c];
         int *nx = next + (c - 2);
         const int chunk = (long long)m > 128LL * grid * 8 ? 4 : 1;   // long lists: fewer counter increments

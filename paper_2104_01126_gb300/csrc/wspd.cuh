@@ -17,9 +17,13 @@ struct TravArgs {
     const float *cd32 = nullptr;                       // HDBSCAN* cd2 per tree position
     const double *cd64 = nullptr;
     double eta = 0.0;          // absolute distance error of the FP32 copy (FP64 input), else 0
+    float delta32 = 0.f;       // largest |x64 - x32| of a coordinate (0 for FP32 input)
     int exact32 = 1;           // eta == 0: the FP32 copy is exact
     int fp64 = 0;              // plain FP64 form
     int beta = 2;
+    int dfs_budget = 8;        // depth-first rounds per warp and traversal step (tuning)
+    int medium_max = 1024;     // pair-size classes (tuning): |A||B| <= medium_max: one warp,
+    long long big_max = 65536; //   <= big_max: tile kernel, larger: dual-tree kernel
     double rho_lo = 0.0, rho_hi = 0.0;
     float rho_lo_f = 0.f, rho_hi_f = 0.f;   // the smallest floats >= rho_lo, rho_hi
     unsigned *rho_bits = nullptr;           // GetRho result: bits of a non-negative float (WriteMin)
@@ -52,13 +56,16 @@ struct TravArgs {
     int *node_out = nullptr, *node_out_n = nullptr;
     unsigned long long *stat = nullptr; // [0] pairs retrieved, [1] evals, [2] fp64 rechecks,
                                         // [3] tile evals, [4] GetPairs visits, [5] GetRho visits,
-                                        // [6] dual-tree evals, [7] peak pending pairs
+                                        // [6] dual-tree evals, [7] peak pending pairs,
+                                        // [8] / [9] retrieved pairs whose BCCP fell below / above
+                                        // the round's range, [10] evaluations of those pairs
+                                        // (group and tile kernels), [11] tile-kernel evaluations
+                                        // skipped by the chunk box bound
 };
 
-// Traversal step (see findpair_dfs_kernel): warps per block, depth-first rounds per warp on its
-// own stack, and the capacity of that stack in shared memory.
+// Traversal step (see findpair_dfs_kernel): warps per block and the capacity of a warp's own
+// stack in shared memory (the depth-first rounds per step are TravArgs::dfs_budget).
 constexpr int kDfsWarpsPerBlock = 8;
-constexpr int kDfsBudget = 8;
 constexpr int kDfsWarpCap = 320;
 // traversal counters: [0] stack size, [1] / [2] counts of the two step output buffers,
 // [3] input dispenser, [4] finished blocks
@@ -76,9 +83,9 @@ struct DfsArgs {
     int chunk = 0, xcap = 0, budget = 0;
 };
 
-int dfs_warps(int chunk);
-long long dfs_out_cap(int chunk);       // pairs one step can write to its output buffer
-long long dfs_step_visits(int chunk);   // pairs one step can visit
+int dfs_warps(int chunk, int budget);
+long long dfs_out_cap(int chunk, int budget);       // pairs one step can write to its output buffer
+long long dfs_step_visits(int chunk, int budget);   // pairs one step can visit
 
 // component label of every node (-1 when its points span several components), into T.comp and
 // meta[x].w; scratch holds 2 n + 1 ints

@@ -49,3 +49,21 @@ def test_error_strings_and_footprint_without_gpu():
     b = ctypes.c_size_t(0)
     assert lib.wm_query_footprint(0, 2, 0, ctypes.byref(b)) == -1
     assert lib.wm_query_footprint(10, 17, 0, ctypes.byref(b)) == -1
+
+
+def test_tuning_get_set_without_gpu():
+    # the tuning calls touch no device: the table lookup and the override are host state
+    base = wm.get_tuning(1_000_000, 3, 0)
+    assert set(base) == set(wm.TUNING_FIELDS)
+    assert ctypes.sizeof(wm._Tuning) == 64
+    try:
+        with pytest.raises(wm.WMError):
+            wm.set_tuning({"dfs_budget": 0})
+        with pytest.raises(wm.WMError):
+            wm.set_tuning({"medium_max": 64})
+        wm.set_tuning({"dfs_budget": 4, "tight_diameters": 0})
+        got = wm.get_tuning(10, 7, 5)
+        assert got["dfs_budget"] == 4 and got["tight_diameters"] == 0
+    finally:
+        wm.set_tuning(None)
+    assert wm.get_tuning(1_000_000, 3, 0) == base
