@@ -332,7 +332,12 @@ typedef struct {
     int32_t medium_max;      /* BCCP: pairs with |A||B| up to this (65..4096) take one warp   */
     int32_t big_max;         /* BCCP: pairs up to this (>= medium_max) take the tile kernel;
                                 larger ones the dual-tree kernel                              */
-    int32_t reserved[10];
+    int32_t combined;        /* 1: a round's GetRho minimum is found during its GetPairs
+                                traversal (one pass); 0: a GetRho traversal first (Algorithm 3);
+                                2: two passes until, after two rounds or more, the GetRho
+                                traversals have visited at least half as many node pairs as
+                                the GetPairs traversals; one pass afterwards                   */
+    int32_t reserved[9];
 } wm_tuning;
 
 /* The parameters a call with these sizes uses (min_pts = 0 for EMST). */

@@ -123,7 +123,7 @@ static size_t estimate_bytes(long long n, int d, int min_pts, const Caps &c)
     b += (size_t)n * 8;                     // small lists
     b += (size_t)N * (32 + 8 * dp);         // packed node records
     b += (size_t)((N / 2 + 2 + (2 * depth + 4) * 2 * c.chunk) * c.frontier_scale + 8 * c.chunk) * 8;   // stack, step outputs
-    b += (size_t)8 * (c.chunk + 1) * (5 * 8 + 16 + 4 + 8);   // pair lists (8 chunks each), huge-pair slots
+    b += (size_t)8 * (c.chunk + 1) * (5 * 12 + 16 + 4 + 8);  // pair lists with bounds (8 chunks each), huge-pair slots
     b += (size_t)num_sms() * 64 * (depth + 4) * 4;                                                           // dual stacks
     b += (size_t)c.edges * 16 * 3 + (size_t)c.edges * 24;   // batch, filtered, sort tmp, kruskal
     b += (size_t)n * 16 * 2;                // output tree + conversion
@@ -159,7 +159,7 @@ static bool tuning_valid(const wm_tuning &t)
     return (t.tight_diameters == 0 || t.tight_diameters == 1) &&
            (t.chunk_log2 == 0 || (t.chunk_log2 >= 12 && t.chunk_log2 <= 24)) && t.dfs_budget >= 1 &&
            t.dfs_budget <= 64 && t.route_big >= 0 && t.medium_max >= 65 && t.medium_max <= 4096 &&
-           t.big_max >= t.medium_max;
+           t.big_max >= t.medium_max && t.combined >= 0 && t.combined <= 2;
 }
 
 static wm_tuning tuning_for(long long n, int d, int min_pts)
@@ -342,7 +342,11 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     const int kPoll = 3, kListChunks = 8;
     const long long lcap = (long long)kListChunks * chunk;
     int2 *lists[5];
-    for (int c = 0; c < 5; ++c) lists[c] = ar.get<int2>(lcap);
+    float *list_lbs[5];
+    for (int c = 0; c < 5; ++c) {
+        lists[c] = ar.get<int2>(lcap);
+        list_lbs[c] = ar.get<float>(lcap);
+    }
     EdgeK *huge_best = ar.get<EdgeK>(lcap + 1);
     unsigned *huge_sbest = ar.get<unsigned>(lcap + 1);
     long long *huge_items = ar.get<long long>(lcap + 1);
@@ -355,7 +359,8 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     EdgeK *batch = ar.get<EdgeK>(caps.edges), *filt = ar.get<EdgeK>(caps.edges), *tmp = ar.get<EdgeK>(caps.edges);
     int *cnts = ar.get<int>(64);
     unsigned *rho = ar.get<unsigned>(2);
-    double *samples = ar.get<double>(4096);
+    int *split_hist = ar.get<int>(kSplitBins);
+    unsigned long long *split_max = ar.get<unsigned long long>(1);
     unsigned *ovf = ar.get<unsigned>(2);
     unsigned long long *stat = ar.get<unsigned long long>(16);
     int *comp_scratch = ar.get<int>(2LL * n + 1);
@@ -390,7 +395,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     }
     a.frontier_cap = (int)fcap;
     a.links = links; a.meta = meta; a.box = box; a.dp = dp;
-    for (int c = 0; c < 5; ++c) { a.list[c] = lists[c]; a.list_cap[c] = (int)lcap; }
+    for (int c = 0; c < 5; ++c) { a.list[c] = lists[c]; a.list_lb[c] = list_lbs[c]; a.list_cap[c] = (int)lcap; }
     a.list_count = lcount;
     a.big = lists[3]; a.big_count = lcount + 3;
     a.huge_best = huge_best; a.huge_sbest = huge_sbest;
@@ -410,31 +415,53 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     int nE = 0;
     double rho_lo = 0.0;
     long long beta = 2;
+    // tuning combined = 2: rounds start as two passes; once, after two rounds or more, the GetRho
+    // traversals have visited at least kOnePassRatio times as many node pairs as the GetPairs
+    // traversals, the remaining rounds find the GetRho minimum during GetPairs instead (the
+    // first round's ratio says little: it is high on every input)
+    constexpr double kOnePassRatio = 0.5;
+    bool adaptive_one_pass = false;
     const double inf = INFINITY;
     int rounds = 0;
     while (nE < target) {
         if (++rounds > 4096) { set_detail("MemoGFK made no progress%s (%lld rounds)", "", rounds); return WM_EINTERNAL; }
         Timer tw;
         WM_TRY(launch_comp_labels(T, P, uf, links, meta, comp_scratch, ar, st));
-        // ---- GetRho
-        fill_i32((int *)rho, 0x7f800000, 1, st);   // +inf
-        set_rho(a, rho_lo, inf);
         a.beta = (int)std::min<long long>(beta, 0x7fffffff);
-        unsigned ob = 0;
-        WM_TRY(run_traversal(a, stack, xbuf, tcnt, chunk, st, C.pin, &ob, nullptr));
-        if (ob) { *overflow_bits = ob; return 0; }
-        WM_CK(cudaMemcpyAsync(C.pin, rho, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-        WM_CK(cudaStreamSynchronize(st));
-        float rho_f;
-        memcpy(&rho_f, C.pin, sizeof rho_f);
-        double rho_hi = std::min<double>(rho_f, rho_cap);
-        if (rho_hi < rho_lo) rho_hi = rho_lo;
+        double rho_hi;
+        // Combined pass (tuning): GetRho's minimum R is kept on the device while GetPairs runs;
+        // each flush takes the R read at that moment as rho_hi and the round ends with the final
+        // R, i.e. GetRho's value, whose edges at or above it are dropped before Kruskal.
+        const bool combined = C.tune.combined == 1 || (C.tune.combined == 2 && adaptive_one_pass);
+        const int tmode = combined ? 2 : 1;
+        double rho_used = 0.0;   // largest rho_hi a flush of this round has used
+        if (!combined) {
+            // ---- GetRho
+            fill_i32((int *)rho, 0x7f800000, 1, st);   // +inf
+            set_rho(a, rho_lo, inf);
+            unsigned ob = 0;
+            WM_TRY(run_traversal(a, stack, xbuf, tcnt, chunk, st, C.pin, &ob, nullptr));
+            if (ob) { *overflow_bits = ob; return 0; }
+            WM_CK(cudaMemcpyAsync(C.pin, rho, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+            WM_CK(cudaStreamSynchronize(st));
+            float rho_f;
+            memcpy(&rho_f, C.pin, sizeof rho_f);
+            rho_hi = std::min<double>(rho_f, rho_cap);
+            if (rho_hi < rho_lo) rho_hi = rho_lo;
+        } else {
+            float cap_f = float_ru(rho_cap);
+            unsigned cap_bits;
+            memcpy(&cap_bits, &cap_f, sizeof cap_bits);
+            fill_i32((int *)rho, (int)cap_bits, 1, st);
+            rho_hi = std::max<double>(std::min<double>(cap_f, rho_cap), rho_lo);
+        }
+        double rho_shrunk = inf;   // bound set by an edge-batch overflow in this round
         // ---- GetPairs in chunks; the retrieved pairs of every chunk get their BCCP right away
         set_rho(a, rho_lo, rho_hi);
         a.edges = batch;
         spare = filt;
         WM_CK(cudaMemsetAsync(cnts + 2, 0, 6 * sizeof(int), st));
-        traversal_init(1, a, stack, tcnt, st);
+        traversal_init(tmode, a, stack, tcnt, st);
         std::vector<cudaEvent_t> evs;   // (start, end) of traversal runs and BCCP flushes, summed per round
         auto mark_event = [&]() {
             if (!C.timing) return;
@@ -449,12 +476,18 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         unsigned last_ovf = 0;
         mark_event();
         while (true) {
-            for (int b = 0; b < kPoll; ++b, ++steps) traversal_step(1, a, stack, xbuf, tcnt, steps, chunk, st);
+            for (int b = 0; b < kPoll; ++b, ++steps) traversal_step(tmode, a, stack, xbuf, tcnt, steps, chunk, st);
             WM_CK(cudaMemcpyAsync(C.pin, cnts, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
             WM_CK(cudaMemcpyAsync(C.pin + 8, ovf, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
             WM_CK(cudaMemcpyAsync(C.pin + 16, tcnt, kTravCounters * sizeof(int), cudaMemcpyDeviceToHost, st));
+            if (combined) WM_CK(cudaMemcpyAsync(C.pin + 24, rho, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
             WM_CK(cudaStreamSynchronize(st));
             if (C.pin[8]) { *overflow_bits = (unsigned)C.pin[8]; return 0; }
+            if (combined) {
+                float rf;
+                memcpy(&rf, C.pin + 24, sizeof rf);
+                rho_hi = std::max<double>(std::min<double>(std::min<double>(rf, rho_cap), rho_shrunk), rho_lo);
+            }
             const bool empty = C.pin[16] == 0 && C.pin[17] == 0 && C.pin[18] == 0;
             int lc[5] = {C.pin[2], C.pin[3], C.pin[4], C.pin[5], C.pin[6]};
             int e = C.pin[7];
@@ -463,6 +496,8 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
             if (!flush) continue;
             mark_event();
             ev_kind.push_back(0);
+            if (combined && rho_hi != a.rho_hi) set_rho(a, rho_lo, rho_hi);
+            rho_used = std::max(rho_used, a.rho_hi);
             // BCCP of the retrieved pairs.  Emission is capacity-checked; if this flush overflows the
             // edge batch, its partial output is dropped, rho_hi is lowered to a quantile of the valid
             // edges (pairs seen so far were retrieved under the larger bound, so they stay complete
@@ -476,10 +511,10 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
                 int lt[5] = {lc[0], lc[1], lc[2], route_big ? 0 : lc[3], lc[4]};
                 run_bccp_tiles(a, lt, cnts + 16, st, hdb != nullptr, a.fp64 != 0);
                 if (route_big)
-                    WM_TRY(run_bccp_huge(a, a.list[3], lc[3], huge_items, (long long *)(cnts + 12), st, ar,
-                                         hdb != nullptr, a.fp64 != 0, stack_warps));
-                WM_TRY(run_bccp_huge(a, a.list[4], lc[4], huge_items, (long long *)(cnts + 12), st, ar, hdb != nullptr,
-                                     a.fp64 != 0, stack_warps));
+                    WM_TRY(run_bccp_huge(a, a.list[3], a.list_lb[3], lc[3], huge_items, (long long *)(cnts + 12), st,
+                                         ar, hdb != nullptr, a.fp64 != 0, stack_warps));
+                WM_TRY(run_bccp_huge(a, a.list[4], a.list_lb[4], lc[4], huge_items, (long long *)(cnts + 12), st, ar,
+                                     hdb != nullptr, a.fp64 != 0, stack_warps));
                 WM_CK(cudaMemcpyAsync(C.pin, ecount, sizeof(int), cudaMemcpyDeviceToHost, st));
                 WM_CK(cudaMemcpyAsync(C.pin + 1, ovf, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
                 WM_CK(cudaStreamSynchronize(st));
@@ -488,20 +523,32 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
                 if (!(C.pin[1] & 2u)) break;
                 if (attempt >= 8) { *overflow_bits = 2; return 0; }
                 const int valid = std::min<long long>(C.pin[0], caps.edges) > 0 ? (int)std::min<long long>(C.pin[0], caps.edges) : 0;
-                const int k = std::min(valid, 4096);
-                if (k < 1) { *overflow_bits = 2; return 0; }
-                sample_w2(a.edges, valid, k, samples, st);
-                WM_CK(cudaMemcpyAsync(C.pin + 64, samples, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+                if (valid < 1) { *overflow_bits = 2; return 0; }
+                // the new bound: the 40% point of the valid edges' weights, from a histogram (the
+                // same choice whatever order the edges were appended in)
+                w2_histogram(a.edges, valid, rho_lo, split_max, split_hist, st);
+                WM_CK(cudaMemcpyAsync(C.pin + 8192, split_hist, sizeof(int) * kSplitBins, cudaMemcpyDeviceToHost, st));
+                WM_CK(cudaMemcpyAsync(C.pin + 64, split_max, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
                 WM_CK(cudaStreamSynchronize(st));
-                std::vector<double> sw((double *)(C.pin + 64), (double *)(C.pin + 64) + k);
-                std::sort(sw.begin(), sw.end());
-                double nh = sw[(size_t)(k * 0.4)];
+                double wmax;
+                memcpy(&wmax, C.pin + 64, sizeof wmax);
+                long long acc = 0;
+                int bin = 0;
+                while (bin < kSplitBins - 1 && acc + C.pin[8192 + bin] < (long long)(0.4 * valid)) acc += C.pin[8192 + bin++];
+                double nh = rho_lo + (wmax - rho_lo) * ((double)(bin + 1) / kSplitBins);
                 if (!(nh > rho_lo)) nh = std::nextafter(rho_lo, inf);
                 if (!(nh < a.rho_hi)) { *overflow_bits = 2; return 0; }   // cannot shrink: grow and restart
                 keep_below(a.edges, e_before, nh, spare, ecount, st);
                 std::swap(a.edges, spare);
                 rho_hi = nh;
+                rho_shrunk = nh;
                 set_rho(a, rho_lo, rho_hi);
+                if (combined) {   // the traversal's running bound may not exceed it either
+                    float nf = float_ru(nh);
+                    unsigned nb;
+                    memcpy(&nb, &nf, sizeof nb);
+                    fill_i32((int *)rho, (int)nb, 1, st);
+                }
                 WM_CK(cudaMemsetAsync(ovf, 0, sizeof(unsigned), st));
                 C.stats.rho_shrinks += 1;
             }
@@ -516,6 +563,15 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         // nothing has run since
         if (last_ovf) { *overflow_bits = last_ovf; return 0; }
         int m = last_e;
+        if (combined && rho_used > rho_hi) {
+            // earlier flushes ran with a larger running bound than the final one: keep only the
+            // edges of this round's range
+            keep_below(a.edges, m, rho_hi, spare, ecount, st);
+            std::swap(a.edges, spare);
+            WM_CK(cudaMemcpyAsync(C.pin, ecount, sizeof(int), cudaMemcpyDeviceToHost, st));
+            WM_CK(cudaStreamSynchronize(st));
+            m = C.pin[0];
+        }
         C.stats.getpairs_launches += steps;
         C.stats.ms_wspd += tw.ms();
         // ---- HDBSCAN*: repair edges of this weight range join the batch
@@ -547,6 +603,13 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
             for (cudaEvent_t e : evs) cudaEventDestroy(e);
         }
         nE += accepted;
+        if (C.tune.combined == 2 && !combined) {
+            WM_CK(cudaMemcpyAsync(C.pin, stat + 4, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+            WM_CK(cudaStreamSynchronize(st));
+            unsigned long long v[2];
+            memcpy(v, C.pin, sizeof v);
+            if (rounds >= 2 && v[1] >= kOnePassRatio * v[0] && v[0] > 0) adaptive_one_pass = true;
+        }
         if (rho_hi >= rho_cap && nE < target) {
             set_detail("MemoGFK round with rho_hi = its cap left the forest incomplete%s (%lld edges)", "", nE);
             return WM_EINTERNAL;

@@ -258,10 +258,14 @@ constexpr int kSmallMax = 64;    // 8 lanes per pair
 
 // One FindPair visit of the node pair me (Algorithm 1's recursion body).  MODE 0 = GetRho
 // (WriteMin candidates into rho_cand, pruned by rho_now), MODE 1 = GetPairs (classifies a
-// retrieved pair into cls).  Sets push = 2 with the two child pairs when the pair is split.
+// retrieved pair into cls), MODE 2 = both in one pass: rho_now is the running GetRho minimum R,
+// a well-separated pair of more than beta points lowers it, and a smaller one is retrieved when
+// its lower bound is below R (R only falls, so every pair GetPairs would take with the final R is
+// taken, plus some the final R excludes, whose edges the host drops).  Sets push = 2 with the
+// two child pairs when the pair is split.
 template <int MODE, int DP>
 __device__ inline void visit_pair(const TravArgs &a, int2 me, float rho_now, int &push, int2 &c0, int2 &c1, int &cls,
-                                  float &rho_cand)
+                                  float &rho_cand, float &lb_out)
 {
     const int P = me.x, Q = me.y;
     const int4 lp = a.links[P], lq = a.links[Q];
@@ -278,11 +282,21 @@ __device__ inline void visit_pair(const TravArgs &a, int2 me, float rho_now, int
         // pairs whose BCCP is certainly below rho_lo were handled by earlier rounds
         if (lbB >= rho_now || ubB < a.rho_lo_f) return;
         if (ws) { rho_cand = fminf(rho_cand, lbB); return; }
+    } else if (MODE == 2) {
+        if (lbB >= rho_now || ubB < a.rho_lo_f) return;
+        if (ws) {
+            if (sp + sq > a.beta) { rho_cand = fminf(rho_cand, lbB); return; }
+            long long prod = (long long)sp * sq;
+            cls = prod <= kTinyMax ? 0 : prod <= kSmallMax ? 1 : prod <= a.medium_max ? 2 : prod <= a.big_max ? 3 : 4;
+            lb_out = lbB;
+            return;
+        }
     } else {
         if (lbB >= a.rho_hi_f || ubB < a.rho_lo_f) return;
         if (ws) {
             long long prod = (long long)sp * sq;
             cls = prod <= kTinyMax ? 0 : prod <= kSmallMax ? 1 : prod <= a.medium_max ? 2 : prod <= a.big_max ? 3 : 4;
+            lb_out = lbB;
             return;
         }
     }
@@ -307,10 +321,12 @@ __global__ void __launch_bounds__(256) findpair_dfs_kernel(TravArgs a, DfsArgs s
     __shared__ int2 wst[kDfsWarpsPerBlock][kDfsWarpCap];
     // GetPairs: retrieved pairs gathered per warp and size class, reserved in the global lists 32
     // at a time
-    __shared__ int2 rbuf[MODE == 1 ? kDfsWarpsPerBlock : 1][5][32];
+    __shared__ int2 rbuf[MODE != 0 ? kDfsWarpsPerBlock : 1][5][32];
+    __shared__ float rlb[MODE != 0 ? kDfsWarpsPerBlock : 1][5][32];   // their lower bounds
     const int lane = threadIdx.x & 31;
     int2 *ws = wst[threadIdx.x >> 5];
-    int2 (*rb)[32] = rbuf[MODE == 1 ? threadIdx.x >> 5 : 0];
+    int2 (*rb)[32] = rbuf[MODE != 0 ? threadIdx.x >> 5 : 0];
+    float (*rl)[32] = rlb[MODE != 0 ? threadIdx.x >> 5 : 0];
     int rcnt[5] = {0, 0, 0, 0, 0};   // warp-uniform fill of each class buffer
     // moves class c's buffer to its global list
     auto flush_class = [&](int c) {
@@ -318,8 +334,12 @@ __global__ void __launch_bounds__(256) findpair_dfs_kernel(TravArgs a, DfsArgs s
         if (lane == 0) base = atomicAdd(a.list_count + c, rcnt[c]);
         base = __shfl_sync(0xffffffffu, base, 0);
         for (int i = lane; i < rcnt[c]; i += 32) {
-            if (base + i < a.list_cap[c]) a.list[c][base + i] = rb[c][i];
-            else atomicOr(a.overflow, 4u);
+            if (base + i < a.list_cap[c]) {
+                a.list[c][base + i] = rb[c][i];
+                a.list_lb[c][base + i] = rl[c][i];
+            } else {
+                atomicOr(a.overflow, 4u);
+            }
         }
         rcnt[c] = 0;
         __syncwarp();
@@ -339,6 +359,8 @@ __global__ void __launch_bounds__(256) findpair_dfs_kernel(TravArgs a, DfsArgs s
     const bool stop = __shfl_sync(0xffffffffu, (int)(*(volatile unsigned *)a.overflow != 0), 0) != 0;
     unsigned long long n_vis = 0, n_ret = 0;
     float rho_w = INFINITY;    // GetRho: smallest candidate this warp has written
+    float rho_g = INFINITY;    // GetRho: the shared minimum as last read (refreshed every 4 rounds)
+    int refresh = 0;
     int sp = 0, it = 0;        // warp stack size (warp-uniform), rounds on the warp's own stack
     bool fed = stop;           // no more input for this warp
     // every popped pair costs one visit in the breadth-first phase: a contiguous share per warp
@@ -374,12 +396,15 @@ __global__ void __launch_bounds__(256) findpair_dfs_kernel(TravArgs a, DfsArgs s
         const bool has = lane < k;
         int push = 0, cls = -1;
         int2 c0 = make_int2(0, 0), c1 = c0;
-        float rho_cand = INFINITY;
+        float rho_cand = INFINITY, lb = 0.f;
+        // the shared GetRho minimum only prunes: a stale (larger) copy is safe, so it is read from
+        // L2 every fourth round and this warp's own minimum is used in between
+        if (MODE != 1 && (refresh++ & 3) == 0) rho_g = __uint_as_float(*(volatile unsigned *)a.rho_bits);
         if (has) {
             ++n_vis;
             float rho_now = 0.f;
-            if (MODE == 0) rho_now = fminf(__uint_as_float(*(volatile unsigned *)a.rho_bits), rho_w);
-            visit_pair<MODE, DP>(a, me, rho_now, push, c0, c1, cls, rho_cand);
+            if (MODE != 1) rho_now = fminf(rho_g, rho_w);
+            visit_pair<MODE, DP>(a, me, rho_now, push, c0, c1, cls, rho_cand, lb);
         }
         int x = push;
         for (int o = 1; o < 32; o <<= 1) {
@@ -401,14 +426,15 @@ __global__ void __launch_bounds__(256) findpair_dfs_kernel(TravArgs a, DfsArgs s
             }
         }
         __syncwarp();
-        if (MODE == 0) {
+        if (MODE != 1) {
             for (int o = 16; o; o >>= 1) rho_cand = fminf(rho_cand, __shfl_xor_sync(0xffffffffu, rho_cand, o));
             if (rho_cand < rho_w) {
                 rho_w = rho_cand;
                 // non-negative floats order like their bit patterns
                 if (lane == 0) atomicMin(a.rho_bits, __float_as_uint(rho_cand));
             }
-        } else {
+        }
+        if (MODE != 0) {
             if (__any_sync(0xffffffffu, cls >= 0)) {
 #pragma unroll
                 for (int c = 0; c < 5; ++c) {
@@ -419,6 +445,7 @@ __global__ void __launch_bounds__(256) findpair_dfs_kernel(TravArgs a, DfsArgs s
                     if (cls == c) {
                         ++n_ret;
                         rb[c][rcnt[c] + __popc(bal & lanemask_lt())] = me;
+                        rl[c][rcnt[c] + __popc(bal & lanemask_lt())] = lb;
                     }
                     rcnt[c] += nc;
                 }
@@ -426,7 +453,7 @@ __global__ void __launch_bounds__(256) findpair_dfs_kernel(TravArgs a, DfsArgs s
             }
         }
     }
-    if (MODE == 1) {
+    if (MODE != 0) {
 #pragma unroll
         for (int c = 0; c < 5; ++c)
             if (rcnt[c] > 0) flush_class(c);
@@ -470,7 +497,7 @@ __global__ void __launch_bounds__(256) findpair_dfs_kernel(TravArgs a, DfsArgs s
 // edge when its FP64 w2 lies in [rho_lo, rho_hi).
 template <int G, int D>
 __global__ void __launch_bounds__(256) bccp_group_kernel(TravArgs a, const int2 *__restrict__ pairs,
-                                                         const int *__restrict__ count)
+                                                         const float *__restrict__ lbs, const int *__restrict__ count)
 {
     const int m = *count;
     const int lane = threadIdx.x & 31, g = lane & (G - 1);
@@ -483,9 +510,10 @@ __global__ void __launch_bounds__(256) bccp_group_kernel(TravArgs a, const int2 
         const int pi = base + lane / G;
         const bool valid = pi < m;
         int pb = 0, qb = 0, na = 0, nb = 0;
-        int2 pr = make_int2(0, 0);
-        if (valid) {
-            pr = pairs[pi];
+        // a pair retrieved under a larger bound than this flush's rho_hi (one-pass rounds, or an
+        // edge-batch overflow) has no edge in the range: it is skipped
+        if (valid && lbs[pi] < a.rho_hi_f) {
+            const int2 pr = pairs[pi];
             int4 lp = a.links[pr.x], lq = a.links[pr.y];
             pb = lp.x; na = lp.y - lp.x; qb = lq.x; nb = lq.y - lq.x;
         }
@@ -585,19 +613,19 @@ __global__ void pack_nodes_kernel(int N, int d, int DP, const float *__restrict_
 __global__ void frontier_init_kernel(TravArgs a, int mode, int2 *__restrict__ out, int *out_count)
 {
     __shared__ int sh[32];
-    // GetRho reads the previous round's node list (every node in the first round) and writes
-    // the survivors; GetPairs reads the survivors
-    const int *in = mode == 0 ? a.node_in : a.node_out;
-    const int m = in ? *(mode == 0 ? a.node_in_n : a.node_out_n) : a.N;
+    // GetRho (and the combined pass, mode 2) reads the previous round's node list (every node in
+    // the first round) and writes the survivors; GetPairs reads the survivors
+    const int *in = mode != 1 ? a.node_in : a.node_out;
+    const int m = in ? *(mode != 1 ? a.node_in_n : a.node_out_n) : a.N;
     for (int b0 = blockIdx.x * blockDim.x; b0 < m; b0 += gridDim.x * blockDim.x) {
         const int t = b0 + threadIdx.x;
         const int x = t < m ? (in ? in[t] : t) : -1;
         const bool cand = x >= 0 && a.left[x] >= 0 && a.comp[x] < 0;
-        if (mode == 0 && a.node_out) {
+        if (mode != 1 && a.node_out) {
             const int s = block_append(a.node_out_n, cand ? 1 : 0, sh);
             if (cand) a.node_out[s] = x;
         }
-        const int push = cand && (mode == 1 || nsize(a, x) > a.beta) ? 1 : 0;
+        const int push = cand && (mode != 0 || nsize(a, x) > a.beta) ? 1 : 0;
         const int slot = block_append(out_count, push, sh);
         if (push) {
             if (slot < a.frontier_cap) out[slot] = make_int2(a.left[x], a.right[x]);
@@ -647,14 +675,16 @@ constexpr int kTileA = 32 * kItems;
 // points of the smaller side staged per warp (8 warps per block, static shared memory < 48 KB)
 __host__ __device__ constexpr int tile_q(int dd) { return dd <= 8 ? 128 : 64; }
 
-__global__ void huge_items_kernel(const TravArgs a, const int2 *__restrict__ pairs, int m, long long *__restrict__ items)
+__global__ void huge_items_kernel(const TravArgs a, const int2 *__restrict__ pairs, const float *__restrict__ lbs, int m,
+                                  long long *__restrict__ items)
 {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j < m) {
         int P = pairs[j].x, Q = pairs[j].y;
         int4 lp = a.links[P], lq = a.links[Q];
         int small = min(lp.y - lp.x, lq.y - lq.x);   // the query side
-        items[j] = (small + 31) / 32;
+        // no work for a pair retrieved under a larger bound than this flush's rho_hi
+        items[j] = lbs[j] < a.rho_hi_f ? (small + 31) / 32 : 0;
         EdgeK none;
         none.hi = ~0ull;
         none.lo = ~0ull;
@@ -909,8 +939,8 @@ __global__ void huge_emit_kernel(TravArgs a, int m)
 // the final band is re-evaluated), warp K-minimum, emitted when its FP64 w2 lies in
 // [rho_lo, rho_hi).
 template <int D, bool HDB, bool FP64>
-__global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const int2 *__restrict__ pairs, int m, int *next,
-                                                             int chunk)
+__global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const int2 *__restrict__ pairs,
+                                                             const float *__restrict__ lbs, int m, int *next, int chunk)
 {
     constexpr int DD = D > 0 ? D : kMaxDim;
     constexpr int kTileQ = tile_q(DD);
@@ -947,7 +977,11 @@ __global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const i
             j = base;
             jend = min(base + chunk, m);
         }
-        const int2 pr = pairs[j++];
+        const int2 pr = pairs[j];
+        if (lbs[j++] >= a.rho_hi_f) {   // retrieved under a larger bound: no edge in the range
+            if (lane == 0) waste.add(1, 0);
+            continue;
+        }
         const int4 lp = a.links[pr.x], lq = a.links[pr.y];
         const bool pa = lp.y - lp.x >= lq.y - lq.x;   // A: the larger side, on the lanes
         const int abeg = pa ? lp.x : lq.x, aend = pa ? lp.y : lq.y;
@@ -1176,7 +1210,7 @@ int launch_comp_labels(const Tree &T, const Points &P, int *uf, const int4 *link
 void traversal_init(int mode, TravArgs &a, int2 *stack, int *cnt, cudaStream_t st)
 {
     cudaMemsetAsync(cnt, 0, sizeof(int) * kTravCounters, st);
-    if (mode == 0 && a.node_out_n) cudaMemsetAsync(a.node_out_n, 0, sizeof(int), st);
+    if (mode != 1 && a.node_out_n) cudaMemsetAsync(a.node_out_n, 0, sizeof(int), st);
     launch(frontier_init_kernel, grid_for(a.N, 256), 256, 0, st, a, mode, stack, cnt + 0);
 }
 
@@ -1222,6 +1256,7 @@ void traversal_step(int mode, TravArgs &a, int2 *stack, int2 *const xbuf[2], int
 #define WM_FP(DPV)                                                                                \
     do {                                                                                          \
         if (mode == 0) launch(findpair_dfs_kernel<0, DPV>, grid, 32 * kDfsWarpsPerBlock, 0, st, a, s); \
+        else if (mode == 2) launch(findpair_dfs_kernel<2, DPV>, grid, 32 * kDfsWarpsPerBlock, 0, st, a, s); \
         else launch(findpair_dfs_kernel<1, DPV>, grid, 32 * kDfsWarpsPerBlock, 0, st, a, s);           \
     } while (0)
     if (a.dp == 4) WM_FP(4);
@@ -1254,10 +1289,28 @@ int run_traversal(TravArgs &a, int2 *stack, int2 *const xbuf[2], int *cnt, int c
 }
 
 // ------------------------------------------------------------- shrinking rho_hi in a round
-__global__ void sample_w2_kernel(const EdgeK *__restrict__ e, int m, int k, double *__restrict__ out)
+// Deterministic split of an edge batch for a smaller rho_hi: the largest w2 (bits WriteMax), then
+// a histogram of the weights over [lo, largest] in kSplitBins equal bins.  Both depend only on the
+// multiset of weights, not on the order in which the edges were appended.
+__global__ void w2_max_kernel(const EdgeK *__restrict__ e, int m, unsigned long long *out)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x)
-        out[i] = edge_w2(e[(long long)i * m / k]);
+    unsigned long long mx = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) mx = max(mx, e[i].hi);
+    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
+}
+
+__global__ void w2_hist_kernel(const EdgeK *__restrict__ e, int m, double lo, const unsigned long long *__restrict__ maxbits,
+                               int *hist)
+{
+    const double hi = __longlong_as_double((long long)*maxbits);
+    const double scale = hi > lo ? (double)kSplitBins / (hi - lo) : 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const double w = edge_w2(e[i]);
+        int b = (int)((w - lo) * scale);
+        b = b < 0 ? 0 : b >= kSplitBins ? kSplitBins - 1 : b;
+        atomicAdd(hist + b, 1);
+    }
 }
 
 __global__ void keep_below_kernel(const EdgeK *__restrict__ in, int m, double bound, EdgeK *__restrict__ out, int *count)
@@ -1276,9 +1329,13 @@ __global__ void keep_below_kernel(const EdgeK *__restrict__ in, int m, double bo
     }
 }
 
-void sample_w2(const EdgeK *e, int m, int k, double *out, cudaStream_t st)
+void w2_histogram(const EdgeK *e, int m, double lo, unsigned long long *maxbits, int *hist, cudaStream_t st)
 {
-    launch(sample_w2_kernel, grid_for(k, 256), 256, 0, st, e, m, k, out);
+    cudaMemsetAsync(maxbits, 0, sizeof(unsigned long long), st);
+    cudaMemsetAsync(hist, 0, sizeof(int) * kSplitBins, st);
+    if (m <= 0) return;
+    launch(w2_max_kernel, grid_for(m, 256), 256, 0, st, e, m, maxbits);
+    launch(w2_hist_kernel, grid_for(m, 256), 256, 0, st, e, m, lo, maxbits, hist);
 }
 
 void keep_below(const EdgeK *in, int m, double bound, EdgeK *out, int *count, cudaStream_t st)
@@ -1293,10 +1350,10 @@ static void run_bccp_groups_d(TravArgs &a, const int *counts_host, cudaStream_t 
 {
     if (counts_host[0] > 0)
         launch(bccp_group_kernel<1, D>, grid_for((long long)counts_host[0], 256), 256, 0, st, a, a.list[0],
-               a.list_count + 0);
+               a.list_lb[0], a.list_count + 0);
     if (counts_host[1] > 0)
         launch(bccp_group_kernel<8, D>, grid_for((long long)counts_host[1] * 8, 256), 256, 0, st, a, a.list[1],
-               a.list_count + 1);
+               a.list_lb[1], a.list_count + 1);
 }
 
 void run_bccp_groups(TravArgs &a, const int *counts_host, cudaStream_t st)
@@ -1318,11 +1375,11 @@ void pack_nodes(const Tree &T, int d, int dp, int4 *links, float4 *meta, float *
 
 // Pruned BCCP of the pairs of a list (the huge pairs, or a short list of big pairs that the
 // tile kernel would give to a few warps only): one warp per 32 points of a pair's smaller side.
-int run_bccp_huge(TravArgs &a, const int2 *pairs, int m, long long *items, long long *total, cudaStream_t st, Arena &ar, bool hdb,
-                  bool fp64, int stack_warps)
+int run_bccp_huge(TravArgs &a, const int2 *pairs, const float *lbs, int m, long long *items, long long *total,
+                  cudaStream_t st, Arena &ar, bool hdb, bool fp64, int stack_warps)
 {
     if (m <= 0) return 0;
-    launch(huge_items_kernel, grid_for(m, 256, 1 << 20), 256, 0, st, a, pairs, m, items);
+    launch(huge_items_kernel, grid_for(m, 256, 1 << 20), 256, 0, st, a, pairs, lbs, m, items);
     int rc = scan_exclusive_i64(items, items, m, total, st, ar);
     if (rc) return rc;
     const int blocks = stack_warps / 8;
@@ -1355,16 +1412,17 @@ void run_bccp_tiles(TravArgs &a, const int *counts_host, int *next, cudaStream_t
         if (m <= 0) continue;
         const int grid = (int)std::min<long long>((long long)num_sms() * 4, ((long long)m + 7) / 8);
         const int2 *pl = a.list[c];
+        const float *pb = a.list_lb[c];
         int *nx = next + (c - 2);
         const int chunk = (long long)m > 128LL * grid * 8 ? 4 : 1;   // long lists: fewer counter increments
 #define WM_TILE(DV)                                                                                    \
     do {                                                                                               \
         if (fp64) {                                                                                    \
-            if (hdb) launch(bccp_pair_tile_kernel<DV, true, true>, grid, 256, 0, st, a, pl, m, nx, chunk);       \
-            else launch(bccp_pair_tile_kernel<DV, false, true>, grid, 256, 0, st, a, pl, m, nx, chunk);          \
+            if (hdb) launch(bccp_pair_tile_kernel<DV, true, true>, grid, 256, 0, st, a, pl, pb, m, nx, chunk);   \
+            else launch(bccp_pair_tile_kernel<DV, false, true>, grid, 256, 0, st, a, pl, pb, m, nx, chunk);      \
         } else {                                                                                       \
-            if (hdb) launch(bccp_pair_tile_kernel<DV, true, false>, grid, 256, 0, st, a, pl, m, nx, chunk);      \
-            else launch(bccp_pair_tile_kernel<DV, false, false>, grid, 256, 0, st, a, pl, m, nx, chunk);         \
+            if (hdb) launch(bccp_pair_tile_kernel<DV, true, false>, grid, 256, 0, st, a, pl, pb, m, nx, chunk);  \
+            else launch(bccp_pair_tile_kernel<DV, false, false>, grid, 256, 0, st, a, pl, pb, m, nx, chunk);     \
         }                                                                                              \
     } while (0)
         switch (a.d) {

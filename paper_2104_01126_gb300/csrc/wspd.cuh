@@ -36,6 +36,7 @@ struct TravArgs {
     // retrieved well-separated pairs by size class: 0 tiny, 1 small, 2 medium, 3 big (tiles),
     // 4 huge (pruned dual-tree BCCP)
     int2 *list[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    float *list_lb[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // each pair's lower bound
     int *list_count = nullptr;          // [5]
     int list_cap[5] = {0, 0, 0, 0, 0};
     int2 *big = nullptr;                // = list[3]
@@ -96,12 +97,15 @@ int run_traversal(TravArgs &a, int2 *stack, int2 *const xbuf[2], int *cnt, int c
 void traversal_init(int mode, TravArgs &a, int2 *stack, int *cnt, cudaStream_t st);
 void traversal_step(int mode, TravArgs &a, int2 *stack, int2 *const xbuf[2], int *cnt, int step, int chunk,
                     cudaStream_t st);
-void sample_w2(const EdgeK *e, int m, int k, double *out, cudaStream_t st);
+// histogram of the w2 of e[0, m) over [lo, largest w2] in kSplitBins equal bins (maxbits: the
+// largest w2's bits); order-independent, so a split chosen from it is deterministic
+constexpr int kSplitBins = 4096;
+void w2_histogram(const EdgeK *e, int m, double lo, unsigned long long *maxbits, int *hist, cudaStream_t st);
 void keep_below(const EdgeK *in, int m, double bound, EdgeK *out, int *count, cudaStream_t st);
 void run_bccp_tiles(TravArgs &a, const int *counts_host, int *next, cudaStream_t st, bool hdb, bool fp64);
 void run_bccp_groups(TravArgs &a, const int *counts_host, cudaStream_t st);
-int run_bccp_huge(TravArgs &a, const int2 *pairs, int m, long long *items, long long *total, cudaStream_t st, Arena &ar, bool hdb,
-                  bool fp64, int stack_warps);
+int run_bccp_huge(TravArgs &a, const int2 *pairs, const float *lbs, int m, long long *items, long long *total,
+                  cudaStream_t st, Arena &ar, bool hdb, bool fp64, int stack_warps);
 void pack_nodes(const Tree &T, int d, int dp, int4 *links, float4 *meta, float *box, cudaStream_t st);
 
 }  // namespace wm

@@ -1,7 +1,8 @@
 """Tuning changes speed, never results: every setting of the wm_tuning parameters must return the
 same K-minimum tree (and for HDBSCAN* the same core distances, dendrogram and plot), equal to the
 FP64 oracle.  Covers the box-diagonal and the tighter diameter bounds, small and large traversal
-chunks and depth-first budgets, and the BCCP size-class cut-offs and dual-tree routing."""
+chunks and depth-first budgets, the BCCP size-class cut-offs and dual-tree routing, and the
+one-pass (combined GetRho / GetPairs) rounds."""
 import numpy as np
 import pytest
 
@@ -20,6 +21,9 @@ SETTINGS = [
     {"medium_max": 65, "big_max": 65, "route_big": 0},
     {"medium_max": 4096, "big_max": 1 << 20, "route_big": 1 << 30},
     {"route_big": 0},
+    {"combined": 1},
+    {"combined": 1, "tight_diameters": 1, "chunk_log2": 12, "dfs_budget": 2},
+    {"combined": 2},
 ]
 
 
