@@ -92,7 +92,7 @@ typedef struct {
     double ms_build_tree;
     double ms_core_dist;
     double ms_wspd;       /* GetRho + GetPairs traversals (including inline BCCP)   */
-    double ms_bccp;       /* BCCP / BCCP* kernels (all size classes), CUDA events   */
+    double ms_bccp;       /* BCCP flushes (all size classes and their readbacks)    */
     double ms_kruskal;    /* batched Kruskal of every round + final sort of the tree */
     double ms_dendrogram;
     int64_t rounds;       /* MemoGFK rounds                                         */
@@ -105,7 +105,11 @@ typedef struct {
     int64_t tree_nodes;
     int64_t tree_depth;
     size_t workspace_bytes_used;   /* peak workspace use of this call               */
-    double max_rel_screen_err;     /* max |fp32 - fp64| / fp64 over rechecked winners */
+    double max_rel_screen_err;     /* largest |fp32 - fp64| / fp64 between a screened FP32
+                                      value and its exact FP64 value, over every BCCP
+                                      candidate re-evaluated in FP64 (every winner among
+                                      them) and every core distance; 0 in the FP64 form.
+                                      A priori bound: 2^-19 for FP32-exact coordinates  */
     int32_t tie_overflow;          /* HDBSCAN*: 1 when the pairs within some point's core
                                       distance (the tie-repair edges) exceeded their
                                       buffer, which takes inputs far from general position
@@ -114,7 +118,8 @@ typedef struct {
                                       from the K-minimum one; 0 otherwise             */
     int32_t reserved;
     double ms_knn_kernel;          /* CUDA-event time of the k-NN kernel (one launch)   */
-    double ms_tile_kernel;         /* CUDA-event time summed over the BCCP flushes      */
+    double ms_tile_kernel;         /* CUDA-event time of the tile BCCP kernel (medium and
+                                      big pairs), summed over the flushes               */
     int64_t tile_launches;         /* BCCP flushes that launched the big-pair kernels   */
     double ms_getpairs;            /* CUDA-event time summed over GetPairs step launches  */
     int64_t getpairs_launches;     /* number of GetPairs step launches                  */
@@ -131,6 +136,9 @@ typedef struct {
                                       and tile kernels)                                   */
     int64_t bccp_tile_evals_skipped; /* point pairs of the tile kernel whose evaluation a
                                         chunk's bounding box ruled out                   */
+    double ms_getrho;              /* CUDA-event time of the GetRho traversals           */
+    double ms_bccp_group;          /* ... of the group BCCP kernels (tiny, small pairs)  */
+    double ms_bccp_dual;           /* ... of the dual-tree BCCP kernel (huge pairs)      */
 } wm_stats;
 
 /* Options.  A zero-initialised struct (or NULL) gives the defaults. */
@@ -366,6 +374,12 @@ const char *wm_last_error_detail(void);
 /* Number of CUDA kernels this library has launched in this process (all devices, all
  * threads) -- a diagnostic counter for benchmarks.  Touches no device. */
 int64_t wm_kernel_launch_count(void);
+
+/* Measured FP32 throughput of the current device, in TFLOP/s (a diagnostic for benchmarks, the
+ * denominator of the BCCP and k-NN roofline): a kernel of independent fused multiply-add chains
+ * filling every SM, timed with CUDA events, best of five runs after a warm-up; *ms (may be NULL)
+ * is that run's time.  Allocates and frees a few bytes of device memory. */
+int wm_fp32_fma_peak(double *tflops, double *ms);
 
 /* Library version string. */
 const char *wm_version(void);

@@ -61,7 +61,8 @@ class _Stats(ctypes.Structure):
                 ("bccp_dual_evals", ctypes.c_int64), ("rho_shrinks", ctypes.c_int64),
                 ("max_pending_pairs", ctypes.c_int64), ("bccp_pairs_below", ctypes.c_int64),
                 ("bccp_pairs_above", ctypes.c_int64), ("bccp_evals_outside", ctypes.c_int64),
-                ("bccp_tile_evals_skipped", ctypes.c_int64)]
+                ("bccp_tile_evals_skipped", ctypes.c_int64), ("ms_getrho", ctypes.c_double),
+                ("ms_bccp_group", ctypes.c_double), ("ms_bccp_dual", ctypes.c_double)]
 
 
 class _Opts(ctypes.Structure):
@@ -138,6 +139,9 @@ class Stats:
     bccp_pairs_above: int = 0
     bccp_evals_outside: int = 0
     bccp_tile_evals_skipped: int = 0
+    ms_getrho: float = 0.0
+    ms_bccp_group: float = 0.0
+    ms_bccp_dual: float = 0.0
 
     @classmethod
     def _from(cls, s: _Stats) -> "Stats":
@@ -196,6 +200,8 @@ def load(build_if_missing: bool = True):
         lib.wm_batch.argtypes = [ctypes.POINTER(_Instance), i32, i32, i32, ctypes.POINTER(_Opts)]
         lib.wm_emst_noalloc.restype = ctypes.c_int
         lib.wm_emst_noalloc.argtypes = [P, i64, i32, i32, i32, P, P, ctypes.POINTER(_Opts)]
+        lib.wm_fp32_fma_peak.restype = ctypes.c_int
+        lib.wm_fp32_fma_peak.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         lib.wm_get_tuning.restype = ctypes.c_int
         lib.wm_get_tuning.argtypes = [i64, i32, i32, ctypes.POINTER(_Tuning)]
         lib.wm_set_tuning.restype = ctypes.c_int
@@ -537,6 +543,14 @@ class tuning:
 
     def __exit__(self, *exc):
         set_tuning(None)
+
+
+def fp32_fma_peak():
+    """Measured FP32 FMA throughput of the current device: (TFLOP/s, ms of the best run)."""
+    t = ctypes.c_double(0.0)
+    ms = ctypes.c_double(0.0)
+    _check(load().wm_fp32_fma_peak(ctypes.byref(t), ctypes.byref(ms)), "wm_fp32_fma_peak")
+    return t.value, ms.value
 
 
 def kernel_launch_count() -> int:

@@ -65,6 +65,43 @@ static int *pinned_scratch()
     return s.p;
 }
 
+// Timing events are reused: creating and destroying CUDA events around every launch of the
+// host-steered rounds would leave the device idle while the host does it.  One pool per thread and
+// device (an event belongs to the device that was current when it was created).
+struct EventPool {
+    std::vector<cudaEvent_t> free_[64];
+    ~EventPool()
+    {
+        for (auto &v : free_)
+            for (cudaEvent_t e : v) cudaEventDestroy(e);
+    }
+};
+static thread_local EventPool g_event_pool;
+
+static cudaEvent_t pooled_event(int dev)
+{
+    std::vector<cudaEvent_t> &v = g_event_pool.free_[dev & 63];
+    if (!v.empty()) {
+        cudaEvent_t e = v.back();
+        v.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+static void return_events(int dev, std::vector<cudaEvent_t> &evs)
+{
+    std::vector<cudaEvent_t> &v = g_event_pool.free_[dev & 63];
+    for (cudaEvent_t e : evs)
+        if (e) v.push_back(e);
+    evs.clear();
+}
+
 // ------------------------------------------------------------------ library-managed cache
 struct DevCache {
     std::mutex mu;
@@ -253,6 +290,24 @@ __global__ void take_range_kernel(const EdgeK *__restrict__ src, int m, double l
     }
 }
 
+// FP32 throughput probe: every thread runs eight independent chains of fused multiply-adds
+// (enough in flight per warp to hide the FMA latency); the result is stored only on a condition
+// that never holds, which keeps the arithmetic from being removed.
+__global__ void __launch_bounds__(256) ffma_probe_kernel(float *out, int iters, float x, float y)
+{
+    float c0 = threadIdx.x * 1e-7f, c1 = c0 + 1e-3f, c2 = c0 + 2e-3f, c3 = c0 + 3e-3f;
+    float c4 = c0 + 4e-3f, c5 = c0 + 5e-3f, c6 = c0 + 6e-3f, c7 = c0 + 7e-3f;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            c0 = fmaf(c0, x, y); c1 = fmaf(c1, x, y); c2 = fmaf(c2, x, y); c3 = fmaf(c3, x, y);
+            c4 = fmaf(c4, x, y); c5 = fmaf(c5, x, y); c6 = fmaf(c6, x, y); c7 = fmaf(c7, x, y);
+        }
+    }
+    const float t = ((c0 + c1) + (c2 + c3)) + ((c4 + c5) + (c6 + c7));
+    if (t == -1.0f) out[blockIdx.x] = t;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------ call state
@@ -412,6 +467,46 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     a.node_out = nodes[0];
     a.node_out_n = cnts + 10;
 
+    // CUDA-event intervals of the round's kernels (when C.timing), summed into the stats per kind
+    enum { kSpanGetPairs, kSpanGetRho, kSpanFlush, kSpanGroup, kSpanTile, kSpanDual };
+    std::vector<cudaEvent_t> evs;
+    std::vector<int3> spans;   // (start event, end event, kind)
+    int dev = 0;
+    cudaGetDevice(&dev);
+    auto mark_event = [&]() -> int {
+        if (!C.timing) return -1;
+        cudaEvent_t e = pooled_event(dev);
+        if (!e) return -1;
+        cudaEventRecord(e, st);
+        evs.push_back(e);
+        return (int)evs.size() - 1;
+    };
+    auto add_span = [&](int i, int j, int kind) {
+        if (i >= 0 && j >= 0) spans.push_back(make_int3(i, j, kind));
+    };
+    struct EventsGuard {   // events left by an early return go back to the pool too
+        std::vector<cudaEvent_t> &v;
+        int dev;
+        ~EventsGuard() { return_events(dev, v); }
+    } events_guard{evs, dev};
+    auto collect_spans = [&]() -> int {
+        if (evs.empty()) return 0;
+        WM_CK(cudaEventSynchronize(evs.back()));
+        for (const int3 &sp : spans) {
+            const double ms = C.event_ms(evs[sp.x], evs[sp.y]);
+            switch (sp.z) {
+            case kSpanGetPairs: C.stats.ms_getpairs += ms; break;
+            case kSpanGetRho: C.stats.ms_getrho += ms; break;
+            case kSpanFlush: C.stats.ms_bccp += ms; break;
+            case kSpanGroup: C.stats.ms_bccp_group += ms; break;
+            case kSpanTile: C.stats.ms_tile_kernel += ms; break;
+            default: C.stats.ms_bccp_dual += ms; break;
+            }
+        }
+        return_events(dev, evs);
+        spans.clear();
+        return 0;
+    };
     int nE = 0;
     double rho_lo = 0.0;
     long long beta = 2;
@@ -440,7 +535,9 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
             fill_i32((int *)rho, 0x7f800000, 1, st);   // +inf
             set_rho(a, rho_lo, inf);
             unsigned ob = 0;
+            const int r0 = mark_event();
             WM_TRY(run_traversal(a, stack, xbuf, tcnt, chunk, st, C.pin, &ob, nullptr));
+            add_span(r0, mark_event(), kSpanGetRho);
             if (ob) { *overflow_bits = ob; return 0; }
             WM_CK(cudaMemcpyAsync(C.pin, rho, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
             WM_CK(cudaStreamSynchronize(st));
@@ -462,19 +559,10 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         spare = filt;
         WM_CK(cudaMemsetAsync(cnts + 2, 0, 6 * sizeof(int), st));
         traversal_init(tmode, a, stack, tcnt, st);
-        std::vector<cudaEvent_t> evs;   // (start, end) of traversal runs and BCCP flushes, summed per round
-        auto mark_event = [&]() {
-            if (!C.timing) return;
-            cudaEvent_t e;
-            cudaEventCreate(&e);
-            cudaEventRecord(e, st);
-            evs.push_back(e);
-        };
-        std::vector<int> ev_kind;        // 0 = traversal interval, 1 = BCCP interval
         int steps = 0;
         int last_e = 0;                  // edge count and overflow bits read after the last flush
         unsigned last_ovf = 0;
-        mark_event();
+        int span0 = mark_event();
         while (true) {
             for (int b = 0; b < kPoll; ++b, ++steps) traversal_step(tmode, a, stack, xbuf, tcnt, steps, chunk, st);
             WM_CK(cudaMemcpyAsync(C.pin, cnts, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -494,8 +582,8 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
             bool flush = empty;
             for (int c = 0; c < 5; ++c) flush = flush || lc[c] > lcap - (long long)kPoll * dfs_step_visits(chunk, a.dfs_budget);
             if (!flush) continue;
-            mark_event();
-            ev_kind.push_back(0);
+            add_span(span0, mark_event(), kSpanGetPairs);
+            const int flush0 = mark_event();
             if (combined && rho_hi != a.rho_hi) set_rho(a, rho_lo, rho_hi);
             rho_used = std::max(rho_used, a.rho_hi);
             // BCCP of the retrieved pairs.  Emission is capacity-checked; if this flush overflows the
@@ -504,17 +592,23 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
             // for the smaller range) and the flush is redone from the intact lists.
             const int e_before = e;
             for (int attempt = 0;; ++attempt) {
+                const int g0 = mark_event();
                 run_bccp_groups(a, lc, st);
+                const int g1 = mark_event();
+                add_span(g0, g1, kSpanGroup);
                 // a short list of big pairs would occupy a few warps for long: the pruned
                 // dual-tree kernel spreads each pair over warps of 32 query points instead
                 const bool route_big = lc[3] > 0 && lc[3] <= C.tune.route_big;
                 int lt[5] = {lc[0], lc[1], lc[2], route_big ? 0 : lc[3], lc[4]};
                 run_bccp_tiles(a, lt, cnts + 16, st, hdb != nullptr, a.fp64 != 0);
+                const int g2 = mark_event();
+                add_span(g1, g2, kSpanTile);
                 if (route_big)
                     WM_TRY(run_bccp_huge(a, a.list[3], a.list_lb[3], lc[3], huge_items, (long long *)(cnts + 12), st,
                                          ar, hdb != nullptr, a.fp64 != 0, stack_warps));
                 WM_TRY(run_bccp_huge(a, a.list[4], a.list_lb[4], lc[4], huge_items, (long long *)(cnts + 12), st, ar,
                                      hdb != nullptr, a.fp64 != 0, stack_warps));
+                add_span(g2, mark_event(), kSpanDual);
                 WM_CK(cudaMemcpyAsync(C.pin, ecount, sizeof(int), cudaMemcpyDeviceToHost, st));
                 WM_CK(cudaMemcpyAsync(C.pin + 1, ovf, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
                 WM_CK(cudaStreamSynchronize(st));
@@ -554,8 +648,8 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
             }
             WM_CK(cudaMemsetAsync(lcount, 0, 5 * sizeof(int), st));
             if (lc[3] > 0 || lc[4] > 0) C.stats.tile_launches += 1;
-            mark_event();
-            ev_kind.push_back(1);
+            span0 = mark_event();
+            add_span(flush0, span0, kSpanFlush);
             if (empty) break;
             if (steps > 10000000) { set_detail("WSPD GetPairs traversal did not terminate%s", ""); return WM_EINTERNAL; }
         }
@@ -592,16 +686,8 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
             WM_TRY(batch_kruskal(a.edges, m, n, uf, R, E_out, nE, &accepted, ar, st, C.pin));
         }
         C.stats.ms_kruskal += tk.ms();
-        // the interval events of this round are complete once the stream has synced (Kruskal)
-        if (!evs.empty()) {
-            WM_CK(cudaEventSynchronize(evs.back()));
-            for (size_t k = 0; k + 1 < evs.size(); ++k) {
-                double ms = C.event_ms(evs[k], evs[k + 1]);
-                if (ev_kind[k] == 0) C.stats.ms_getpairs += ms;
-                else { C.stats.ms_bccp += ms; C.stats.ms_tile_kernel += ms; }
-            }
-            for (cudaEvent_t e : evs) cudaEventDestroy(e);
-        }
+        // the timed intervals of this round are complete once the stream has synced (Kruskal)
+        WM_TRY(collect_spans());
         nE += accepted;
         if (C.tune.combined == 2 && !combined) {
             WM_CK(cudaMemcpyAsync(C.pin, stat + 4, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
@@ -648,6 +734,12 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     C.stats.bccp_pairs_above = (int64_t)hs[9];
     C.stats.bccp_evals_outside = (int64_t)hs[10];
     C.stats.bccp_tile_evals_skipped = (int64_t)hs[11];
+    {
+        float e;
+        const unsigned eb = (unsigned)hs[12];
+        memcpy(&e, &eb, sizeof e);
+        C.stats.max_rel_screen_err = std::max(C.stats.max_rel_screen_err, (double)e);
+    }
     ar.off = mark;
     return 0;
 }
@@ -1310,11 +1402,13 @@ int wm_batch(const wm_instance *inst, int32_t count, int32_t dtype, int32_t layo
         sum.getpairs_launches += gs.getpairs_launches; sum.bccp_dual_evals += gs.bccp_dual_evals;
         sum.rho_shrinks += gs.rho_shrinks; sum.tile_launches += gs.tile_launches;
         sum.ms_knn_kernel += gs.ms_knn_kernel; sum.ms_tile_kernel += gs.ms_tile_kernel;
+        sum.ms_getrho += gs.ms_getrho; sum.ms_bccp_group += gs.ms_bccp_group; sum.ms_bccp_dual += gs.ms_bccp_dual;
         sum.ms_getpairs += gs.ms_getpairs;
         sum.max_pending_pairs = std::max(sum.max_pending_pairs, gs.max_pending_pairs);
         sum.bccp_pairs_below += gs.bccp_pairs_below; sum.bccp_pairs_above += gs.bccp_pairs_above;
         sum.bccp_evals_outside += gs.bccp_evals_outside;
         sum.bccp_tile_evals_skipped += gs.bccp_tile_evals_skipped;
+        sum.max_rel_screen_err = std::max(sum.max_rel_screen_err, gs.max_rel_screen_err);
     }
     if (opts && opts->stats) *opts->stats = sum;
     return rc;
@@ -1384,6 +1478,39 @@ const char *wm_strerror(int code)
 const char *wm_last_error_detail(void) { return g_detail.c_str(); }
 
 int64_t wm_kernel_launch_count(void) { return (int64_t)g_launch_count.load(); }
+
+int wm_fp32_fma_peak(double *tflops, double *ms)
+{
+    if (!tflops) return WM_EINVAL;
+    g_detail.clear();
+    const int blocks = num_sms() * 8, threads = 256, iters = 1 << 13;
+    float *out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    WM_CK(cudaMalloc((void **)&out, sizeof(float) * blocks));
+    int rc = WM_OK;
+    float best = 1e30f;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = WM_ECUDA;
+    for (int rep = 0; rc == WM_OK && rep < 6; ++rep) {   // the first run warms up
+        cudaEventRecord(e0, nullptr);
+        launch(ffma_probe_kernel, blocks, threads, 0, nullptr, out, iters, 0.999999f, 1e-7f);
+        cudaEventRecord(e1, nullptr);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = WM_ECUDA; break; }
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (rep > 0) best = std::min(best, t);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(out);
+    if (rc != WM_OK) {
+        set_detail("FMA probe failed: %s%lld", cudaGetErrorString(cudaGetLastError()), 0);
+        return rc;
+    }
+    const double flops = 2.0 * 8 * 4 * (double)iters * blocks * threads;
+    *tflops = flops / (best * 1e-3) / 1e12;
+    if (ms) *ms = best;
+    return WM_OK;
+}
 
 const char *wm_version(void) { return "wspdmst 0.1 (sm_103a)"; }
 

@@ -47,7 +47,8 @@ struct KnnArgs {
     int *slow_cnt;
     int *next_group;     // dispenser of 32-query groups
     int *err;            // set when a traversal stack would overflow (an internal error)
-    unsigned long long *stat;   // [0] evals, [1] fp64 rechecks
+    unsigned long long *stat;   // [0] evals, [1] fp64 rechecks, [2] bits of the largest relative
+                                //     error of a screened k-th value against the exact one
 };
 
 __device__ inline double d64(const double *__restrict__ x64, int n, int d, int i, int j)
@@ -107,6 +108,7 @@ __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
     const int n = a.n, d = a.d;
     const bool exact32 = a.eta == 0.0;   // FP32 copy is exact: threshold in FP32
     unsigned long long n_ev = 0, n_re = 0;
+    float kerr = 0.f;   // largest relative error of a screened k-th value (FP32 screen)
     // 32-query groups handed out dynamically: their costs differ too much for a static deal
     while (true) {
         int q0 = 0;
@@ -296,6 +298,10 @@ __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
             a.slow[s] = i;
             continue;
         }
+        if (!FP64 && cd2 > 0.0) {
+            const double sk = (double)sv[(k - 1) * 32 + lane];
+            kerr = fmaxf(kerr, __double2float_ru(fabs(sk - cd2) / cd2));
+        }
         a.cd64[i] = cd2;
         a.cd32[i] = __double2float_rn(cd2);
         int r = 0;
@@ -313,10 +319,12 @@ __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
     for (int o = 16; o; o >>= 1) {
         n_ev += __shfl_xor_sync(0xffffffffu, n_ev, o);
         n_re += __shfl_xor_sync(0xffffffffu, n_re, o);
+        kerr = fmaxf(kerr, __shfl_xor_sync(0xffffffffu, kerr, o));
     }
     if (lane == 0) {
         atomicAdd(a.stat + 0, n_ev);
         atomicAdd(a.stat + 1, n_re);
+        if (kerr > 0.f) atomicMax(a.stat + 2, (unsigned long long)__float_as_uint(kerr));
     }
 }
 
@@ -574,8 +582,8 @@ int core_distances(Points &P, Tree &T, int min_pts, bool fp64, HdbState &H, Aren
     launch(rep_emit_extra_kernel, grid_for(extra_cap, 256), 256, 0, st, ex_p, ex_q, ex_d, cnts + 1, extra_cap, H.cd64,
            P.pid, rep, cnts + 3);
     cudaMemcpyAsync(pin, cnts, 8 * sizeof(int), cudaMemcpyDeviceToHost, st);
-    unsigned long long hs[2];
-    cudaMemcpyAsync(pin + 8, a.stat, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+    unsigned long long hs[3];
+    cudaMemcpyAsync(pin + 8, a.stat, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;
     memcpy(hs, pin + 8, sizeof hs);
     if (pin[5]) {
@@ -587,6 +595,10 @@ int core_distances(Points &P, Tree &T, int min_pts, bool fp64, HdbState &H, Aren
         stats->knn_evals = (int64_t)hs[0];
         stats->fp64_rechecks += (int64_t)hs[1];
         stats->tie_overflow = pin[2] ? 1 : 0;
+        float ke;
+        const unsigned kb = (unsigned)hs[2];
+        memcpy(&ke, &kb, sizeof ke);
+        stats->max_rel_screen_err = std::max(stats->max_rel_screen_err, (double)ke);
     }
     H.rep = rep;
     H.nrep = nrep;

@@ -114,6 +114,25 @@ __device__ inline double exact_w2(const TravArgs &a, int i, int j, float d32, fl
     return dist64(a.x64, a.n, a.d, i, j);
 }
 
+// exact_w2, also noting the relative error of the FP32 screened value (sd, or for HDBSCAN* its
+// maximum with the FP32 core distances c32) against the exact weight in err
+__device__ inline double checked_w2(const TravArgs &a, int i, int j, float sd, float c32, float &err)
+{
+    const double w = exact_w2(a, i, j, sd, c32);
+    if (w > 0.0) {
+        const double sv = a.cd64 ? fmax((double)sd, (double)c32) : (double)sd;
+        err = fmaxf(err, __double2float_ru(fabs(sv - w) / w));
+    }
+    return w;
+}
+
+// the largest relative screen error of a warp into stat[12] (bits of a non-negative float)
+__device__ inline void err_flush(const TravArgs &a, float err)
+{
+    for (int o = 16; o; o >>= 1) err = fmaxf(err, __shfl_xor_sync(0xffffffffu, err, o));
+    if ((threadIdx.x & 31) == 0 && err > 0.f) atomicMax(a.stat + 12, (unsigned long long)__float_as_uint(err));
+}
+
 // a recheck candidate held back so that the FP64 work of several lanes runs in one instruction
 struct Deferred {
     int i = -1, j = 0;
@@ -505,6 +524,7 @@ __global__ void __launch_bounds__(256) bccp_group_kernel(TravArgs a, const int2 
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
     const int n = a.n, d = a.d;
     unsigned long long n_ev = 0, n_re = 0;
+    float serr = 0.f;   // largest relative screen error of this thread's rechecks
     Waste waste;
     for (int base = warp * PPW; base < m; base += nwarps * PPW) {
         const int pi = base + lane / G;
@@ -565,12 +585,12 @@ __global__ void __launch_bounds__(256) bccp_group_kernel(TravArgs a, const int2 
                     const float sd = dist32t<D>(a.x32, n, d, i, j);
                     const float c32 = a.cd32 ? fmaxf(a.cd32[i], a.cd32[j]) : 0.f;
                     if (df.i < 0) df = Deferred{i, j, sd, c32};
-                    else kmin_update(best, exact_w2(a, i, j, sd, c32), a.pid[i], a.pid[j]);
+                    else kmin_update(best, checked_w2(a, i, j, sd, c32, serr), a.pid[i], a.pid[j]);
                     ++n_re;
                 }
             }
             __syncwarp();
-            if (df.i >= 0) kmin_update(best, exact_w2(a, df.i, df.j, df.sd, df.c32), a.pid[df.i], a.pid[df.j]);
+            if (df.i >= 0) kmin_update(best, checked_w2(a, df.i, df.j, df.sd, df.c32, serr), a.pid[df.i], a.pid[df.j]);
         }
 #pragma unroll
         for (int o = G / 2; o; o >>= 1) {
@@ -583,6 +603,7 @@ __global__ void __launch_bounds__(256) bccp_group_kernel(TravArgs a, const int2 
         warp_emit(a, valid && g == 0 && in_range(a, best), best);
     }
     waste_flush(a, waste);
+    err_flush(a, serr);
     n_ev = warp_sum_u64(n_ev);
     n_re = warp_sum_u64(n_re);
     if (lane == 0 && n_ev) {
@@ -705,6 +726,7 @@ __global__ void __launch_bounds__(256) bccp_dual_kernel(TravArgs a, const int2 *
     const int n = a.n, d = a.d;
     const float rho_hi_f = a.rho_hi_f;
     unsigned long long n_ev = 0, n_re = 0;
+    float serr = 0.f;
     for (long long item = gw; item < TI; item += nw) {
         int lo = 0, hi = m - 1;
         while (lo < hi) {
@@ -850,7 +872,7 @@ __global__ void __launch_bounds__(256) bccp_dual_kernel(TravArgs a, const int2 *
                         if (HDB) acc = fmaxf(acc, c32);
                         int bp = __shfl_sync(0xffffffffu, ppid, p);
                         if (valid && acc <= thr) {
-                            kmin_update(best, exact_w2(a, ii, b0 + p, sd, c32), qpid, bp);
+                            kmin_update(best, checked_w2(a, ii, b0 + p, sd, c32, serr), qpid, bp);
                             ++n_re;
                         }
                     }
@@ -908,6 +930,7 @@ __global__ void __launch_bounds__(256) bccp_dual_kernel(TravArgs a, const int2 *
         }
         __syncwarp();
     }
+    err_flush(a, serr);
     n_ev = warp_sum_u64(n_ev);
     n_re = warp_sum_u64(n_re);
     if (lane == 0 && n_ev) {
@@ -964,6 +987,7 @@ __global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const i
     const int d = D > 0 ? D : a.d;
     const int n = a.n;
     unsigned long long n_ev = 0, n_re = 0, n_skip = 0;
+    float serr = 0.f;
     Waste waste;
     // pairs handed out `chunk` at a time (sizes vary too much for a static deal; on long lists
     // one counter increment per pair would serialise the warps on it)
@@ -1133,7 +1157,7 @@ __global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const i
                             if (HDB) s = fmaxf(s, c32);
                             if (s <= T) {
                                 if (df.i < 0) df = Deferred{i, b0 + jj, sd, c32};
-                                else kmin_update(best, exact_w2(a, i, b0 + jj, sd, c32), a.pid[i], a.pid[b0 + jj]);
+                                else kmin_update(best, checked_w2(a, i, b0 + jj, sd, c32, serr), a.pid[i], a.pid[b0 + jj]);
                                 ++nre;
                             }
                         }
@@ -1156,7 +1180,7 @@ __global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const i
         }
         __syncwarp();
         if (!FP64 && df.i >= 0 && !screened_above(run_min, a) && screen_value(df, HDB) <= screen_threshold(run_min, a))
-            kmin_update(best, exact_w2(a, df.i, df.j, df.sd, df.c32), a.pid[df.i], a.pid[df.j]);
+            kmin_update(best, checked_w2(a, df.i, df.j, df.sd, df.c32, serr), a.pid[df.i], a.pid[df.j]);
         // warp K-minimum of the pair
         for (int o = 16; o; o >>= 1) {
             unsigned long long oh = __shfl_xor_sync(0xffffffffu, best.hi, o);
@@ -1177,6 +1201,7 @@ __global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const i
     }
     if (ecnt > 0) flush_edges();
     waste_flush(a, waste);
+    err_flush(a, serr);
     n_re = warp_sum_u64(n_re);
     if (lane == 0 && n_ev) {
         atomicAdd(a.stat + 1, n_ev);

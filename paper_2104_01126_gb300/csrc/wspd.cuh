@@ -61,7 +61,8 @@ struct TravArgs {
                                         // [8] / [9] retrieved pairs whose BCCP fell below / above
                                         // the round's range, [10] evaluations of those pairs
                                         // (group and tile kernels), [11] tile-kernel evaluations
-                                        // skipped by the chunk box bound
+                                        // skipped by the chunk box bound, [12] bits of the largest
+                                        // relative FP32 screen error among the rechecks
 };
 
 // Traversal step (see findpair_dfs_kernel): warps per block and the capacity of a warp's own

@@ -121,3 +121,13 @@ def test_hdbscan_duplicate_overflow_reported():
     assert math.isclose(math.fsum(w), math.fsum(ref["w"]), rel_tol=1e-12)
     assert np.array_equal(np.sort(w), np.sort(ref["w"]))   # MST weights form a unique multiset
     assert r["size"][-1] == n and np.array_equal(np.sort(r["order"]), np.arange(n))
+
+
+def test_screen_error_is_measured_and_within_the_band():
+    # the FP32 screen's error against the exact FP64 value, measured per result on the device:
+    # positive (rounding happens) and within the a priori relative band 2^-19 for FP32 coordinates
+    x = synthdata.generate("gmm", 20000, 3, seed=27)
+    for r in (wm.hdbscan(x, min_pts=10, return_stats=True), wm.emst(x, return_stats=True)):
+        e = r["stats"].max_rel_screen_err
+        assert 0.0 < e <= 2.0 ** -19, e
+    assert wm.emst(x, precision="fp64", return_stats=True)["stats"].max_rel_screen_err == 0.0
