@@ -1,0 +1,189 @@
+"""Autotuner of the library's speed parameters (wm_tuning), run on the target GPU.
+
+For every (problem, dimension, size bucket) the tuner starts from the defaults and walks the
+parameters one at a time (coordinate descent), keeping each value that lowers the summed time of
+the bucket's workloads, two generators per problem:
+    EMST      uniform in [0,1)^d and variable-density blobs,
+    HDBSCAN*  Gaussian mixture and variable-density blobs, minPts = 10,
+at n = 10^5, 10^6 and 10^7 (HDBSCAN*: 10^5 and 10^6).  Every candidate must return the same tree
+as the defaults (the tuning changes speed, never results): the tuner compares the edge lists
+and stops on a difference.  The chosen table is written to csrc/tuning_table.inc (rebuild the
+library to use it) and a summary, with each bucket's time under the defaults and tuned, to the
+JSON file named by --report.
+
+    python -m paper_2104_01126_gb300.autotune --report gpurun_out/autotune.json
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+TABLE = os.path.join(HERE, "csrc", "tuning_table.inc")
+
+# the values of a call when the table has no row for it (also the starting point of the descent)
+DEFAULTS = {"tight_diameters": 0, "chunk_log2": 0, "dfs_budget": 8, "route_big": 1024, "medium_max": 1024,
+            "big_max": 65536, "combined": 0}
+# the values tried, in the order the descent visits the parameters
+GRID = [
+    ("combined", [0, 1, 2]),
+    ("tight_diameters", [0, 1]),
+    ("dfs_budget", [4, 8, 16, 32]),
+    ("chunk_log2", [0, 19, 20, 22]),
+    ("medium_max", [256, 1024, 4096]),
+    ("big_max", [16384, 65536, 262144]),
+    ("route_big", [0, 256, 1024, 8192]),
+]
+DIMS = (2, 3, 5, 7)
+SIZES = {"emst": (100_000, 1_000_000, 10_000_000), "hdbscan": (100_000, 1_000_000)}
+GENS = {"emst": ("uniform", "varden"), "hdbscan": ("gmm", "varden")}
+
+
+def _inputs(problem, d, n, torch):
+    import synthdata
+    out = []
+    for g in GENS[problem]:
+        x = synthdata.generate(g, n, d, seed=1, dtype=np.float32)
+        out.append(torch.from_numpy(x).cuda())
+    return out
+
+
+def _run(wm, problem, x):
+    if problem == "emst":
+        r = wm.emst(x)
+        return r["u"], r["v"]
+    r = wm.hdbscan(x, min_pts=10)
+    return r["u"], r["v"]
+
+
+def _time(wm, torch, problem, xs, params, reps, ref=None):
+    """Summed best-of-reps time (ms) of the bucket's workloads under params; checks the trees."""
+    total = 0.0
+    trees = []
+    with wm.tuning(**params):
+        for i, x in enumerate(xs):
+            tree = _run(wm, problem, x)   # warm-up, and the result check
+            if ref is not None:
+                u, v = tree
+                if not (torch.equal(u, ref[i][0]) and torch.equal(v, ref[i][1])):
+                    raise RuntimeError(f"tuning {params} changed the result of {problem} d={x.shape[1]}")
+            trees.append(tree)
+            best = float("inf")
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                _run(wm, problem, x)
+                e1.record()
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            total += best
+    return total, trees
+
+
+def tune(problems=("emst", "hdbscan"), dims=DIMS, reps=2, log=print):
+    import torch
+    import paper_2104_01126_gb300 as wm
+    wm.load()
+    rows = []
+    for problem in problems:
+        for d in dims:
+            for n in SIZES[problem]:
+                t0 = time.time()
+                xs = _inputs(problem, d, n, torch)
+                base_ms, ref = _time(wm, torch, problem, xs, DEFAULTS, reps)
+                best = dict(DEFAULTS)
+                best_ms = base_ms
+                for key, values in GRID:
+                    for v in values:
+                        if v == best[key]:
+                            continue
+                        cand = dict(best)
+                        cand[key] = v
+                        if cand["big_max"] < cand["medium_max"]:
+                            continue
+                        ms, _ = _time(wm, torch, problem, xs, cand, reps, ref)
+                        if ms < 0.97 * best_ms:   # keep a change only when it clearly helps
+                            best, best_ms = cand, ms
+                rows.append({"problem": problem, "d": d, "n": n, "default_ms": base_ms, "tuned_ms": best_ms,
+                             "params": best, "seconds": time.time() - t0})
+                log(json.dumps(rows[-1]))
+                del xs, ref
+                torch.cuda.empty_cache()
+    return rows
+
+
+def write_table(rows, path=TABLE):
+    """C source of builtin_tuning(): the rows of the call's problem (HDBSCAN* falls back to the
+    EMST rows when it has none), the nearest tuned dimension among them, then the smallest tuned
+    size at or above n (the largest when n exceeds them all)."""
+    fields = list(DEFAULTS)
+    lines = ["// tuning_table.inc -- the built-in speed parameters of a call by (problem, d, n).",
+             "// Written by paper_2104_01126_gb300/autotune.py from measurements on the target GPU; every",
+             "// entry gives the same results as any other (the parameters change speed only).",
+             "struct TuneRow {",
+             "    int hdb, d;",
+             "    long long n;",
+             "    int " + ", ".join(fields) + ";",
+             "};",
+             "static const TuneRow kTuneRows[] = {"]
+    for r in sorted(rows, key=lambda r: (r["problem"], r["d"], r["n"])):
+        p = r["params"]
+        lines.append("    {%d, %d, %dLL, %s},   // %.1f ms -> %.1f ms" % (
+            1 if r["problem"] == "hdbscan" else 0, r["d"], r["n"], ", ".join(str(int(p[f])) for f in fields),
+            r["default_ms"], r["tuned_ms"]))
+    lines.append("    {-1, 0, 0LL, %s},   // end (never matches)" % ", ".join(str(DEFAULTS[f]) for f in fields))
+    lines += ["};",
+              "",
+              "static void builtin_tuning(long long n, int d, int min_pts, wm_tuning *t)",
+              "{"]
+    for f in fields:
+        lines.append(f"    t->{f} = {DEFAULTS[f]};")
+    lines += ["    const TuneRow *pick = nullptr;",
+              "    for (int hdb = min_pts > 1 ? 1 : 0; hdb >= 0 && !pick; --hdb) {",
+              "        int bestd = -1;",
+              "        for (const TuneRow &r : kTuneRows)",
+              "            if (r.hdb == hdb && (bestd < 0 || (r.d > d ? r.d - d : d - r.d) < (bestd > d ? bestd - d : d - bestd)))",
+              "                bestd = r.d;",
+              "        const TuneRow *ge = nullptr, *largest = nullptr;",
+              "        for (const TuneRow &r : kTuneRows) {",
+              "            if (r.hdb != hdb || r.d != bestd) continue;",
+              "            if (r.n >= n && (!ge || r.n < ge->n)) ge = &r;",
+              "            if (!largest || r.n > largest->n) largest = &r;",
+              "        }",
+              "        pick = ge ? ge : largest;",
+              "    }",
+              "    if (!pick) return;"]
+    for f in fields:
+        lines.append(f"    t->{f} = pick->{f};")
+    lines += ["}", ""]
+    with open(path, "w") as f:
+        f.write("\n".join(lines))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--report", default="autotune.json")
+    ap.add_argument("--problems", default="emst,hdbscan")
+    ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--table", default=TABLE, help="where to write the table (default: csrc/tuning_table.inc)")
+    ap.add_argument("--no-write", action="store_true", help="report only; write no table")
+    args = ap.parse_args()
+    rows = tune(problems=tuple(p for p in args.problems.split(",") if p), reps=args.reps)
+    with open(args.report, "w") as f:
+        json.dump(rows, f, indent=1)
+    if not args.no_write:
+        write_table(rows, args.table)
+
+
+if __name__ == "__main__":
+    main()
