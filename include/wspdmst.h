@@ -67,6 +67,19 @@ extern "C" {
                                   rigorous error band (default) */
 #define WM_PREC_FP64 1        /* the plain form: every point distance evaluated in FP64 */
 
+/* Methods (wm_opts.method): an algorithm, optionally OR'ed with WM_SEPARATION_GEOMETRIC; all
+ * compute the same tree. */
+#define WM_METHOD_MEMOGFK 0   /* MemoGFK rounds (Sec. 3.2.3, Algorithm 3), the default */
+#define WM_METHOD_GFK 1       /* GFK (Sec. 3.2.2, Algorithm 2): the full WSPD is materialised and each
+                                 pair's BCCP computed once and kept until its round */
+#define WM_METHOD_NAIVE 2     /* EMST-Naive (Sec. 5): the BCCP of every pair of the full WSPD, then
+                                 one Kruskal over all of them */
+#define WM_SEPARATION_GEOMETRIC 0x100   /* HDBSCAN*: pairs are well-separated by geometry alone,
+                                 without the mutual-unreachability disjunction of Sec. 3.1.2 */
+#define WM_METHOD_GANTAO (WM_METHOD_MEMOGFK | WM_SEPARATION_GEOMETRIC)
+                              /* HDBSCAN*: the baseline of Sec. 3.1.1 (standard WSPD, BCCP*, MemoGFK
+                                 rounds); for EMST the same as WM_METHOD_MEMOGFK */
+
 /* ------------------------------------------------------------------------- records */
 
 /* One tree edge: endpoints (u < v) and weight w (Euclidean or mutual-reachability distance,
@@ -139,13 +152,14 @@ typedef struct {
     double ms_getrho;              /* CUDA-event time of the GetRho traversals           */
     double ms_bccp_group;          /* ... of the group BCCP kernels (tiny, small pairs)  */
     double ms_bccp_dual;           /* ... of the dual-tree BCCP kernel (huge pairs)      */
+    int64_t wspd_pairs;            /* GFK / EMST-Naive: pairs of the materialised WSPD     */
 } wm_stats;
 
 /* Options.  A zero-initialised struct (or NULL) gives the defaults. */
 typedef struct {
     void *stream;           /* cudaStream_t to issue work on; NULL = legacy default stream */
     int32_t precision;      /* WM_PREC_FP32_SCREEN (0, default) or WM_PREC_FP64            */
-    int32_t reserved0;
+    int32_t method;         /* WM_METHOD_* (0, default: MemoGFK)                           */
     void *workspace;        /* optional caller-owned device scratch arena; NULL = the
                                library manages a grow-only per-device cache               */
     size_t workspace_bytes; /* size of `workspace` in bytes                                */
@@ -348,7 +362,8 @@ typedef struct {
     int32_t reserved[9];
 } wm_tuning;
 
-/* The parameters a call with these sizes uses (min_pts = 0 for EMST). */
+/* The parameters a call with these sizes uses (min_pts = 0 for EMST); n = 0 gives the built-in
+ * defaults (the values before any table row or override). */
 int wm_get_tuning(int64_t n, int32_t d, int32_t min_pts, wm_tuning *out);
 /* Overrides the table for every later call of the process (NULL restores it).  WM_EINVAL for
  * out-of-range values.  Not for use while other threads are inside library calls. */

@@ -26,6 +26,7 @@ __all__ = ["emst", "hdbscan", "single_linkage", "query_footprint", "library_path
 WM_F32, WM_F64 = 0, 1
 WM_AOS, WM_SOA = 0, 1
 PREC = {"fp32": 0, "fp32_screen": 0, "fp64": 1}
+METHODS = {"memogfk": 0, "gfk": 1, "naive": 2, "gantao": 0x100, "gfk-geometric": 0x101, "naive-geometric": 0x102}
 
 
 class WMError(RuntimeError):
@@ -62,12 +63,13 @@ class _Stats(ctypes.Structure):
                 ("max_pending_pairs", ctypes.c_int64), ("bccp_pairs_below", ctypes.c_int64),
                 ("bccp_pairs_above", ctypes.c_int64), ("bccp_evals_outside", ctypes.c_int64),
                 ("bccp_tile_evals_skipped", ctypes.c_int64), ("ms_getrho", ctypes.c_double),
-                ("ms_bccp_group", ctypes.c_double), ("ms_bccp_dual", ctypes.c_double)]
+                ("ms_bccp_group", ctypes.c_double), ("ms_bccp_dual", ctypes.c_double),
+                ("wspd_pairs", ctypes.c_int64)]
 
 
 class _Opts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("precision", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("workspace", ctypes.c_void_p),
+                ("method", ctypes.c_int32), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t), ("stats", ctypes.POINTER(_Stats))]
 
 
@@ -142,6 +144,7 @@ class Stats:
     ms_getrho: float = 0.0
     ms_bccp_group: float = 0.0
     ms_bccp_dual: float = 0.0
+    wspd_pairs: int = 0
 
     @classmethod
     def _from(cls, s: _Stats) -> "Stats":
@@ -267,9 +270,10 @@ def _points_aos(x):
     return a, a.ctypes.data, a.shape[0], a.shape[1], code, False, None
 
 
-def _opts(precision: str, stream, stats: _Stats, workspace=None):
+def _opts(precision: str, stream, stats: _Stats, workspace=None, method: str = "memogfk"):
     o = _Opts()
     o.precision = PREC[precision]
+    o.method = METHODS[method]
     o.stream = stream or None
     o.stats = ctypes.pointer(stats)
     if workspace is not None:
@@ -322,10 +326,11 @@ def _dnode_result(buf, m: int, device):
 
 # ---------------------------------------------------------------------------------- API
 def emst(points, precision: str = "fp32", stream=None, return_stats: bool = False, workspace=None,
-         layout: str = "aos"):
+         layout: str = "aos", method: str = "memogfk"):
     """Euclidean MST (wm_emst).  Returns dict(u, v, w, total[, stats]); edges in K order.
     workspace: optional (device pointer, bytes) of a caller-owned arena; layout: "aos" for an
-    (n, d) array, "soa" for a (d, n) array."""
+    (n, d) array, "soa" for a (d, n) array; method: "memogfk" (default), "gfk" (the full WSPD
+    materialised, Algorithm 2) or "naive" (EMST-Naive)."""
     lib = load()
     keep, ptr, n, d, code, on_dev, dev = _points(points, layout)
     m = max(n - 1, 0)
@@ -334,7 +339,7 @@ def emst(points, precision: str = "fp32", stream=None, return_stats: bool = Fals
     st = _Stats()
     if stream is None and on_dev:
         stream = _current_stream(dev)
-    o = _opts(precision, stream, st, workspace)
+    o = _opts(precision, stream, st, workspace, method)
     rc = lib.wm_emst(ptr, n, d, code, WM_SOA if layout == "soa" else WM_AOS, bptr if m > 0 else None,
                      ctypes.byref(total), ctypes.byref(o))
     _check(rc, "wm_emst")
@@ -367,9 +372,11 @@ def emst_noalloc(points, precision: str = "fp32", stream=None):
 
 
 def hdbscan(points, min_pts: int = 10, start: int = 0, precision: str = "fp32", stream=None,
-            return_stats: bool = False, workspace=None, layout: str = "aos"):
+            return_stats: bool = False, workspace=None, layout: str = "aos", method: str = "memogfk"):
     """HDBSCAN* (wm_hdbscan): MST of G_MR, core distances, ordered dendrogram, reachability plot.
-    workspace and layout as for emst()."""
+    workspace and layout as for emst(); method: "memogfk", "gfk", "naive" or "gantao" (the
+    baseline with geometric separation only; "gfk-geometric" / "naive-geometric" combine it with
+    the materialised WSPD)."""
     lib = load()
     keep, ptr, n, d, code, on_dev, dev = _points(points, layout)
     m = max(n - 1, 0)
@@ -381,7 +388,7 @@ def hdbscan(points, min_pts: int = 10, start: int = 0, precision: str = "fp32", 
     st = _Stats()
     if stream is None and on_dev:
         stream = _current_stream(dev)
-    o = _opts(precision, stream, st, workspace)
+    o = _opts(precision, stream, st, workspace, method)
     rc = lib.wm_hdbscan(ptr, n, d, code, WM_SOA if layout == "soa" else WM_AOS, int(min_pts), eptr if m else None,
                         cptr, dptr if m else None,
                         optr, rptr, int(start), ctypes.byref(o))
@@ -518,12 +525,12 @@ def get_tuning(n: int, d: int, min_pts: int = 0) -> dict:
 
 def set_tuning(params=None):
     """Overrides the built-in tuning table for every later call (wm_set_tuning); None restores it.
-    params: a dict of TUNING_FIELDS (missing fields keep the table's value for n = 10^6, d = 3)."""
+    params: a dict of TUNING_FIELDS (missing fields take the built-in defaults)."""
     lib = load()
     if params is None:
         _check(lib.wm_set_tuning(None), "wm_set_tuning")
         return
-    base = get_tuning(1_000_000, 3, 0)
+    base = get_tuning(0, 1, 0)
     base.update(params)
     t = _Tuning()
     for f in TUNING_FIELDS:

@@ -148,7 +148,8 @@ def write_table(rows, path=TABLE):
               "{"]
     for f in fields:
         lines.append(f"    t->{f} = {DEFAULTS[f]};")
-    lines += ["    const TuneRow *pick = nullptr;",
+    lines += ["    if (n <= 0) return;   // n = 0 asks for the defaults themselves",
+              "    const TuneRow *pick = nullptr;",
               "    for (int hdb = min_pts > 1 ? 1 : 0; hdb >= 0 && !pick; --hdb) {",
               "        int bestd = -1;",
               "        for (const TuneRow &r : kTuneRows)",

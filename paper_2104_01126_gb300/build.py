@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libwspdmst.so")
-SOURCES = ["util.cu", "kdtree.cu", "wspd.cu", "kruskal.cu", "knn.cu", "dendro.cu", "batch.cu", "api.cu"]
+SOURCES = ["util.cu", "kdtree.cu", "wspd.cu", "gfk.cu", "kruskal.cu", "knn.cu", "dendro.cu", "batch.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -143,7 +143,17 @@ struct Caps {
     long long edges;        // candidate edges per round
     int frontier_scale;     // multiplier of the stack bound (grown after an overflow)
     long long extra_bytes;  // additional arena bytes (grown after the arena ran out)
+    long long wspd_pairs;   // GFK / EMST-Naive: capacity of the materialised WSPD (0 otherwise)
 };
+
+// Well-separated pairs per point of the full WSPD by dimension (measured on uniform and
+// clustered inputs; it grows with the dimension and slowly with n): the first capacity of the
+// materialised WSPD, grown after an overflow.
+static long long wspd_pairs_guess(long long n, int d)
+{
+    const long long per = d <= 1 ? 4 : d == 2 ? 16 : d == 3 ? 64 : d == 4 ? 200 : d == 5 ? 800 : 4000;
+    return std::max<long long>(1 << 16, per * n);
+}
 
 static size_t estimate_bytes(long long n, int d, int min_pts, const Caps &c)
 {
@@ -159,11 +169,14 @@ static size_t estimate_bytes(long long n, int d, int min_pts, const Caps &c)
     b += (size_t)N * (8 * d + 48);          // tree arrays (+ build scratch counters)
     b += (size_t)n * 8;                     // small lists
     b += (size_t)N * (32 + 8 * dp);         // packed node records
+    b += (size_t)n * 4 * dp;                // point-major FP32 copy
     b += (size_t)((N / 2 + 2 + (2 * depth + 4) * 2 * c.chunk) * c.frontier_scale + 8 * c.chunk) * 8;   // stack, step outputs
     b += (size_t)8 * (c.chunk + 1) * (5 * 12 + 16 + 4 + 8);  // pair lists with bounds (8 chunks each), huge-pair slots
     b += (size_t)num_sms() * 64 * (depth + 4) * 4;                                                           // dual stacks
     b += (size_t)c.edges * 16 * 3 + (size_t)c.edges * 24;   // batch, filtered, sort tmp, kruskal
     b += (size_t)n * 16 * 2;                // output tree + conversion
+    if (c.wspd_pairs > 0)                   // GFK / EMST-Naive: pairs and bounds (x2), pool (x2), batch, sort
+        b += (size_t)c.wspd_pairs * (12 * 2 + 16 * 2 + 16 + 16) + (size_t)n * 16;
     if (min_pts > 0) {
         long long kk = min_pts + 16;
         b += (size_t)n * 12 + (size_t)n * 8;            // cd64, cd32, node bounds
@@ -180,6 +193,7 @@ static Caps default_caps(long long n, int min_pts)
     c.edges = 4 * n + (1 << 20) + (min_pts > 0 ? (long long)n * (min_pts + 16) : 0);
     c.frontier_scale = 1;
     c.extra_bytes = 0;
+    c.wspd_pairs = 0;
     return c;
 }
 
@@ -208,6 +222,17 @@ static wm_tuning tuning_for(long long n, int d, int min_pts)
     wm_tuning t{};
     builtin_tuning(n, d, min_pts, &t);
     return t;
+}
+
+// Capacities of a call: the defaults, with the traversal chunk of the tuning (never above the
+// default's max(2^12, 4n): a larger chunk only enlarges the stack of a small problem).  Every
+// estimate of a call's workspace (wm_query_footprint, the batch and serving workspaces) uses it.
+static Caps caps_for(long long n, int d, int min_pts)
+{
+    Caps c = default_caps(n, min_pts);
+    const wm_tuning t = tuning_for(n, d, min_pts);
+    if (t.chunk_log2) c.chunk = std::min<long long>(1LL << t.chunk_log2, std::max<long long>(1 << 12, 4 * n));
+    return c;
 }
 
 // ------------------------------------------------------------------------------- kernels
@@ -317,6 +342,8 @@ struct Call {
     int *pin = nullptr;
     wm_stats stats{};
     wm_tuning tune{};
+    int method = WM_METHOD_MEMOGFK;   // wm_opts.method
+    int disjunctive = 1;              // HDBSCAN*: the separation of Sec. 3.1.2 (0: GanTao's)
     int precision = WM_PREC_FP32_SCREEN;
     bool timing = true;   // per-kernel CUDA-event timing into stats
     double event_ms(cudaEvent_t a, cudaEvent_t b)
@@ -365,12 +392,28 @@ static float float_ru(double r)
     return f;
 }
 
+// The smallest float s whose rigorous lower bound on the exact FP64 weight of a pair screened at s
+// reaches hi.  The FP32 screen errs by at most 2^-19 relative plus subnormal rounding when the FP32
+// copy is exact, so the weight is at least s (1 - 2^-18) - 2e-42; otherwise the copy's distance
+// error eta (absolute) comes on top: (sqrt(s (1 - 2^-18) - 2e-42) - eta)^2 (1 - 2^-40).  For
+// HDBSCAN* a screened value may be a core distance, which bounds its FP64 value from below within
+// 2^-22, so s must also reach hi / (1 - 2^-22).  Inverted with outward margins.
+static float above_threshold(double hi, const TravArgs &a)
+{
+    if (!(hi < INFINITY)) return INFINITY;
+    double t = a.exact32 ? hi : std::pow(std::sqrt(hi / (1.0 - 1.0 / 1099511627776.0)) + a.eta, 2.0);
+    t = (t * (1.0 + 1e-15) + 2e-42) / (1.0 - 1.0 / 262144.0);
+    if (a.cd64) t = std::max(t, hi / (1.0 - 1.0 / 4194304.0));
+    return float_ru(t * (1.0 + 1e-12));
+}
+
 static void set_rho(TravArgs &a, double lo, double hi)
 {
     a.rho_lo = lo;
     a.rho_hi = hi;
     a.rho_lo_f = float_ru(lo);
     a.rho_hi_f = float_ru(hi);
+    a.above_f = above_threshold(hi, a);
 }
 
 // MemoGFK rounds (Algorithm 3).  On return E_out holds the tree edges in K order: n-1 of them, or
@@ -411,6 +454,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     int4 *links = ar.get<int4>(T.N);
     float4 *meta = ar.get<float4>(T.N);
     float *box = ar.get<float>((size_t)T.N * 2 * dp);
+    float4 *x4 = ar.get<float4>((size_t)n * (dp / 4));
     EdgeK *batch = ar.get<EdgeK>(caps.edges), *filt = ar.get<EdgeK>(caps.edges), *tmp = ar.get<EdgeK>(caps.edges);
     int *cnts = ar.get<int>(64);
     unsigned *rho = ar.get<unsigned>(2);
@@ -428,6 +472,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         Tree T2 = T;
         if (hdb) { T2.cdmin = hdb->cdmin; T2.cdmax = hdb->cdmax; }
         pack_nodes(T2, P.d, dp, links, meta, box, st);
+        point_major(P.x32, n, P.d, dp, x4, st);
     }
     WM_CK(cudaMemsetAsync(stat, 0, 16 * sizeof(unsigned long long), st));
     WM_CK(cudaMemsetAsync(ovf, 0, 2 * sizeof(unsigned), st));
@@ -437,7 +482,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     a.N = T.N; a.n = n; a.d = P.d;
     a.lo = T.lo; a.hi = T.hi; a.diam2 = T.diam2;
     a.begin = T.begin; a.end = T.end; a.left = T.left; a.right = T.right; a.comp = T.comp;
-    a.x32 = P.x32; a.x64 = P.x64; a.pid = P.pid;
+    a.x32 = P.x32; a.x4 = x4; a.x64 = P.x64; a.pid = P.pid;
     a.fp64 = C.precision == WM_PREC_FP64;
     a.eta = a.fp64 ? 0.0 : 2.0 * (double)P.delta * std::sqrt((double)P.d) * (1.0 + 1e-6);
     a.exact32 = a.eta == 0.0;
@@ -445,6 +490,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     a.dfs_budget = C.tune.dfs_budget;
     a.medium_max = C.tune.medium_max;
     a.big_max = C.tune.big_max;
+    a.disjunctive = C.disjunctive;
     if (hdb) {
         a.cdmin = hdb->cdmin; a.cdmax = hdb->cdmax; a.cd32 = hdb->cd32; a.cd64 = hdb->cd64;
     }
@@ -521,7 +567,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     while (nE < target) {
         if (++rounds > 4096) { set_detail("MemoGFK made no progress%s (%lld rounds)", "", rounds); return WM_EINTERNAL; }
         Timer tw;
-        WM_TRY(launch_comp_labels(T, P, uf, links, meta, comp_scratch, ar, st));
+        WM_TRY(launch_comp_labels(T, P, uf, links, comp_scratch, ar, st));
         a.beta = (int)std::min<long long>(beta, 0x7fffffff);
         double rho_hi;
         // Combined pass (tuning): GetRho's minimum R is kept on the device while GetPairs runs;
@@ -744,6 +790,224 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     return 0;
 }
 
+// The GFK form (Sec. 3.2.2, Algorithm 2) and, with naive = true, EMST-Naive (the BCCP of every
+// pair, then one Kruskal): the full WSPD is materialised by one traversal over [0, +inf) without
+// connectivity pruning.  A round then computes the BCCP of the pairs of at most beta points (its
+// edge joins the pool, which caches it), sets rho_hi to the smallest lower bound d(A,B) of the
+// pairs left, hands the pool's edges lighter than rho_hi (and, for HDBSCAN*, the repair edges of
+// [rho_lo, rho_hi)) to Kruskal, drops the pairs whose points are all connected and the pool edges
+// whose endpoints are, and doubles beta.  Overflow bits as memogfk (bit 2 for the pair list).
+static int gfk_rounds(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps &caps, EdgeK *E_out, int *uf,
+                      unsigned long long *R, unsigned *overflow_bits, bool naive)
+{
+    const int n = P.n;
+    const long long target = (long long)n - 1;
+    cudaStream_t st = C.st;
+    Arena &ar = C.ar;
+    *overflow_bits = 0;
+    if (n <= 1) return 0;
+    size_t mark = ar.off;
+    const int chunk = (int)caps.chunk;
+    const long long fcap = ((long long)T.N / 2 + 2 + (2LL * T.depth + 4) * 2 * chunk) * caps.frontier_scale;
+    const long long scap = caps.wspd_pairs;
+    if (fcap > 0x7fffffffLL || scap > 0x7fffffffLL) { set_detail("GFK capacities exceed 2^31%s", ""); return WM_ENOMEM; }
+    int2 *stack = ar.get<int2>(fcap);
+    int2 *const xbuf[2] = {ar.get<int2>(4LL * chunk), ar.get<int2>(4LL * chunk)};
+    const long long lcap = 8LL * chunk;   // BCCP size-class lists: the pairs are split in segments of lcap
+    int2 *lists[5];
+    float *list_lbs[5];
+    for (int c = 0; c < 5; ++c) {
+        lists[c] = ar.get<int2>(lcap);
+        list_lbs[c] = ar.get<float>(lcap);
+    }
+    EdgeK *huge_best = ar.get<EdgeK>(lcap + 1);
+    unsigned *huge_sbest = ar.get<unsigned>(lcap + 1);
+    long long *huge_items = ar.get<long long>(lcap + 1);
+    const int stack_warps = num_sms() * 8 * 8;
+    int *dual_stack = ar.get<int>((size_t)stack_warps * (T.depth + 4));
+    const int dp = P.d <= 4 ? 4 : P.d <= 8 ? 8 : 16;
+    int4 *links = ar.get<int4>(T.N);
+    float4 *meta = ar.get<float4>(T.N);
+    float *box = ar.get<float>((size_t)T.N * 2 * dp);
+    float4 *x4 = ar.get<float4>((size_t)n * (dp / 4));
+    int2 *S[2] = {ar.get<int2>(scap), ar.get<int2>(scap)};
+    float *Slb[2] = {ar.get<float>(scap), ar.get<float>(scap)};
+    EdgeK *pool[2] = {ar.get<EdgeK>(scap), ar.get<EdgeK>(scap)};
+    EdgeK *batch = ar.get<EdgeK>(scap + 1), *tmp = ar.get<EdgeK>(std::max<long long>(scap, n) + 1);
+    int *cnts = ar.get<int>(64);
+    unsigned *rho = ar.get<unsigned>(2);
+    unsigned *ovf = ar.get<unsigned>(2);
+    unsigned long long *stat = ar.get<unsigned long long>(16);
+    int *comp_scratch = ar.get<int>(2LL * n + 1);
+    if (ar.failed) return WM_ENOMEM;
+    // counters: [2..6] class-list counts, [7] pool count, [8] kept pairs, [9] batch count,
+    // [10..11] node lists, [12..13] huge items, [16..17] tile dispensers, [32..] traversal state
+    int *lcount = cnts + 2, *pcount = cnts + 7, *kcount = cnts + 8, *bcount = cnts + 9, *tcnt = cnts + 32;
+    {
+        Tree T2 = T;
+        if (hdb) { T2.cdmin = hdb->cdmin; T2.cdmax = hdb->cdmax; }
+        pack_nodes(T2, P.d, dp, links, meta, box, st);
+        point_major(P.x32, n, P.d, dp, x4, st);
+    }
+    WM_CK(cudaMemsetAsync(stat, 0, 16 * sizeof(unsigned long long), st));
+    WM_CK(cudaMemsetAsync(ovf, 0, 2 * sizeof(unsigned), st));
+    WM_CK(cudaMemsetAsync(cnts, 0, 64 * sizeof(int), st));
+    TravArgs a;
+    a.N = T.N; a.n = n; a.d = P.d;
+    a.lo = T.lo; a.hi = T.hi; a.diam2 = T.diam2;
+    a.begin = T.begin; a.end = T.end; a.left = T.left; a.right = T.right; a.comp = T.comp;
+    a.x32 = P.x32; a.x4 = x4; a.x64 = P.x64; a.pid = P.pid;
+    a.fp64 = C.precision == WM_PREC_FP64;
+    a.eta = a.fp64 ? 0.0 : 2.0 * (double)P.delta * std::sqrt((double)P.d) * (1.0 + 1e-6);
+    a.exact32 = a.eta == 0.0;
+    a.delta32 = P.delta;
+    a.dfs_budget = C.tune.dfs_budget;
+    a.medium_max = C.tune.medium_max;
+    a.big_max = C.tune.big_max;
+    a.disjunctive = C.disjunctive;
+    if (hdb) { a.cdmin = hdb->cdmin; a.cdmax = hdb->cdmax; a.cd32 = hdb->cd32; a.cd64 = hdb->cd64; }
+    a.frontier_cap = (int)fcap;
+    a.links = links; a.meta = meta; a.box = box; a.dp = dp;
+    a.list_count = lcount;
+    a.big = lists[3]; a.big_count = lcount + 3;
+    a.huge_best = huge_best; a.huge_sbest = huge_sbest;
+    a.stack = dual_stack; a.stack_cap = T.depth + 4;
+    a.overflow = ovf;
+    a.stat = stat;
+    a.rho_bits = rho;
+    // no node lists: the collecting traversal starts from every internal node
+    a.node_in = nullptr; a.node_in_n = nullptr;
+    a.node_out = nullptr; a.node_out_n = nullptr;
+    Timer tw;
+    // ---- the full WSPD: every well-separated pair into S[0]
+    WM_TRY(launch_comp_labels(T, P, uf, links, comp_scratch, ar, st));
+    set_rho(a, 0.0, INFINITY);
+    a.collect_all = 1;
+    a.list[0] = S[0]; a.list_lb[0] = Slb[0]; a.list_cap[0] = (int)scap;
+    for (int c = 1; c < 5; ++c) { a.list[c] = lists[c]; a.list_lb[c] = list_lbs[c]; a.list_cap[c] = (int)lcap; }
+    traversal_init(1, a, stack, tcnt, st);
+    for (int steps = 0;; steps += 3) {
+        for (int b = 0; b < 3; ++b) traversal_step(1, a, stack, xbuf, tcnt, steps + b, chunk, st);
+        WM_CK(cudaMemcpyAsync(C.pin, cnts, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        WM_CK(cudaMemcpyAsync(C.pin + 8, ovf, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        WM_CK(cudaMemcpyAsync(C.pin + 16, tcnt, kTravCounters * sizeof(int), cudaMemcpyDeviceToHost, st));
+        WM_CK(cudaStreamSynchronize(st));
+        if (C.pin[8]) { *overflow_bits = (unsigned)C.pin[8]; return 0; }
+        if (C.pin[16] == 0 && C.pin[17] == 0 && C.pin[18] == 0) break;
+        if (steps > 10000000) { set_detail("WSPD traversal did not terminate%s", ""); return WM_EINTERNAL; }
+        C.stats.getpairs_launches += 3;
+    }
+    int mS = C.pin[2];
+    C.stats.wspd_pairs = mS;
+    a.collect_all = 0;
+    for (int c = 0; c < 5; ++c) { a.list[c] = lists[c]; a.list_lb[c] = list_lbs[c]; a.list_cap[c] = (int)lcap; }
+    WM_CK(cudaMemsetAsync(cnts + 2, 0, 8 * sizeof(int), st));
+    C.stats.ms_wspd += tw.ms();
+    int cur = 0, pcur = 0, mP = 0, nE = 0, rounds = 0;
+    long long bccp_pairs = 0;   // pairs whose BCCP was computed (each once)
+    long long beta = naive ? (1LL << 62) : 2;
+    double rho_lo = 0.0;
+    while (nE < target) {
+        if (++rounds > 4096) { set_detail("GFK made no progress%s (%lld rounds)", "", rounds); return WM_EINTERNAL; }
+        Timer tb;
+        // ---- BCCP of the pairs of at most beta points, in segments of the class lists' capacity;
+        // every edge is emitted (range [0, +inf)) into the pool
+        set_rho(a, 0.0, INFINITY);
+        a.edges = pool[pcur]; a.edge_count = pcount; a.edge_cap = (int)scap;
+        WM_CK(cudaMemsetAsync(kcount, 0, sizeof(int), st));
+        for (long long off = 0; off < mS; off += lcap) {
+            const int seg = (int)std::min<long long>(lcap, mS - off);
+            WM_CK(cudaMemsetAsync(lcount, 0, 5 * sizeof(int), st));
+            gfk_split(a, S[cur] + off, Slb[cur] + off, seg, beta, S[cur ^ 1], Slb[cur ^ 1], kcount, st);
+            WM_CK(cudaMemcpyAsync(C.pin, lcount, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
+            WM_CK(cudaStreamSynchronize(st));
+            int lc[5] = {C.pin[0], C.pin[1], C.pin[2], C.pin[3], C.pin[4]};
+            for (int c = 0; c < 5; ++c) bccp_pairs += lc[c];
+            run_bccp_groups(a, lc, st);
+            run_bccp_tiles(a, lc, cnts + 16, st, hdb != nullptr, a.fp64 != 0);
+            WM_TRY(run_bccp_huge(a, a.list[4], a.list_lb[4], lc[4], huge_items, (long long *)(cnts + 12), st, ar,
+                                 hdb != nullptr, a.fp64 != 0, stack_warps));
+        }
+        WM_CK(cudaMemcpyAsync(C.pin, cnts, 10 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        WM_CK(cudaMemcpyAsync(C.pin + 16, ovf, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        WM_CK(cudaStreamSynchronize(st));
+        if (C.pin[16]) { *overflow_bits = (unsigned)C.pin[16]; return 0; }
+        mP = C.pin[7];
+        mS = C.pin[8];
+        cur ^= 1;
+        C.stats.ms_bccp += tb.ms();
+        // ---- rho_hi: the smallest lower bound of the pairs left (+inf when none is left)
+        gfk_min_lb(Slb[cur], mS, rho, st);
+        WM_CK(cudaMemcpyAsync(C.pin, rho, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        WM_CK(cudaStreamSynchronize(st));
+        float rf;
+        memcpy(&rf, C.pin, sizeof rf);
+        const double rho_hi = std::max<double>(rf, rho_lo);
+        // ---- the pool's edges below rho_hi form the round's batch
+        WM_CK(cudaMemsetAsync(bcount, 0, sizeof(int), st));
+        WM_CK(cudaMemsetAsync(pcount, 0, sizeof(int), st));
+        gfk_partition(pool[pcur], mP, rho_hi, batch, bcount, (int)scap, pool[pcur ^ 1], pcount, ovf, st);
+        pcur ^= 1;
+        if (hdb && hdb->nrep > 0 && rho_hi > rho_lo)
+            launch(take_range_kernel, grid_for(hdb->nrep, 256), 256, 0, st, hdb->rep, hdb->nrep, rho_lo, rho_hi, batch,
+                   bcount, (int)scap, ovf);
+        WM_CK(cudaMemcpyAsync(C.pin, cnts, 10 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        WM_CK(cudaMemcpyAsync(C.pin + 16, ovf, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        WM_CK(cudaStreamSynchronize(st));
+        if (C.pin[16]) { *overflow_bits = (unsigned)C.pin[16]; return 0; }
+        const int m = C.pin[9];
+        mP = C.pin[7];
+        Timer tk;
+        int accepted = 0;
+        if (m > 0) {
+            C.stats.candidate_edges += m;
+            WM_TRY(batch_kruskal(batch, m, n, uf, R, E_out, nE, &accepted, ar, st, C.pin));
+        }
+        C.stats.ms_kruskal += tk.ms();
+        nE += accepted;
+        if (nE >= target) break;
+        if (!(rho_hi < INFINITY) && mS == 0 && mP == 0) {
+            set_detail("GFK ran out of pairs before the tree was complete%s (%lld edges)", "", nE);
+            return WM_EINTERNAL;
+        }
+        // ---- filter: pairs whose points are all connected, pool edges whose endpoints are
+        WM_TRY(launch_comp_labels(T, P, uf, links, comp_scratch, ar, st));
+        WM_CK(cudaMemsetAsync(kcount, 0, sizeof(int), st));
+        gfk_filter_pairs(S[cur], Slb[cur], mS, links, S[cur ^ 1], Slb[cur ^ 1], kcount, st);
+        WM_CK(cudaMemsetAsync(pcount, 0, sizeof(int), st));
+        gfk_filter_edges(pool[pcur], mP, uf, pool[pcur ^ 1], pcount, st);
+        WM_CK(cudaMemcpyAsync(C.pin, cnts, 10 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        WM_CK(cudaStreamSynchronize(st));
+        mS = C.pin[8];
+        mP = C.pin[7];
+        cur ^= 1;
+        pcur ^= 1;
+        rho_lo = rho_hi;
+        beta *= 2;
+    }
+    {
+        Timer ts;
+        EdgeK *sorted = E_out;
+        WM_TRY(radix_sort_edges(E_out, tmp, (int)target, st, ar, &sorted, C.pin + 4096));
+        if (sorted != E_out) WM_CK(cudaMemcpyAsync(E_out, sorted, sizeof(EdgeK) * target, cudaMemcpyDeviceToDevice, st));
+        WM_CK(cudaStreamSynchronize(st));
+        C.stats.ms_kruskal += ts.ms();
+    }
+    WM_CK(cudaMemcpyAsync(C.pin, stat, 16 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    WM_CK(cudaStreamSynchronize(st));
+    unsigned long long hs[16];
+    memcpy(hs, C.pin, sizeof hs);
+    C.stats.rounds = rounds;
+    C.stats.getpairs_visits = (int64_t)hs[4];
+    C.stats.pairs_retrieved = bccp_pairs;
+    C.stats.bccp_evals = (int64_t)hs[1];
+    C.stats.fp64_rechecks += (int64_t)hs[2];
+    C.stats.bccp_tile_evals = (int64_t)hs[3];
+    C.stats.bccp_dual_evals = (int64_t)hs[6];
+    ar.off = mark;
+    return 0;
+}
+
 // ---------------------------------------------------------------------- shared front half
 struct Prepared {
     Points P;
@@ -822,12 +1086,21 @@ static int run_call(const wm_opts *opts, long long n, int d, int min_pts, Body b
         set_detail("bad precision%s %lld", "", C.precision);
         return WM_EINVAL;
     }
+    {
+        const int m = opts ? opts->method : WM_METHOD_MEMOGFK;
+        C.method = m & 0xff;
+        C.disjunctive = (m & WM_SEPARATION_GEOMETRIC) ? 0 : 1;
+        if (C.method > WM_METHOD_NAIVE || (m & ~(0xff | WM_SEPARATION_GEOMETRIC))) {
+            set_detail("bad method%s %lld", "", m);
+            return WM_EINVAL;
+        }
+    }
     C.pin = pinned_scratch();
     if (!C.pin) { set_detail("cudaMallocHost failed%s", ""); return WM_ENOMEM; }
-    Caps caps = default_caps(n, min_pts);
+    Caps caps = caps_for(n, d, min_pts);
     caps.extra_bytes = extra_bytes;
+    if (C.method == WM_METHOD_GFK || C.method == WM_METHOD_NAIVE) caps.wspd_pairs = wspd_pairs_guess(n, d);
     C.tune = tuning_for(n, d, min_pts);
-    if (C.tune.chunk_log2) caps.chunk = 1LL << C.tune.chunk_log2;
     const bool user_ws = opts && opts->workspace;
     int rc = 0;
     unsigned ovf_seen = 0;   // capacities that overflowed in earlier attempts
@@ -884,6 +1157,7 @@ static int run_call(const wm_opts *opts, long long n, int d, int min_pts, Body b
         // grow whichever capacity overflowed and start over
         if (ovf & 1u) caps.frontier_scale *= 2;
         if (ovf & 2u) caps.edges *= 2;
+        if ((ovf & 6u) && caps.wspd_pairs) caps.wspd_pairs *= 2;   // the materialised WSPD or its pool
         if (user_ws && ovf && estimate_bytes(n, d, min_pts, caps) > opts->workspace_bytes) {
             rc = WM_ENOMEM;
             set_detail("caller workspace too small: this input needs about %lld bytes%s",
@@ -923,7 +1197,10 @@ static int emst_body(Call &C, void *vctx, const Caps &caps, unsigned *ovf)
     EdgeK *E = C.ar.get<EdgeK>(n);
     if (C.ar.failed) return WM_ENOMEM;
     launch(init_uf_kernel, grid_for(n, 256), 256, 0, C.st, uf, R, n);
-    WM_TRY(memogfk(C, S.P, S.T, nullptr, caps, E, uf, R, ovf));
+    if (C.method == WM_METHOD_GFK || C.method == WM_METHOD_NAIVE)
+        WM_TRY(gfk_rounds(C, S.P, S.T, nullptr, caps, E, uf, R, ovf, C.method == WM_METHOD_NAIVE));
+    else
+        WM_TRY(memogfk(C, S.P, S.T, nullptr, caps, E, uf, R, ovf));
     if (*ovf) return 0;
     return write_edges(C, E, n - 1, x.out, x.total);
 }
@@ -954,7 +1231,10 @@ static int hdbscan_body(Call &C, void *vctx, const Caps &caps, unsigned *ovf)
     EdgeK *E = C.ar.get<EdgeK>(n);
     if (C.ar.failed) return WM_ENOMEM;
     launch(init_uf_kernel, grid_for(n, 256), 256, 0, C.st, uf, R, n);
-    WM_TRY(memogfk(C, S.P, S.T, &H, caps, E, uf, R, ovf));
+    if (C.method == WM_METHOD_GFK || C.method == WM_METHOD_NAIVE)
+        WM_TRY(gfk_rounds(C, S.P, S.T, &H, caps, E, uf, R, ovf, C.method == WM_METHOD_NAIVE));
+    else
+        WM_TRY(memogfk(C, S.P, S.T, &H, caps, E, uf, R, ovf));
     if (*ovf) return 0;
     WM_TRY(write_core_distances(S.P, H, x.cd, C.ar, C.st));
     WM_TRY(write_edges(C, E, n - 1, x.mst, nullptr));
@@ -1347,7 +1627,7 @@ int wm_batch(const wm_instance *inst, int32_t count, int32_t dtype, int32_t layo
                 group_args(g, ptotal, d, mp);
                 BatchCtx c{inst, &groups[g], d, mp, dtype, layout};
                 const long long extra = ptotal * (8LL * (d + 1) + 200) + (long long)groups[g].size() * 64;
-                Caps cp = default_caps(ptotal, mp > 1 ? mp : 0);
+                Caps cp = caps_for(ptotal, d + 1, mp > 1 ? mp : 0);
                 cp.extra_bytes = extra;
                 size_t bytes = estimate_bytes(ptotal, d + 1, mp > 1 ? mp : 0, cp);
                 int rc = WM_ENOMEM;
@@ -1402,7 +1682,7 @@ int wm_batch(const wm_instance *inst, int32_t count, int32_t dtype, int32_t layo
         sum.getpairs_launches += gs.getpairs_launches; sum.bccp_dual_evals += gs.bccp_dual_evals;
         sum.rho_shrinks += gs.rho_shrinks; sum.tile_launches += gs.tile_launches;
         sum.ms_knn_kernel += gs.ms_knn_kernel; sum.ms_tile_kernel += gs.ms_tile_kernel;
-        sum.ms_getrho += gs.ms_getrho; sum.ms_bccp_group += gs.ms_bccp_group; sum.ms_bccp_dual += gs.ms_bccp_dual;
+        sum.wspd_pairs += gs.wspd_pairs; sum.ms_getrho += gs.ms_getrho; sum.ms_bccp_group += gs.ms_bccp_group; sum.ms_bccp_dual += gs.ms_bccp_dual;
         sum.ms_getpairs += gs.ms_getpairs;
         sum.max_pending_pairs = std::max(sum.max_pending_pairs, gs.max_pending_pairs);
         sum.bccp_pairs_below += gs.bccp_pairs_below; sum.bccp_pairs_above += gs.bccp_pairs_above;
@@ -1416,7 +1696,13 @@ int wm_batch(const wm_instance *inst, int32_t count, int32_t dtype, int32_t layo
 
 int wm_get_tuning(int64_t n, int32_t d, int32_t min_pts, wm_tuning *out)
 {
-    if (!out || n < 1 || d < 1 || d > kMaxDim || min_pts < 0) return WM_EINVAL;
+    if (!out || n < 0 || d < 1 || d > kMaxDim || min_pts < 0) return WM_EINVAL;
+    if (n == 0) {   // the built-in defaults, before any table row or override
+        wm_tuning t{};
+        builtin_tuning(0, d, min_pts, &t);
+        *out = t;
+        return WM_OK;
+    }
     *out = tuning_for(n, d, min_pts);
     return WM_OK;
 }
@@ -1437,7 +1723,7 @@ int wm_set_tuning(const wm_tuning *t)
 int wm_query_footprint(int64_t n, int32_t d, int32_t min_pts, size_t *bytes)
 {
     if (!bytes || n < 1 || d < 1 || d > kMaxDim || min_pts < 0) return WM_EINVAL;
-    *bytes = estimate_bytes(n, d, min_pts, default_caps(n, min_pts));
+    *bytes = estimate_bytes(n, d, min_pts, caps_for(n, d, min_pts));
     return WM_OK;
 }
 

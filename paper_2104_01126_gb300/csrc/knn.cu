@@ -298,9 +298,9 @@ __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
             a.slow[s] = i;
             continue;
         }
-        if (!FP64 && cd2 > 0.0) {
+        if (!FP64 && cd2 > 0.0) {   // the ratio in FP32 with outward rounding
             const double sk = (double)sv[(k - 1) * 32 + lane];
-            kerr = fmaxf(kerr, __double2float_ru(fabs(sk - cd2) / cd2));
+            kerr = fmaxf(kerr, __fdiv_ru(__double2float_ru(fabs(sk - cd2)), __double2float_rd(cd2)));
         }
         a.cd64[i] = cd2;
         a.cd32[i] = __double2float_rn(cd2);

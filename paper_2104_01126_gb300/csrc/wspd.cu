@@ -44,21 +44,10 @@ __device__ inline float screen_threshold(float s, const TravArgs &a)
 }
 
 // True when a screened value s proves that the exact FP64 weight of its point pair is at or above
-// rho_hi, so that the pair's edge cannot belong to this round and needs no FP64 recheck.  The
-// bound used is a rigorous lower bound of that weight: with an exact FP32 copy, w2 >= s (1 - 2^-18)
-// - 2e-42 (the screen errs by at most 2^-19 relative plus subnormal rounding, the FP64 evaluation
-// by 2^-48); otherwise (sqrt of that - eta)^2 (1 - 2^-40).  For HDBSCAN* s may be a core distance
-// cd32, which bounds cd64 from below within 2^-22, so the smaller of the two bounds is taken.
-__device__ inline bool screened_above(float s, const TravArgs &a)
-{
-    double lo = (double)s * (1.0 - 1.0 / 262144.0) - 2e-42;
-    if (!a.exact32) {
-        const double r = lo > 0.0 ? sqrt(lo) - a.eta : 0.0;
-        lo = r > 0.0 ? r * r * (1.0 - 1.0 / 1099511627776.0) : 0.0;
-    }
-    if (a.cd64) lo = fmin(lo, (double)s * (1.0 - 1.0 / 4194304.0));
-    return lo >= a.rho_hi;
-}
+// rho_hi, so that the pair's edge cannot belong to this round and needs no FP64 recheck: s is at
+// least TravArgs::above_f, the smallest float whose rigorous lower bound on that weight reaches
+// rho_hi (computed on the host, see above_threshold).
+__device__ inline bool screened_above(float s, const TravArgs &a) { return s >= a.above_f; }
 
 __device__ inline float dist32(const float *__restrict__ x32, int n, int d, int i, int j)
 {
@@ -80,6 +69,30 @@ __device__ inline float dist32t(const float *__restrict__ x32, int n, int d, int
     for (int k = 0; k < (D > 0 ? D : 1); ++k) {
         float t = x32[(size_t)k * n + i] - x32[(size_t)k * n + j];
         s = fmaf(t, t, s);
+    }
+    return s;
+}
+
+// dist32 from the point-major copy: the same subtractions and fused multiply-adds in dimension
+// order (a padded coordinate is 0 on both sides and adds exactly 0)
+template <int D>
+__device__ inline float dist32p(const float4 *__restrict__ x4, int i, int j)
+{
+    constexpr int Q = (D + 3) / 4;                          // float4s holding coordinates
+    constexpr int S = Q <= 1 ? 1 : Q <= 2 ? 2 : 4;          // float4s per point (dp / 4)
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < Q; ++c) {
+        const float4 p = x4[(size_t)i * S + c];
+        const float4 q = x4[(size_t)j * S + c];
+        const float pv[4] = {p.x, p.y, p.z, p.w}, qv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            if (4 * c + r < D) {
+                const float t = pv[r] - qv[r];
+                s = fmaf(t, t, s);
+            }
+        }
     }
     return s;
 }
@@ -119,9 +132,9 @@ __device__ inline double exact_w2(const TravArgs &a, int i, int j, float d32, fl
 __device__ inline double checked_w2(const TravArgs &a, int i, int j, float sd, float c32, float &err)
 {
     const double w = exact_w2(a, i, j, sd, c32);
-    if (w > 0.0) {
-        const double sv = a.cd64 ? fmax((double)sd, (double)c32) : (double)sd;
-        err = fmaxf(err, __double2float_ru(fabs(sv - w) / w));
+    if (w > 0.0) {   // the ratio in FP32 with outward rounding (a single FP64 subtraction)
+        const double sv = a.cd64 ? pos_dmax((double)sd, (double)c32) : (double)sd;
+        err = fmaxf(err, __fdiv_ru(__double2float_ru(fabs(sv - w)), __double2float_rd(w)));
     }
     return w;
 }
@@ -229,8 +242,10 @@ __device__ inline void warp_emit(const TravArgs &a, bool has, const KMin &m)
 
 
 // ------------------------------------------------------------------ packed node records
-// links = {begin, end, left, right}; meta = {diam2 bound, cdmin, cdmax, comp label};
-// box[node][2*DP] = lo[0..DP), hi[0..DP) with padded dimensions set to 0.
+// links = {begin, end, left, comp label} (the right child is always left + 1, and the label of
+// the round is what a visit tests first, with the sizes, before it reads anything else);
+// meta = {diam2 bound, cdmin, cdmax, 0}; box[node][2*DP] = lo[0..DP), hi[0..DP) with padded
+// dimensions set to 0.
 template <int DP>
 __device__ inline void pair_bounds_packed(const TravArgs &a, int P, int Q, const int4 &lp, const int4 &lq,
                                           const float4 &mp, const float4 &mq, float &lbB, float &ubB, bool &ws,
@@ -262,7 +277,7 @@ __device__ inline void pair_bounds_packed(const TravArgs &a, int P, int Q, const
     if (a.cdmin) {
         float lhs = fmaxf(lb, fmaxf(mp.y, mq.y));
         float rhs = fmaxf(dm, fmaxf(mp.z, mq.z));
-        ws = ws || lhs >= rhs;
+        if (a.disjunctive) ws = ws || lhs >= rhs;   // or mutually unreachable (Sec. 3.1.2)
         lbB = lhs;
         ubB = fmaxf(ub, fmaxf(mp.z, mq.z));
     }
@@ -290,9 +305,8 @@ __device__ inline void visit_pair(const TravArgs &a, int2 me, float rho_now, int
     const int4 lp = a.links[P], lq = a.links[Q];
     const int sp = lp.y - lp.x, sq = lq.y - lq.x;
     if (MODE == 0 && sp + sq <= a.beta) return;
+    if (lp.w >= 0 && lp.w == lq.w) return;   // all points already connected
     const float4 mp = a.meta[P], mq = a.meta[Q];
-    const int cp = __float_as_int(mp.w);
-    if (cp >= 0 && cp == __float_as_int(mq.w)) return;   // all points already connected
     float lbB, ubB, dP, dQ;
     bool ws;
     pair_bounds_packed<DP>(a, P, Q, lp, lq, mp, mq, lbB, ubB, ws, dP, dQ);
@@ -314,7 +328,8 @@ __device__ inline void visit_pair(const TravArgs &a, int2 me, float rho_now, int
         if (lbB >= a.rho_hi_f || ubB < a.rho_lo_f) return;
         if (ws) {
             long long prod = (long long)sp * sq;
-            cls = prod <= kTinyMax ? 0 : prod <= kSmallMax ? 1 : prod <= a.medium_max ? 2 : prod <= a.big_max ? 3 : 4;
+            cls = a.collect_all ? 0
+                                : prod <= kTinyMax ? 0 : prod <= kSmallMax ? 1 : prod <= a.medium_max ? 2 : prod <= a.big_max ? 3 : 4;
             lb_out = lbB;
             return;
         }
@@ -323,7 +338,7 @@ __device__ inline void visit_pair(const TravArgs &a, int2 me, float rho_now, int
     const bool splitP = lp.z >= 0 && (lq.z < 0 || dP >= dQ);
     const int O = splitP ? Q : P;
     c0 = make_int2(splitP ? lp.z : lq.z, O);
-    c1 = make_int2(splitP ? lp.w : lq.w, O);
+    c1 = make_int2((splitP ? lp.z : lq.z) + 1, O);
     push = 2;
 }
 
@@ -532,8 +547,13 @@ __global__ void __launch_bounds__(256) bccp_group_kernel(TravArgs a, const int2 
         int pb = 0, qb = 0, na = 0, nb = 0;
         // a pair retrieved under a larger bound than this flush's rho_hi (one-pass rounds, or an
         // edge-batch overflow) has no edge in the range: it is skipped
-        if (valid && lbs[pi] < a.rho_hi_f) {
-            const int2 pr = pairs[pi];
+        int2 pr = make_int2(0, 0);
+        float plb = 0.f;
+        if (valid) {   // the pair and its bound are independent loads
+            pr = pairs[pi];
+            plb = lbs[pi];
+        }
+        if (valid && plb < a.rho_hi_f) {
             int4 lp = a.links[pr.x], lq = a.links[pr.y];
             pb = lp.x; na = lp.y - lp.x; qb = lq.x; nb = lq.y - lq.x;
         }
@@ -560,7 +580,7 @@ __global__ void __launch_bounds__(256) bccp_group_kernel(TravArgs a, const int2 
                 for (int t = 0; t < kPer; ++t) {
                     sv[t] = INFINITY;
                     if (g + t * G < tot) {
-                        const float sd = dist32t<D>(a.x32, n, d, i, j);
+                        const float sd = D > 0 ? dist32p<D>(a.x4, i, j) : dist32t<D>(a.x32, n, d, i, j);
                         sv[t] = a.cd32 ? fmaxf(sd, fmaxf(a.cd32[i], a.cd32[j])) : sd;
                         smin = fminf(smin, sv[t]);
                         j += G;
@@ -582,7 +602,7 @@ __global__ void __launch_bounds__(256) bccp_group_kernel(TravArgs a, const int2 
                 if (g + t * G < tot && sv[t] <= T) {
                     const int e = g + t * G;
                     const int i = pb + e / nb, j = qb + e % nb;
-                    const float sd = dist32t<D>(a.x32, n, d, i, j);
+                    const float sd = D > 0 ? dist32p<D>(a.x4, i, j) : dist32t<D>(a.x32, n, d, i, j);
                     const float c32 = a.cd32 ? fmaxf(a.cd32[i], a.cd32[j]) : 0.f;
                     if (df.i < 0) df = Deferred{i, j, sd, c32};
                     else kmin_update(best, checked_w2(a, i, j, sd, c32, serr), a.pid[i], a.pid[j]);
@@ -620,7 +640,7 @@ __global__ void pack_nodes_kernel(int N, int d, int DP, const float *__restrict_
                                   float *__restrict__ box)
 {
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x) {
-        links[x] = make_int4(begin[x], end[x], left[x], right[x]);
+        links[x] = make_int4(begin[x], end[x], left[x], -1);   // right[x] == left[x] + 1
         meta[x] = make_float4(diam2[x], cdmin ? cdmin[x] : 0.f, cdmax ? cdmax[x] : 0.f, 0.f);
         for (int k = 0; k < DP; ++k) {
             box[(size_t)x * 2 * DP + k] = k < d ? lo[(size_t)k * N + x] : 0.f;
@@ -679,14 +699,14 @@ __global__ void pos_labels_kernel(const int *__restrict__ pid, const int *__rest
     }
 }
 
-__global__ void node_labels_kernel(int N, const int4 *__restrict__ links, const int *__restrict__ lab,
-                                   const int *__restrict__ E, int *__restrict__ comp, float4 *__restrict__ meta)
+__global__ void node_labels_kernel(int N, int4 *__restrict__ links, const int *__restrict__ lab,
+                                   const int *__restrict__ E, int *__restrict__ comp)
 {
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x) {
         const int4 L = links[x];
         const int c = E[L.y] == E[L.x + 1] ? lab[L.x] : -1;
         comp[x] = c;
-        ((int *)(meta + x))[3] = c;
+        ((int *)(links + x))[3] = c;
     }
 }
 
@@ -881,7 +901,7 @@ __global__ void __launch_bounds__(256) bccp_dual_kernel(TravArgs a, const int2 *
                 if (FP64) thr = cur_thr();
             } else {
                 // push the farther child first so the nearer one is visited next
-                const int c0 = ln.z, c1 = ln.w;
+                const int c0 = ln.z, c1 = ln.z + 1;
                 const float *b0x = a.box + (size_t)c0 * 2 * DP, *b1x = a.box + (size_t)c1 * 2 * DP;
                 float l0 = 0.f, l1 = 0.f;
 #pragma unroll
@@ -1215,7 +1235,7 @@ __global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const i
 
 // ----------------------------------------------------------------------------- host side
 
-int launch_comp_labels(const Tree &T, const Points &P, int *uf, const int4 *links, float4 *meta, int *scratch,
+int launch_comp_labels(const Tree &T, const Points &P, int *uf, int4 *links, int *scratch,
                        Arena &ar, cudaStream_t st)
 {
     const int n = P.n;
@@ -1224,7 +1244,7 @@ int launch_comp_labels(const Tree &T, const Points &P, int *uf, const int4 *link
     launch(pos_labels_kernel, grid_for(n, 256), 256, 0, st, P.pid, uf, n, lab, E);
     int rc = scan_exclusive_i32(E, E, n, E + n, st, ar);
     if (rc) return rc;
-    launch(node_labels_kernel, grid_for(T.N, 256), 256, 0, st, T.N, links, lab, E, T.comp, meta);
+    launch(node_labels_kernel, grid_for(T.N, 256), 256, 0, st, T.N, links, lab, E, T.comp);
     return 0;
 }
 
@@ -1390,6 +1410,23 @@ void run_bccp_groups(TravArgs &a, const int *counts_host, cudaStream_t st)
     case 7: run_bccp_groups_d<7>(a, counts_host, st); break;
     default: run_bccp_groups_d<0>(a, counts_host, st); break;
     }
+}
+
+__global__ void point_major_kernel(const float *__restrict__ x32, int n, int d, int dq, float4 *__restrict__ x4)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)n * dq;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / dq), c = (int)(t % dq);
+        float v[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) v[r] = 4 * c + r < d ? x32[(size_t)(4 * c + r) * n + i] : 0.f;
+        x4[t] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+}
+
+void point_major(const float *x32, int n, int d, int dp, float4 *x4, cudaStream_t st)
+{
+    launch(point_major_kernel, grid_for((long long)n * (dp / 4), 256), 256, 0, st, x32, n, d, dp / 4, x4);
 }
 
 void pack_nodes(const Tree &T, int d, int dp, int4 *links, float4 *meta, float *box, cudaStream_t st)

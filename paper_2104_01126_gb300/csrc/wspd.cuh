@@ -12,6 +12,8 @@ struct TravArgs {
     const int *comp = nullptr;
     const float *cdmin = nullptr, *cdmax = nullptr;   // HDBSCAN* node bounds (null for EMST)
     const float *x32 = nullptr;
+    const float4 *x4 = nullptr;        // the FP32 copy point-major: dp / 4 float4s per point, padded
+                                       // coordinates 0 (the group BCCP kernel reads whole points)
     const double *x64 = nullptr;
     const int *pid = nullptr;
     const float *cd32 = nullptr;                       // HDBSCAN* cd2 per tree position
@@ -21,11 +23,14 @@ struct TravArgs {
     int exact32 = 1;           // eta == 0: the FP32 copy is exact
     int fp64 = 0;              // plain FP64 form
     int beta = 2;
+    int collect_all = 0;       // GetPairs sends every retrieved pair to list 0 (the full WSPD)
+    int disjunctive = 1;       // HDBSCAN*: the separation of Sec. 3.1.2 (0: geometric only)
     int dfs_budget = 8;        // depth-first rounds per warp and traversal step (tuning)
     int medium_max = 1024;     // pair-size classes (tuning): |A||B| <= medium_max: one warp,
     long long big_max = 65536; //   <= big_max: tile kernel, larger: dual-tree kernel
     double rho_lo = 0.0, rho_hi = 0.0;
     float rho_lo_f = 0.f, rho_hi_f = 0.f;   // the smallest floats >= rho_lo, rho_hi
+    float above_f = 0.f;                    // a screened value >= this proves a weight >= rho_hi
     unsigned *rho_bits = nullptr;           // GetRho result: bits of a non-negative float (WriteMin)
     int frontier_cap = 0;
     // packed node records used by the traversals (see wspd.cu)
@@ -90,8 +95,8 @@ long long dfs_out_cap(int chunk, int budget);       // pairs one step can write 
 long long dfs_step_visits(int chunk, int budget);   // pairs one step can visit
 
 // component label of every node (-1 when its points span several components), into T.comp and
-// meta[x].w; scratch holds 2 n + 1 ints
-int launch_comp_labels(const Tree &T, const Points &P, int *uf, const int4 *links, float4 *meta, int *scratch,
+// links[x].w; scratch holds 2 n + 1 ints
+int launch_comp_labels(const Tree &T, const Points &P, int *uf, int4 *links, int *scratch,
                        Arena &ar, cudaStream_t st);
 int run_traversal(TravArgs &a, int2 *stack, int2 *const xbuf[2], int *cnt, int chunk, cudaStream_t st, int *pinned,
                   unsigned *overflow_out, int *steps_out);
@@ -108,5 +113,17 @@ void run_bccp_groups(TravArgs &a, const int *counts_host, cudaStream_t st);
 int run_bccp_huge(TravArgs &a, const int2 *pairs, const float *lbs, int m, long long *items, long long *total,
                   cudaStream_t st, Arena &ar, bool hdb, bool fp64, int stack_warps);
 void pack_nodes(const Tree &T, int d, int dp, int4 *links, float4 *meta, float *box, cudaStream_t st);
+// the point-major copy x4 of x32 (dp / 4 float4s per point)
+void point_major(const float *x32, int n, int d, int dp, float4 *x4, cudaStream_t st);
+
+// gfk.cu: the list steps of the GFK and EMST-Naive forms
+void gfk_split(const TravArgs &a, const int2 *S, const float *lb, int m, long long beta, int2 *keep, float *keep_lb,
+               int *keep_count, cudaStream_t st);
+void gfk_min_lb(const float *lb, int m, unsigned *rho_bits, cudaStream_t st);
+void gfk_partition(const EdgeK *pool, int m, double hi, EdgeK *batch, int *batch_count, int batch_cap, EdgeK *rest,
+                   int *rest_count, unsigned *overflow, cudaStream_t st);
+void gfk_filter_pairs(const int2 *S, const float *lb, int m, const int4 *links, int2 *out, float *out_lb, int *count,
+                      cudaStream_t st);
+void gfk_filter_edges(const EdgeK *pool, int m, const int *uf, EdgeK *out, int *count, cudaStream_t st);
 
 }  // namespace wm

@@ -67,3 +67,5 @@ def test_tuning_get_set_without_gpu():
     finally:
         wm.set_tuning(None)
     assert wm.get_tuning(1_000_000, 3, 0) == base
+    from paper_2104_01126_gb300 import autotune
+    assert wm.get_tuning(0, 3, 0) == autotune.DEFAULTS   # n = 0: the built-in defaults
