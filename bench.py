@@ -286,6 +286,45 @@ def serving_sweep(wm, args, rank):
     return out
 
 
+def run_ablation(wm, torch, call, timed_pass, release):
+    """MemoGFK (the default) against GFK (the full WSPD materialised, Algorithm 2) and EMST-Naive
+    on the EMST of 10^7 uniform points in 3-D; and, on the HDBSCAN* workload, the disjunctive
+    separation of Sec. 3.1.2 against the geometric one of the GanTao baseline (the full WSPD of
+    each counted by the GFK form).  One warm-up and one timed call per method."""
+    def run(w, x, method):
+        def fn():
+            if w["problem"] == "hdbscan":
+                return wm.hdbscan(x, min_pts=w["min_pts"], start=0, method=method, return_stats=True)
+            return wm.emst(x, method=method, return_stats=True)
+        fn()
+        stream = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        e1.synchronize()
+        s = r["stats"]
+        return {"ms": e0.elapsed_time(e1), "wspd_pairs": int(s.wspd_pairs), "bccp_pairs": int(s.pairs_retrieved),
+                "bccp_evals": int(s.bccp_evals), "rounds": int(s.rounds),
+                "traversal_visits": int(s.getpairs_visits + s.getrho_visits), "candidate_edges": int(s.candidate_edges)}
+    out = {}
+    w = WORKLOADS["emst-uniform-10m-3d"]
+    x = torch.from_numpy(make_points(w)).cuda()
+    out["emst-uniform-10m-3d"] = {m: run(w, x, m) for m in ("memogfk", "gfk", "naive")}
+    del x
+    release()
+    w = WORKLOADS[CFG2]
+    x = torch.from_numpy(make_points(w)).cuda()
+    out[CFG2] = {m: run(w, x, m) for m in ("memogfk", "gantao", "gfk", "gfk-geometric")}
+    del x
+    release()
+    out["note"] = ("every method returns the same tree; wspd_pairs: size of the materialised WSPD (GFK forms); "
+                   "bccp_pairs: pairs whose BCCP was evaluated (MemoGFK counts a pair again in each round that "
+                   "retrieves it)")
+    return out
+
+
 # ------------------------------------------------------------------------------ rooflines
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per unit of work of a kernel, from an
 # ncu capture of a smaller case of the same kernel, scaled to the bench's launches by their units
@@ -501,6 +540,7 @@ def main():
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     ap.add_argument("--batch-instances", type=int, default=4096)
+    ap.add_argument("--no-ablation", action="store_true")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
 
@@ -676,6 +716,12 @@ def main():
         del xd, xh
         torch.cuda.empty_cache()
 
+    # ---- ablation: the paper's method against GFK and EMST-Naive (EMST, uniform 3-D, 10^7 points),
+    # and the disjunctive separation against GanTao's geometric one (the HDBSCAN* workload)
+    ablation = None
+    if not args.no_ablation:
+        ablation = run_ablation(wm, torch, call, timed_pass, release=wm.release_cache)
+
     served = serving_sweep(wm, args, rank) if args.serve_requests > 0 else None
     batched = run_batched(wm, torch, args.batch_instances, seed=rank) if args.batch_instances > 0 else None
 
@@ -695,7 +741,8 @@ def main():
                 "cpu_baseline": cpu, "max_rel_screen_err": screen_err,
                 "screen_error_band": "a priori 2^-19 = 1.9e-6 relative for FP32 coordinates",
                 "fp32_peak_tflops": fp32_peak, "plain_form": plain, "workloads": workloads, "cfg2": cfg2,
-                "served": served, "batched": batched, "step_ms": [round(t, 3) for t in steps_ms]}
+                "served": served, "batched": batched, "ablation": ablation,
+                "step_ms": [round(t, 3) for t in steps_ms]}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -23,6 +23,7 @@
 #include <type_traits>
 
 #include "hdb.cuh"
+#include "wspd.cuh"
 
 namespace wm {
 
@@ -32,11 +33,12 @@ struct KnnArgs {
     int N, n, d, k, KL;
     const float *lo, *hi;
     const int *begin, *end, *left, *right;
+    const int4 *links;   // packed node records {begin, end, left, -} (right = left + 1)
+    const float *box;    // packed boxes: lo[DMP], hi[DMP] per node (DMP = d rounded up to 4, 8, 16)
     const float *x32;
     const double *x64;
     double eta;
-    int *stack;
-    int stack_cap;
+    int stack_cap;       // entries of a warp's traversal stack (in shared memory): depth + 4
     double *wscratch;    // [warps][KL][32] FP64 candidate values
     double *cd64;
     float *cd32;
@@ -83,8 +85,18 @@ __device__ inline float knn_threshold_fast(float s)
     return __fadd_ru(__fmul_ru(s, 1.0f + 4.0f / 524288.0f), 1.6e-42f);
 }
 
-// coordinates per leaf point in the shared-memory broadcast buffer (d rounded up to 4)
-template <int DM> constexpr int knn_dmp() { return (DM + 3) / 4 * 4; }
+// coordinates per leaf point in the shared-memory broadcast buffer (d rounded up to 4, 8 or 16:
+// the stride of the packed boxes as well)
+template <int DM> constexpr int knn_dmp() { return DM <= 4 ? 4 : DM <= 8 ? 8 : 16; }
+
+// shared memory of one warp of the k-NN kernel: leaf points, screened lists, indices, stack,
+// rounded up to 16 bytes so that the next warp's region starts float4-aligned
+__host__ __device__ inline size_t knn_warp_smem(int dmp, int KL, size_t vsize, int stack_cap)
+{
+    const size_t b = (size_t)32 * dmp * sizeof(float) + (size_t)KL * 32 * (vsize + sizeof(int)) +
+                     (size_t)stack_cap * sizeof(int);
+    return (b + 15) & ~(size_t)15;
+}
 
 template <int DM, bool FP64>
 __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
@@ -94,17 +106,18 @@ __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
     const int KL = a.KL;
     // per-warp shared region: float4 leaf[32][DMP/4] (the scanned subtree's points, read as
-    // broadcasts); V sv[KL][32]; int sj[KL][32] (slot-major, one bank per lane); the FP64
-    // candidate values of the epilogue live in global scratch: double sw[KL][32]
+    // broadcasts); V sv[KL][32]; int sj[KL][32] (slot-major, one bank per lane); int stk[stack_cap]
+    // (the warp's traversal stack); the FP64 candidate values of the epilogue live in global
+    // scratch: double sw[KL][32]
     constexpr int DMP = knn_dmp<DM>(), DQ = DMP / 4;
-    size_t per_warp = (size_t)32 * DMP * sizeof(float) + (size_t)KL * 32 * (sizeof(V) + sizeof(int));
+    size_t per_warp = knn_warp_smem(DMP, KL, sizeof(V), a.stack_cap);
     unsigned char *base = smem_raw + per_warp * wib;
     float4 *leaf = (float4 *)base;
     V *sv = (V *)(base + (size_t)32 * DMP * sizeof(float));
     int *sj = (int *)((unsigned char *)sv + (size_t)KL * 32 * sizeof(V));
+    int *stk = sj + (size_t)KL * 32;
     const int gw = blockIdx.x * nwb + wib;
     double *sw = a.wscratch + (size_t)gw * KL * 32;
-    int *stk = a.stack + (size_t)gw * a.stack_cap;
     const int n = a.n, d = a.d;
     const bool exact32 = a.eta == 0.0;   // FP32 copy is exact: threshold in FP32
     unsigned long long n_ev = 0, n_re = 0;
@@ -127,6 +140,18 @@ __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
                 if (FP64) qx64[k] = valid ? a.x64[(size_t)k * n + i] : 0.0;
             }
         }
+        // the group's centroid orders the children of a visited node (nearer first) without a
+        // reduction over the lanes at every node
+        float cent[DMP];
+        {
+            const float nv = (float)__popc(__ballot_sync(0xffffffffu, valid));
+#pragma unroll
+            for (int k = 0; k < DMP; ++k) {
+                float v = valid ? qx[k] : 0.f;
+                for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                cent[k] = v / nv;
+            }
+        }
         int cnt = 0;
         V thr = (V)INFINITY;   // KL-th kept value (list full) or +inf
         // cut: the band threshold of the current k-th value; a point screened above it can never
@@ -143,15 +168,21 @@ __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
             int node = stk[sp - 1];
             __syncwarp();
             --sp;
-            const int b = a.begin[node], e = a.end[node];
-            // prune test for each lane
+            const int4 L = a.links[node];
+            const int b = L.x, e = L.y;
+            // prune test for each lane (packed box: lo[DMP] then hi[DMP], padding 0 on both)
             float lb = 0.f;
+            {
+                const float4 *bx = (const float4 *)(a.box + (size_t)node * 2 * DMP);
 #pragma unroll
-            for (int k = 0; k < DM; ++k) {
-                if (k < d) {
-                    float l = a.lo[(size_t)k * a.N + node], h = a.hi[(size_t)k * a.N + node];
-                    float g = fmaxf(fmaxf(l - qx[k], qx[k] - h), 0.f);
-                    lb = fmaf(g, g, lb);
+                for (int c = 0; c < DQ; ++c) {
+                    const float4 l4 = bx[c], h4 = bx[DQ + c];
+                    const float lv[4] = {l4.x, l4.y, l4.z, l4.w}, hv[4] = {h4.x, h4.y, h4.z, h4.w};
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const float g = fmaxf(fmaxf(lv[r] - qx[4 * c + r], qx[4 * c + r] - hv[r]), 0.f);
+                        lb = fmaf(g, g, lb);
+                    }
                 }
             }
             bool need = valid && (V)lower_w2(lb) <= cut * (V)(1.0f + 1.0f / 131072.0f) &&
@@ -227,22 +258,24 @@ __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
                 if (!FP64) __syncwarp();   // the leaf buffer is reused by the next scan
                 n_ev += (unsigned long long)m;
             } else {
-                // push the farther child first so the nearer one is visited next
-                int c0 = a.left[node], c1 = a.right[node];
+                // push the farther child (from the group's centroid) first so the nearer one is
+                // visited next
+                const int c0 = L.z, c1 = L.z + 1;
+                const float4 *b0 = (const float4 *)(a.box + (size_t)c0 * 2 * DMP);
+                const float4 *b1 = (const float4 *)(a.box + (size_t)c1 * 2 * DMP);
                 float l0 = 0.f, l1 = 0.f;
 #pragma unroll
-                for (int k = 0; k < DM; ++k) {
-                    if (k < d) {
-                        float g0 = fmaxf(fmaxf(a.lo[(size_t)k * a.N + c0] - qx[k], qx[k] - a.hi[(size_t)k * a.N + c0]), 0.f);
-                        float g1 = fmaxf(fmaxf(a.lo[(size_t)k * a.N + c1] - qx[k], qx[k] - a.hi[(size_t)k * a.N + c1]), 0.f);
+                for (int c = 0; c < DQ; ++c) {
+                    const float4 lo0 = b0[c], hi0 = b0[DQ + c], lo1 = b1[c], hi1 = b1[DQ + c];
+                    const float a0[4] = {lo0.x, lo0.y, lo0.z, lo0.w}, z0[4] = {hi0.x, hi0.y, hi0.z, hi0.w};
+                    const float a1[4] = {lo1.x, lo1.y, lo1.z, lo1.w}, z1[4] = {hi1.x, hi1.y, hi1.z, hi1.w};
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const float g0 = fmaxf(fmaxf(a0[r] - cent[4 * c + r], cent[4 * c + r] - z0[r]), 0.f);
+                        const float g1 = fmaxf(fmaxf(a1[r] - cent[4 * c + r], cent[4 * c + r] - z1[r]), 0.f);
                         l0 = fmaf(g0, g0, l0);
                         l1 = fmaf(g1, g1, l1);
                     }
-                }
-                if (!valid) { l0 = 0.f; l1 = 0.f; }
-                for (int o = 16; o; o >>= 1) {
-                    l0 += __shfl_xor_sync(0xffffffffu, l0, o);
-                    l1 += __shfl_xor_sync(0xffffffffu, l1, o);
                 }
                 int first = l0 <= l1 ? c1 : c0, second = l0 <= l1 ? c0 : c1;
                 if (sp + 2 > a.stack_cap) {   // cannot happen: cap = depth + 4; reported, not ignored
@@ -521,17 +554,23 @@ int core_distances(Points &P, Tree &T, int min_pts, bool fp64, HdbState &H, Aren
     cudaMemsetAsync(cnts, 0, 8 * sizeof(int), st);
     cudaMemsetAsync(a.stat, 0, 4 * sizeof(unsigned long long), st);
     // launch shape: warps per block limited by shared memory; the grid fills the SMs
-    const int dmp = d <= 3 ? 4 : d <= 7 ? 8 : 16;
-    size_t per_warp = (size_t)32 * dmp * 4 + (size_t)KL * 32 * ((fp64 ? 8 : 4) + 4);
+    const int dmp = d <= 3 ? 4 : d <= 7 ? 8 : 16;   // = knn_dmp<DM> of the instantiation used
+    size_t per_warp = knn_warp_smem(dmp, KL, fp64 ? 8 : 4, a.stack_cap);
     int wpb = (int)std::min<size_t>(8, std::max<size_t>(1, (48u << 10) / per_warp));
     size_t smem = per_warp * wpb;
     int blocks = num_sms() * std::max(1, 32 / wpb);
     int total_warps = blocks * wpb;
     a.next_group = cnts + 6;
     a.err = cnts + 5;
-    a.stack = ar.get<int>((size_t)total_warps * a.stack_cap);
     a.wscratch = ar.get<double>((size_t)total_warps * KL * 32);
-    if (!a.stack || !a.wscratch) return WM_ENOMEM;
+    // packed node records and boxes (the traversal reads a node with two or three vector loads)
+    int4 *links = ar.get<int4>(N);
+    float4 *meta = ar.get<float4>(N);
+    float *box = ar.get<float>((size_t)N * 2 * dmp);
+    if (!a.wscratch || !links || !meta || !box) return WM_ENOMEM;
+    pack_nodes(T, d, dmp, links, meta, box, st);
+    a.links = links;
+    a.box = box;
 #define WM_KNN(DM)                                                                                           \
     do {                                                                                                     \
         if (fp64) {                                                                                          \
