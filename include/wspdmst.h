@@ -359,7 +359,10 @@ typedef struct {
                                 2: two passes until, after two rounds or more, the GetRho
                                 traversals have visited at least half as many node pairs as
                                 the GetPairs traversals; one pass afterwards                   */
-    int32_t reserved[9];
+    int32_t getrho_sample;   /* GetRho starts from every getrho_sample-th frontier pair (0 or 1:
+                                all of them, Algorithm 3); its minimum is then an upper bound of
+                                the exact one, a larger rho_hi with fewer GetRho visits         */
+    int32_t reserved[8];
 } wm_tuning;
 
 /* The parameters a call with these sizes uses (min_pts = 0 for EMST); n = 0 gives the built-in

@@ -76,10 +76,11 @@ class _Opts(ctypes.Structure):
 class _Tuning(ctypes.Structure):
     _fields_ = [("tight_diameters", ctypes.c_int32), ("chunk_log2", ctypes.c_int32), ("dfs_budget", ctypes.c_int32),
                 ("route_big", ctypes.c_int32), ("medium_max", ctypes.c_int32), ("big_max", ctypes.c_int32),
-                ("combined", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+                ("combined", ctypes.c_int32), ("getrho_sample", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
 
 
-TUNING_FIELDS = ("tight_diameters", "chunk_log2", "dfs_budget", "route_big", "medium_max", "big_max", "combined")
+TUNING_FIELDS = ("tight_diameters", "chunk_log2", "dfs_budget", "route_big", "medium_max", "big_max", "combined",
+                 "getrho_sample")
 
 
 class _Instance(ctypes.Structure):

@@ -210,7 +210,8 @@ static bool tuning_valid(const wm_tuning &t)
     return (t.tight_diameters == 0 || t.tight_diameters == 1) &&
            (t.chunk_log2 == 0 || (t.chunk_log2 >= 12 && t.chunk_log2 <= 24)) && t.dfs_budget >= 1 &&
            t.dfs_budget <= 64 && t.route_big >= 0 && t.medium_max >= 65 && t.medium_max <= 4096 &&
-           t.big_max >= t.medium_max && t.combined >= 0 && t.combined <= 2;
+           t.big_max >= t.medium_max && t.combined >= 0 && t.combined <= 2 && t.getrho_sample >= 0 &&
+           t.getrho_sample <= 1024;
 }
 
 static wm_tuning tuning_for(long long n, int d, int min_pts)
@@ -491,6 +492,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     a.medium_max = C.tune.medium_max;
     a.big_max = C.tune.big_max;
     a.disjunctive = C.disjunctive;
+    a.rho_sample = C.tune.getrho_sample > 0 ? C.tune.getrho_sample : 1;
     if (hdb) {
         a.cdmin = hdb->cdmin; a.cdmax = hdb->cdmax; a.cd32 = hdb->cd32; a.cd64 = hdb->cd64;
     }
@@ -865,6 +867,7 @@ static int gfk_rounds(Call &C, Points &P, Tree &T, const HdbState *hdb, const Ca
     a.medium_max = C.tune.medium_max;
     a.big_max = C.tune.big_max;
     a.disjunctive = C.disjunctive;
+    a.rho_sample = C.tune.getrho_sample > 0 ? C.tune.getrho_sample : 1;
     if (hdb) { a.cdmin = hdb->cdmin; a.cdmax = hdb->cdmax; a.cd32 = hdb->cd32; a.cd64 = hdb->cd64; }
     a.frontier_cap = (int)fcap;
     a.links = links; a.meta = meta; a.box = box; a.dp = dp;

@@ -666,7 +666,9 @@ __global__ void frontier_init_kernel(TravArgs a, int mode, int2 *__restrict__ ou
             const int s = block_append(a.node_out_n, cand ? 1 : 0, sh);
             if (cand) a.node_out[s] = x;
         }
-        const int push = cand && (mode != 0 || nsize(a, x) > a.beta) ? 1 : 0;
+        // GetRho may start from a sample of the frontier: the minimum over fewer pairs is an
+        // upper bound of the exact one, which is still a valid split of the weight range
+        const int push = cand && (mode != 0 || (nsize(a, x) > a.beta && t % a.rho_sample == 0)) ? 1 : 0;
         const int slot = block_append(out_count, push, sh);
         if (push) {
             if (slot < a.frontier_cap) out[slot] = make_int2(a.left[x], a.right[x]);

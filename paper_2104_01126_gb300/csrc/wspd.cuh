@@ -24,6 +24,7 @@ struct TravArgs {
     int fp64 = 0;              // plain FP64 form
     int beta = 2;
     int collect_all = 0;       // GetPairs sends every retrieved pair to list 0 (the full WSPD)
+    int rho_sample = 1;        // GetRho starts from every rho_sample-th frontier pair (tuning)
     int disjunctive = 1;       // HDBSCAN*: the separation of Sec. 3.1.2 (0: geometric only)
     int dfs_budget = 8;        // depth-first rounds per warp and traversal step (tuning)
     int medium_max = 1024;     // pair-size classes (tuning): |A||B| <= medium_max: one warp,

@@ -24,6 +24,8 @@ SETTINGS = [
     {"combined": 1},
     {"combined": 1, "tight_diameters": 1, "chunk_log2": 12, "dfs_budget": 2},
     {"combined": 2},
+    {"getrho_sample": 16},
+    {"getrho_sample": 4, "combined": 2, "tight_diameters": 1},
 ]
 
 
