@@ -330,7 +330,15 @@ def run_ablation(wm, torch, call, timed_pass, release):
 # ncu capture of a smaller case of the same kernel, scaled to the bench's launches by their units
 # (the node-pair visits of a traversal, the distance evaluations of the k-NN kernel).  A figure is
 # reported only while the kernel's source file is the measured version (sha256), else null.
-MEASURED_TRAFFIC = {}
+# Captured on emst-uniform-10m-3d run at n = 2x10^6 (--points 2000000), every traversal launch of
+# one call (69 GetPairs, 57 GetRho): 10.459 GB over 113,220,189 visits and 3.843 GB over
+# 54,161,908 visits.
+MEASURED_TRAFFIC = {
+    "getpairs": {"bytes_per_unit": 92.38, "source": "paper_2104_01126_gb300/csrc/wspd.cu",
+                 "sha256": "77191141f67c54457dd22b77ab53151d83f1fe8d7ca7dbf505bca582efc8c486"},
+    "getrho": {"bytes_per_unit": 70.96, "source": "paper_2104_01126_gb300/csrc/wspd.cu",
+               "sha256": "77191141f67c54457dd22b77ab53151d83f1fe8d7ca7dbf505bca582efc8c486"},
+}
 
 
 def measured_traffic(key, units):
@@ -381,7 +389,9 @@ def kernel_rooflines(runs, peaks, fp32_peak, fp32_basis, hdb=False):
         gbs = byts / (ms * 1e-3) / 1e9
         ks.append({"kernel": name, "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                    "frac": gbs / peaks["hbm_gbs"], "ms": ms, "launches": launches,
-                   "traffic": measured_traffic(key, tot(lambda d, s: visits(s))),
+                   "traffic": (measured_traffic(key, tot(lambda d, s: visits(s))) / launches
+                               if launches and measured_traffic(key, 1) else None),
+                   "traffic_total": measured_traffic(key, tot(lambda d, s: visits(s))),
                    "work": f"{tot(lambda d, s: visits(s))} visited node pairs x {visit_bytes(runs[0][0])} B "
                            f"(d = {runs[0][0]}; the byte count grows with d)",
                    "peak_basis": peaks["hbm_basis"]})
@@ -541,6 +551,9 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     ap.add_argument("--batch-instances", type=int, default=4096)
     ap.add_argument("--no-ablation", action="store_true")
+    ap.add_argument("--points", type=int, default=0,
+                    help="run the workload's generator and dimension at this n instead (profiling captures "
+                         "of a smaller case; the line then says so in config.points)")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
 
@@ -609,7 +622,8 @@ def main():
 
     # ---- the headline workloads, device resident
     names = workload_names(args.workload)
-    host = [(WORKLOADS[nm], make_points(WORKLOADS[nm])) for nm in names]
+    sel = [dict(WORKLOADS[nm], n=args.points) if args.points else WORKLOADS[nm] for nm in names]
+    host = [(w, make_points(w)) for w in sel]
     dev = [(w, torch.from_numpy(x).cuda()) for w, x in host]
     n_total = sum(int(x.shape[0]) for _, x in host)
     for _ in range(args.warmup):
@@ -734,6 +748,8 @@ def main():
                "points_per_step": n_total, "seed": 0, "precision": args.precision,
                "coordinates": "FP32", "l2": "256 MiB buffer written before every timed call",
                "parallelism": f"replicas{ws}"}
+        if args.points:
+            cfg["points"] = args.points
         line = {"metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",

@@ -67,6 +67,11 @@ def test_kernel_rooflines_arithmetic():
     assert abs(by["bccp_pair_tile_kernel"]["achieved"] - 0.04) < 1e-12
     assert abs(by["bccp_dual_kernel"]["frac"] - 0.16 / 50.0) < 1e-12
     assert roof["kernel"].startswith("findpair_dfs_kernel<1>")   # the most device time
+    # measured traffic: bytes per visit x visits, per launch
+    if bench.measured_traffic("getpairs", 1):
+        per = bench.MEASURED_TRAFFIC["getpairs"]["bytes_per_unit"]
+        assert abs(gp["traffic"] - per * 10**9 / 7) < 1e-3 * per
+        assert abs(gp["traffic_total"] - per * 10**9) < 1e-3 * per
     # mutual reachability adds two maxima per evaluation
     roof_h = bench.kernel_rooflines([(3, s3)], peaks, 50.0, "test", hdb=True)
     byh = {k["kernel"].split(" ")[0]: k for k in roof_h["all"]}
