@@ -452,8 +452,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     const int stack_warps = num_sms() * 8 * 8;   // warps of the dual-tree kernel (grid-stride)
     int *dual_stack = ar.get<int>((size_t)stack_warps * (T.depth + 4));
     const int dp = P.d <= 4 ? 4 : P.d <= 8 ? 8 : 16;
-    int4 *links = ar.get<int4>(T.N);
-    float4 *meta = ar.get<float4>(T.N);
+    NodeRec *rec = ar.get<NodeRec>(T.N);
     float *box = ar.get<float>((size_t)T.N * 2 * dp);
     float4 *x4 = ar.get<float4>((size_t)n * (dp / 4));
     EdgeK *batch = ar.get<EdgeK>(caps.edges), *filt = ar.get<EdgeK>(caps.edges), *tmp = ar.get<EdgeK>(caps.edges);
@@ -472,7 +471,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     {
         Tree T2 = T;
         if (hdb) { T2.cdmin = hdb->cdmin; T2.cdmax = hdb->cdmax; }
-        pack_nodes(T2, P.d, dp, links, meta, box, st);
+        pack_nodes(T2, P.d, dp, rec, box, st);
         point_major(P.x32, n, P.d, dp, x4, st);
     }
     WM_CK(cudaMemsetAsync(stat, 0, 16 * sizeof(unsigned long long), st));
@@ -497,7 +496,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         a.cdmin = hdb->cdmin; a.cdmax = hdb->cdmax; a.cd32 = hdb->cd32; a.cd64 = hdb->cd64;
     }
     a.frontier_cap = (int)fcap;
-    a.links = links; a.meta = meta; a.box = box; a.dp = dp;
+    a.rec = rec; a.box = box; a.dp = dp;
     for (int c = 0; c < 5; ++c) { a.list[c] = lists[c]; a.list_lb[c] = list_lbs[c]; a.list_cap[c] = (int)lcap; }
     a.list_count = lcount;
     a.big = lists[3]; a.big_count = lcount + 3;
@@ -569,7 +568,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     while (nE < target) {
         if (++rounds > 4096) { set_detail("MemoGFK made no progress%s (%lld rounds)", "", rounds); return WM_EINTERNAL; }
         Timer tw;
-        WM_TRY(launch_comp_labels(T, P, uf, links, comp_scratch, ar, st));
+        WM_TRY(launch_comp_labels(T, P, uf, rec, comp_scratch, ar, st));
         a.beta = (int)std::min<long long>(beta, 0x7fffffff);
         double rho_hi;
         // Combined pass (tuning): GetRho's minimum R is kept on the device while GetPairs runs;
@@ -828,8 +827,7 @@ static int gfk_rounds(Call &C, Points &P, Tree &T, const HdbState *hdb, const Ca
     const int stack_warps = num_sms() * 8 * 8;
     int *dual_stack = ar.get<int>((size_t)stack_warps * (T.depth + 4));
     const int dp = P.d <= 4 ? 4 : P.d <= 8 ? 8 : 16;
-    int4 *links = ar.get<int4>(T.N);
-    float4 *meta = ar.get<float4>(T.N);
+    NodeRec *rec = ar.get<NodeRec>(T.N);
     float *box = ar.get<float>((size_t)T.N * 2 * dp);
     float4 *x4 = ar.get<float4>((size_t)n * (dp / 4));
     int2 *S[2] = {ar.get<int2>(scap), ar.get<int2>(scap)};
@@ -848,7 +846,7 @@ static int gfk_rounds(Call &C, Points &P, Tree &T, const HdbState *hdb, const Ca
     {
         Tree T2 = T;
         if (hdb) { T2.cdmin = hdb->cdmin; T2.cdmax = hdb->cdmax; }
-        pack_nodes(T2, P.d, dp, links, meta, box, st);
+        pack_nodes(T2, P.d, dp, rec, box, st);
         point_major(P.x32, n, P.d, dp, x4, st);
     }
     WM_CK(cudaMemsetAsync(stat, 0, 16 * sizeof(unsigned long long), st));
@@ -870,7 +868,7 @@ static int gfk_rounds(Call &C, Points &P, Tree &T, const HdbState *hdb, const Ca
     a.rho_sample = C.tune.getrho_sample > 0 ? C.tune.getrho_sample : 1;
     if (hdb) { a.cdmin = hdb->cdmin; a.cdmax = hdb->cdmax; a.cd32 = hdb->cd32; a.cd64 = hdb->cd64; }
     a.frontier_cap = (int)fcap;
-    a.links = links; a.meta = meta; a.box = box; a.dp = dp;
+    a.rec = rec; a.box = box; a.dp = dp;
     a.list_count = lcount;
     a.big = lists[3]; a.big_count = lcount + 3;
     a.huge_best = huge_best; a.huge_sbest = huge_sbest;
@@ -883,7 +881,7 @@ static int gfk_rounds(Call &C, Points &P, Tree &T, const HdbState *hdb, const Ca
     a.node_out = nullptr; a.node_out_n = nullptr;
     Timer tw;
     // ---- the full WSPD: every well-separated pair into S[0]
-    WM_TRY(launch_comp_labels(T, P, uf, links, comp_scratch, ar, st));
+    WM_TRY(launch_comp_labels(T, P, uf, rec, comp_scratch, ar, st));
     set_rho(a, 0.0, INFINITY);
     a.collect_all = 1;
     a.list[0] = S[0]; a.list_lb[0] = Slb[0]; a.list_cap[0] = (int)scap;
@@ -974,9 +972,9 @@ static int gfk_rounds(Call &C, Points &P, Tree &T, const HdbState *hdb, const Ca
             return WM_EINTERNAL;
         }
         // ---- filter: pairs whose points are all connected, pool edges whose endpoints are
-        WM_TRY(launch_comp_labels(T, P, uf, links, comp_scratch, ar, st));
+        WM_TRY(launch_comp_labels(T, P, uf, rec, comp_scratch, ar, st));
         WM_CK(cudaMemsetAsync(kcount, 0, sizeof(int), st));
-        gfk_filter_pairs(S[cur], Slb[cur], mS, links, S[cur ^ 1], Slb[cur ^ 1], kcount, st);
+        gfk_filter_pairs(S[cur], Slb[cur], mS, rec, S[cur ^ 1], Slb[cur ^ 1], kcount, st);
         WM_CK(cudaMemsetAsync(pcount, 0, sizeof(int), st));
         gfk_filter_edges(pool[pcur], mP, uf, pool[pcur ^ 1], pcount, st);
         WM_CK(cudaMemcpyAsync(C.pin, cnts, 10 * sizeof(int), cudaMemcpyDeviceToHost, st));

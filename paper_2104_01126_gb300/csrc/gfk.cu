@@ -41,7 +41,7 @@ __global__ void gfk_split_kernel(TravArgs a, const int2 *__restrict__ S, const f
         if (t < m) {
             p = S[t];
             l = lb[t];
-            const int4 u = a.links[p.x], v = a.links[p.y];
+            const int4 u = a.rec[p.x].l, v = a.rec[p.y].l;
             sz = (long long)(u.y - u.x) + (v.y - v.x);
             prod = (long long)(u.y - u.x) * (v.y - v.x);
         }
@@ -90,9 +90,9 @@ __global__ void gfk_partition_kernel(const EdgeK *__restrict__ pool, int m, doub
     }
 }
 
-// drops the pairs whose points all lie in one component (node labels in links[x].w)
+// drops the pairs whose points all lie in one component (node labels in rec[x].l.w)
 __global__ void gfk_filter_pairs_kernel(const int2 *__restrict__ S, const float *__restrict__ lb, int m,
-                                        const int4 *__restrict__ links, int2 *__restrict__ out, float *__restrict__ out_lb,
+                                        const NodeRec *__restrict__ rec, int2 *__restrict__ out, float *__restrict__ out_lb,
                                         int *count)
 {
     const int limit = (m + 31) & ~31;
@@ -103,7 +103,7 @@ __global__ void gfk_filter_pairs_kernel(const int2 *__restrict__ S, const float 
         if (t < m) {
             p = S[t];
             l = lb[t];
-            const int ca = links[p.x].w, cb = links[p.y].w;
+            const int ca = rec[p.x].l.w, cb = rec[p.y].l.w;
             keep = !(ca >= 0 && ca == cb);
         }
         const int s = warp_slot(count, keep);
@@ -152,10 +152,10 @@ void gfk_partition(const EdgeK *pool, int m, double hi, EdgeK *batch, int *batch
                rest_count, overflow);
 }
 
-void gfk_filter_pairs(const int2 *S, const float *lb, int m, const int4 *links, int2 *out, float *out_lb, int *count,
+void gfk_filter_pairs(const int2 *S, const float *lb, int m, const NodeRec *rec, int2 *out, float *out_lb, int *count,
                       cudaStream_t st)
 {
-    if (m > 0) launch(gfk_filter_pairs_kernel, grid_for(m, 256), 256, 0, st, S, lb, m, links, out, out_lb, count);
+    if (m > 0) launch(gfk_filter_pairs_kernel, grid_for(m, 256), 256, 0, st, S, lb, m, rec, out, out_lb, count);
 }
 
 void gfk_filter_edges(const EdgeK *pool, int m, const int *uf, EdgeK *out, int *count, cudaStream_t st)

@@ -33,8 +33,9 @@ struct KnnArgs {
     int N, n, d, k, KL;
     const float *lo, *hi;
     const int *begin, *end, *left, *right;
-    const int4 *links;   // packed node records {begin, end, left, -} (right = left + 1)
-    const float *box;    // packed boxes: lo[DMP], hi[DMP] per node (DMP = d rounded up to 4, 8, 16)
+    const NodeRec *rec;  // packed node records (right child = left + 1)
+    const float *box;    // packed boxes, 2 DMP floats per node (DMP = d rounded up to 4, 8, 16) in groups of
+                         // four dimensions: lo[4c..4c+3], hi[4c..4c+3]
     const float *x32;
     const double *x64;
     double eta;
@@ -168,15 +169,15 @@ __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
             int node = stk[sp - 1];
             __syncwarp();
             --sp;
-            const int4 L = a.links[node];
+            const int4 L = a.rec[node].l;
             const int b = L.x, e = L.y;
-            // prune test for each lane (packed box: lo[DMP] then hi[DMP], padding 0 on both)
+            // prune test for each lane (packed box: groups of four dimensions, lo then hi, padding 0)
             float lb = 0.f;
             {
                 const float4 *bx = (const float4 *)(a.box + (size_t)node * 2 * DMP);
 #pragma unroll
                 for (int c = 0; c < DQ; ++c) {
-                    const float4 l4 = bx[c], h4 = bx[DQ + c];
+                    const float4 l4 = bx[2 * c], h4 = bx[2 * c + 1];
                     const float lv[4] = {l4.x, l4.y, l4.z, l4.w}, hv[4] = {h4.x, h4.y, h4.z, h4.w};
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(256) knn_fast_kernel(KnnArgs a)
                 float l0 = 0.f, l1 = 0.f;
 #pragma unroll
                 for (int c = 0; c < DQ; ++c) {
-                    const float4 lo0 = b0[c], hi0 = b0[DQ + c], lo1 = b1[c], hi1 = b1[DQ + c];
+                    const float4 lo0 = b0[2 * c], hi0 = b0[2 * c + 1], lo1 = b1[2 * c], hi1 = b1[2 * c + 1];
                     const float a0[4] = {lo0.x, lo0.y, lo0.z, lo0.w}, z0[4] = {hi0.x, hi0.y, hi0.z, hi0.w};
                     const float a1[4] = {lo1.x, lo1.y, lo1.z, lo1.w}, z1[4] = {hi1.x, hi1.y, hi1.z, hi1.w};
 #pragma unroll
@@ -564,12 +565,11 @@ int core_distances(Points &P, Tree &T, int min_pts, bool fp64, HdbState &H, Aren
     a.err = cnts + 5;
     a.wscratch = ar.get<double>((size_t)total_warps * KL * 32);
     // packed node records and boxes (the traversal reads a node with two or three vector loads)
-    int4 *links = ar.get<int4>(N);
-    float4 *meta = ar.get<float4>(N);
+    NodeRec *rec = ar.get<NodeRec>(N);
     float *box = ar.get<float>((size_t)N * 2 * dmp);
-    if (!a.wscratch || !links || !meta || !box) return WM_ENOMEM;
-    pack_nodes(T, d, dmp, links, meta, box, st);
-    a.links = links;
+    if (!a.wscratch || !rec || !box) return WM_ENOMEM;
+    pack_nodes(T, d, dmp, rec, box, st);
+    a.rec = rec;
     a.box = box;
 #define WM_KNN(DM)                                                                                           \
     do {                                                                                                     \

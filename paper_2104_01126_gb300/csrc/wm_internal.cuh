@@ -70,7 +70,9 @@ struct Arena {
     bool failed = false;
     void *take(size_t bytes)
     {
-        size_t a = (off + 255) & ~size_t(255);
+        // 256-byte aligned device addresses (a caller's arena may start anywhere)
+        const size_t mis = (size_t)(reinterpret_cast<uintptr_t>(base) & 255);
+        size_t a = ((off + mis + 255) & ~size_t(255)) - mis;
         if (a + bytes > cap) { failed = true; return nullptr; }
         off = a + bytes;
         if (off > peak) peak = off;
@@ -135,6 +137,36 @@ __device__ inline double sqdist64(const double *__restrict__ x64, int n, int d, 
 // Rigorous bounds on the FP64 w2 of any point pair inside boxes from FP32 box arithmetic.
 __device__ inline float lower_w2(float q) { float r = __fsub_rd(__fmul_rd(q, 1.0f - kBoxRel), kAbsTiny); return r > 0.f ? r : 0.f; }
 __device__ inline float upper_w2(float q) { return __fadd_ru(__fmul_ru(q, 1.0f + kBoxRel), kAbsTiny); }
+
+// Packed node record of the traversals: l = {begin, end, left child, component label of the
+// round} (the right child is always left + 1), m = {diam2 bound, cdmin, cdmax, 0}.  32 bytes,
+// read in one 256-bit load.
+struct __align__(32) NodeRec {
+    int4 l;
+    float4 m;
+};
+
+// 256-bit read-only global load (sm_100 and later): 32 bytes from a 32-byte aligned address that
+// no thread writes during the kernel.  One load touches one 32-byte sector, where two 128-bit
+// loads would each cost a pass of the L1 data pipe.
+__device__ __forceinline__ void ldg256(const void *p, float4 &a, float4 &b)
+{
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+// Packed node boxes: a row of 2 DP floats per node (DP = d rounded up to 4, 8 or 16) in groups of
+// four dimensions, lo[4c .. 4c+3] then hi[4c .. 4c+3] for group c (padded dimensions 0 on both
+// sides), so that one 256-bit load brings both bounds of four dimensions.
+__host__ __device__ constexpr int box_lo(int k) { return 8 * (k >> 2) + (k & 3); }
+__host__ __device__ constexpr int box_hi(int k) { return 8 * (k >> 2) + 4 + (k & 3); }
+
+__device__ __forceinline__ void load_rec(const NodeRec *r, int x, int4 &l, float4 &m)
+{
+    float4 f;
+    ldg256(r + x, f, m);
+    l = make_int4(__float_as_int(f.x), __float_as_int(f.y), __float_as_int(f.z), __float_as_int(f.w));
+}
 
 __device__ inline unsigned lanemask_lt() { unsigned m; asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m)); return m; }
 

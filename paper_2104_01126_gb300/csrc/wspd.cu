@@ -242,30 +242,38 @@ __device__ inline void warp_emit(const TravArgs &a, bool has, const KMin &m)
 
 
 // ------------------------------------------------------------------ packed node records
-// links = {begin, end, left, comp label} (the right child is always left + 1, and the label of
-// the round is what a visit tests first, with the sizes, before it reads anything else);
-// meta = {diam2 bound, cdmin, cdmax, 0}; box[node][2*DP] = lo[0..DP), hi[0..DP) with padded
-// dimensions set to 0.
+// rec[node] = {l = {begin, end, left, comp label}, m = {diam2 bound, cdmin, cdmax, 0}} (the right
+// child is always left + 1, and the label of the round is what a visit tests first, with the
+// sizes); box[node][2*DP] holds the bounds in groups of four dimensions (box_lo / box_hi).  A visit
+// reads each node's record and box with 256-bit loads, 1 + DP / 4 of them per node.
+__device__ inline void box_terms(const float4 &plo, const float4 &phi, const float4 &qlo, const float4 &qhi, float &s,
+                                 float &t)
+{
+    const float al[4] = {plo.x, plo.y, plo.z, plo.w}, ah[4] = {phi.x, phi.y, phi.z, phi.w};
+    const float bl[4] = {qlo.x, qlo.y, qlo.z, qlo.w}, bh[4] = {qhi.x, qhi.y, qhi.z, qhi.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float g = fmaxf(fmaxf(bl[k] - ah[k], al[k] - bh[k]), 0.f);
+        float m = fmaxf(bh[k] - al[k], ah[k] - bl[k]);
+        s = fmaf(g, g, s);
+        t = fmaf(m, m, t);
+    }
+}
+
 template <int DP>
 __device__ inline void pair_bounds_packed(const TravArgs &a, int P, int Q, const int4 &lp, const int4 &lq,
                                           const float4 &mp, const float4 &mq, float &lbB, float &ubB, bool &ws,
                                           float &dP, float &dQ)
 {
-    const float4 *bp = (const float4 *)(a.box + (size_t)P * 2 * DP);
-    const float4 *bq = (const float4 *)(a.box + (size_t)Q * 2 * DP);
-    float s = 0.f, t = 0.f;
+    const float *bp = a.box + (size_t)P * 2 * DP;
+    const float *bq = a.box + (size_t)Q * 2 * DP;
+    float s = 0.f, t = 0.f;   // squared gap and squared extent, dimension by dimension in order
 #pragma unroll
     for (int c = 0; c < DP / 4; ++c) {
-        float4 plo = bp[c], phi = bp[DP / 4 + c], qlo = bq[c], qhi = bq[DP / 4 + c];
-        float al[4] = {plo.x, plo.y, plo.z, plo.w}, ah[4] = {phi.x, phi.y, phi.z, phi.w};
-        float bl[4] = {qlo.x, qlo.y, qlo.z, qlo.w}, bh[4] = {qhi.x, qhi.y, qhi.z, qhi.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float g = fmaxf(fmaxf(bl[k] - ah[k], al[k] - bh[k]), 0.f);
-            float m = fmaxf(bh[k] - al[k], ah[k] - bl[k]);
-            s = fmaf(g, g, s);
-            t = fmaf(m, m, t);
-        }
+        float4 plo, phi, qlo, qhi;
+        ldg256(bp + 8 * c, plo, phi);
+        ldg256(bq + 8 * c, qlo, qhi);
+        box_terms(plo, phi, qlo, qhi, s, t);
     }
     float lb = lower_w2(s), ub = upper_w2(t);
     dP = mp.x;
@@ -302,11 +310,13 @@ __device__ inline void visit_pair(const TravArgs &a, int2 me, float rho_now, int
                                   float &rho_cand, float &lb_out)
 {
     const int P = me.x, Q = me.y;
-    const int4 lp = a.links[P], lq = a.links[Q];
+    int4 lp, lq;
+    float4 mp, mq;
+    load_rec(a.rec, P, lp, mp);
+    load_rec(a.rec, Q, lq, mq);
     const int sp = lp.y - lp.x, sq = lq.y - lq.x;
     if (MODE == 0 && sp + sq <= a.beta) return;
     if (lp.w >= 0 && lp.w == lq.w) return;   // all points already connected
-    const float4 mp = a.meta[P], mq = a.meta[Q];
     float lbB, ubB, dP, dQ;
     bool ws;
     pair_bounds_packed<DP>(a, P, Q, lp, lq, mp, mq, lbB, ubB, ws, dP, dQ);
@@ -391,18 +401,19 @@ __global__ void __launch_bounds__(256) findpair_dfs_kernel(TravArgs a, DfsArgs s
     }
     auto input = [&](int i) -> int2 { return i < mx ? s.xin[xc - mx + i] : s.S[tp - ms + (i - mx)]; };
     const bool stop = __shfl_sync(0xffffffffu, (int)(*(volatile unsigned *)a.overflow != 0), 0) != 0;
-    unsigned long long n_vis = 0, n_ret = 0;
+    unsigned n_vis = 0, n_ret = 0;   // per warp and launch: far below 2^32
     float rho_w = INFINITY;    // GetRho: smallest candidate this warp has written
     float rho_g = INFINITY;    // GetRho: the shared minimum as last read (refreshed every 4 rounds)
     int refresh = 0;
     int sp = 0, it = 0;        // warp stack size (warp-uniform), rounds on the warp's own stack
     bool fed = stop;           // no more input for this warp
     // every popped pair costs one visit in the breadth-first phase: a contiguous share per warp
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long share = (m + nw - 1) / nw;
-    long long in_next = gw * share;
-    const long long in_end = min((long long)m, in_next + share);
+    // (m <= chunk <= 2^24 and gw * share < m + nw: 32-bit arithmetic suffices)
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int share = (m + nw - 1) / nw;
+    int in_next = gw * share;
+    const int in_end = min(m, in_next + share);
     while (!stop) {
         // one round: the next 32 popped pairs while there are any (every popped pair is visited
         // in this step, breadth first), then up to `budget` rounds of the warp's own stack
@@ -410,13 +421,13 @@ __global__ void __launch_bounds__(256) findpair_dfs_kernel(TravArgs a, DfsArgs s
         int k = 0;
         bool from_input = false;
         if (!fed) {
-            const long long base = in_next;
-            k = base < in_end ? (int)min(32LL, in_end - base) : 0;
+            const int base = in_next;
+            k = base < in_end ? min(32, in_end - base) : 0;
             if (k == 0) fed = true;
             else {
                 from_input = true;
                 in_next += 32;
-                if (lane < k) me = input((int)base + lane);
+                if (lane < k) me = input(base + lane);
             }
         }
         if (!from_input) {
@@ -502,11 +513,10 @@ __global__ void __launch_bounds__(256) findpair_dfs_kernel(TravArgs a, DfsArgs s
             else atomicOr(a.overflow, 1u);
         }
     }
-    n_vis = warp_sum_u64(n_vis);
-    n_ret = warp_sum_u64(n_ret);
-    if (lane == 0 && n_vis) {
-        atomicAdd(a.stat + (MODE == 0 ? 5 : 4), n_vis);
-        if (n_ret) atomicAdd(a.stat + 0, n_ret);
+    const unsigned long long t_vis = warp_sum_u64(n_vis), t_ret = warp_sum_u64(n_ret);
+    if (lane == 0 && t_vis) {
+        atomicAdd(a.stat + (MODE == 0 ? 5 : 4), t_vis);
+        if (t_ret) atomicAdd(a.stat + 0, t_ret);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -554,7 +564,7 @@ __global__ void __launch_bounds__(256) bccp_group_kernel(TravArgs a, const int2 
             plb = lbs[pi];
         }
         if (valid && plb < a.rho_hi_f) {
-            int4 lp = a.links[pr.x], lq = a.links[pr.y];
+            int4 lp = a.rec[pr.x].l, lq = a.rec[pr.y].l;
             pb = lp.x; na = lp.y - lp.x; qb = lq.x; nb = lq.y - lq.x;
         }
         const int tot = na * nb;
@@ -636,15 +646,16 @@ __global__ void pack_nodes_kernel(int N, int d, int DP, const float *__restrict_
                                   const int *__restrict__ begin, const int *__restrict__ end,
                                   const int *__restrict__ left, const int *__restrict__ right,
                                   const float *__restrict__ diam2, const float *__restrict__ cdmin,
-                                  const float *__restrict__ cdmax, int4 *__restrict__ links, float4 *__restrict__ meta,
-                                  float *__restrict__ box)
+                                  const float *__restrict__ cdmax, NodeRec *__restrict__ rec, float *__restrict__ box)
 {
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x) {
-        links[x] = make_int4(begin[x], end[x], left[x], -1);   // right[x] == left[x] + 1
-        meta[x] = make_float4(diam2[x], cdmin ? cdmin[x] : 0.f, cdmax ? cdmax[x] : 0.f, 0.f);
+        NodeRec r;
+        r.l = make_int4(begin[x], end[x], left[x], -1);   // right[x] == left[x] + 1
+        r.m = make_float4(diam2[x], cdmin ? cdmin[x] : 0.f, cdmax ? cdmax[x] : 0.f, 0.f);
+        rec[x] = r;
         for (int k = 0; k < DP; ++k) {
-            box[(size_t)x * 2 * DP + k] = k < d ? lo[(size_t)k * N + x] : 0.f;
-            box[(size_t)x * 2 * DP + DP + k] = k < d ? hi[(size_t)k * N + x] : 0.f;
+            box[(size_t)x * 2 * DP + box_lo(k)] = k < d ? lo[(size_t)k * N + x] : 0.f;
+            box[(size_t)x * 2 * DP + box_hi(k)] = k < d ? hi[(size_t)k * N + x] : 0.f;
         }
     }
 }
@@ -701,14 +712,14 @@ __global__ void pos_labels_kernel(const int *__restrict__ pid, const int *__rest
     }
 }
 
-__global__ void node_labels_kernel(int N, int4 *__restrict__ links, const int *__restrict__ lab,
+__global__ void node_labels_kernel(int N, NodeRec *__restrict__ rec, const int *__restrict__ lab,
                                    const int *__restrict__ E, int *__restrict__ comp)
 {
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x) {
-        const int4 L = links[x];
+        const int4 L = rec[x].l;
         const int c = E[L.y] == E[L.x + 1] ? lab[L.x] : -1;
         comp[x] = c;
-        ((int *)(links + x))[3] = c;
+        rec[x].l.w = c;
     }
 }
 
@@ -724,7 +735,7 @@ __global__ void huge_items_kernel(const TravArgs a, const int2 *__restrict__ pai
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j < m) {
         int P = pairs[j].x, Q = pairs[j].y;
-        int4 lp = a.links[P], lq = a.links[Q];
+        int4 lp = a.rec[P].l, lq = a.rec[Q].l;
         int small = min(lp.y - lp.x, lq.y - lq.x);   // the query side
         // no work for a pair retrieved under a larger bound than this flush's rho_hi
         items[j] = lbs[j] < a.rho_hi_f ? (small + 31) / 32 : 0;
@@ -757,7 +768,7 @@ __global__ void __launch_bounds__(256) bccp_dual_kernel(TravArgs a, const int2 *
         }
         const int j = lo;
         const int P = pairs[j].x, Q = pairs[j].y;
-        const int4 lp = a.links[P], lq = a.links[Q];
+        const int4 lp = a.rec[P].l, lq = a.rec[Q].l;
         // queries: the smaller side; its points far from the other side are pruned at the other
         // tree's root, the rest run a nearest-first descent into it
         const bool pq = lp.y - lp.x <= lq.y - lq.x;   // P is the query side
@@ -799,18 +810,18 @@ __global__ void __launch_bounds__(256) bccp_dual_kernel(TravArgs a, const int2 *
             const int node = stk[sp - 1];
             __syncwarp();
             --sp;
-            const int4 ln = a.links[node];
+            const int4 ln = a.rec[node].l;
             const float *bx = a.box + (size_t)node * 2 * DP;
             float lb = 0.f;
 #pragma unroll
             for (int k = 0; k < DM; ++k) {
                 if (k < d) {
-                    float g = fmaxf(fmaxf(bx[k] - qx[k], qx[k] - bx[DP + k]), 0.f);
+                    float g = fmaxf(fmaxf(bx[box_lo(k)] - qx[k], qx[k] - bx[box_hi(k)]), 0.f);
                     lb = fmaf(g, g, lb);
                 }
             }
             float lbw = lower_w2(lb);
-            if (HDB) lbw = fmaxf(lbw, fmaxf(qcd * (1.0f - 1.0f / 4194304.0f), a.meta[node].y));
+            if (HDB) lbw = fmaxf(lbw, fmaxf(qcd * (1.0f - 1.0f / 4194304.0f), a.rec[node].m.y));
             const bool need = valid && lbw <= thr * (1.0f + 1.0f / 131072.0f);
             if (!__any_sync(0xffffffffu, need)) continue;
             const int bsz = ln.y - ln.x;
@@ -909,8 +920,8 @@ __global__ void __launch_bounds__(256) bccp_dual_kernel(TravArgs a, const int2 *
 #pragma unroll
                 for (int k = 0; k < DM; ++k) {
                     if (k < d) {
-                        float g0 = fmaxf(fmaxf(b0x[k] - qx[k], qx[k] - b0x[DP + k]), 0.f);
-                        float g1 = fmaxf(fmaxf(b1x[k] - qx[k], qx[k] - b1x[DP + k]), 0.f);
+                        float g0 = fmaxf(fmaxf(b0x[box_lo(k)] - qx[k], qx[k] - b0x[box_hi(k)]), 0.f);
+                        float g1 = fmaxf(fmaxf(b1x[box_lo(k)] - qx[k], qx[k] - b1x[box_hi(k)]), 0.f);
                         l0 = fmaf(g0, g0, l0);
                         l1 = fmaf(g1, g1, l1);
                     }
@@ -1028,7 +1039,7 @@ __global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const i
             if (lane == 0) waste.add(1, 0);
             continue;
         }
-        const int4 lp = a.links[pr.x], lq = a.links[pr.y];
+        const int4 lp = a.rec[pr.x].l, lq = a.rec[pr.y].l;
         const bool pa = lp.y - lp.x >= lq.y - lq.x;   // A: the larger side, on the lanes
         const int abeg = pa ? lp.x : lq.x, aend = pa ? lp.y : lq.y;
         const int bbeg = pa ? lq.x : lp.x, bend = pa ? lq.y : lp.y;
@@ -1237,7 +1248,7 @@ __global__ void __launch_bounds__(256) bccp_pair_tile_kernel(TravArgs a, const i
 
 // ----------------------------------------------------------------------------- host side
 
-int launch_comp_labels(const Tree &T, const Points &P, int *uf, int4 *links, int *scratch,
+int launch_comp_labels(const Tree &T, const Points &P, int *uf, NodeRec *rec, int *scratch,
                        Arena &ar, cudaStream_t st)
 {
     const int n = P.n;
@@ -1246,7 +1257,7 @@ int launch_comp_labels(const Tree &T, const Points &P, int *uf, int4 *links, int
     launch(pos_labels_kernel, grid_for(n, 256), 256, 0, st, P.pid, uf, n, lab, E);
     int rc = scan_exclusive_i32(E, E, n, E + n, st, ar);
     if (rc) return rc;
-    launch(node_labels_kernel, grid_for(T.N, 256), 256, 0, st, T.N, links, lab, E, T.comp);
+    launch(node_labels_kernel, grid_for(T.N, 256), 256, 0, st, T.N, rec, lab, E, T.comp);
     return 0;
 }
 
@@ -1431,10 +1442,10 @@ void point_major(const float *x32, int n, int d, int dp, float4 *x4, cudaStream_
     launch(point_major_kernel, grid_for((long long)n * (dp / 4), 256), 256, 0, st, x32, n, d, dp / 4, x4);
 }
 
-void pack_nodes(const Tree &T, int d, int dp, int4 *links, float4 *meta, float *box, cudaStream_t st)
+void pack_nodes(const Tree &T, int d, int dp, NodeRec *rec, float *box, cudaStream_t st)
 {
     launch(pack_nodes_kernel, grid_for(T.N, 256), 256, 0, st, T.N, d, dp, T.lo, T.hi, T.begin, T.end, T.left, T.right,
-           T.diam2, T.cdmin, T.cdmax, links, meta, box);
+           T.diam2, T.cdmin, T.cdmax, rec, box);
 }
 
 // Pruned BCCP of the pairs of a list (the huge pairs, or a short list of big pairs that the

@@ -35,9 +35,8 @@ struct TravArgs {
     unsigned *rho_bits = nullptr;           // GetRho result: bits of a non-negative float (WriteMin)
     int frontier_cap = 0;
     // packed node records used by the traversals (see wspd.cu)
-    const int4 *links = nullptr;
-    const float4 *meta = nullptr;
-    const float *box = nullptr;
+    const NodeRec *rec = nullptr;
+    const float *box = nullptr;         // [N][2 dp], groups of four dimensions (box_lo, box_hi)
     int dp = 4;                         // box stride: d rounded up to 4, 8 or 16
     // retrieved well-separated pairs by size class: 0 tiny, 1 small, 2 medium, 3 big (tiles),
     // 4 huge (pruned dual-tree BCCP)
@@ -96,8 +95,8 @@ long long dfs_out_cap(int chunk, int budget);       // pairs one step can write 
 long long dfs_step_visits(int chunk, int budget);   // pairs one step can visit
 
 // component label of every node (-1 when its points span several components), into T.comp and
-// links[x].w; scratch holds 2 n + 1 ints
-int launch_comp_labels(const Tree &T, const Points &P, int *uf, int4 *links, int *scratch,
+// rec[x].l.w; scratch holds 2 n + 1 ints
+int launch_comp_labels(const Tree &T, const Points &P, int *uf, NodeRec *rec, int *scratch,
                        Arena &ar, cudaStream_t st);
 int run_traversal(TravArgs &a, int2 *stack, int2 *const xbuf[2], int *cnt, int chunk, cudaStream_t st, int *pinned,
                   unsigned *overflow_out, int *steps_out);
@@ -113,7 +112,7 @@ void run_bccp_tiles(TravArgs &a, const int *counts_host, int *next, cudaStream_t
 void run_bccp_groups(TravArgs &a, const int *counts_host, cudaStream_t st);
 int run_bccp_huge(TravArgs &a, const int2 *pairs, const float *lbs, int m, long long *items, long long *total,
                   cudaStream_t st, Arena &ar, bool hdb, bool fp64, int stack_warps);
-void pack_nodes(const Tree &T, int d, int dp, int4 *links, float4 *meta, float *box, cudaStream_t st);
+void pack_nodes(const Tree &T, int d, int dp, NodeRec *rec, float *box, cudaStream_t st);
 // the point-major copy x4 of x32 (dp / 4 float4s per point)
 void point_major(const float *x32, int n, int d, int dp, float4 *x4, cudaStream_t st);
 
@@ -123,7 +122,7 @@ void gfk_split(const TravArgs &a, const int2 *S, const float *lb, int m, long lo
 void gfk_min_lb(const float *lb, int m, unsigned *rho_bits, cudaStream_t st);
 void gfk_partition(const EdgeK *pool, int m, double hi, EdgeK *batch, int *batch_count, int batch_cap, EdgeK *rest,
                    int *rest_count, unsigned *overflow, cudaStream_t st);
-void gfk_filter_pairs(const int2 *S, const float *lb, int m, const int4 *links, int2 *out, float *out_lb, int *count,
+void gfk_filter_pairs(const int2 *S, const float *lb, int m, const NodeRec *rec, int2 *out, float *out_lb, int *count,
                       cudaStream_t st);
 void gfk_filter_edges(const EdgeK *pool, int m, const int *uf, EdgeK *out, int *count, cudaStream_t st);
 
