@@ -129,7 +129,11 @@ typedef struct {
                                       (many exact duplicates).  The call still returns
                                       WM_OK with an MST of G_MR, but that tree may differ
                                       from the K-minimum one; 0 otherwise             */
-    int32_t reserved;
+    int32_t edge_batch_grown;      /* 1 when a round's candidate edges outgrew the first
+                                      part of the batch and the call, its work so far
+                                      mostly traversal, grew the batch to the tuned
+                                      capacity (wm_tuning.edges_per_point) instead of
+                                      lowering rho_hi                                  */
     double ms_knn_kernel;          /* CUDA-event time of the k-NN kernel (one launch)   */
     double ms_tile_kernel;         /* CUDA-event time of the tile BCCP kernel (medium and
                                       big pairs), summed over the flushes               */
@@ -362,7 +366,12 @@ typedef struct {
     int32_t getrho_sample;   /* GetRho starts from every getrho_sample-th frontier pair (0 or 1:
                                 all of them, Algorithm 3); its minimum is then an upper bound of
                                 the exact one, a larger rho_hi with fewer GetRho visits         */
-    int32_t reserved[8];
+    int32_t edges_per_point; /* capacity of a round's candidate-edge batch: this many edges per
+                                point (+ 2^20); 0 = 4.  A round whose edges would overflow it
+                                lowers its rho_hi, and the dropped edges are found again in a
+                                later round; a larger batch costs 48 bytes of workspace per
+                                edge (0..64)                                                  */
+    int32_t reserved[7];
 } wm_tuning;
 
 /* The parameters a call with these sizes uses (min_pts = 0 for EMST); n = 0 gives the built-in

@@ -55,7 +55,7 @@ class _Stats(ctypes.Structure):
                 ("candidate_edges", ctypes.c_int64), ("tree_nodes", ctypes.c_int64),
                 ("tree_depth", ctypes.c_int64), ("workspace_bytes_used", ctypes.c_size_t),
                 ("max_rel_screen_err", ctypes.c_double), ("tie_overflow", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("ms_knn_kernel", ctypes.c_double),
+                ("edge_batch_grown", ctypes.c_int32), ("ms_knn_kernel", ctypes.c_double),
                 ("ms_tile_kernel", ctypes.c_double), ("tile_launches", ctypes.c_int64),
                 ("ms_getpairs", ctypes.c_double), ("getpairs_launches", ctypes.c_int64),
                 ("getpairs_visits", ctypes.c_int64), ("getrho_visits", ctypes.c_int64),
@@ -76,11 +76,12 @@ class _Opts(ctypes.Structure):
 class _Tuning(ctypes.Structure):
     _fields_ = [("tight_diameters", ctypes.c_int32), ("chunk_log2", ctypes.c_int32), ("dfs_budget", ctypes.c_int32),
                 ("route_big", ctypes.c_int32), ("medium_max", ctypes.c_int32), ("big_max", ctypes.c_int32),
-                ("combined", ctypes.c_int32), ("getrho_sample", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
+                ("combined", ctypes.c_int32), ("getrho_sample", ctypes.c_int32), ("edges_per_point", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
 
 
 TUNING_FIELDS = ("tight_diameters", "chunk_log2", "dfs_budget", "route_big", "medium_max", "big_max", "combined",
-                 "getrho_sample")
+                 "getrho_sample", "edges_per_point")
 
 
 class _Instance(ctypes.Structure):
@@ -128,6 +129,7 @@ class Stats:
     workspace_bytes_used: int = 0
     max_rel_screen_err: float = 0.0
     tie_overflow: int = 0
+    edge_batch_grown: int = 0
     ms_knn_kernel: float = 0.0
     ms_tile_kernel: float = 0.0
     tile_launches: int = 0

@@ -12,6 +12,9 @@ library to use it) and a summary, with each bucket's time under the defaults and
 JSON file named by --report.
 
     python -m paper_2104_01126_gb300.autotune --report gpurun_out/autotune.json
+
+--dims / --sizes retune a subset of the buckets; with --merge OLD_REPORT the rows of OLD_REPORT that
+were not retuned are kept, and the table and report are written for the union.
 """
 from __future__ import annotations
 
@@ -32,11 +35,12 @@ TABLE = os.path.join(HERE, "csrc", "tuning_table.inc")
 
 # the values of a call when the table has no row for it (also the starting point of the descent)
 DEFAULTS = {"tight_diameters": 0, "chunk_log2": 0, "dfs_budget": 8, "route_big": 1024, "medium_max": 1024,
-            "big_max": 65536, "combined": 0, "getrho_sample": 1}
+            "big_max": 65536, "combined": 0, "getrho_sample": 1, "edges_per_point": 0}
 # the values tried, in the order the descent visits the parameters
 GRID = [
     ("combined", [0, 1, 2]),
     ("getrho_sample", [1, 4, 16]),
+    ("edges_per_point", [0, 16, 32]),
     ("tight_diameters", [0, 1]),
     ("dfs_budget", [4, 8, 16, 32]),
     ("chunk_log2", [0, 19, 20, 22]),
@@ -91,14 +95,16 @@ def _time(wm, torch, problem, xs, params, reps, ref=None):
     return total, trees
 
 
-def tune(problems=("emst", "hdbscan"), dims=DIMS, reps=2, log=print):
+def tune(problems=("emst", "hdbscan"), dims=DIMS, reps=2, log=print, sizes=None):
     import torch
     import paper_2104_01126_gb300 as wm
     wm.load()
     rows = []
     for problem in problems:
         for d in dims:
-            for n in SIZES[problem]:
+            for n in (sizes or SIZES[problem]):
+                if n not in SIZES[problem]:
+                    continue
                 t0 = time.time()
                 xs = _inputs(problem, d, n, torch)
                 base_ms, ref = _time(wm, torch, problem, xs, DEFAULTS, reps)
@@ -123,6 +129,12 @@ def tune(problems=("emst", "hdbscan"), dims=DIMS, reps=2, log=print):
     return rows
 
 
+def merge_rows(old, new):
+    """The rows of `old` whose (problem, d, n) bucket `new` does not hold, plus `new`."""
+    done = {(r["problem"], r["d"], r["n"]) for r in new}
+    return [r for r in old if (r["problem"], r["d"], r["n"]) not in done] + list(new)
+
+
 def write_table(rows, path=TABLE):
     """C source of builtin_tuning(): the rows of the call's problem (HDBSCAN* falls back to the
     EMST rows when it has none), the nearest tuned dimension among them, then the smallest tuned
@@ -140,7 +152,7 @@ def write_table(rows, path=TABLE):
     for r in sorted(rows, key=lambda r: (r["problem"], r["d"], r["n"])):
         p = r["params"]
         lines.append("    {%d, %d, %dLL, %s},   // %.1f ms -> %.1f ms" % (
-            1 if r["problem"] == "hdbscan" else 0, r["d"], r["n"], ", ".join(str(int(p[f])) for f in fields),
+            1 if r["problem"] == "hdbscan" else 0, r["d"], r["n"], ", ".join(str(int(p.get(f, DEFAULTS[f]))) for f in fields),
             r["default_ms"], r["tuned_ms"]))
     lines.append("    {-1, 0, 0LL, %s},   // end (never matches)" % ", ".join(str(DEFAULTS[f]) for f in fields))
     lines += ["};",
@@ -179,8 +191,15 @@ def main():
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--table", default=TABLE, help="where to write the table (default: csrc/tuning_table.inc)")
     ap.add_argument("--no-write", action="store_true", help="report only; write no table")
+    ap.add_argument("--dims", default=",".join(str(d) for d in DIMS))
+    ap.add_argument("--sizes", default="", help="comma-separated n (default: every tuned size)")
+    ap.add_argument("--merge", default="", help="an earlier report whose other rows are kept")
     args = ap.parse_args()
-    rows = tune(problems=tuple(p for p in args.problems.split(",") if p), reps=args.reps)
+    sizes = tuple(int(float(x)) for x in args.sizes.split(",") if x) or None
+    rows = tune(problems=tuple(p for p in args.problems.split(",") if p), reps=args.reps,
+                dims=tuple(int(x) for x in args.dims.split(",") if x), sizes=sizes)
+    if args.merge:
+        rows = merge_rows(json.load(open(args.merge)), rows)
     with open(args.report, "w") as f:
         json.dump(rows, f, indent=1)
     if not args.no_write:

@@ -140,7 +140,9 @@ static cudaMemPool_t batch_pool(int dev)
 
 struct Caps {
     long long chunk;        // pairs popped per traversal step (= capacity of each pair list)
-    long long edges;        // candidate edges per round
+    long long edges;        // candidate edges per round (the allocated batch)
+    long long edges_soft;   // MemoGFK: the batch a round fills before it may grow to `edges`
+                            // (0: all of it; see the overflow policy in memogfk)
     int frontier_scale;     // multiplier of the stack bound (grown after an overflow)
     long long extra_bytes;  // additional arena bytes (grown after the arena ran out)
     long long wspd_pairs;   // GFK / EMST-Naive: capacity of the materialised WSPD (0 otherwise)
@@ -191,6 +193,7 @@ static Caps default_caps(long long n, int min_pts)
     Caps c;
     c.chunk = std::min<long long>(1 << 21, std::max<long long>(1 << 12, 4 * n));
     c.edges = 4 * n + (1 << 20) + (min_pts > 0 ? (long long)n * (min_pts + 16) : 0);
+    c.edges_soft = 0;
     c.frontier_scale = 1;
     c.extra_bytes = 0;
     c.wspd_pairs = 0;
@@ -211,7 +214,7 @@ static bool tuning_valid(const wm_tuning &t)
            (t.chunk_log2 == 0 || (t.chunk_log2 >= 12 && t.chunk_log2 <= 24)) && t.dfs_budget >= 1 &&
            t.dfs_budget <= 64 && t.route_big >= 0 && t.medium_max >= 65 && t.medium_max <= 4096 &&
            t.big_max >= t.medium_max && t.combined >= 0 && t.combined <= 2 && t.getrho_sample >= 0 &&
-           t.getrho_sample <= 1024;
+           t.getrho_sample <= 1024 && t.edges_per_point >= 0 && t.edges_per_point <= 64;
 }
 
 static wm_tuning tuning_for(long long n, int d, int min_pts)
@@ -226,13 +229,18 @@ static wm_tuning tuning_for(long long n, int d, int min_pts)
 }
 
 // Capacities of a call: the defaults, with the traversal chunk of the tuning (never above the
-// default's max(2^12, 4n): a larger chunk only enlarges the stack of a small problem).  Every
-// estimate of a call's workspace (wm_query_footprint, the batch and serving workspaces) uses it.
+// default's max(2^12, 4n): a larger chunk only enlarges the stack of a small problem) and its
+// edge batch.  Every estimate of a call's workspace (wm_query_footprint, the batch and serving
+// workspaces) uses it.
 static Caps caps_for(long long n, int d, int min_pts)
 {
     Caps c = default_caps(n, min_pts);
     const wm_tuning t = tuning_for(n, d, min_pts);
     if (t.chunk_log2) c.chunk = std::min<long long>(1LL << t.chunk_log2, std::max<long long>(1 << 12, 4 * n));
+    if (t.edges_per_point > 4) {
+        c.edges_soft = c.edges;
+        c.edges += (long long)(t.edges_per_point - 4) * n;
+    }
     return c;
 }
 
@@ -502,7 +510,8 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
     a.big = lists[3]; a.big_count = lcount + 3;
     a.huge_best = huge_best; a.huge_sbest = huge_sbest;
     a.stack = dual_stack; a.stack_cap = T.depth + 4;
-    a.edges = batch; a.edge_count = ecount; a.edge_cap = (int)caps.edges;
+    a.edges = batch; a.edge_count = ecount;
+    a.edge_cap = (int)(caps.edges_soft > 0 && caps.edges_soft < caps.edges ? caps.edges_soft : caps.edges);
     a.overflow = ovf;
     a.stat = stat;
     a.rho_bits = rho;
@@ -663,7 +672,30 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
                 last_ovf = (unsigned)C.pin[1];
                 if (!(C.pin[1] & 2u)) break;
                 if (attempt >= 8) { *overflow_bits = 2; return 0; }
-                const int valid = std::min<long long>(C.pin[0], caps.edges) > 0 ? (int)std::min<long long>(C.pin[0], caps.edges) : 0;
+                // Overflow policy.  Lowering rho_hi defers the rest of the round's range to later
+                // rounds, where more points are connected and more pairs are filtered out before
+                // their BCCP; but every later round traverses the WSPD again.  So a call whose work
+                // so far is mostly traversal (node-pair visits >= kGrowRatio x BCCP evaluations)
+                // first grows its batch to the allocated capacity and redoes the flush with the
+                // same range; otherwise (or once grown) it lowers rho_hi.  On GB300 the ratio at
+                // the first overflow was 64-114 for uniform 7-D points (10^6, 10^7), where growing
+                // halved the call's time, and at most 13 for variable-density blobs in 5-D and 7-D,
+                // where lowering rho_hi was faster.
+                if (a.edge_cap < caps.edges) {
+                    constexpr double kGrowRatio = 20.0;
+                    WM_CK(cudaMemcpyAsync(C.pin + 64, stat, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+                    WM_CK(cudaStreamSynchronize(st));
+                    unsigned long long hs6[6];
+                    memcpy(hs6, C.pin + 64, sizeof hs6);
+                    if ((double)(hs6[4] + hs6[5]) >= kGrowRatio * (double)hs6[1]) {
+                        a.edge_cap = (int)caps.edges;
+                        fill_i32(ecount, e_before, 1, st);
+                        WM_CK(cudaMemsetAsync(ovf, 0, sizeof(unsigned), st));
+                        C.stats.edge_batch_grown = 1;
+                        continue;
+                    }
+                }
+                const int valid = std::min<long long>(C.pin[0], a.edge_cap) > 0 ? (int)std::min<long long>(C.pin[0], a.edge_cap) : 0;
                 if (valid < 1) { *overflow_bits = 2; return 0; }
                 // the new bound: the 40% point of the valid edges' weights, from a histogram (the
                 // same choice whatever order the edges were appended in)
@@ -1682,6 +1714,8 @@ int wm_batch(const wm_instance *inst, int32_t count, int32_t dtype, int32_t layo
         sum.getpairs_visits += gs.getpairs_visits; sum.getrho_visits += gs.getrho_visits;
         sum.getpairs_launches += gs.getpairs_launches; sum.bccp_dual_evals += gs.bccp_dual_evals;
         sum.rho_shrinks += gs.rho_shrinks; sum.tile_launches += gs.tile_launches;
+        sum.edge_batch_grown = std::max(sum.edge_batch_grown, gs.edge_batch_grown);
+        sum.tie_overflow = std::max(sum.tie_overflow, gs.tie_overflow);
         sum.ms_knn_kernel += gs.ms_knn_kernel; sum.ms_tile_kernel += gs.ms_tile_kernel;
         sum.wspd_pairs += gs.wspd_pairs; sum.ms_getrho += gs.ms_getrho; sum.ms_bccp_group += gs.ms_bccp_group; sum.ms_bccp_dual += gs.ms_bccp_dual;
         sum.ms_getpairs += gs.ms_getpairs;

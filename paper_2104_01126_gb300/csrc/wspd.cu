@@ -260,16 +260,19 @@ __device__ inline void box_terms(const float4 &plo, const float4 &phi, const flo
     }
 }
 
+// g0 = the first four-dimension group of both boxes {P lo, P hi, Q lo, Q hi}, loaded by the caller
+// together with the records so that the two loads overlap
 template <int DP>
 __device__ inline void pair_bounds_packed(const TravArgs &a, int P, int Q, const int4 &lp, const int4 &lq,
-                                          const float4 &mp, const float4 &mq, float &lbB, float &ubB, bool &ws,
-                                          float &dP, float &dQ)
+                                          const float4 &mp, const float4 &mq, const float4 (&g0)[4], float &lbB,
+                                          float &ubB, bool &ws, float &dP, float &dQ)
 {
     const float *bp = a.box + (size_t)P * 2 * DP;
     const float *bq = a.box + (size_t)Q * 2 * DP;
     float s = 0.f, t = 0.f;   // squared gap and squared extent, dimension by dimension in order
+    box_terms(g0[0], g0[1], g0[2], g0[3], s, t);
 #pragma unroll
-    for (int c = 0; c < DP / 4; ++c) {
+    for (int c = 1; c < DP / 4; ++c) {
         float4 plo, phi, qlo, qhi;
         ldg256(bp + 8 * c, plo, phi);
         ldg256(bq + 8 * c, qlo, qhi);
@@ -310,6 +313,11 @@ __device__ inline void visit_pair(const TravArgs &a, int2 me, float rho_now, int
                                   float &rho_cand, float &lb_out)
 {
     const int P = me.x, Q = me.y;
+    // the records and the first box group of both nodes in one round trip (a pair that the
+    // checks below reject has read its box group for nothing; the overlap pays for that)
+    float4 g0[4];
+    ldg256(a.box + (size_t)P * 2 * DP, g0[0], g0[1]);
+    ldg256(a.box + (size_t)Q * 2 * DP, g0[2], g0[3]);
     int4 lp, lq;
     float4 mp, mq;
     load_rec(a.rec, P, lp, mp);
@@ -319,7 +327,7 @@ __device__ inline void visit_pair(const TravArgs &a, int2 me, float rho_now, int
     if (lp.w >= 0 && lp.w == lq.w) return;   // all points already connected
     float lbB, ubB, dP, dQ;
     bool ws;
-    pair_bounds_packed<DP>(a, P, Q, lp, lq, mp, mq, lbB, ubB, ws, dP, dQ);
+    pair_bounds_packed<DP>(a, P, Q, lp, lq, mp, mq, g0, lbB, ubB, ws, dP, dQ);
     // (double)x >= r  <=>  x >= (smallest float >= r), for a float x; likewise for <
     if (MODE == 0) {
         // pairs whose BCCP is certainly below rho_lo were handled by earlier rounds

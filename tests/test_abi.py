@@ -61,6 +61,12 @@ def test_tuning_get_set_without_gpu():
             wm.set_tuning({"dfs_budget": 0})
         with pytest.raises(wm.WMError):
             wm.set_tuning({"medium_max": 64})
+        with pytest.raises(wm.WMError):
+            wm.set_tuning({"edges_per_point": 65})
+        # a larger edge batch is part of the workspace estimate: 3 buffers of 16-byte edges
+        small = wm.query_footprint(1_000_000, 3, 0)
+        wm.set_tuning({"edges_per_point": 36})
+        assert wm.query_footprint(1_000_000, 3, 0) - small >= 32 * 1_000_000 * 48
         wm.set_tuning({"dfs_budget": 4, "tight_diameters": 0})
         got = wm.get_tuning(10, 7, 5)
         assert got["dfs_budget"] == 4 and got["tight_diameters"] == 0

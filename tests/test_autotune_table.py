@@ -77,3 +77,22 @@ def test_empty_table_gives_defaults(tmp_path):
                     str(exe)], check=True)
     out = subprocess.run([str(exe), "1000", "3", "0"], capture_output=True, text=True, check=True).stdout
     assert tuple(int(v) for v in out.split()) == (autotune.DEFAULTS["dfs_budget"], autotune.DEFAULTS["combined"])
+
+
+def test_merge_keeps_the_rows_not_retuned():
+    old = [_row("emst", 2, 100_000, 4), _row("emst", 7, 1_000_000, 8), _row("hdbscan", 7, 1_000_000, 8)]
+    new = [_row("emst", 7, 1_000_000, 32)]
+    got = autotune.merge_rows(old, new)
+    assert len(got) == 3
+    by = {(r["problem"], r["d"], r["n"]): r["params"]["dfs_budget"] for r in got}
+    assert by[("emst", 7, 1_000_000)] == 32 and by[("emst", 2, 100_000)] == 4 and by[("hdbscan", 7, 1_000_000)] == 8
+
+
+def test_rows_without_a_newer_field_take_its_default(tmp_path):
+    # a report written before a field existed still gives a complete table
+    r = _row("emst", 3, 1_000_000, 4)
+    del r["params"]["edges_per_point"]
+    path = tmp_path / "t.inc"
+    autotune.write_table([r], str(path))
+    line = [x for x in path.read_text().splitlines() if x.startswith("    {0, 3, 1000000LL")][0]
+    assert line.split("}")[0].split(",")[-1].strip() == str(autotune.DEFAULTS["edges_per_point"])

@@ -8,6 +8,7 @@ force in tests/test_oracle.py) and compare every output of the CUDA path with th
   - EMST on the scale generators: 10^7 points (uniform 2-D and 3-D, varden 2-D), and 10^6 points
     for the other generator / dimension pairs (3 x 10^5 for varden 7-D).
 """
+import functools
 import math
 
 import numpy as np
@@ -46,8 +47,28 @@ def test_emst_full_parity(kind, d, n):
     import torch
     x = synthdata.generate(kind, n, d, seed=0)
     got = wm.emst(torch.from_numpy(x).cuda())
-    ref = oracle.emst_at_scale(x)
+    _check_emst(got, _emst_ref(kind, d, n))
+
+
+@functools.lru_cache(maxsize=2)
+def _emst_ref(kind, d, n):
+    return oracle.emst_at_scale(synthdata.generate(kind, n, d, seed=0))
+
+
+def _check_emst(got, ref):
     assert np.array_equal(to_np(got["u"]), ref["u"])
     assert np.array_equal(to_np(got["v"]), ref["v"])
     assert np.array_equal(to_np(got["w"]), ref["w"])
     assert math.isclose(got["total"], ref["total"], rel_tol=1e-12)
+
+
+def test_emst_grown_edge_batch_full_parity():
+    """A round whose candidate edges overflow the first part of the batch, in a call whose work so
+    far is mostly traversal, grows the batch and redoes the flush with the same range (instead of
+    lowering rho_hi): uniform 7-D points at 10^6 with a 16-edges-per-point batch take that path."""
+    import torch
+    x = synthdata.generate("uniform", 1_000_000, 7, seed=0)
+    with wm.tuning(edges_per_point=16, combined=0, getrho_sample=1):
+        got = wm.emst(torch.from_numpy(x).cuda(), return_stats=True)
+    assert got["stats"].edge_batch_grown == 1 and got["stats"].rho_shrinks == 0
+    _check_emst(got, _emst_ref("uniform", 7, 1_000_000))

@@ -26,6 +26,7 @@ SETTINGS = [
     {"combined": 2},
     {"getrho_sample": 16},
     {"getrho_sample": 4, "combined": 2, "tight_diameters": 1},
+    {"edges_per_point": 64},
 ]
 
 
