@@ -371,7 +371,15 @@ typedef struct {
                                 lowers its rho_hi, and the dropped edges are found again in a
                                 later round; a larger batch costs 48 bytes of workspace per
                                 edge (0..64)                                                  */
-    int32_t reserved[7];
+    int32_t range_ratio;     /* MemoGFK: a round's rho_hi is at most range_ratio x its rho_lo
+                                (once rho_lo > 0); 0 = no limit (GetRho's bound, Algorithm 3).
+                                A smaller range means fewer retrieved pairs whose BCCP lies
+                                above what the round's edge batch can hold, and more rounds
+                                (0 or 2..2^20)                                                */
+    int32_t range_gate;      /* with range_ratio: 0 = the limit applies in every round; else
+                                only in rounds where the call's node-pair visits so far are
+                                below range_gate x its BCCP distance evaluations (0..2^20)   */
+    int32_t reserved[5];
 } wm_tuning;
 
 /* The parameters a call with these sizes uses (min_pts = 0 for EMST); n = 0 gives the built-in

@@ -77,11 +77,11 @@ class _Tuning(ctypes.Structure):
     _fields_ = [("tight_diameters", ctypes.c_int32), ("chunk_log2", ctypes.c_int32), ("dfs_budget", ctypes.c_int32),
                 ("route_big", ctypes.c_int32), ("medium_max", ctypes.c_int32), ("big_max", ctypes.c_int32),
                 ("combined", ctypes.c_int32), ("getrho_sample", ctypes.c_int32), ("edges_per_point", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("range_ratio", ctypes.c_int32), ("range_gate", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 TUNING_FIELDS = ("tight_diameters", "chunk_log2", "dfs_budget", "route_big", "medium_max", "big_max", "combined",
-                 "getrho_sample", "edges_per_point")
+                 "getrho_sample", "edges_per_point", "range_ratio", "range_gate")
 
 
 class _Instance(ctypes.Structure):

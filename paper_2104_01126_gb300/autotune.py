@@ -35,12 +35,15 @@ TABLE = os.path.join(HERE, "csrc", "tuning_table.inc")
 
 # the values of a call when the table has no row for it (also the starting point of the descent)
 DEFAULTS = {"tight_diameters": 0, "chunk_log2": 0, "dfs_budget": 8, "route_big": 1024, "medium_max": 1024,
-            "big_max": 65536, "combined": 0, "getrho_sample": 1, "edges_per_point": 0}
+            "big_max": 65536, "combined": 0, "getrho_sample": 1, "edges_per_point": 0, "range_ratio": 0,
+            "range_gate": 0}
 # the values tried, in the order the descent visits the parameters
 GRID = [
     ("combined", [0, 1, 2]),
     ("getrho_sample", [1, 4, 16]),
     ("edges_per_point", [0, 16, 32]),
+    ("range_ratio", [0, 4, 8, 16]),
+    ("range_gate", [0, 4, 10, 32]),
     ("tight_diameters", [0, 1]),
     ("dfs_budget", [4, 8, 16, 32]),
     ("chunk_log2", [0, 19, 20, 22]),

@@ -214,7 +214,9 @@ static bool tuning_valid(const wm_tuning &t)
            (t.chunk_log2 == 0 || (t.chunk_log2 >= 12 && t.chunk_log2 <= 24)) && t.dfs_budget >= 1 &&
            t.dfs_budget <= 64 && t.route_big >= 0 && t.medium_max >= 65 && t.medium_max <= 4096 &&
            t.big_max >= t.medium_max && t.combined >= 0 && t.combined <= 2 && t.getrho_sample >= 0 &&
-           t.getrho_sample <= 1024 && t.edges_per_point >= 0 && t.edges_per_point <= 64;
+           t.getrho_sample <= 1024 && t.edges_per_point >= 0 && t.edges_per_point <= 64 &&
+           (t.range_ratio == 0 || (t.range_ratio >= 2 && t.range_ratio <= 1 << 20)) && t.range_gate >= 0 &&
+           t.range_gate <= 1 << 20;
 }
 
 static wm_tuning tuning_for(long long n, int d, int min_pts)
@@ -584,6 +586,25 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
         // each flush takes the R read at that moment as rho_hi and the round ends with the final
         // R, i.e. GetRho's value, whose edges at or above it are dropped before Kruskal.
         const bool combined = C.tune.combined == 1 || (C.tune.combined == 2 && adaptive_one_pass);
+        // Tuning range_ratio: the round's range [rho_lo, rho_hi) ends at most at range_ratio x
+        // rho_lo.  Any rho_hi up to GetRho's bound is correct (GetPairs takes pairs of any size
+        // whose lower bound is below it); a smaller one retrieves fewer pairs whose BCCP lies
+        // beyond what the edge batch can hold, at the price of more rounds.
+        // With range_gate > 0 the limit applies only while the call's BCCP work is not small
+        // beside its traversal work so far (node-pair visits < range_gate x BCCP evaluations):
+        // a traversal-bound call loses more to the extra rounds than it saves in BCCPs.
+        double round_cap = rho_cap;
+        if (C.tune.range_ratio > 0 && rho_lo > 0.0) {
+            bool apply = true;
+            if (C.tune.range_gate > 0) {
+                WM_CK(cudaMemcpyAsync(C.pin + 64, stat, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+                WM_CK(cudaStreamSynchronize(st));
+                unsigned long long hs6[6];
+                memcpy(hs6, C.pin + 64, sizeof hs6);
+                apply = (double)(hs6[4] + hs6[5]) < (double)C.tune.range_gate * (double)hs6[1];
+            }
+            if (apply) round_cap = std::min<double>(rho_cap, rho_lo * C.tune.range_ratio);
+        }
         const int tmode = combined ? 2 : 1;
         double rho_used = 0.0;   // largest rho_hi a flush of this round has used
         if (!combined) {
@@ -599,14 +620,14 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
             WM_CK(cudaStreamSynchronize(st));
             float rho_f;
             memcpy(&rho_f, C.pin, sizeof rho_f);
-            rho_hi = std::min<double>(rho_f, rho_cap);
+            rho_hi = std::min<double>(rho_f, round_cap);
             if (rho_hi < rho_lo) rho_hi = rho_lo;
         } else {
-            float cap_f = float_ru(rho_cap);
+            float cap_f = float_ru(round_cap);
             unsigned cap_bits;
             memcpy(&cap_bits, &cap_f, sizeof cap_bits);
             fill_i32((int *)rho, (int)cap_bits, 1, st);
-            rho_hi = std::max<double>(std::min<double>(cap_f, rho_cap), rho_lo);
+            rho_hi = std::max<double>(std::min<double>(cap_f, round_cap), rho_lo);
         }
         double rho_shrunk = inf;   // bound set by an edge-batch overflow in this round
         // ---- GetPairs in chunks; the retrieved pairs of every chunk get their BCCP right away
@@ -630,7 +651,7 @@ static int memogfk(Call &C, Points &P, Tree &T, const HdbState *hdb, const Caps 
             if (combined) {
                 float rf;
                 memcpy(&rf, C.pin + 24, sizeof rf);
-                rho_hi = std::max<double>(std::min<double>(std::min<double>(rf, rho_cap), rho_shrunk), rho_lo);
+                rho_hi = std::max<double>(std::min<double>(std::min<double>(rf, round_cap), rho_shrunk), rho_lo);
             }
             const bool empty = C.pin[16] == 0 && C.pin[17] == 0 && C.pin[18] == 0;
             int lc[5] = {C.pin[2], C.pin[3], C.pin[4], C.pin[5], C.pin[6]};

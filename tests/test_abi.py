@@ -63,6 +63,8 @@ def test_tuning_get_set_without_gpu():
             wm.set_tuning({"medium_max": 64})
         with pytest.raises(wm.WMError):
             wm.set_tuning({"edges_per_point": 65})
+        with pytest.raises(wm.WMError):
+            wm.set_tuning({"range_ratio": 1})
         # a larger edge batch is part of the workspace estimate: 3 buffers of 16-byte edges
         small = wm.query_footprint(1_000_000, 3, 0)
         wm.set_tuning({"edges_per_point": 36})

@@ -27,6 +27,9 @@ SETTINGS = [
     {"getrho_sample": 16},
     {"getrho_sample": 4, "combined": 2, "tight_diameters": 1},
     {"edges_per_point": 64},
+    {"range_ratio": 2},
+    {"range_ratio": 8, "combined": 1},
+    {"range_ratio": 4, "range_gate": 10},
 ]
 
 
