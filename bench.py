@@ -331,13 +331,13 @@ def run_ablation(wm, torch, call, timed_pass, release):
 # (the node-pair visits of a traversal, the distance evaluations of the k-NN kernel).  A figure is
 # reported only while the kernel's source file is the measured version (sha256), else null.
 # Captured on emst-uniform-10m-3d run at n = 2x10^6 (--points 2000000), every traversal launch of
-# one call (69 GetPairs, 57 GetRho): 10.459 GB over 113,220,189 visits and 3.843 GB over
-# 54,161,908 visits.
+# one call (90 GetPairs, 54 GetRho): 8.962 GB over 110,660,742 visits and 1.088 GB over
+# 19,169,412 visits.
 MEASURED_TRAFFIC = {
-    "getpairs": {"bytes_per_unit": 92.38, "source": "paper_2104_01126_gb300/csrc/wspd.cu",
-                 "sha256": "77191141f67c54457dd22b77ab53151d83f1fe8d7ca7dbf505bca582efc8c486"},
-    "getrho": {"bytes_per_unit": 70.96, "source": "paper_2104_01126_gb300/csrc/wspd.cu",
-               "sha256": "77191141f67c54457dd22b77ab53151d83f1fe8d7ca7dbf505bca582efc8c486"},
+    "getpairs": {"bytes_per_unit": 80.99, "source": "paper_2104_01126_gb300/csrc/wspd.cu",
+                 "sha256": "027e4fa02ba56ff6c3a2110c7325f5a8fa9cbdd99ca7ec172ad17532d667af12"},
+    "getrho": {"bytes_per_unit": 56.75, "source": "paper_2104_01126_gb300/csrc/wspd.cu",
+               "sha256": "027e4fa02ba56ff6c3a2110c7325f5a8fa9cbdd99ca7ec172ad17532d667af12"},
 }
 
 
