@@ -188,11 +188,15 @@ static size_t estimate_bytes(long long n, int d, int min_pts, const Caps &c)
     return b + (8u << 20) + (size_t)n * 64 + (size_t)c.extra_bytes;
 }
 
+// Edge counters and capacities are 32-bit ints on the device; the batch stays below 2^31 with
+// room for the appends in flight past its end (a round that needs more lowers its rho_hi).
+constexpr long long kMaxEdgeCap = (1LL << 31) - (1LL << 24);
+
 static Caps default_caps(long long n, int min_pts)
 {
     Caps c;
     c.chunk = std::min<long long>(1 << 21, std::max<long long>(1 << 12, 4 * n));
-    c.edges = 4 * n + (1 << 20) + (min_pts > 0 ? (long long)n * (min_pts + 16) : 0);
+    c.edges = std::min(kMaxEdgeCap, 4 * n + (1 << 20) + (min_pts > 0 ? (long long)n * (min_pts + 16) : 0));
     c.edges_soft = 0;
     c.frontier_scale = 1;
     c.extra_bytes = 0;
@@ -241,7 +245,8 @@ static Caps caps_for(long long n, int d, int min_pts)
     if (t.chunk_log2) c.chunk = std::min<long long>(1LL << t.chunk_log2, std::max<long long>(1 << 12, 4 * n));
     if (t.edges_per_point > 4) {
         c.edges_soft = c.edges;
-        c.edges += (long long)(t.edges_per_point - 4) * n;
+        c.edges = std::min(kMaxEdgeCap, c.edges + (long long)(t.edges_per_point - 4) * n);
+        if (c.edges_soft >= c.edges) c.edges_soft = 0;
     }
     return c;
 }
@@ -1210,7 +1215,7 @@ static int run_call(const wm_opts *opts, long long n, int d, int min_pts, Body b
         ovf_seen |= ovf;
         // grow whichever capacity overflowed and start over
         if (ovf & 1u) caps.frontier_scale *= 2;
-        if (ovf & 2u) caps.edges *= 2;
+        if (ovf & 2u) caps.edges = std::min(kMaxEdgeCap, caps.edges * 2);
         if ((ovf & 6u) && caps.wspd_pairs) caps.wspd_pairs *= 2;   // the materialised WSPD or its pool
         if (user_ws && ovf && estimate_bytes(n, d, min_pts, caps) > opts->workspace_bytes) {
             rc = WM_ENOMEM;
@@ -1961,7 +1966,7 @@ extern "C" int wm_emst_noalloc(const void *pts, int64_t n, int32_t d, int32_t dt
         }
         if (rc != 0 || ovf == 0) break;
         if (ovf & 1u) caps.frontier_scale *= 2;
-        if (ovf & 2u) caps.edges *= 2;
+        if (ovf & 2u) caps.edges = std::min(kMaxEdgeCap, caps.edges * 2);
     }
     if (rc == 0 && ovf) {
         rc = WM_ENOMEM;
