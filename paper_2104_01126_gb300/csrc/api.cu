@@ -139,13 +139,13 @@ static cudaMemPool_t batch_pool(int dev)
 }
 
 struct Caps {
-    long long chunk;        // pairs popped per traversal step (= capacity of each pair list)
-    long long edges;        // candidate edges per round (the allocated batch)
-    long long edges_soft;   // MemoGFK: the batch a round fills before it may grow to `edges`
-                            // (0: all of it; see the overflow policy in memogfk)
-    int frontier_scale;     // multiplier of the stack bound (grown after an overflow)
-    long long extra_bytes;  // additional arena bytes (grown after the arena ran out)
-    long long wspd_pairs;   // GFK / EMST-Naive: capacity of the materialised WSPD (0 otherwise)
+    long long chunk = 0;        // pairs popped per traversal step (= capacity of each pair list)
+    long long edges = 0;        // candidate edges per round (the allocated batch)
+    long long edges_soft = 0;   // MemoGFK: the batch a round fills before it may grow to `edges`
+                                // (0: all of it; see the overflow policy in memogfk)
+    int frontier_scale = 1;     // multiplier of the stack bound (grown after an overflow)
+    long long extra_bytes = 0;  // additional arena bytes (grown after the arena ran out)
+    long long wspd_pairs = 0;   // GFK / EMST-Naive: capacity of the materialised WSPD (0 otherwise)
 };
 
 // Well-separated pairs per point of the full WSPD by dimension (measured on uniform and
