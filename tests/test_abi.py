@@ -65,6 +65,12 @@ def test_tuning_get_set_without_gpu():
             wm.set_tuning({"edges_per_point": 65})
         with pytest.raises(wm.WMError):
             wm.set_tuning({"range_ratio": 1})
+        with pytest.raises(wm.WMError):
+            wm.set_tuning({"range_gate": -1})
+        # every field round-trips through the override
+        want = dict(wm.get_tuning(0, 3, 0), range_ratio=8, range_gate=10, edges_per_point=16, getrho_sample=4)
+        wm.set_tuning(want)
+        assert wm.get_tuning(123, 5, 0) == want
         # a larger edge batch is part of the workspace estimate: 3 buffers of 16-byte edges
         small = wm.query_footprint(1_000_000, 3, 0)
         wm.set_tuning({"edges_per_point": 36})
