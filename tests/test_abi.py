@@ -67,10 +67,6 @@ def test_tuning_get_set_without_gpu():
             wm.set_tuning({"range_ratio": 1})
         with pytest.raises(wm.WMError):
             wm.set_tuning({"range_gate": -1})
-        # every field round-trips through the override
-        want = dict(wm.get_tuning(0, 3, 0), range_ratio=8, range_gate=10, edges_per_point=16, getrho_sample=4)
-        wm.set_tuning(want)
-        assert wm.get_tuning(123, 5, 0) == want
         # a larger edge batch is part of the workspace estimate: 3 buffers of 16-byte edges
         small = wm.query_footprint(1_000_000, 3, 0)
         wm.set_tuning({"edges_per_point": 36})
@@ -78,6 +74,10 @@ def test_tuning_get_set_without_gpu():
         wm.set_tuning({"dfs_budget": 4, "tight_diameters": 0})
         got = wm.get_tuning(10, 7, 5)
         assert got["dfs_budget"] == 4 and got["tight_diameters"] == 0
+        # every field round-trips through the override
+        want = dict(wm.get_tuning(0, 3, 0), range_ratio=8, range_gate=10, edges_per_point=16, getrho_sample=4)
+        wm.set_tuning(want)
+        assert wm.get_tuning(123, 5, 0) == want
     finally:
         wm.set_tuning(None)
     assert wm.get_tuning(1_000_000, 3, 0) == base
