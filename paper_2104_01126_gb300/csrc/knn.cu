@@ -593,7 +593,11 @@ int core_distances(Points &P, Tree &T, int min_pts, bool fp64, HdbState &H, Aren
 #undef WM_KNN
     cudaEventRecord(k1, st);
     cudaMemcpyAsync(pin, cnts, sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (cudaStreamSynchronize(st) != cudaSuccess) return WM_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaEventDestroy(k0);
+        cudaEventDestroy(k1);
+        return WM_ECUDA;
+    }
     if (stats) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, k0, k1);
