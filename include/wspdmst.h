@@ -11,7 +11,9 @@
  * Both follow the method of Sec. 3: a spatial-median k-d tree, the well-separated pair
  * decomposition traversed lazily by MemoGFK rounds (Algorithm 3) with batched BCCP / BCCP*
  * computations, and batched Kruskal over a union-find shared across rounds; the dendrogram and
- * plot come from the top-down heavy/light construction of Sec. 4.2.
+ * plot come from a top-down heavy/light construction after Sec. 4.2 (the heavy set of a
+ * subproblem is the upper half of its rank interval, light components come from a union-find,
+ * and the output equals the sequential definition exactly).
  *
  * Canonical result.  Every edge comparison uses the strict total key
  *     K(u,v) = (w2, min(u,v), max(u,v))   (lexicographic),
