@@ -119,21 +119,6 @@ __device__ inline void atomicMinPosD(double *addr, double v)
     atomicMin((unsigned long long *)addr, (unsigned long long)__double_as_longlong(v));
 }
 
-// Exact FP64 squared distance in dimension order, one rounding per operation, no FMA.
-template <int D>
-__device__ inline double sqdist64(const double *__restrict__ x64, int n, int d, int i, int j)
-{
-    double s = 0.0;
-    const int dd = D > 0 ? D : d;
-#pragma unroll
-    for (int k = 0; k < (D > 0 ? D : kMaxDim); ++k) {
-        if (D <= 0 && k >= dd) break;
-        double t = __dsub_rn(x64[(size_t)k * n + i], x64[(size_t)k * n + j]);
-        s = __dadd_rn(s, __dmul_rn(t, t));
-    }
-    return s;
-}
-
 // Rigorous bounds on the FP64 w2 of any point pair inside boxes from FP32 box arithmetic.
 __device__ inline float lower_w2(float q) { float r = __fsub_rd(__fmul_rd(q, 1.0f - kBoxRel), kAbsTiny); return r > 0.f ? r : 0.f; }
 __device__ inline float upper_w2(float q) { return __fadd_ru(__fmul_ru(q, 1.0f + kBoxRel), kAbsTiny); }
