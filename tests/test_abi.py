@@ -83,3 +83,18 @@ def test_tuning_get_set_without_gpu():
     assert wm.get_tuning(1_000_000, 3, 0) == base
     from paper_2104_01126_gb300 import autotune
     assert wm.get_tuning(0, 3, 0) == autotune.DEFAULTS   # n = 0: the built-in defaults
+
+
+def test_every_built_in_tuning_row_is_a_valid_setting():
+    # the table is generated; each row a call can pick must pass the same range checks as an
+    # override (wm_set_tuning rejects what the kernels do not support)
+    try:
+        for min_pts in (0, 10):
+            for d in (1, 2, 3, 4, 5, 6, 7, 8, 12, 16):
+                for n in (10, 100_000, 1_000_000, 10_000_000, 100_000_000):
+                    row = wm.get_tuning(n, d, min_pts)
+                    wm.set_tuning(row)
+                    assert wm.get_tuning(n, d, min_pts) == row
+                    wm.set_tuning(None)
+    finally:
+        wm.set_tuning(None)
