@@ -319,7 +319,7 @@ def run_ablation(wm, torch, call, timed_pass, release):
     out[CFG2] = {m: run(w, x, m) for m in ("memogfk", "gantao", "gfk", "gfk-geometric")}
     del x
     release()
-    out["note"] = ("every method returns the same tree; wspd_pairs: size of the materialised WSPD (GFK forms); "
+    out["note"] = ("every method returns the same tree (tests/test_gpu_methods.py checks it); wspd_pairs: size of the materialised WSPD (GFK forms); "
                    "bccp_pairs: pairs whose BCCP was evaluated (MemoGFK counts a pair again in each round that "
                    "retrieves it)")
     return out
